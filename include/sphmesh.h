@@ -1,0 +1,276 @@
+/*
+ * sphmesh.h -- C ABI of the GB300 feature-aware SPH relaxation library (libsphmesh.so).
+ *
+ * The library evolves mesh-vertex particles of every feature type (singular points, feature
+ * curves, feature surfaces, volume) concurrently under the SPH pressure-like interaction
+ * forces of Ji, Fu, Hu and Adams, "A Feature-aware SPH for Isotropic Unstructured Mesh
+ * Generation" (arXiv 2003.01061), towards a target feature-size field h_t(x), driven by the
+ * paper's two-phase controller.  All per-step work runs in the library's own CUDA kernels on
+ * one GPU; the host only marshals descriptors and copies states in and out.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns sph_status and never aborts or exits.  On failure
+ *    sph_last_error() returns a message describing the most recent failure of the calling
+ *    thread.  Inputs that fail validation give SPH_E_INVALID and change no state.
+ *  - Positions, velocities and normals are arrays of 3 doubles per particle in host memory,
+ *    row-major [n][3]; in 2D the third entry is ignored on input and written as 0.
+ *  - "Original order" is the order of the particles passed to sph_mesh_set_state; every
+ *    per-particle output is returned in that order.
+ *  - The library never keeps caller pointers past the call.  Device memory is owned by the
+ *    handle and released by sph_mesh_destroy.
+ *  - Work is enqueued on the handle's CUDA stream (the one passed to sph_mesh_create, or a
+ *    stream the library created).  Functions that return host data synchronise that stream.
+ *  - A handle may be used by one thread at a time.
+ */
+#ifndef SPHMESH_H
+#define SPHMESH_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_E_INVALID = 1,        /* a descriptor, size or pointer failed validation            */
+    SPH_E_NOMEM = 2,          /* device or host allocation failed                            */
+    SPH_E_CUDA = 3,           /* a CUDA call failed (the message names it)                   */
+    SPH_E_DIVERGED = 4,       /* a non-finite acceleration or position was detected          */
+    SPH_E_NOT_CONVERGED = 5,  /* run_until_converged reached max_iters; the state is valid   */
+    SPH_E_OVERFLOW = 6        /* a particle left the cell grid or a debug buffer was short   */
+} sph_status;
+
+#define SPH_MAX_FEATURES 64
+#define SPH_MAX_HOLES 8
+#define SPH_MAX_LEVELS 8
+
+/* Feature kinds (Sec. 3.2, "feature definition"): particles carry the type and index of the
+ * feature they belong to.  The intrinsic dimension d of each kind is given in brackets. */
+typedef enum {
+    SPH_FEAT_VOLUME = 0,   /* [D] the positive phase phi > 0 of the level set (Eq. 1)          */
+    SPH_FEAT_POINT = 1,    /* [0] singularity point; its particle never moves                  */
+    SPH_FEAT_SEGMENT = 2,  /* [1] straight feature curve from geom[0..2] to geom[3..5]         */
+    SPH_FEAT_CIRCLE = 3,   /* [1] 2D circle, centre geom[0..1], radius geom[2]                  */
+    SPH_FEAT_RECT = 4,     /* [2] 3D planar face: origin geom[0..2], unit axes geom[3..5] and
+                                  geom[6..8], extents geom[9], geom[10]                         */
+    SPH_FEAT_SPHERE = 5    /* [2] 3D sphere surface, centre geom[0..2], radius geom[3]          */
+} sph_feature_kind;
+
+typedef struct {
+    int32_t kind;        /* sph_feature_kind                                                   */
+    int32_t dim;         /* intrinsic dimension (0..3); must match the kind (VOLUME: D)        */
+    double geom[12];     /* geometry, see sph_feature_kind                                     */
+    double normal[3];    /* POINT, SEGMENT, RECT: unit outward normal of the domain at the
+                            feature (edges and corners: bisector of the incident faces).  It is
+                            the n_b of the boundary term of Eq. 19 when this feature's particles
+                            act as boundary particles.                                         */
+    double orient;       /* CIRCLE, SPHERE: +1 when the domain is inside (outer boundary),
+                            -1 when it is outside (a hole)                                     */
+} sph_feature;
+
+/* The domain (Sec. 2.1, Sec. 3.1): phi > 0 is the volume.  phi is given analytically as a box
+ * (base 0, the bounding box itself) or a ball (base 1) minus up to SPH_MAX_HOLES balls. */
+typedef struct {
+    int32_t dim;                       /* ambient dimension D: 2 or 3                          */
+    int32_t base;                      /* 0: box [bbox_lo, bbox_hi]; 1: ball (ball_center, r)  */
+    double bbox_lo[3], bbox_hi[3];     /* bounding box of every particle position              */
+    double ball_center[3];
+    double ball_radius;
+    int32_t n_holes;
+    double hole_center[SPH_MAX_HOLES][3];
+    double hole_radius[SPH_MAX_HOLES];
+    int32_t n_features;                /* 1..SPH_MAX_FEATURES; a particle's group = its index  */
+    sph_feature features[SPH_MAX_FEATURES];
+} sph_domain_desc;
+
+/* Target feature size h_t(x) (Eq. 2, rho_t = h_t^-d), analytic:
+ *   kind 0 CONST:      h = a
+ *   kind 1 HOLE_DIST:  h = clamp(a + b * min_k | |x - ref_center_k| - ref_radius_k |, lo, hi)
+ *   kind 2 RADIAL:     h = clamp(a + b * |x - center|, lo, hi)      (the form of Eqs. 25-28)
+ * lo and hi must bound h everywhere (they size the cell grid). */
+typedef struct {
+    int32_t kind;
+    double a, b, lo, hi;
+    double center[3];
+    int32_t n_ref;
+    double ref_center[SPH_MAX_HOLES][3];
+    double ref_radius[SPH_MAX_HOLES];
+} sph_sizing_desc;
+
+/* Method parameters.  Defaults in brackets are the paper's (see each field). */
+typedef struct {
+    double kappa;          /* support radius r_c = kappa*h of the Wendland C2 kernel      [2]  */
+    double p0;             /* EOS constant P0, Eq. 6                                     [1]  */
+    double visc;           /* nu = visc * r_c * |v|, Eq. 8; 0 disables viscosity         [0.1]*/
+    double cfl_a;          /* Eq. 24 acceleration constant                               [0.25]*/
+    double cfl_v;          /* Eq. 24 velocity constant                                   [1/40]*/
+    double eps1;           /* Phase-One damping epsilon, Eq. 23 (paper: 0..0.2)          [0]  */
+    double dt_cap;         /* step size of a group with no acceleration and no velocity  [1e30]*/
+    double dt_collapse;    /* nullify velocities when dt drops below this factor of the
+                              previous step (Sec. 3.4.3: "an order of magnitude")         [0.1]*/
+    double threshold;      /* E_sys threshold of Sec. 3.4.2                              [5e-6]*/
+    int32_t reset_period;  /* Phase-One nullification period, Sec. 3.4.3                 [100]*/
+    int32_t sample_every;  /* steps between samples of V-bar, Sec. 3.4.2                 [20] */
+    int32_t window;        /* samples per averaging window, Sec. 3.4.2                   [10] */
+    int32_t ramp_len;      /* steps of the Phase-One -> Phase-Two transition, Sec. 3.4.4 [200]*/
+    int32_t boundary_rho;  /* 1: boundary sum of Eq. 19 carries rho_b (units-consistent);
+                              0: the sum exactly as printed                              [1]  */
+    int32_t precision;     /* 32: FP32 pair sums (FP64 projection and reductions);
+                              64: FP64 everywhere                                         [32] */
+} sph_params;
+
+/* Controller phases (Sec. 3.4) */
+typedef enum { SPH_PHASE1 = 1, SPH_RAMP = 2, SPH_PHASE2 = 3, SPH_DONE = 4 } sph_phase;
+
+typedef struct {
+    int32_t phase;                     /* sph_phase                                           */
+    int32_t n_groups;
+    int64_t iteration;                 /* completed steps                                      */
+    int64_t ramp_start;                /* step at which Phase One ended (RAMP began)           */
+    int64_t escapes;                   /* volume particles moved back inside the domain        */
+    uint32_t status;                   /* bit 0: non-finite value seen; bit 1: particle outside
+                                          the cell grid; bit 2: h outside [lo, hi]             */
+    uint32_t pad;
+    double E_t, E_avg, E_sys;          /* convergence errors of the last evaluated sample       */
+    double vbar[SPH_MAX_FEATURES];     /* last sampled V-bar per group (Eq. 22, V_ref = 1)     */
+    double dt[SPH_MAX_FEATURES];       /* step size of each group in the last step (Eq. 24)    */
+    int32_t reset[SPH_MAX_FEATURES];   /* 1 if the group's velocities were nullified            */
+} sph_report;
+
+typedef struct sph_mesh sph_mesh;
+
+/* Creates a relaxation instance: checks the descriptors, derives the cell grid from the
+ * bounding box and [sizing.lo, sizing.hi] and allocates device memory for up to
+ * max_particles particles.  stream: a cudaStream_t to enqueue work on, or NULL for a stream
+ * owned by the library.  Problem statement: Sec. 2.1-2.2 and Sec. 3.1-3.2 (geometry, target
+ * feature size, feature tags).  Errors: SPH_E_INVALID, SPH_E_NOMEM, SPH_E_CUDA. */
+sph_status sph_mesh_create(const sph_domain_desc* domain, const sph_sizing_desc* sizing,
+                           const sph_params* params, int64_t max_particles, void* stream,
+                           sph_mesh** out);
+
+/* Fills params with the paper's defaults (bracketed values above). */
+sph_status sph_params_default(sph_params* params);
+
+/* Loads a particle set (Algorithm 1, "allocate particles ... initial particle sampling") and
+ * resets the controller to Phase One, step 0.  x: [n][3] positions; group: feature index of
+ * each particle; v: [n][3] velocities or NULL for zero; h: per-particle smoothing length or
+ * NULL for h_t(x).  Positions must lie inside the bounding box and h inside [lo, hi].
+ * Errors: SPH_E_INVALID (n > max_particles, bad group, position or h out of range). */
+sph_status sph_mesh_set_state(sph_mesh* m, int64_t n, const double* x, const int32_t* group,
+                              const double* v, const double* h);
+
+/* Enqueues n_steps relaxation steps (Algorithm 1, one pass of the while loop each: cell-list
+ * rebuild, pressure pass with the feature-boundary correction of Eq. 19, per-group step size
+ * of Eq. 24 and the two-phase controller of Sec. 3.4, viscous pass, update and projection).
+ * Returns without waiting for the GPU.  The step sequence is captured once into a CUDA
+ * graph.  Errors: SPH_E_CUDA. */
+sph_status sph_mesh_step(sph_mesh* m, int32_t n_steps);
+
+/* Waits for all work enqueued on the handle and checks the device status word.
+ * Errors: SPH_E_CUDA, SPH_E_DIVERGED (non-finite value), SPH_E_OVERFLOW (left the grid). */
+sph_status sph_mesh_sync(sph_mesh* m);
+
+/* Steps until the controller reports the end of Phase Two (Sec. 3.4: Phase One until E_sys
+ * falls below the threshold, transition, Phase Two until the criterion holds again) or until
+ * max_iters steps have run.  iters_out (may be NULL) receives the completed step count.
+ * Errors: SPH_E_NOT_CONVERGED when max_iters was reached, plus those of sph_mesh_sync. */
+sph_status sph_mesh_run_until_converged(sph_mesh* m, int64_t max_iters, int64_t* iters_out);
+
+/* Copies the current state to host buffers in original order (any pointer may be NULL):
+ * x_out [n][3], group_out [n], v_out [n][3], h_out [n].  capacity is the number of particles
+ * the buffers hold.  Errors: SPH_E_INVALID (capacity < n). */
+sph_status sph_mesh_positions(sph_mesh* m, double* x_out, int32_t* group_out, double* v_out,
+                              double* h_out, int64_t capacity, int64_t* n_out);
+
+/* Copies the controller state (Sec. 3.4) and the device status word. */
+sph_status sph_mesh_report(sph_mesh* m, sph_report* out);
+
+/* Releases the handle and its device memory.  NULL is ignored. */
+void sph_mesh_destroy(sph_mesh* m);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* sph_last_error(void);
+
+/* ------------------------------------------------------------------------------------------
+ * Cell grid (Algorithm 1, "update the multi-level data structure").  Pure host function.
+ * Level l has cubic cells of edge c0 * 2^l; a particle goes to the first level whose
+ * threshold thr[l] is >= its h.  Keys number the cells of all levels consecutively
+ * (row-major within a level, x fastest).  Specification:
+ *   c0 = kappa*h_lo*(1+2^-10) rounded up to float; L = the least count with
+ *   c0*2^(L-1) >= kappa*h_hi*(1+2^-10) (at most SPH_MAX_LEVELS); thr[l] = c0*2^l /
+ *   (kappa*(1+2^-10)) rounded down to float for l < L-1, +inf for the top level;
+ *   origin = bbox_lo - c0*2^(L-1) rounded down to float; dims[l] = ceil((bbox_hi +
+ *   c0*2^(L-1) - origin) / (c0*2^l)) + 1 per axis (1 for unused axes).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int32_t dim, levels;
+    float c0;
+    float origin[3];
+    float thr[SPH_MAX_LEVELS];
+    int64_t dims[SPH_MAX_LEVELS][3];
+    int64_t base[SPH_MAX_LEVELS];
+    int64_t n_cells;
+} sph_grid_info;
+
+sph_status sph_grid_spec(int32_t dim, const double* bbox_lo, const double* bbox_hi, double h_lo,
+                         double h_hi, double kappa, sph_grid_info* out);
+sph_status sph_mesh_grid(const sph_mesh* m, sph_grid_info* out);
+
+/* ------------------------------------------------------------------------------------------
+ * Inspection entry points, for parity checks.  Each runs parts of one step on the GPU on
+ * the current state without advancing it (the controller state is left untouched).
+ * ------------------------------------------------------------------------------------------ */
+
+/* Rebuilds the cell lists of the current state (Algorithm 1, Verlet list construction by
+ * cell key + stable counting sort).  key_out [n]: cell key of each particle in the order the
+ * state is currently stored (right after set_state that is the original order);
+ * cell_start_out [n_cells + 1]: first sorted slot of every cell; perm_out [n]: for every
+ * sorted slot, the index of the particle in the stored order.  Any pointer may be NULL. */
+sph_status sph_debug_rebuild(sph_mesh* m, int64_t* key_out, int64_t* cell_start_out,
+                             int64_t* perm_out);
+
+/* Neighbour sets seen by the pair sums, for every particle in original order.
+ * mode 0: all j != i with |x_i - x_j| < kappa*(h_i+h_j)/2, any group (Eq. 7, Eq. 19);
+ * mode 1: all j (i included) with |x_i - x_j| < kappa*h_i, any group (Eq. 18, Eq. 20).
+ * counts_out [n]; lists_out receives the concatenated lists (original indices, ascending)
+ * for particles in original order, up to list_capacity entries; total_out the total.
+ * Errors: SPH_E_OVERFLOW when list_capacity < total (counts are still complete). */
+sph_status sph_debug_neighbors(sph_mesh* m, int32_t mode, int64_t* counts_out, int32_t* lists_out,
+                               int64_t list_capacity, int64_t* total_out);
+
+/* Pressure pass of the current state (Eqs. 18-20, Eq. 24), per particle in original order:
+ * a_p [n][3] (Eq. 19 after the map onto the feature), sigma [n] (kernel sum of Eq. 20),
+ * gamma [n] (Eq. 18), and per group dta/dtv [n_groups] (the minima of 0.25 sqrt(r_c/|a|) and
+ * r_c/(40|v|) of Eq. 24).  Any pointer may be NULL. */
+sph_status sph_debug_interact(sph_mesh* m, double* a_p, double* sigma, double* gamma, double* dta,
+                              double* dtv);
+
+/* One full update of the current state with the step parameters given explicitly instead of
+ * the controller's: per group dt[g] and reset[g] (velocity nullification), damping eps and
+ * velocity attenuation f (Algorithm 1: mid-point velocity, viscous force, update, map).
+ * Outputs in original order: x_out [n][3], v_out [n][3], h_out [n], a_v [n][3] (the viscous
+ * acceleration after the map).  The stored state is NOT changed.  Any pointer may be NULL. */
+sph_status sph_debug_update(sph_mesh* m, const double* dt, const int32_t* reset, double eps,
+                            double f, double* x_out, double* v_out, double* h_out, double* a_v);
+
+/* Per-kernel timing.  When enabled, sph_mesh_step records CUDA events around every kernel
+ * launch; sph_mesh_kernel_times returns, for each kernel name, the launch count and the
+ * summed device time in milliseconds since timing was enabled (up to cap entries). */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} sph_kernel_time;
+
+sph_status sph_mesh_set_timing(sph_mesh* m, int32_t enable);
+sph_status sph_mesh_kernel_times(sph_mesh* m, sph_kernel_time* out, int32_t cap, int32_t* n_out);
+
+/* Pair statistics of the current state's neighbour search (for the FLOP account): number of
+ * candidate pairs visited and pairs inside the support, over one pressure pass. */
+sph_status sph_debug_pair_counts(sph_mesh* m, int64_t* candidates, int64_t* accepted);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

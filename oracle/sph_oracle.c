@@ -292,8 +292,10 @@ int64_t orc_neighbors_brute(int64_t n, int D, const double* x, const double* h, 
  *   thr[l] = c_l/(kappa*(1+2^-10)) rounded down to a float (l < L-1), thr[L-1] = +inf;
  *   a particle's level is the first l with h <= thr[l];
  *   origin = (lo - c_{L-1}) rounded down to floats;  dims_l = ceil((hi + c_{L-1} - origin)/c_l)+1;
- *   cell = floor((x - origin)/c_l) (clamped into the grid), key = base_l + row-major cell;
- *   offset = (x - origin) - cell*c_l, rounded to the working precision. */
+ *   cell = floor((x - origin) * (1/c_l)) with 1/c_l rounded once in FP64 (clamped into the
+ *          grid), key = base_l + row-major cell (x fastest);
+ *   offset = (x - origin) - cell*c_l, rounded to the working precision (it may fall an ulp
+ *          outside [0, c_l) where the rounded inverse puts x on the other side of a face). */
 static float f_round_up(double v) {
     float f = (float)v;
     if ((double)f < v) f = nextafterf(f, INFINITY);
@@ -350,7 +352,7 @@ static void repr_one(const orc_grid* g, const double* x, double h, int prec, int
     for (int a = 0; a < 3; ++a) {
         if (a >= g->D) { cell[a] = 0; off[a] = 0; continue; }
         double rel = x[a] - (double)g->origin[a];
-        int64_t c = (int64_t)floor(rel / cl);
+        int64_t c = (int64_t)floor(rel * (1.0 / cl));
         if (c < 0) { c = 0; *clamped = 1; }
         if (c > g->dims[l][a] - 1) { c = g->dims[l][a] - 1; *clamped = 1; }
         cell[a] = c;

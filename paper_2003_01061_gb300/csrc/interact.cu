@@ -1,0 +1,242 @@
+// interact.cu -- the fused pressure pass of one relaxation step (Algorithm 1: renormalisation
+// gamma_i, pressure force with the feature-boundary correction, map onto the feature, step-size
+// candidates), one thread per particle in sorted order.
+//
+// For particle i of group g (intrinsic dimension d, kernel W_d, rho = h^-d, P = p0 h^(2d)):
+//   sigma_i = sum_{j in g, r < kappa h_i} W_d(r_ij, h_i)             (Eq. 20 denominator, j = i included)
+//   gamma_i = sum_{j in g, r < kappa h_i} W_d(r_ij, h_i) h_j^d         (Eq. 18)
+//   F_i     = sum_{j in g, j != i, r < kappa h_ij} (P_i + P_j) W_d'(r_ij, h_ij) e_ij          (Eq. 19, 1st sum)
+//           + sum_{b: d_b < d, r < kappa h_ib} rho_b (P_i + P_b) W_d(r_ib, h_ib) n_b|i A_b  (Eq. 19, 2nd sum)
+//   a_p,i   = Pi_i(-F_i / gamma_i),  V~_i = 1 / sigma_i
+// and the Eq. 24 candidates 0.25 sqrt(r_c/|a_p|), r_c/(40 |v|), reduced to per-group minima.
+// On sampling steps each block also writes its per-group sums of V~ (Eq. 22) in a fixed order.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+template <typename T, int D>
+__global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s, T* dbg_sigma, T* dbg_gamma) {
+    __shared__ unsigned long long sh_dta[MAXF], sh_dtv[MAXF];
+    __shared__ double sh_part[BLOCK / 32][MAXF];
+    const int G = p.G;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < G; t += blockDim.x) {
+        sh_dta[t] = inf_bits<T>();
+        sh_dtv[t] = inf_bits<T>();
+    }
+    const bool sample = s.ctrl->sample_now != 0;
+    if (sample)
+        for (int t = threadIdx.x; t < (BLOCK / 32) * MAXF; t += blockDim.x) (&sh_part[0][0])[t] = 0.0;
+    __syncthreads();
+
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int gi = -1, di = 0;
+    T vtil = T(0);
+    if (k < s.n) {
+        T offi[3], hi;
+        unsigned mi;
+        Rec<T, D>::load(s.P, s.Ms, k, offi, hi, mi);
+        gi = meta_group(mi);
+        di = meta_dim(mi);
+        T ap[3] = {T(0), T(0), T(0)};
+        T sig = T(0), gam = T(0);
+        if (di > 0) {
+            int li, ci[3];
+            decode_key(g, s.Ks[k], li, ci);
+            const Feat& fi = s.dom->f[gi];
+            T tg[3] = {T(0), T(0), T(0)};
+            if (di < D) {
+                T xi[3] = {(T)s.Xs[0][k], (T)s.Xs[1][k], D == 3 ? (T)s.Xs[2][k] : T(0)};
+                feature_tangent<T>(fi, xi, tg);
+            }
+            const T kappa = (T)p.kappa, hk = T(0.5) * kappa, p0 = (T)p.p0;
+            const T rci2 = self_rc2(hi, kappa);
+            const T invRi = T(1) / (kappa * hi);
+            const T alpha_i = wendland_alpha<T>(di, invRi);
+            const T Pi = p0 * ipow(hi, 2 * di);
+            const bool brho = p.boundary_rho != 0;
+            const T c0 = (T)g.c0;
+            const T org[3] = {(T)g.origin[0], (T)g.origin[1], (T)g.origin[2]};
+            T F[3] = {T(0), T(0), T(0)};
+            walk<T, D>(g, s.cell_start, s.n, s.P, s.Ms, li, ci, offi, hi, kappa,
+                       [&](int j, const T dx[3], T r2, T hj, unsigned mj, const T offj[3], int l, int cxj, int cy,
+                           int cz) {
+                           const int gj = meta_group(mj);
+                           if (gj == gi) {
+                               if (r2 < rci2) {
+                                   T q = t_sqrt(r2) * invRi;
+                                   T t = T(1) - q;
+                                   T w = alpha_i * (t * t) * (t * t) * (T(1) + T(4) * q);
+                                   sig += w;
+                                   gam += w * ipow(hj, di);
+                               }
+                               if (j != k && r2 < pair_rc2(hi, hj, hk)) {
+                                   T r = t_sqrt(r2);
+                                   if (r > T(0)) {
+                                       T invR = T(2) / (kappa * (hi + hj));
+                                       T q = r * invR;
+                                       T t = T(1) - q;
+                                       T dW = wendland_alpha<T>(di, invR) * (T(-20) * q * t * t * t) * invR;
+                                       T c1 = (Pi + p0 * ipow(hj, 2 * di)) * dW / r;
+                                       F[0] += c1 * dx[0];
+                                       F[1] += c1 * dx[1];
+                                       if (D == 3) F[2] += c1 * dx[2];
+                                   }
+                               }
+                           } else if (meta_dim(mj) < di && r2 < pair_rc2(hi, hj, hk)) {
+                               T r = t_sqrt(r2);
+                               T invR = T(2) / (kappa * (hi + hj));
+                               T q = r * invR;
+                               T t = T(1) - q;
+                               T w = wendland_alpha<T>(di, invR) * (t * t) * (t * t) * (T(1) + T(4) * q);
+                               const int cj[3] = {cxj, cy, cz};
+                               T xb[3] = {T(0), T(0), T(0)};
+                               for (int a = 0; a < D; ++a) xb[a] = org[a] + (T)(cj[a] << l) * c0 + offj[a];
+                               T nb[3];
+                               boundary_normal<T>(s.dom->f[gj], xb, nb);
+                               tangent_map<T>(di, D, tg, nb);
+                               T nn = t_sqrt(nb[0] * nb[0] + nb[1] * nb[1] + nb[2] * nb[2]);
+                               if (nn > T(1e-6)) {
+                                   T Ab = brho ? T(1) / hj : ipow(hj, di - 1);
+                                   T c2 = Ab * (Pi + p0 * ipow(hj, 2 * di)) * w / nn;
+                                   F[0] += c2 * nb[0];
+                                   F[1] += c2 * nb[1];
+                                   if (D == 3) F[2] += c2 * nb[2];
+                               }
+                           }
+                       });
+            const T ig = T(1) / gam;
+            for (int a = 0; a < 3; ++a) ap[a] = -F[a] * ig;
+            tangent_map<T>(di, D, tg, ap);
+            vtil = T(1) / sig;
+            const T rc = kappa * hi;
+            T an = t_sqrt(ap[0] * ap[0] + ap[1] * ap[1] + ap[2] * ap[2]);
+            T v0 = s.Vs[0][k], v1 = s.Vs[1][k], v2 = D == 3 ? s.Vs[2][k] : T(0);
+            T vn = t_sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+            T dta = an > T(0) ? (T)p.cfl_a * t_sqrt(rc / an) : (T)CUDART_INF;
+            T dtv = vn > T(0) ? (T)p.cfl_v * rc / vn : (T)CUDART_INF;
+            if (!(an == an) || !isfinite(an)) atomicOr(&s.ctrl->status, ST_NONFINITE);
+            atomicMin(&sh_dta[gi], min_bits(dta));
+            atomicMin(&sh_dtv[gi], min_bits(dtv));
+        }
+        Vec4<T> a4;
+        a4.x = ap[0];
+        a4.y = ap[1];
+        a4.z = ap[2];
+        a4.w = vtil;
+        s.A[k] = a4;
+        if (dbg_sigma) dbg_sigma[k] = sig;
+        if (dbg_gamma) dbg_gamma[k] = gam;
+    }
+    if (sample) {
+        // deterministic per-warp, per-group sums of V~: one fixed shuffle tree per group present
+        const unsigned full = 0xffffffffu;
+        const int gk = (k < s.n && di > 0) ? gi : -1;
+        unsigned pending = __ballot_sync(full, gk >= 0);
+        while (pending) {
+            int leader = __ffs(pending) - 1;
+            int gg = __shfl_sync(full, gk, leader);
+            double v = (gk == gg) ? (double)vtil : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(full, v, o);
+            if (lane == 0) sh_part[wid][gg] = v;
+            pending &= ~__ballot_sync(full, gk == gg);
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < G; t += blockDim.x) {
+        if (sh_dta[t] != inf_bits<T>()) atomicMin(&s.ctrl->dta_bits[t], sh_dta[t]);
+        if (sh_dtv[t] != inf_bits<T>()) atomicMin(&s.ctrl->dtv_bits[t], sh_dtv[t]);
+        if (sample) {
+            double acc = 0.0;
+            for (int w = 0; w < BLOCK / 32; ++w) acc += sh_part[w][t];
+            s.partials[(size_t)blockIdx.x * G + t] = acc;
+        }
+    }
+}
+
+// neighbour sets for inspection: mode 0 pair predicate (j != i), mode 1 self predicate (j = i
+// included), over all groups.  lists == nullptr: count only.
+template <typename T, int D>
+__global__ void __launch_bounds__(BLOCK) k_neighbors(Grid g, Params p, State<T> s, int mode, int* counts,
+                                                     const long long* offsets, int* lists) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= s.n) return;
+    T offi[3], hi;
+    unsigned mi;
+    Rec<T, D>::load(s.P, s.Ms, k, offi, hi, mi);
+    int li, ci[3];
+    decode_key(g, s.Ks[k], li, ci);
+    const T kappa = (T)p.kappa, hk = T(0.5) * kappa;
+    const T rci2 = self_rc2(hi, kappa);
+    int cnt = 0;
+    long long base = lists ? offsets[k] : 0;
+    walk<T, D>(g, s.cell_start, s.n, s.P, s.Ms, li, ci, offi, hi, kappa,
+               [&](int j, const T*, T r2, T hj, unsigned, const T*, int, int, int, int) {
+                   bool acc = mode == 0 ? (j != k && r2 < pair_rc2(hi, hj, hk)) : (r2 < rci2);
+                   if (acc) {
+                       if (lists) lists[base + cnt] = j;
+                       ++cnt;
+                   }
+               });
+    if (!lists) counts[k] = cnt;
+}
+
+// candidate pairs visited and pairs inside the interaction support, summed over all particles
+template <typename T, int D>
+__global__ void __launch_bounds__(BLOCK) k_pair_counts(Grid g, Params p, State<T> s, unsigned long long* out2) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long cand = 0, accd = 0;
+    if (k < s.n) {
+        T offi[3], hi;
+        unsigned mi;
+        Rec<T, D>::load(s.P, s.Ms, k, offi, hi, mi);
+        const int gi = meta_group(mi), di = meta_dim(mi);
+        if (di > 0) {
+            int li, ci[3];
+            decode_key(g, s.Ks[k], li, ci);
+            const T kappa = (T)p.kappa, hk = T(0.5) * kappa;
+            walk<T, D>(g, s.cell_start, s.n, s.P, s.Ms, li, ci, offi, hi, kappa,
+                       [&](int j, const T*, T r2, T hj, unsigned mj, const T*, int, int, int, int) {
+                           ++cand;
+                           int gj = meta_group(mj);
+                           if ((gj == gi || meta_dim(mj) < di) && j != k && r2 < pair_rc2(hi, hj, hk)) ++accd;
+                       });
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        cand += __shfl_down_sync(0xffffffffu, cand, o);
+        accd += __shfl_down_sync(0xffffffffu, accd, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out2, cand);
+        atomicAdd(out2 + 1, accd);
+    }
+}
+
+template <typename T, int D>
+void launch_interact(const Grid& g, const Params& p, const State<T>& s, T* dbg_sigma, T* dbg_gamma, cudaStream_t st) {
+    k_interact<T, D><<<s.nblk, BLOCK, 0, st>>>(g, p, s, dbg_sigma, dbg_gamma);
+}
+template <typename T, int D>
+void launch_neighbors(const Grid& g, const Params& p, const State<T>& s, int mode, int* counts,
+                      const long long* offsets, int* lists, cudaStream_t st) {
+    k_neighbors<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(g, p, s, mode, counts, offsets, lists);
+}
+template <typename T, int D>
+void launch_pair_counts(const Grid& g, const Params& p, const State<T>& s, unsigned long long* out2, cudaStream_t st) {
+    k_pair_counts<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(g, p, s, out2);
+}
+
+#define SPH_INST(T, D)                                                                                        \
+    template void launch_interact<T, D>(const Grid&, const Params&, const State<T>&, T*, T*, cudaStream_t);     \
+    template void launch_neighbors<T, D>(const Grid&, const Params&, const State<T>&, int, int*,              \
+                                         const long long*, int*, cudaStream_t);                               \
+    template void launch_pair_counts<T, D>(const Grid&, const Params&, const State<T>&, unsigned long long*,  \
+                                           cudaStream_t);
+SPH_INST(float, 2)
+SPH_INST(float, 3)
+SPH_INST(double, 2)
+SPH_INST(double, 3)
+
+}  // namespace sph

@@ -1,0 +1,203 @@
+// rebuild.cu -- cell-list rebuild (Algorithm 1: "update the multi-level data structure",
+// "construct Verlet neighbour list"): cell key per particle, per-cell histogram, exclusive scan,
+// scatter, per-cell ordering by stored index (which makes the counting sort stable and
+// deterministic), and the gather of the state into sorted order with cell-relative offsets.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// ---- key + histogram ----
+template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_hash(Grid g, State<T> s) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.n) return;
+    double x[3] = {s.X[0][i], s.X[1][i], D == 3 ? s.X[2][i] : 0.0};
+    T h = s.H[i];
+    int l = level_of(g, h);
+    int cell[3];
+    T off[3];
+    bool clamped = cell_of<T, D>(g, l, x, cell, off);
+    int key = key_of(g, l, cell);
+    s.K[i] = key;
+    atomicAdd(s.count + key, 1);
+    if (clamped) atomicOr(&s.ctrl->status, ST_OUTSIDE_GRID);
+}
+
+// ---- exclusive scan of the per-cell counts: three passes over tiles of SCAN_TILE cells ----
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int& total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;   // inclusive scan of warp totals
+    }
+    __syncthreads();
+    total = warp_sums[(blockDim.x >> 5) - 1];
+    int before = wid > 0 ? warp_sums[wid - 1] : 0;
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(int ncell, const int* __restrict__ count,
+                                                              int* __restrict__ bsum) {
+    __shared__ int ws[32];
+    int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int v = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+        if (base + k < ncell) v += count[base + k];
+    int total;
+    block_exclusive_scan(v, ws, total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(int nb, int ncell, int* __restrict__ bsum,
+                                                           int* __restrict__ cell_start) {
+    __shared__ int ws[32];
+    int base = threadIdx.x * SCAN_ITEMS;
+    int loc[SCAN_ITEMS];
+    int v = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        loc[k] = (base + k < nb) ? bsum[base + k] : 0;
+        v += loc[k];
+    }
+    int total;
+    int ex = block_exclusive_scan(v, ws, total);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < nb) bsum[base + k] = ex;
+        ex += loc[k];
+    }
+    if (threadIdx.x == 0) cell_start[ncell] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(int ncell, int* __restrict__ count,
+                                                            const int* __restrict__ bsum,
+                                                            int* __restrict__ cell_start) {
+    __shared__ int ws[32];
+    int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int loc[SCAN_ITEMS];
+    int v = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        loc[k] = (base + k < ncell) ? count[base + k] : 0;
+        v += loc[k];
+    }
+    int total;
+    int ex = block_exclusive_scan(v, ws, total) + bsum[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < ncell) {
+            cell_start[base + k] = ex;
+            count[base + k] = ex;    // scatter cursor
+        }
+        ex += loc[k];
+    }
+}
+
+// ---- scatter into cells (order inside a cell fixed afterwards) ----
+template <typename T> __global__ void __launch_bounds__(BLOCK) k_scatter(State<T> s) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.n) return;
+    int pos = atomicAdd(s.count + s.K[i], 1);
+    if ((unsigned)pos < (unsigned)s.n) s.perm[pos] = i;
+}
+
+// ---- per cell: order by stored index (stable sort), reset the count for the next rebuild ----
+__global__ void __launch_bounds__(BLOCK) k_cellsort(int ncell, int n, const int* __restrict__ cell_start, int* perm,
+                                                    int* __restrict__ count) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int s = cell_start[c], e = cell_start[c + 1];
+    if (s < 0 || e > n) e = s;   // defensive: never index outside perm
+    for (int a = s + 1; a < e; ++a) {
+        int v = perm[a], b = a - 1;
+        while (b >= s && perm[b] > v) {
+            perm[b + 1] = perm[b];
+            --b;
+        }
+        perm[b + 1] = v;
+    }
+    count[c] = 0;
+}
+
+// ---- gather into sorted order + cell-relative offsets ----
+template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_gather(Grid g, State<T> s) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= s.n) return;
+    int i = s.perm[k];
+    if ((unsigned)i >= (unsigned)s.n) {   // defensive: a broken permutation is reported, not followed
+        atomicOr(&s.ctrl->status, ST_NONFINITE);
+        i = 0;
+    }
+    double x[3] = {s.X[0][i], s.X[1][i], D == 3 ? s.X[2][i] : 0.0};
+    T h = s.H[i];
+    unsigned meta = s.G[i];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        s.Xs[a][k] = x[a];
+        s.Vs[a][k] = s.V[a][i];
+    }
+    s.Hs[k] = h;
+    s.IDs[k] = s.ID[i];
+    s.Ks[k] = s.K[i];
+    int l = level_of(g, h);
+    int cell[3];
+    T off[3];
+    cell_of<T, D>(g, l, x, cell, off);
+    Rec<T, D>::store(s.P, s.Ms, k, off, h, (meta & 255u) | ((unsigned)cell[0] << 8));
+}
+
+// ---- initial smoothing lengths h = h_t(x) ----
+template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_init_h(State<T> s) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.n) return;
+    double x[3] = {s.X[0][i], s.X[1][i], D == 3 ? s.X[2][i] : 0.0};
+    s.H[i] = (T)sizing_h(*s.siz, x);
+}
+
+template <typename T, int D> void launch_hash(const Grid& g, const State<T>& s, cudaStream_t st) {
+    k_hash<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(g, s);
+}
+void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t st) {
+    int nb = div_up(ncell, SCAN_TILE);
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(ncell, count, bsum);
+    k_scan_top<<<1, SCAN_THREADS, 0, st>>>(nb, ncell, bsum, cell_start);
+    k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(ncell, count, bsum, cell_start);
+}
+template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st) {
+    k_scatter<T><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s);
+}
+void launch_cellsort(int ncell, int n, const int* cell_start, int* perm, int* count, cudaStream_t st) {
+    k_cellsort<<<div_up(ncell, BLOCK), BLOCK, 0, st>>>(ncell, n, cell_start, perm, count);
+}
+template <typename T, int D> void launch_gather(const Grid& g, const State<T>& s, cudaStream_t st) {
+    k_gather<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(g, s);
+}
+template <typename T, int D> void launch_init_h(const State<T>& s, cudaStream_t st) {
+    k_init_h<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s);
+}
+
+#define SPH_INST(T, D)                                                          \
+    template void launch_hash<T, D>(const Grid&, const State<T>&, cudaStream_t);   \
+    template void launch_gather<T, D>(const Grid&, const State<T>&, cudaStream_t); \
+    template void launch_init_h<T, D>(const State<T>&, cudaStream_t);
+SPH_INST(float, 2)
+SPH_INST(float, 3)
+SPH_INST(double, 2)
+SPH_INST(double, 3)
+template void launch_scatter<float>(const State<float>&, cudaStream_t);
+template void launch_scatter<double>(const State<double>&, cudaStream_t);
+
+}  // namespace sph

@@ -1,0 +1,418 @@
+// sph_device.cuh -- device-side data layout and inline helpers of the relaxation kernels.
+//
+// Layout in HBM (one instance, n particles, all arrays sized for the handle's capacity):
+//   stored state ("cur", in the order of the previous step's sort):
+//     X[a][n] double  positions (FP64 master copy, used by the update and the projection)
+//     V[a][n] T       velocities;  H[n] T smoothing length;  G[n] uint32 meta;  ID[n] int32
+//   sorted state ("srt", written by the gather of the rebuild, read by the pair passes):
+//     Xs, Vs, Hs, IDs as above, Ks[n] cell key, Ms[n] meta with the particle's x-cell,
+//     P[n] T4 = cell-relative offsets + h (FP32 build, 2D: (ox, oy, h, meta bits)),
+//     A[n] T4 = (a_p.x, a_p.y, a_p.z, V~) from the pressure pass.
+//   meta bits: 0-5 group (feature index), 6-7 intrinsic dimension, 8-31 x index of the cell
+//   (sorted arrays only).
+// T is float (FP32 pair sums) or double (FP64 build); D is 2 or 3.
+#pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+namespace sph {
+
+constexpr int MAXF = 64;
+constexpr int MAXH = 8;
+constexpr int MAXL = 8;
+constexpr int BLOCK = 256;
+
+enum { K_VOLUME = 0, K_POINT = 1, K_SEGMENT = 2, K_CIRCLE = 3, K_RECT = 4, K_SPHERE = 5 };
+enum { PH1 = 1, PH_RAMP = 2, PH2 = 3, PH_DONE = 4 };
+enum { ST_NONFINITE = 1u, ST_OUTSIDE_GRID = 2u, ST_H_RANGE = 4u };
+
+struct Feat {
+    int kind, dim;
+    double g[12];
+    double nb[3];
+    double orient;
+    float fnb[3];        // float copies used by the FP32 pair sums
+    float ftg[3];        // SEGMENT: unit tangent; RECT: unit normal
+    float fc[3];         // CIRCLE / SPHERE centre
+    float forient;
+};
+
+struct Domain {
+    int D, base;
+    double lo[3], hi[3], bc[3], br;
+    int nh;
+    double hc[MAXH][3];
+    double hr[MAXH];
+    int nf;
+    Feat f[MAXF];
+};
+
+struct Sizing {
+    int kind;
+    double a, b, lo, hi;
+    double q[3];
+    int nref;
+    double rc[MAXH][3];
+    double rr[MAXH];
+};
+
+struct Grid {
+    int D, L;
+    float c0;
+    float origin[3];
+    double c[MAXL];      // c0 * 2^l
+    double inv_c[MAXL];  // 1 / c_l rounded once in FP64
+    float thr[MAXL];
+    int dims[MAXL][3];
+    int base[MAXL + 1];
+    int ncell;
+};
+
+struct Params {
+    double kappa, p0, visc, cfl_a, cfl_v, eps1, dt_cap, dt_collapse, threshold;
+    int reset_period, sample_every, window, ramp_len, boundary_rho;
+    int G;
+};
+
+// controller state + per-step accumulators (one per instance, in device memory)
+struct Ctrl {
+    int phase, wcount, nwin, sample_now;
+    long long n, ramp_start;
+    unsigned long long escapes;
+    unsigned int status;
+    int pad;
+    double wsum[MAXF], A_last[MAXF], A_prev[MAXF], Vbar[MAXF], dt_prev[MAXF], dt[MAXF];
+    int reset[MAXF];
+    double E_t, E_avg, E_sys, eps, f;
+    unsigned long long dta_bits[MAXF], dtv_bits[MAXF];   // per-group minima of Eq. 24 terms
+};
+
+template <typename T> struct alignas(4 * sizeof(T)) Vec4 { T x, y, z, w; };
+
+// ---- rounding-explicit arithmetic (the neighbour predicate must be evaluated op by op) ----
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+
+__device__ __forceinline__ unsigned long long min_bits(float v) { return (unsigned long long)__float_as_uint(v); }
+__device__ __forceinline__ unsigned long long min_bits(double v) { return (unsigned long long)__double_as_longlong(v); }
+template <typename T> __device__ __forceinline__ T from_bits(unsigned long long b);
+template <> __device__ __forceinline__ float from_bits<float>(unsigned long long b) { return __uint_as_float((unsigned)b); }
+template <> __device__ __forceinline__ double from_bits<double>(unsigned long long b) { return __longlong_as_double((long long)b); }
+template <typename T> __host__ __device__ __forceinline__ unsigned long long inf_bits();
+template <> __host__ __device__ __forceinline__ unsigned long long inf_bits<float>() { return 0x7f800000ull; }
+template <> __host__ __device__ __forceinline__ unsigned long long inf_bits<double>() { return 0x7ff0000000000000ull; }
+
+template <typename T> __device__ __forceinline__ T t_sqrt(T v);
+template <> __device__ __forceinline__ float t_sqrt<float>(float v) { return sqrtf(v); }
+template <> __device__ __forceinline__ double t_sqrt<double>(double v) { return sqrt(v); }
+template <typename T> __device__ __forceinline__ T t_floor(T v);
+template <> __device__ __forceinline__ float t_floor<float>(float v) { return floorf(v); }
+template <> __device__ __forceinline__ double t_floor<double>(double v) { return floor(v); }
+
+// h^k for small non-negative integer k
+template <typename T> __device__ __forceinline__ T ipow(T h, int k) {
+    T r = T(1);
+    for (int i = 0; i < k; ++i) r *= h;
+    return r;
+}
+
+// Wendland C2 normalisation alpha_d / (its R-dependence): alpha_1 = 3/(2R), alpha_2 = 7/(pi R^2),
+// alpha_3 = 21/(2 pi R^3); given invR = 1/R.
+template <typename T> __device__ __forceinline__ T wendland_alpha(int d, T invR) {
+    if (d == 1) return T(1.5) * invR;
+    if (d == 2) return T(7.0 / CUDART_PI) * invR * invR;
+    return T(21.0 / (2.0 * CUDART_PI)) * invR * invR * invR;
+}
+
+// ---- particle record access (sorted arrays) ----
+template <typename T, int D> struct Rec {
+    // (float, 2D): P = (ox, oy, h, meta); every other case: P = (ox, oy, oz, h) + M
+    static constexpr bool packed = (sizeof(T) == 4 && D == 2);
+    __device__ __forceinline__ static void load(const Vec4<T>* __restrict__ P, const unsigned* __restrict__ M, int j,
+                                                T off[3], T& h, unsigned& meta) {
+        Vec4<T> p = P[j];
+        off[0] = p.x;
+        off[1] = p.y;
+        if (packed) {
+            off[2] = T(0);
+            h = p.z;
+            meta = __float_as_uint((float)p.w);
+        } else {
+            off[2] = p.z;
+            h = p.w;
+            meta = M[j];
+        }
+    }
+    __device__ __forceinline__ static void store(Vec4<T>* P, unsigned* M, int j, const T off[3], T h, unsigned meta) {
+        Vec4<T> p;
+        p.x = off[0];
+        p.y = off[1];
+        if (packed) {
+            p.z = h;
+            p.w = (T)__uint_as_float(meta);
+        } else {
+            p.z = off[2];
+            p.w = h;
+        }
+        P[j] = p;
+        M[j] = meta;
+    }
+};
+
+__device__ __forceinline__ int meta_group(unsigned m) { return (int)(m & 63u); }
+__device__ __forceinline__ int meta_dim(unsigned m) { return (int)((m >> 6) & 3u); }
+__device__ __forceinline__ int meta_cx(unsigned m) { return (int)(m >> 8); }
+
+// level of a smoothing length: first l with h <= thr[l] (the top level takes the rest)
+template <typename T> __device__ __forceinline__ int level_of(const Grid& g, T h) {
+    int l = 0;
+    while (l < g.L - 1 && h > (T)g.thr[l]) ++l;
+    return l;
+}
+
+// cell coordinates and cell-relative offset of an FP64 position at level l:
+//   cell = floor((x - origin) * inv_c_l), off = (x - origin) - cell * c_l  (rounded to T)
+template <typename T, int D>
+__device__ __forceinline__ bool cell_of(const Grid& g, int l, const double x[3], int cell[3], T off[3]) {
+    bool clamped = false;
+    for (int a = 0; a < 3; ++a) {
+        if (a >= D) { cell[a] = 0; off[a] = T(0); continue; }
+        double rel = __dsub_rn(x[a], (double)g.origin[a]);
+        double t = floor(__dmul_rn(rel, g.inv_c[l]));
+        int c = (int)fmax(fmin(t, 2.0e9), -2.0e9);
+        if (c < 0) { c = 0; clamped = true; }
+        if (c > g.dims[l][a] - 1) { c = g.dims[l][a] - 1; clamped = true; }
+        cell[a] = c;
+        off[a] = (T)__dsub_rn(rel, __dmul_rn((double)c, g.c[l]));
+    }
+    return clamped;
+}
+
+__device__ __forceinline__ int key_of(const Grid& g, int l, const int cell[3]) {
+    return g.base[l] + (cell[2] * g.dims[l][1] + cell[1]) * g.dims[l][0] + cell[0];
+}
+
+// decode a key into level and cell coordinates
+__device__ __forceinline__ void decode_key(const Grid& g, int key, int& l, int cell[3]) {
+    l = 0;
+    while (l < g.L - 1 && key >= g.base[l + 1]) ++l;
+    int r = key - g.base[l];
+    cell[0] = r % g.dims[l][0];
+    r /= g.dims[l][0];
+    cell[1] = r % g.dims[l][1];
+    cell[2] = r / g.dims[l][1];
+}
+
+// ---- analytic geometry (FP64) ----
+__device__ __forceinline__ double dnorm3(const double v[3]) { return sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); }
+
+__device__ inline double sizing_h(const Sizing& s, const double x[3]) {
+    if (s.kind == 0) return s.a;
+    double h;
+    if (s.kind == 1) {
+        double dmin = 1e300;
+        for (int k = 0; k < s.nref; ++k) {
+            double d[3] = {x[0] - s.rc[k][0], x[1] - s.rc[k][1], x[2] - s.rc[k][2]};
+            double dk = fabs(dnorm3(d) - s.rr[k]);
+            dmin = fmin(dmin, dk);
+        }
+        h = s.a + s.b * dmin;
+    } else {
+        double d[3] = {x[0] - s.q[0], x[1] - s.q[1], x[2] - s.q[2]};
+        h = s.a + s.b * dnorm3(d);
+    }
+    return fmin(fmax(h, s.lo), s.hi);
+}
+
+// level set of the domain and its gradient (positive inside)
+__device__ inline double domain_phi(const Domain& dom, const double x[3], double grad[3]) {
+    double phi = 1e300;
+    grad[0] = grad[1] = grad[2] = 0.0;
+    if (dom.base == 0) {
+        for (int a = 0; a < dom.D; ++a) {
+            double dlo = x[a] - dom.lo[a], dhi = dom.hi[a] - x[a];
+            if (dlo < phi) { phi = dlo; grad[0] = grad[1] = grad[2] = 0.0; grad[a] = 1.0; }
+            if (dhi < phi) { phi = dhi; grad[0] = grad[1] = grad[2] = 0.0; grad[a] = -1.0; }
+        }
+    } else {
+        double d[3] = {x[0] - dom.bc[0], x[1] - dom.bc[1], dom.D == 3 ? x[2] - dom.bc[2] : 0.0};
+        double r = dnorm3(d);
+        phi = dom.br - r;
+        for (int a = 0; a < 3; ++a) grad[a] = r > 0 ? -d[a] / r : (a == 0 ? -1.0 : 0.0);
+    }
+    for (int k = 0; k < dom.nh; ++k) {
+        double d[3] = {x[0] - dom.hc[k][0], x[1] - dom.hc[k][1], dom.D == 3 ? x[2] - dom.hc[k][2] : 0.0};
+        double r = dnorm3(d);
+        double pk = r - dom.hr[k];
+        if (pk < phi) {
+            phi = pk;
+            for (int a = 0; a < 3; ++a) grad[a] = r > 0 ? d[a] / r : (a == 0 ? 1.0 : 0.0);
+        }
+    }
+    return phi;
+}
+
+// closest point on a curve / surface / point feature (FP64)
+__device__ inline void project_feature(const Feat& f, int D, double x[3]) {
+    if (f.kind == K_POINT) {
+        for (int a = 0; a < 3; ++a) x[a] = a < D ? f.g[a] : 0.0;
+    } else if (f.kind == K_SEGMENT) {
+        double ab[3], ax[3];
+        for (int a = 0; a < 3; ++a) { ab[a] = f.g[3 + a] - f.g[a]; ax[a] = x[a] - f.g[a]; }
+        double t = (ax[0] * ab[0] + ax[1] * ab[1] + ax[2] * ab[2]) / (ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2]);
+        t = fmin(fmax(t, 0.0), 1.0);
+        for (int a = 0; a < 3; ++a) x[a] = f.g[a] + t * ab[a];
+    } else if (f.kind == K_CIRCLE || f.kind == K_SPHERE) {
+        double c[3] = {f.g[0], f.g[1], f.kind == K_SPHERE ? f.g[2] : 0.0};
+        double R = f.kind == K_SPHERE ? f.g[3] : f.g[2];
+        double d[3] = {0, 0, 0};
+        for (int a = 0; a < D; ++a) d[a] = x[a] - c[a];
+        double r = dnorm3(d);
+        for (int a = 0; a < 3; ++a) {
+            double u = r > 0 ? d[a] / r : (a == 0 ? 1.0 : 0.0);
+            x[a] = a < D ? c[a] + R * u : 0.0;
+        }
+    } else if (f.kind == K_RECT) {
+        double ox[3];
+        for (int a = 0; a < 3; ++a) ox[a] = x[a] - f.g[a];
+        double s = ox[0] * f.g[3] + ox[1] * f.g[4] + ox[2] * f.g[5];
+        double t = ox[0] * f.g[6] + ox[1] * f.g[7] + ox[2] * f.g[8];
+        s = fmin(fmax(s, 0.0), f.g[9]);
+        t = fmin(fmax(t, 0.0), f.g[10]);
+        for (int a = 0; a < 3; ++a) x[a] = f.g[a] + s * f.g[3 + a] + t * f.g[6 + a];
+    }
+}
+
+// the tangent-space descriptor of a particle of feature f at position x: unit tangent for
+// curves (SEGMENT, CIRCLE), unit normal for surfaces (RECT, SPHERE)
+template <typename T> __device__ inline void feature_tangent(const Feat& f, const T x[3], T tg[3]) {
+    tg[0] = tg[1] = tg[2] = T(0);
+    if (f.kind == K_SEGMENT || f.kind == K_RECT) {
+        for (int a = 0; a < 3; ++a) tg[a] = (T)f.ftg[a];
+        if (sizeof(T) == 8) {   // FP64 build: exact descriptor
+            if (f.kind == K_RECT) { for (int a = 0; a < 3; ++a) tg[a] = (T)f.nb[a]; }
+            else {
+                double ab[3] = {f.g[3] - f.g[0], f.g[4] - f.g[1], f.g[5] - f.g[2]};
+                double L = dnorm3(ab);
+                for (int a = 0; a < 3; ++a) tg[a] = (T)(ab[a] / L);
+            }
+        }
+    } else if (f.kind == K_CIRCLE) {
+        T d0 = x[0] - (T)f.g[0], d1 = x[1] - (T)f.g[1];
+        T r = t_sqrt(d0 * d0 + d1 * d1);
+        T u0 = r > T(0) ? d0 / r : T(1), u1 = r > T(0) ? d1 / r : T(0);
+        tg[0] = -u1;
+        tg[1] = u0;
+    } else if (f.kind == K_SPHERE) {
+        T d[3] = {x[0] - (T)f.g[0], x[1] - (T)f.g[1], x[2] - (T)f.g[2]};
+        T r = t_sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        for (int a = 0; a < 3; ++a) tg[a] = r > T(0) ? d[a] / r : (a == 0 ? T(1) : T(0));
+    }
+}
+
+// v <- Pi v : identity (volume), t t^T (curves), I - n n^T (surfaces), 0 (points)
+template <typename T> __device__ __forceinline__ void tangent_map(int dim, int D, const T tg[3], T v[3]) {
+    if (dim == D) return;
+    if (dim == 0) { v[0] = v[1] = v[2] = T(0); return; }
+    T s = v[0] * tg[0] + v[1] * tg[1] + v[2] * tg[2];
+    if (dim == 1) { for (int a = 0; a < 3; ++a) v[a] = s * tg[a]; }
+    else { for (int a = 0; a < 3; ++a) v[a] = v[a] - s * tg[a]; }
+}
+
+// outward normal n_b of a boundary particle of feature f at (absolute) position x
+template <typename T> __device__ __forceinline__ void boundary_normal(const Feat& f, const T x[3], T nb[3]) {
+    if (f.kind == K_CIRCLE || f.kind == K_SPHERE) {
+        T d[3] = {x[0] - (T)f.fc[0], x[1] - (T)f.fc[1], f.kind == K_SPHERE ? x[2] - (T)f.fc[2] : T(0)};
+        if (sizeof(T) == 8) {
+            d[0] = x[0] - (T)f.g[0];
+            d[1] = x[1] - (T)f.g[1];
+            if (f.kind == K_SPHERE) d[2] = x[2] - (T)f.g[2];
+        }
+        T r = t_sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        T s = (T)f.forient / (r > T(0) ? r : T(1));
+        for (int a = 0; a < 3; ++a) nb[a] = s * d[a];
+    } else {
+        for (int a = 0; a < 3; ++a) nb[a] = sizeof(T) == 8 ? (T)f.nb[a] : (T)f.fnb[a];
+    }
+}
+
+// ---- the multi-level stencil walk ----
+// For query particle i at level li with cell coordinates ci (at li) and offsets offi, visits every
+// particle j stored in the cells that can hold a j with |x_i-x_j| < max(kappa*(h_i+h_j)/2, kappa*h_i):
+// at level l all particles have kappa*h_j <= c_l, so the radius R_l = max((kappa h_i + c_l)/2,
+// kappa h_i) (widened by 2^-10) bounds every candidate.  For each candidate the functor receives
+// j, dx = x_i - x_j computed as (off_i - off_j) + m*c0 with m = ci*2^li - cj*2^l (exact
+// integers), r2 = |dx|^2, h_j, meta_j and j's cell coordinates at level l.
+template <typename T, int D, typename F>
+__device__ __forceinline__ void walk(const Grid& g, const int* __restrict__ cell_start, int n,
+                                     const Vec4<T>* __restrict__ P, const unsigned* __restrict__ M, int li,
+                                     const int ci[3], const T offi[3], T hi, T kappa, F&& fn) {
+    const T c0 = (T)g.c0;
+    const T inv_c0 = T(1) / c0;
+    int Pi[3];
+    T fi[3];
+    for (int a = 0; a < 3; ++a) {
+        Pi[a] = ci[a] << li;
+        fi[a] = offi[a] * inv_c0;
+    }
+    const T rhi = kappa * hi;
+    for (int l = 0; l < g.L; ++l) {
+        T cl = (T)g.c[l];
+        T R = T(0.5) * (rhi + cl);
+        R = (R > rhi ? R : rhi) * T(1.0 + 1.0 / 1024.0);
+        T Rc = R * inv_c0;
+        int lo[3] = {0, 0, 0}, hiC[3] = {0, 0, 0};
+        for (int a = 0; a < D; ++a) {
+            int a0 = Pi[a] + (int)t_floor(fi[a] - Rc);
+            int a1 = Pi[a] + (int)t_floor(fi[a] + Rc);
+            a0 >>= l;
+            a1 >>= l;
+            lo[a] = a0 < 0 ? 0 : a0;
+            hiC[a] = a1 > g.dims[l][a] - 1 ? g.dims[l][a] - 1 : a1;
+        }
+        if (lo[0] > hiC[0] || lo[1] > hiC[1] || (D == 3 && lo[2] > hiC[2])) continue;
+        for (int cz = lo[2]; cz <= hiC[2]; ++cz) {
+            T mcz = T(0);
+            if (D == 3) mcz = rn_mul((T)(Pi[2] - (cz << l)), c0);
+            for (int cy = lo[1]; cy <= hiC[1]; ++cy) {
+                const int row = g.base[l] + (cz * g.dims[l][1] + cy) * g.dims[l][0];
+                const int s = max(__ldg(cell_start + row + lo[0]), 0);
+                const int e = min(__ldg(cell_start + row + hiC[0] + 1), n);
+                if (s >= e) continue;
+                const T mcy = rn_mul((T)(Pi[1] - (cy << l)), c0);
+                for (int j = s; j < e; ++j) {
+                    T offj[3], hj;
+                    unsigned mj;
+                    Rec<T, D>::load(P, M, j, offj, hj, mj);
+                    const int cxj = meta_cx(mj);
+                    const T mcx = rn_mul((T)(Pi[0] - (cxj << l)), c0);
+                    T dx[3];
+                    dx[0] = rn_add(rn_sub(offi[0], offj[0]), mcx);
+                    dx[1] = rn_add(rn_sub(offi[1], offj[1]), mcy);
+                    dx[2] = D == 3 ? rn_add(rn_sub(offi[2], offj[2]), mcz) : T(0);
+                    T r2 = rn_add(rn_mul(dx[0], dx[0]), rn_mul(dx[1], dx[1]));
+                    if (D == 3) r2 = rn_add(r2, rn_mul(dx[2], dx[2]));
+                    fn(j, dx, r2, hj, mj, offj, l, cxj, cy, cz);
+                }
+            }
+        }
+    }
+}
+
+// the two predicates of the pair sums, evaluated op by op:
+//   pair: r2 < ((h_i + h_j) * kappa/2)^2   (j != i);   self: r2 < (kappa h_i)^2
+template <typename T> __device__ __forceinline__ T pair_rc2(T hi, T hj, T half_kappa) {
+    T rc = rn_mul(rn_add(hi, hj), half_kappa);
+    return rn_mul(rc, rc);
+}
+template <typename T> __device__ __forceinline__ T self_rc2(T hi, T kappa) {
+    T rc = rn_mul(hi, kappa);
+    return rn_mul(rc, rc);
+}
+
+}  // namespace sph

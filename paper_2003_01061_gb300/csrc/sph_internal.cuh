@@ -1,0 +1,79 @@
+// sph_internal.cuh -- device pointers of one instance and the kernel launchers shared by the
+// translation units of libsphmesh.so.  Not part of the public ABI.
+#pragma once
+#include "sph_device.cuh"
+
+namespace sph {
+
+template <typename T> struct State {
+    int n;
+    // stored state (order of the previous sort)
+    double* X[3];
+    T* V[3];
+    T* H;
+    unsigned* G;
+    int* ID;
+    int* K;            // cell key of every stored particle (written by the hash)
+    // sorted state
+    double* Xs[3];
+    T* Vs[3];
+    T* Hs;
+    unsigned* Ms;
+    int* IDs;
+    int* Ks;
+    Vec4<T>* P;
+    Vec4<T>* A;
+    // rebuild scratch: per-cell counts (also the scatter cursors), cell starts, scan block
+    // sums, and the sorted-slot -> stored-index permutation
+    int* count;
+    int* cell_start;
+    int* bsum;
+    int* perm;
+    // per-block, per-group partial sums of V~ (sample steps)
+    double* partials;
+    int nblk;
+    Ctrl* ctrl;
+    const Domain* dom;
+    const Sizing* siz;
+};
+
+// output set of the update kernel (the stored state, or scratch for inspection calls)
+template <typename T> struct Out {
+    double* X[3];
+    T* V[3];
+    T* H;
+    unsigned* G;
+    int* ID;
+    T* av[3];          // optional: viscous acceleration (inspection only)
+};
+
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// rebuild.cu
+template <typename T, int D> void launch_hash(const Grid& g, const State<T>& s, cudaStream_t st);
+void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t st);
+template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st);
+void launch_cellsort(int ncell, int n, const int* cell_start, int* perm, int* count, cudaStream_t st);
+template <typename T, int D> void launch_gather(const Grid& g, const State<T>& s, cudaStream_t st);
+template <typename T, int D> void launch_init_h(const State<T>& s, cudaStream_t st);
+
+// interact.cu
+template <typename T, int D>
+void launch_interact(const Grid& g, const Params& p, const State<T>& s, T* dbg_sigma, T* dbg_gamma, cudaStream_t st);
+template <typename T, int D>
+void launch_neighbors(const Grid& g, const Params& p, const State<T>& s, int mode, int* counts,
+                      const long long* offsets, int* lists, cudaStream_t st);
+template <typename T, int D>
+void launch_pair_counts(const Grid& g, const Params& p, const State<T>& s, unsigned long long* out2, cudaStream_t st);
+
+// integrate.cu
+template <typename T> void launch_control(const Params& p, const State<T>& s, cudaStream_t st);
+template <typename T, int D>
+void launch_integrate(const Grid& g, const Params& p, const State<T>& s, const Ctrl* use, const Out<T>& o,
+                      cudaStream_t st);
+
+}  // namespace sph

@@ -1,0 +1,91 @@
+"""Host-side checks of libsphmesh.so that need no GPU: it builds for sm_103a, loads, exports
+every entry point declared in include/sphmesh.h, its cell-grid specification matches the
+oracle's independent implementation bit for bit, and invalid descriptors are rejected before
+any device work."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2003_01061_gb300 import build as B
+from paper_2003_01061_gb300 import sphmesh as S
+from paper_2003_01061_gb300 import workloads as WL
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "sphmesh.h")).read()
+    return sorted(set(re.findall(r"^(?:sph_status|void|const char\*)\s+(sph_\w+)\s*\(", src, re.M)))
+
+
+def test_library_exports_every_declared_function():
+    names = header_functions()
+    assert len(names) >= 15
+    L = S.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(S.EXPORTS)
+
+
+@pytest.mark.parametrize("D,lo,hi,hlo,hhi", [
+    (2, [0, 0, 0], [1, 1, 0], 0.02, 0.02),
+    (2, [-1, -1, 0], [1, 1, 0], 0.0018, 0.018),
+    (3, [0, 0, 0], [1, 1, 1], 0.0053, 0.033),
+    (3, [-0.3, 0.1, 2.0], [0.7, 0.4, 2.5], 0.001, 0.05),
+])
+def test_grid_spec_matches_oracle(D, lo, hi, hlo, hhi):
+    a = S.sph_grid_spec(D, lo, hi, hlo, hhi, 2.0)
+    b = O.grid_spec(D, lo, hi, hlo, hhi, 2.0)
+    assert a.levels == b.L and a.c0 == b.c0 and a.n_cells == b.ncell
+    for l in range(8):
+        assert a.thr[l] == b.thr[l]
+    for k in range(3):
+        assert a.origin[k] == b.origin[k]
+    for l in range(a.levels):
+        assert a.base[l] == b.base[l]
+        for k in range(3):
+            assert a.dims[l][k] == b.dims[l][k]
+
+
+def _descs(w):
+    return S.domain_desc(w["domain"]), S.sizing_desc(w["sizing"]), S.params_struct(w["params"])
+
+
+def test_invalid_descriptors_are_rejected():
+    w = WL.square2d(h=0.1)
+    d, z, p = _descs(w)
+    d.dim = 4
+    with pytest.raises(S.SphError) as e:
+        S.sph_mesh_create(d, z, p, 10)
+    assert e.value.status == S.SPH_E_INVALID
+    d, z, p = _descs(w)
+    d.features[1].dim = 2            # a segment must be a curve
+    with pytest.raises(S.SphError) as e:
+        S.sph_mesh_create(d, z, p, 10)
+    assert e.value.status == S.SPH_E_INVALID
+    d, z, p = _descs(w)
+    z.lo = 0.0
+    with pytest.raises(S.SphError) as e:
+        S.sph_mesh_create(d, z, p, 10)
+    assert e.value.status == S.SPH_E_INVALID
+    d, z, p = _descs(w)
+    p.precision = 16
+    with pytest.raises(S.SphError) as e:
+        S.sph_mesh_create(d, z, p, 10)
+    assert e.value.status == S.SPH_E_INVALID
+    with pytest.raises(S.SphError):
+        S.sph_grid_spec(2, [0, 0, 0], [1, 1, 0], 1e-6, 1.0)     # needs more than 8 levels
+
+
+def test_params_default_are_the_papers():
+    q = S.params_struct({})
+    for k in ("kappa", "p0", "visc", "cfl_a", "cfl_v", "threshold", "reset_period", "sample_every", "window"):
+        assert getattr(q, k) == WL.PAPER_PARAMS[k], k

@@ -1,0 +1,227 @@
+"""GPU-vs-oracle parity of the relaxation hot path, through the C ABI (needs a GB300).
+
+* rebuild:     cell keys, cell starts and the stable permutation are bit-exact against the
+               oracle's representation + counting sort;
+* neighbours:  the pair and self neighbour sets are bit-exact against brute force on the same
+               stored representation and predicate;
+* pressure:    a_p within 1e-5 S_i (FP32) / 1e-12 S_i (FP64), S_i = sum of term magnitudes;
+               sigma, gamma and the per-group step candidates of Eq. 24 likewise;
+* update:      viscous acceleration, velocity, position and h after one update with given
+               step parameters;
+* edge cases:  empty state, a lone particle, singular-only states, lattice points on cell faces.
+Sizes: the 2D square (2,601 particles: 11 blocks of 256 with a ragged tail), a multi-level disk
+with holes and a 3D cube minus sphere.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2003_01061_gb300 import build as B
+from paper_2003_01061_gb300 import sphmesh as S
+from paper_2003_01061_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+TOL = {32: 1e-5, 64: 1e-12}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+_cache = {}
+
+
+def workload(name):
+    if name not in _cache:
+        if name == "square":
+            w = WL.square2d()
+        elif name == "square_coarse":
+            w = WL.square2d(h=0.05, seed=7, jitter=0.3)
+        elif name == "disk":
+            w = WL.disk_holes(n_target=6000, seed=2)
+        elif name == "cube":
+            w = WL.cube_sphere(n_target=12000, seed=3)
+        _cache[name] = w
+    return _cache[name]
+
+
+def oracle_h(w):
+    o = O.Oracle(w)
+    return o.h
+
+
+def make(w, prec, h=None, v=None):
+    m = S.Mesh(w, precision=prec)
+    m.set_state(v=v, h=h)
+    return m
+
+
+CASES = [("square", 32), ("square", 64), ("disk", 32), ("disk", 64), ("cube", 32), ("cube", 64)]
+
+
+@pytest.mark.parametrize("name,prec", CASES)
+def test_rebuild_bit_exact(name, prec):
+    w = workload(name)
+    h = oracle_h(w)
+    m = make(w, prec, h=h)
+    g = S.sph_mesh_grid(m.h)
+    key, cs, perm = S.sph_debug_rebuild(m.h, m.n, g.n_cells)
+    og = O.grid_spec(w["domain"]["D"], w["domain"]["lo"], w["domain"]["hi"], w["h_lo"], w["h_hi"])
+    rep = O.grid_repr(og, w["x"], h, prec=prec)
+    assert not rep["clamped"].any()
+    ocs, operm = O.counting_sort(rep["key"], og.ncell)
+    assert np.array_equal(key, rep["key"])
+    assert np.array_equal(cs, ocs)
+    assert np.array_equal(perm, operm)
+    if name == "disk":
+        assert len(np.unique(rep["level"])) >= 3          # the multi-level path is exercised
+    m.close()
+
+
+def _split(counts, lists):
+    off = np.concatenate([[0], np.cumsum(counts)])
+    return [lists[off[i]:off[i + 1]] for i in range(len(counts))]
+
+
+@pytest.mark.parametrize("name,prec", CASES)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_neighbor_sets_bit_exact(name, prec, mode):
+    w = workload(name)
+    h = oracle_h(w)
+    m = make(w, prec, h=h)
+    counts, lists = S.sph_debug_neighbors(m.h, m.n, mode)
+    got = _split(counts, lists)
+    og = O.grid_spec(w["domain"]["D"], w["domain"]["lo"], w["domain"]["hi"], w["h_lo"], w["h_hi"])
+    n = m.n
+    rng = np.random.default_rng(1)
+    idx = np.arange(n) if n <= 3000 else np.sort(rng.choice(n, 1500, replace=False))
+    for i in idx:
+        ref = O.neighbors_repr(og, w["x"], h, int(i), prec=prec, self_radius=(mode == 1))
+        assert np.array_equal(got[i], ref), (i, got[i], ref)
+    m.close()
+
+
+def _oracle_pressure(w, h, prec, sub=None):
+    o = O.Oracle(w, h=h)
+    return o, o.interact(sub=sub, use_grid=True)
+
+
+@pytest.mark.parametrize("name,prec", CASES)
+def test_pressure_pass_parity(name, prec):
+    w = workload(name)
+    h = oracle_h(w)
+    if prec == 32:
+        h = h.astype(np.float32).astype(np.float64)    # both sides see the same stored h
+    rng = np.random.default_rng(3)
+    v = np.zeros((len(w["x"]), 3))
+    v[:, : w["domain"]["D"]] = rng.normal(0, 1e-3, (len(w["x"]), w["domain"]["D"]))
+    if prec == 32:
+        v = v.astype(np.float32).astype(np.float64)
+    m = make(w, prec, h=h, v=v)
+    got = S.sph_debug_interact(m.h, m.n, m.n_groups)
+    o = O.Oracle(w, h=h, v=v)
+    ref = o.interact(use_grid=True)
+    tol = TOL[prec]
+    err = np.linalg.norm(got["a_p"] - ref["a_p"], axis=1)
+    assert np.all(err <= tol * ref["S"] + 1e-300), (err / np.maximum(ref["S"], 1e-300)).max()
+    moving = o.gdim[w["group"]] > 0
+    assert np.allclose(got["sigma"][moving], ref["sigma"][moving], rtol=10 * tol, atol=0)
+    assert np.allclose(got["gamma"][moving], ref["gamma"][moving], rtol=10 * tol, atol=0)
+    for g in range(m.n_groups):
+        for key in ("dta", "dtv"):
+            a, b = got[key][g], ref[key][g]
+            if np.isinf(b):
+                assert np.isinf(a)
+            else:
+                assert abs(a - b) <= 20 * tol * b, (key, g, a, b)
+    m.close()
+
+
+@pytest.mark.parametrize("name,prec", CASES)
+@pytest.mark.parametrize("reset", [1, 0])
+def test_update_parity(name, prec, reset):
+    w = workload(name)
+    h = oracle_h(w)
+    D = w["domain"]["D"]
+    rng = np.random.default_rng(5)
+    v = np.zeros((len(w["x"]), 3))
+    v[:, :D] = rng.normal(0, 2e-3, (len(w["x"]), D))
+    if prec == 32:
+        h = h.astype(np.float32).astype(np.float64)
+        v = v.astype(np.float32).astype(np.float64)
+    o = O.Oracle(w, h=h, v=v)
+    r = o.interact(use_grid=True)
+    G = o.G
+    dt = np.where(o.gdim > 0, np.minimum(r["dta"], 1e3), 0.0)
+    eps, f = 0.1, 0.75
+    o.ctrl.eps, o.ctrl.ramp_f = eps, f
+    for g in range(G):
+        o.ctrl.dt[g] = dt[g]
+        o.ctrl.reset[g] = reset
+    ref = o.integrate(r["a_p"], use_grid=True)
+    m = make(w, prec, h=h, v=v)
+    got = S.sph_debug_update(m.h, m.n, dt, np.full(G, reset, np.int32), eps, f)
+    tol = TOL[prec]
+    moving = o.gdim[w["group"]] > 0
+    dtp = dt[w["group"]]
+    # the scale of the update: dt^2 S for the pressure part, dt |v| for the carried velocity
+    scale = dtp ** 2 * r["S"] + dtp * np.linalg.norm(v, axis=1) + 1e-300
+    ex = np.linalg.norm(got["x"] - ref["x"], axis=1)
+    assert np.all(ex[moving] <= 50 * tol * scale[moving] + 4e-16 * np.abs(ref["x"]).max()), (ex / scale).max()
+    assert np.array_equal(got["x"][~moving], w["x"][~moving])
+    vs = dtp * r["S"] + np.linalg.norm(v, axis=1) + 1e-300
+    ev = np.linalg.norm(got["v"] - ref["v"], axis=1)
+    assert np.all(ev[moving] <= 50 * tol * vs[moving]), (ev / vs).max()
+    assert np.allclose(got["h"], ref["h"], rtol=4 * tol if prec == 32 else 1e-14, atol=0)
+    m.close()
+
+
+def test_empty_and_lone_particle_states():
+    w = workload("square_coarse")
+    m = S.Mesh(w, precision=32)
+    m.set_state(x=np.zeros((0, 3)), group=np.zeros(0, np.int32))
+    m.step(3)
+    m.sync()
+    assert m.positions()["x"].shape == (0, 3)
+    x = np.array([[0.5, 0.5, 0.0]])
+    m.set_state(x=x, group=np.array([0], np.int32))
+    m.step(5)
+    m.sync()
+    p = m.positions()
+    assert np.array_equal(p["x"], x) and np.all(p["v"] == 0)
+    r = m.report()
+    assert r.iteration == 5
+    corners = w["group"] >= 5
+    m.set_state(x=w["x"][corners], group=w["group"][corners])
+    m.step(4)
+    m.sync()
+    assert np.array_equal(m.positions()["x"], w["x"][corners])
+    m.close()
+
+
+def test_lattice_on_cell_faces_bit_exact():
+    # particles placed exactly on cell faces of the finest level: the floor of the rounded
+    # product decides the cell on both sides in the same way
+    w = WL.square2d(h=0.05, seed=2, jitter=0.0)
+    g = O.grid_spec(2, w["domain"]["lo"], w["domain"]["hi"], 0.05, 0.05)
+    x = w["x"].copy()
+    vol = w["group"] == 0
+    c0 = float(g.c0)
+    k = np.arange(vol.sum())
+    x[vol, 0] = np.float64(g.origin[0]) + c0 * (1 + (k % 9))
+    x[vol, 1] = np.float64(g.origin[1]) + c0 * (1 + (k // 9) % 9) + 0.01 * (k // 81)
+    x[vol, :2] = np.clip(x[vol, :2], 0.001, 0.999)
+    w2 = dict(w)
+    w2["x"] = x
+    h = oracle_h(w2)
+    m = make(w2, 32, h=h)
+    key, cs, perm = S.sph_debug_rebuild(m.h, m.n, g.ncell)
+    rep = O.grid_repr(g, x, h, prec=32)
+    assert np.array_equal(key, rep["key"])
+    counts, lists = S.sph_debug_neighbors(m.h, m.n, 0)
+    got = _split(counts, lists)
+    for i in range(0, m.n, 3):
+        assert np.array_equal(got[i], O.neighbors_repr(g, x, h, i, prec=32))
+    m.close()

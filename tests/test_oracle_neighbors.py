@@ -39,7 +39,7 @@ def test_grid_spec_levels_cover_supports(D):
     # offsets inside [0, c_l) and the representation reproduces x
     for i in range(0, 3000, 97):
         l = rep["level"][i]
-        assert np.all(rep["off"][i, :D] >= 0) and np.all(rep["off"][i, :D] < c[l])
+        assert np.all(rep["off"][i, :D] >= -1e-12 * c[l]) and np.all(rep["off"][i, :D] < c[l] * (1 + 1e-12))
         xr = np.asarray(g.origin)[:D] + rep["cell"][i, :D] * c[l] + rep["off"][i, :D]
         assert np.all(np.abs(xr - x[i, :D]) < 1e-7 * c[l])
 
