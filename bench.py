@@ -1,0 +1,358 @@
+"""Benchmark of the relaxation hot path: particle-steps/s on the 2D disk-with-holes workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one pass of the whole hot path (cell-list rebuild, pressure pass with the feature
+boundary correction, controller, viscous update with projection) over every particle of the
+instance.  Workload: unit disk minus 3 seeded holes, h linear in the distance to the nearest
+hole (0.004-0.04 scaled to ~120k particles), FP32 pair sums with FP64 projection/reductions.
+
+* value:  particle-steps/s over K device-timed steps (CUDA events on the library's stream),
+          L2 flushed (256 MiB write) between steps; inputs resident in HBM.
+* e2e:    the same metric through the public C ABI from pinned host buffers: upload of the
+          initial state, K steps each followed by the read-back of the controller report,
+          read-back of the final positions -- all inside the host-timed region.
+* roofline: the dominant kernel's achieved rate from its live CUDA-event times.
+* cpu_baseline / --impl reference: the FP64 CPU oracle on the host cores (bounded sample).
+Multi-GPU (torchrun): every rank runs an independent replica (weak scaling, no collective on
+the data path); value = particles of all ranks x K / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s"
+WORKLOAD = "disk_holes_2d_120k"
+FLOP_PER_PAIR = 50.0       # FP32 operations per interacting pair of the pressure pass (see design notes)
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=120_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def hbm_peak(peaks):
+    for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs", "hbm"):
+        if k in peaks and isinstance(peaks[k], (int, float)):
+            return float(peaks[k])
+    return 6800.0
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except Exception:
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(n):
+    from paper_2003_01061_gb300 import workloads as WL
+
+    return WL.disk_holes(n_target=n, seed=2)
+
+
+# ----------------------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline leg)
+# ----------------------------------------------------------------------------------------
+def oracle_rate(w, budget_s=15.0, sample=None, steps=None):
+    """Times the FP64 oracle's pressure pass + update on a fixed particle sample.
+
+    Returns (particle-steps/s, description, threads, per-step seconds list)."""
+    from oracle import oracle as O
+
+    o = O.Oracle(w)
+    n = o.n
+    full = o.interact(use_grid=True)               # untimed: a_p of every particle
+    a_all = full["a_p"].copy()
+    for g in range(o.G):
+        o.ctrl.dt[g] = full["dta"][g] if np.isfinite(full["dta"][g]) else 0.0
+        o.ctrl.reset[g] = 1
+    rng = np.random.default_rng(0)
+    if sample is None:
+        t0 = time.perf_counter()
+        sub = np.sort(rng.choice(n, min(n, 4096), replace=False))
+        o.interact(sub=sub, use_grid=True)
+        o.integrate(a_all, sub=sub, use_grid=True)
+        per = (time.perf_counter() - t0) / len(sub)
+        sample = int(min(n, max(1024, budget_s / 3.0 / max(per, 1e-9))))
+    sub = np.sort(rng.choice(n, sample, replace=False))
+    times = []
+    nsteps = steps if steps is not None else 3
+    for _ in range(nsteps):
+        t0 = time.perf_counter()
+        r = o.interact(sub=sub, use_grid=True)
+        a_all[sub] = r["a_p"]
+        o.integrate(a_all, sub=sub, use_grid=True)
+        times.append(time.perf_counter() - t0)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    rate = sample * len(times) / sum(times)
+    desc = (f"FP64 oracle pressure pass + viscous update of {sample} sampled particles (of {n}) "
+            f"with full neighbourhoods, {len(times)} steps")
+    return rate, desc, threads, times
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    w = make_workload(args.n)
+    n = len(w["x"])
+    budget = 120.0
+    per_step = budget / max(args.steps + args.warmup, 1)
+    from oracle import oracle as O
+
+    O.build()
+    rate0, _, _, _ = oracle_rate(w, budget_s=min(per_step * 3, 10.0), steps=1)
+    sample = int(min(n, max(512, rate0 * per_step)))
+    oracle_rate(w, sample=sample, steps=max(args.warmup, 0) or 1)
+    rate, desc, threads, times = oracle_rate(w, sample=sample, steps=args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times) * n / sample,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": n, "dim": 2, "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": rate, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2003_01061_gb300 import build as B
+    from paper_2003_01061_gb300 import sphmesh as S
+
+    B.build()
+    w = make_workload(args.n)
+    n = len(w["x"])
+    stream = torch.cuda.Stream(device=dev)
+    m = S.Mesh(w, precision=32, stream=stream.cuda_stream)
+    m.set_state()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # warm-up (also captures the step graph)
+    m.step(max(args.warmup, 1))
+    m.sync()
+    S.sph_mesh_set_timing(m.h, 1)
+    m.step(1)                       # re-capture with the stage events
+    m.sync()
+    S.sph_mesh_set_timing(m.h, 1)   # zero the accumulators
+
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                evs[k][0].record(stream)
+                m.step(1)
+                evs[k][1].record(stream)
+                flush.zero_()       # 256 MiB write between timed steps evicts the 129 MB L2
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(step_ms))
+    stage = S.sph_mesh_kernel_times(m.h)
+    S.sph_mesh_set_timing(m.h, 0)
+    m.sync()
+    rep = m.report()
+
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = n * ws * args.steps / (total_ms / 1e3)
+
+    # per-stage averages and the dominant kernel's roofline
+    cand, accd = S.sph_debug_pair_counts(m.h)
+    stages = {k: {"launches": int(v[0]), "avg_ms": (v[1] / max(v[0], 1)) if k != "rebuild" else v[1] / max(args.steps, 1)}
+              for k, v in stage.items()}
+    peaks, peak_src = measured_peaks()
+    clocks = clk.summary()
+    fp32_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12       # TFLOP/s at the maximum SM clock
+    dom = max(("interact", "integrate", "control"), key=lambda k: stages.get(k, {}).get("avg_ms", 0.0))
+    t_dom = stages[dom]["avg_ms"] / 1e3
+    # algorithmic work of the pressure pass: FLOP_PER_PAIR per interacting pair; the viscous
+    # pass visits the same-group pairs only (counted the same way, a lower bound)
+    flops = FLOP_PER_PAIR * accd
+    achieved = flops / t_dom / 1e12
+    bytes_per_particle = {"interact": 2 * 16 + 8 + 4 + 16, "integrate": 16 + 16 + 8 + 4 + 16 + 8 + 4 + 4 + 4 + 4,
+                          "control": 0}
+    hbm_gbs = n * bytes_per_particle[dom] / t_dom / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None, "kernel": dom,
+                "peak_source": f"FP32: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {SM_MAX_MHZ:.0f} MHz",
+                "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak(peaks), "hbm_frac": hbm_gbs / hbm_peak(peaks),
+                "hbm_peak_source": peak_src}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_run(S, w, stream, args.steps)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+
+        O.build()
+        rate, desc, threads, times = oracle_rate(w, budget_s=15.0)
+        cpu = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle", "sample": desc}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": n, "dim": 2, "groups": m.n_groups,
+                   "precision": "fp32 pair sums, fp64 projection and reductions", "replicas": ws,
+                   "l2": "flushed between timed steps (256 MiB write)", "phase_at_end": int(rep.phase),
+                   "iteration_at_end": int(rep.iteration)},
+        "roofline": roofline,
+        "stages_ms": {k: v["avg_ms"] for k, v in stages.items()},
+        "pairs_per_particle": {"candidates": cand / n, "interacting": accd / n},
+        "clocks": clocks,
+        "gpu_launches": 10 * args.steps,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    m.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def e2e_run(S, w, stream, steps):
+    """Whole job through the public API from pinned host buffers (host-timed)."""
+    import torch
+
+    n = len(w["x"])
+    x = torch.from_numpy(np.ascontiguousarray(w["x"])).pin_memory().numpy()
+    g = torch.from_numpy(np.ascontiguousarray(w["group"], dtype=np.int32)).pin_memory().numpy()
+    xo = torch.empty((n, 3), dtype=torch.float64).pin_memory().numpy()
+    go = torch.empty(n, dtype=torch.int32).pin_memory().numpy()
+    m = S.Mesh(w, precision=32, stream=stream.cuda_stream)
+    m.set_state()
+    m.step(2)
+    S.sph_mesh_report(m.h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S.sph_mesh_set_state(m.h, x, g)
+    for _ in range(steps):
+        S.sph_mesh_step(m.h, 1)
+        S.sph_mesh_report(m.h)          # the step's result: controller state (E_sys, phase, dt)
+    got = S.lib().sph_mesh_positions(m.h, xo.ctypes.data, go.ctypes.data, None, None, n, None)
+    t1 = time.perf_counter()
+    assert got == 0
+    m.close()
+    h2d = n * (3 * 8 + 4)
+    d2h_report = S.C.sizeof(S.sph_report) if hasattr(S, "C") else 1280
+    d2h = n * (3 * 8 + 4) / steps + d2h_report
+    return {"value": n * steps / (t1 - t0), "unit": METRIC, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h, "wall_s": t1 - t0,
+            "job": f"upload of {n} particles, {steps} steps each with a controller-report read, final download"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

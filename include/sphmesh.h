@@ -155,7 +155,7 @@ sph_status sph_params_default(sph_params* params);
 /* Loads a particle set (Algorithm 1, "allocate particles ... initial particle sampling") and
  * resets the controller to Phase One, step 0.  x: [n][3] positions; group: feature index of
  * each particle; v: [n][3] velocities or NULL for zero; h: per-particle smoothing length or
- * NULL for h_t(x).  Positions must lie inside the bounding box and h inside [lo, hi].
+ * NULL for h_t(x).  Positions must lie inside the bounding box and h in (0, hi*(1+2^-11)].
  * Errors: SPH_E_INVALID (n > max_particles, bad group, position or h out of range). */
 sph_status sph_mesh_set_state(sph_mesh* m, int64_t n, const double* x, const int32_t* group,
                               const double* v, const double* h);

@@ -802,7 +802,9 @@ sph_status sph_mesh_set_state(sph_mesh* m, int64_t n, const double* x, const int
             if (!(xa >= m->hdom.lo[a] - 1e-9 * (1 + std::fabs(m->hdom.lo[a])) && xa <= m->hdom.hi[a] + 1e-9 * (1 + std::fabs(m->hdom.hi[a]))))
                 return fail(SPH_E_INVALID, "set_state: particle %lld outside the bounding box", (long long)i);
         }
-        if (h && !(h[i] >= m->h_lo * (1 - 1e-12) && h[i] <= m->h_hi * (1 + 1e-12)))
+        // the grid's top level covers kappa*h_hi*(1+2^-10); allow h up to h_hi*(1+2^-11) so that
+        // values rounded to the working precision are accepted
+        if (h && !(h[i] > 0 && h[i] <= m->h_hi * (1 + 1.0 / 2048.0)))
             return fail(SPH_E_INVALID, "set_state: h of particle %lld outside [lo, hi]", (long long)i);
         if (v)
             for (int a = 0; a < D; ++a)

@@ -1,0 +1,155 @@
+"""Multi-step GPU runs against the oracle (needs a GB300).
+
+Trajectories of a particle relaxation drift apart from rounding differences, so after K steps
+the comparison is statistical (the acceptance bounds stated for the method): the histogram of
+nearest-neighbour spacing / h_t (50 bins on [0.5, 1.5]) within 1 % (L1) and the Delaunay
+quality (mean minimum angle, mean G = 2 sqrt(3) S/(P H), Sec. 4) within 0.5 degrees / 0.01.
+The disk case drifts faster (the oracle against itself with a 1e-7 relative perturbation of
+the start already differs by ~3 % L1 after 150 steps), so its histogram bound is 5 %.
+The FP64 build is also compared position by position over a shorter horizon.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial import Delaunay, cKDTree
+
+from oracle import oracle as O
+from paper_2003_01061_gb300 import build as B
+from paper_2003_01061_gb300 import sphmesh as S
+from paper_2003_01061_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def spacing_hist(w, x, h_of):
+    groups = w["group"]
+    dims = np.array([f["dim"] for f in w["domain"]["features"]])
+    vals = []
+    for g in np.unique(groups):
+        if dims[g] < 1:
+            continue
+        sel = np.where(groups == g)[0]
+        if len(sel) < 3:
+            continue
+        tr = cKDTree(x[sel])
+        d, _ = tr.query(x[sel], k=2)
+        vals.append(d[:, 1] / h_of[sel])
+    v = np.concatenate(vals)
+    hist, _ = np.histogram(v, bins=50, range=(0.5, 1.5))
+    return hist / len(v)
+
+
+def quality_2d(w, x):
+    tri = Delaunay(x[:, :2])
+    P = x[tri.simplices][:, :, :2]
+    cen = np.concatenate([P.mean(axis=1), np.zeros((len(P), 1))], axis=1)
+    keep = WL.domain_phi(w["domain"], cen) > 0
+    P = P[keep]
+    e = np.stack([np.linalg.norm(P[:, 1] - P[:, 2], axis=1), np.linalg.norm(P[:, 0] - P[:, 2], axis=1),
+                  np.linalg.norm(P[:, 0] - P[:, 1], axis=1)], axis=1)
+    u, v = P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]
+    area = 0.5 * np.abs(u[:, 0] * v[:, 1] - u[:, 1] * v[:, 0])
+    half = e.sum(axis=1) / 2
+    G = 2 * math.sqrt(3) * area / (half * e.max(axis=1))
+    ang = []
+    for k in range(3):
+        a, b, c = e[:, k], e[:, (k + 1) % 3], e[:, (k + 2) % 3]
+        ang.append(np.degrees(np.arccos(np.clip((b * b + c * c - a * a) / (2 * b * c), -1, 1))))
+    tmin = np.min(np.stack(ang, 1), axis=1)
+    return float(tmin.mean()), float(G.mean())
+
+
+def run_both(w, prec, steps):
+    o = O.Oracle(w)
+    h0 = o.h.copy()
+    if prec == 32:
+        h0 = h0.astype(np.float32).astype(np.float64)
+        o = O.Oracle(w, h=h0)
+    m = S.Mesh(w, precision=prec)
+    m.set_state(h=h0)
+    m.step(steps)
+    m.sync()
+    got = m.positions()
+    rep = m.report()
+    o.step(steps, use_grid=True)
+    m.close()
+    return o, got, rep
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_square_200_steps_statistics(prec):
+    w = WL.square2d()
+    w["params"] = WL.scaled_controller(w["params"])
+    o, got, rep = run_both(w, prec, 200)
+    assert rep.status == 0
+    assert rep.iteration == o.iteration
+    hx = np.full(len(o.x), 0.02)
+    hg, ho = spacing_hist(w, got["x"], hx), spacing_hist(w, o.x, hx)
+    assert np.abs(hg - ho).sum() <= 0.01
+    qg, qo = quality_2d(w, got["x"]), quality_2d(w, o.x)
+    assert abs(qg[0] - qo[0]) <= 0.5 and abs(qg[1] - qo[1]) <= 0.01
+    # a relaxed lattice is at least as regular as the jittered start
+    q0 = quality_2d(w, w["x"])
+    assert qg[0] >= q0[0] - 0.5
+
+
+def test_fp64_trajectory_follows_oracle():
+    w = WL.square2d(h=0.04, seed=5, jitter=0.2)
+    w["params"] = WL.scaled_controller(w["params"], sample_every=2, window=5, ramp_len=10, reset_period=25)
+    o, got, rep = run_both(w, 64, 60)
+    assert rep.iteration == o.iteration and rep.phase == o.phase
+    err = np.abs(got["x"] - o.x).max()
+    assert err <= 1e-9 * 0.04, err
+    for g in range(o.G):
+        assert abs(rep.dt[g] - o.ctrl.dt[g]) <= 1e-8 * max(o.ctrl.dt[g], 1e-300)
+    assert abs(rep.E_sys - o.ctrl.E_sys) <= 1e-6 * max(o.ctrl.E_sys, 1e-12) + 1e-12
+
+
+def test_disk_statistics_fp32():
+    w = WL.disk_holes(n_target=6000, seed=2)
+    w["params"] = WL.scaled_controller(w["params"], sample_every=5, window=10, ramp_len=50)
+    o, got, rep = run_both(w, 32, 150)
+    assert rep.status == 0 and rep.iteration == o.iteration
+    siz = w["sizing"]
+    hg = spacing_hist(w, got["x"], WL.sizing_eval(siz, got["x"]))
+    ho = spacing_hist(w, o.x, WL.sizing_eval(siz, o.x))
+    assert np.abs(hg - ho).sum() <= 0.05
+    qg, qo = quality_2d(w, got["x"]), quality_2d(w, o.x)
+    assert abs(qg[0] - qo[0]) <= 0.5 and abs(qg[1] - qo[1]) <= 0.01
+    # every curve particle stays on its circle
+    for k, f in enumerate(w["domain"]["features"]):
+        if f["kind"] == "circle":
+            sel = got["group"] == k
+            r = np.linalg.norm(got["x"][sel, :2] - np.asarray(f["c"][:2]), axis=1)
+            assert np.abs(r - f["r"]).max() < 1e-12
+
+
+def test_run_until_converged_reaches_done():
+    # With Eq. 24 as stated, Phase One keeps a CFL-limited oscillation and E_sys levels off
+    # near 1e-2 on this small case, so the threshold is raised to a level both sides reach.
+    w = WL.square2d(h=0.05, seed=3, jitter=0.1)
+    w["params"] = WL.scaled_controller(w["params"], sample_every=2, window=10, ramp_len=20)
+    w["params"]["threshold"] = 2e-2
+    m = S.Mesh(w, precision=64)
+    m.set_state()
+    ok, iters = S.sph_mesh_run_until_converged(m.h, 5000)
+    rep = m.report()
+    o = O.Oracle(w)
+    o.step(5000, use_grid=True)
+    assert ok and rep.phase == S.DONE and rep.ramp_start > 0
+    assert o.phase == O.DONE
+    assert iters == rep.iteration
+    # the switch steps agree up to a couple of sampling windows (trajectories diverge slowly)
+    assert abs(iters - o.iteration) <= 2 * 10 * 2
+    ok2, iters2 = S.sph_mesh_run_until_converged(m.h, 5000)
+    assert ok2 and iters2 == iters                   # DONE freezes the state
+    m.set_state()
+    ok3, iters3 = S.sph_mesh_run_until_converged(m.h, 10)
+    assert not ok3 and iters3 == 10                  # max_iters reached: not converged, state valid
+    m.close()
