@@ -214,15 +214,15 @@ template <typename T> Out<T> out_stored(const State<T>& s) {
 template <typename T, int D> void enqueue_step(sph_mesh* m, bool timed) {
     const State<T>& s = st<T>(m);
     cudaStream_t stream = m->stream;
-    if (timed) cudaEventRecord(m->ev[0], stream);
+    if (timed) cudaEventRecordWithFlags(m->ev[0], stream, cudaEventRecordExternal);
     enqueue_rebuild<T, D>(m, s, stream);
-    if (timed) cudaEventRecord(m->ev[1], stream);
+    if (timed) cudaEventRecordWithFlags(m->ev[1], stream, cudaEventRecordExternal);
     launch_interact<T, D>(m->grid, m->params, s, nullptr, nullptr, stream);
-    if (timed) cudaEventRecord(m->ev[2], stream);
+    if (timed) cudaEventRecordWithFlags(m->ev[2], stream, cudaEventRecordExternal);
     launch_control<T>(m->params, s, stream);
-    if (timed) cudaEventRecord(m->ev[3], stream);
+    if (timed) cudaEventRecordWithFlags(m->ev[3], stream, cudaEventRecordExternal);
     launch_integrate<T, D>(m->grid, m->params, s, s.ctrl, out_stored<T>(s), stream);
-    if (timed) cudaEventRecord(m->ev[4], stream);
+    if (timed) cudaEventRecordWithFlags(m->ev[4], stream, cudaEventRecordExternal);
 }
 
 sph_status collect_timing(sph_mesh* m) {

@@ -1,0 +1,114 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py times (needs a
+GB300): the 2D disk with holes at ~120k particles (every particle compared) and the 3D cube
+minus sphere at ~1.2M particles (sampled particles, each computed by brute force in the
+oracle), plus invariants of a multi-step full-size run."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2003_01061_gb300 import build as B
+from paper_2003_01061_gb300 import sphmesh as S
+from paper_2003_01061_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+@pytest.fixture(scope="module")
+def disk():
+    return WL.disk_holes(n_target=120_000, seed=2)
+
+
+@pytest.fixture(scope="module")
+def cube():
+    return WL.cube_sphere(n_target=1_200_000, seed=3)
+
+
+def f32(a):
+    return np.asarray(a).astype(np.float32).astype(np.float64)
+
+
+def test_disk_full_pressure_pass(disk):
+    w = disk
+    o0 = O.Oracle(w)
+    h = f32(o0.h)
+    o = O.Oracle(w, h=h)
+    ref = o.interact(use_grid=True)
+    m = S.Mesh(w, precision=32)
+    m.set_state(h=h)
+    got = S.sph_debug_interact(m.h, m.n, m.n_groups)
+    err = np.linalg.norm(got["a_p"] - ref["a_p"], axis=1)
+    rel = err / np.maximum(ref["S"], 1e-300)
+    assert rel.max() <= 1e-5, rel.max()
+    for g in range(m.n_groups):
+        assert abs(got["dta"][g] - ref["dta"][g]) <= 2e-4 * ref["dta"][g]
+    m.close()
+
+
+def test_disk_full_update_sampled(disk):
+    w = disk
+    h = f32(O.Oracle(w).h)
+    o = O.Oracle(w, h=h)
+    r = o.interact(use_grid=True)
+    dt = np.where(o.gdim > 0, r["dta"], 0.0)
+    for g in range(o.G):
+        o.ctrl.dt[g] = dt[g]
+        o.ctrl.reset[g] = 1
+    o.ctrl.eps, o.ctrl.ramp_f = 0.0, 1.0
+    sub = np.sort(np.random.default_rng(1).choice(o.n, 2000, replace=False))
+    ref = o.integrate(r["a_p"], sub=sub, use_grid=True)
+    m = S.Mesh(w, precision=32)
+    m.set_state(h=h)
+    got = S.sph_debug_update(m.h, m.n, dt, np.ones(o.G, np.int32), 0.0, 1.0)
+    dtp = dt[w["group"][sub]]
+    scale = dtp ** 2 * r["S"][sub] + 1e-300
+    ex = np.linalg.norm(got["x"][sub] - ref["x"], axis=1)
+    assert np.all(ex <= 5e-4 * scale + 4e-16), (ex / scale).max()
+    assert np.allclose(got["h"][sub], ref["h"], rtol=4e-5, atol=0)
+    m.close()
+
+
+def test_cube_full_pressure_pass_sampled(cube):
+    w = cube
+    h = f32(WL.sizing_eval(w["sizing"], w["x"]))      # the input h_t(x), given to both sides
+    m = S.Mesh(w, precision=32)
+    m.set_state(h=h)
+    got = S.sph_debug_interact(m.h, m.n, m.n_groups)
+    o = O.Oracle(w, h=h)
+    rng = np.random.default_rng(2)
+    # every group is represented in the sample
+    sub = np.concatenate([rng.choice(np.where(w["group"] == g)[0], min(12, (w["group"] == g).sum()), replace=False)
+                          for g in range(o.G) if o.gdim[g] > 0] + [rng.choice(o.n, 150, replace=False)])
+    ref = o.interact(sub=sub, use_grid=False)
+    err = np.linalg.norm(got["a_p"][sub] - ref["a_p"], axis=1)
+    rel = err / np.maximum(ref["S"], 1e-300)
+    assert rel.max() <= 1e-5, rel.max()
+    assert np.allclose(got["sigma"][sub], ref["sigma"], rtol=1e-5)
+    m.close()
+
+
+def test_disk_full_run_invariants(disk):
+    w = disk
+    m = S.Mesh(w, precision=32)
+    m.set_state()
+    m.step(60)
+    m.sync()
+    p = m.positions()
+    rep = m.report()
+    assert rep.iteration == 60 and rep.status == 0
+    assert np.all(np.isfinite(p["x"]))
+    phi = WL.domain_phi(w["domain"], p["x"])
+    vol = p["group"] == 0
+    assert phi[vol].min() >= -1e-12
+    for k, f in enumerate(w["domain"]["features"]):
+        if f["kind"] == "circle":
+            sel = p["group"] == k
+            r = np.linalg.norm(p["x"][sel, :2] - np.asarray(f["c"][:2]), axis=1)
+            assert np.abs(r - f["r"]).max() < 1e-12
+    assert np.allclose(p["h"], f32(WL.sizing_eval(w["sizing"], p["x"])), rtol=2e-6)
+    assert np.array_equal(p["group"], w["group"])
+    m.close()
