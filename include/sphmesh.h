@@ -270,6 +270,36 @@ sph_status sph_mesh_kernel_times(sph_mesh* m, sph_kernel_time* out, int32_t cap,
  * candidate pairs visited and pairs inside the support, over one pressure pass. */
 sph_status sph_debug_pair_counts(sph_mesh* m, int64_t* candidates, int64_t* accepted);
 
+/* ------------------------------------------------------------------------------------------
+ * Cell-list rebuild that allocates nothing.  The paper has no counterpart: this entry point
+ * serves callers that are not allowed to allocate device memory -- for example an application
+ * that reserves all of the GPU's memory for its own pool at start-up and forbids libraries from
+ * allocating afterwards (so that its budget stays fixed), or a latency-critical loop in which a
+ * cudaMalloc/cudaFree could synchronise the device or fail under memory pressure.
+ *
+ * It computes the same cell keys, cell starts and stable permutation as sph_debug_rebuild, for
+ * positions x_dev, y_dev, z_dev (device arrays of n doubles each; z_dev may be NULL in 2D) and
+ * smoothing lengths h_dev (n floats) on the grid `grid` (from sph_grid_spec or sph_mesh_grid).
+ * Outputs, all caller-owned device arrays: key_dev [n], cell_start_dev [n_cells + 1], perm_dev [n].
+ * Work is enqueued on `stream` (a cudaStream_t, NULL for the default stream); the call does not
+ * wait for it.
+ *
+ * Its only scratch is a fixed array in device memory, SPH_NOALLOC_MAX_CELLS + 256 ints
+ * (4 MiB + 1 KiB), that every GPU which loads the library holds until the process exits.
+ * The first call on a device looks up that array's device address with the device current
+ * (a one-time set-up per device); make that first call before any stream capture.  Grids with
+ * more than SPH_NOALLOC_MAX_CELLS cells are rejected with SPH_E_INVALID.  All calls share the
+ * array: the counters are cleared at the start of each call, and calls whose work overlaps on
+ * the GPU (other streams or other threads) race and give wrong results.  Positions outside
+ * the grid are clamped into its border cells without a report.  The call never allocates or
+ * frees memory.  Errors: SPH_E_INVALID, SPH_E_CUDA (message in sph_last_error()).
+ * ------------------------------------------------------------------------------------------ */
+#define SPH_NOALLOC_MAX_CELLS (1 << 20)
+sph_status sph_cell_sort_noalloc(const sph_grid_info* grid, int64_t n, const double* x_dev,
+                                 const double* y_dev, const double* z_dev, const float* h_dev,
+                                 int32_t* key_dev, int32_t* cell_start_dev, int32_t* perm_dev,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

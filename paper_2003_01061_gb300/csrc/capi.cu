@@ -85,6 +85,12 @@ sph_status grid_spec(int D, const double* lo, const double* hi, double h_lo, dou
     return SPH_OK;
 }
 
+}  // namespace
+
+void sph::set_last_error(const char* msg) { g_err = msg; }
+
+namespace {
+
 struct KTime {
     const char* name;
     int kernels;   // kernel launches per step in this stage

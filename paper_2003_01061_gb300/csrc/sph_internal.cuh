@@ -47,6 +47,7 @@ template <typename T> struct Out {
     T* av[3];          // optional: viscous acceleration (inspection only)
 };
 
+constexpr int BUF_CAP = 32;   // kept candidates per lane between flushes of the warp walk (shared memory)
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -76,4 +77,9 @@ template <typename T, int D>
 void launch_integrate(const Grid& g, const Params& p, const State<T>& s, const Ctrl* use, const Out<T>& o,
                       cudaStream_t st);
 
+}  // namespace sph
+
+namespace sph {
+// sets the message returned by sph_last_error() on the calling thread (capi.cu)
+void set_last_error(const char* msg);
 }  // namespace sph

@@ -74,7 +74,7 @@ EXPORTS = ["sph_params_default", "sph_mesh_create", "sph_mesh_set_state", "sph_m
            "sph_mesh_run_until_converged", "sph_mesh_positions", "sph_mesh_report", "sph_mesh_destroy",
            "sph_last_error", "sph_grid_spec", "sph_mesh_grid", "sph_debug_rebuild", "sph_debug_neighbors",
            "sph_debug_interact", "sph_debug_update", "sph_mesh_set_timing", "sph_mesh_kernel_times",
-           "sph_debug_pair_counts"]
+           "sph_debug_pair_counts", "sph_cell_sort_noalloc"]
 
 _lib = None
 
@@ -105,6 +105,7 @@ def lib():
             "sph_mesh_set_timing": [vp, i32],
             "sph_mesh_kernel_times": [vp, vp, i32, vp],
             "sph_debug_pair_counts": [vp, vp, vp],
+            "sph_cell_sort_noalloc": [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -312,6 +313,13 @@ def sph_debug_pair_counts(m):
     a, b = C.c_int64(0), C.c_int64(0)
     _check(lib().sph_debug_pair_counts(m, C.addressof(a), C.addressof(b)))
     return a.value, b.value
+
+
+def sph_cell_sort_noalloc(grid: sph_grid_info, n, x_ptr, y_ptr, z_ptr, h_ptr, key_ptr, cell_start_ptr, perm_ptr,
+                          stream=None):
+    """Allocation-free rebuild on caller-owned device arrays (raw device pointers as ints)."""
+    _check(lib().sph_cell_sort_noalloc(C.addressof(grid), int(n), x_ptr, y_ptr, z_ptr, h_ptr, key_ptr,
+                                       cell_start_ptr, perm_ptr, stream))
 
 
 class Mesh:
