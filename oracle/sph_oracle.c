@@ -292,10 +292,13 @@ int64_t orc_neighbors_brute(int64_t n, int D, const double* x, const double* h, 
  *   thr[l] = c_l/(kappa*(1+2^-10)) rounded down to a float (l < L-1), thr[L-1] = +inf;
  *   a particle's level is the first l with h <= thr[l];
  *   origin = (lo - c_{L-1}) rounded down to floats;  dims_l = ceil((hi + c_{L-1} - origin)/c_l)+1;
- *   cell = floor((x - origin) * (1/c_l)) with 1/c_l rounded once in FP64 (clamped into the
- *          grid), key = base_l + row-major cell (x fastest);
- *   offset = (x - origin) - cell*c_l, rounded to the working precision (it may fall an ulp
- *          outside [0, c_l) where the rounded inverse puts x on the other side of a face). */
+ *   finest cell c = floor((x - origin) * (1/c0)) with 1/c0 rounded once in FP64 (clamped into
+ *          the finest grid) and finest offset o = (x - origin) - c*c0 rounded to the working
+ *          precision (it may fall an ulp outside [0, c0) where the rounded inverse puts x on
+ *          the other side of a face);
+ *   level l: cell = c >> l, offset = o + (c - (cell << l))*c0, each operation rounded in the
+ *          working precision (the stored state is the finest cell + offset, so coarser levels
+ *          are derived from it without the FP64 position); key = base_l + row-major cell. */
 static float f_round_up(double v) {
     float f = (float)v;
     if ((double)f < v) f = nextafterf(f, INFINITY);
@@ -346,17 +349,28 @@ static int level_of(const orc_grid* g, double h, int prec) {
 static void repr_one(const orc_grid* g, const double* x, double h, int prec, int* lvl,
                      int64_t* cell, double* off, int* clamped) {
     int l = level_of(g, h, prec);
-    double cl = ldexp((double)g->c0, l);
+    const double c0 = (double)g->c0;
     *lvl = l;
     *clamped = 0;
     for (int a = 0; a < 3; ++a) {
         if (a >= g->D) { cell[a] = 0; off[a] = 0; continue; }
+        /* finest-level cell and offset, from the FP64 position */
         double rel = x[a] - (double)g->origin[a];
-        int64_t c = (int64_t)floor(rel * (1.0 / cl));
+        int64_t c = (int64_t)floor(rel * (1.0 / c0));
         if (c < 0) { c = 0; *clamped = 1; }
-        if (c > g->dims[l][a] - 1) { c = g->dims[l][a] - 1; *clamped = 1; }
-        cell[a] = c;
-        off[a] = to_prec(rel - (double)c * cl, prec);
+        if (c > g->dims[0][a] - 1) { c = g->dims[0][a] - 1; *clamped = 1; }
+        double o0 = to_prec(rel - (double)c * c0, prec);
+        /* level l: cell = c >> l; offset = o0 + (c - (cell << l)) * c0, each operation rounded
+         * in the working precision */
+        int64_t cl = c >> l;
+        int64_t rem = c - (cl << l);
+        if (prec == 32) {
+            float t = (float)rem * g->c0;
+            off[a] = (double)((float)o0 + t);
+        } else {
+            off[a] = o0 + (double)rem * c0;
+        }
+        cell[a] = cl;
     }
 }
 

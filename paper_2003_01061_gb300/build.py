@@ -19,7 +19,7 @@ LIB = os.path.join(OUT_DIR, "libsphmesh.so")
 UNITS = ["rebuild.cu", "interact.cu", "integrate.cu", "capi.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-         "--expt-relaxed-constexpr", "-I", INCLUDE]
+         "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-I", INCLUDE]
 
 
 def nvcc() -> str:

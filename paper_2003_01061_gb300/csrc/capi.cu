@@ -140,7 +140,9 @@ template <> State<double>& st<double>(sph_mesh* m) { return m->sd; }
 template <typename T> size_t layout(sph_mesh* m, char* base, bool assign) {
     const size_t cap = (size_t)std::max<int64_t>(m->cap, 1);
     const size_t ncell = (size_t)m->grid.ncell;
-    const size_t nblk = (size_t)div_up((long long)cap, BLOCK);
+    const size_t nblk = (size_t)div_up((long long)cap * LPP_MAX, BLOCK);
+    const int t = m->grid.L - 1;
+    const size_t nocc = (size_t)m->grid.dims[t][0] * m->grid.dims[t][1] * m->grid.dims[t][2];
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         off = (off + 255) & ~(size_t)255;
@@ -151,9 +153,11 @@ template <typename T> size_t layout(sph_mesh* m, char* base, bool assign) {
     State<T> s;
     std::memset(&s, 0, sizeof s);
     for (int a = 0; a < 3; ++a) {
-        s.X[a] = (double*)take(cap * sizeof(double));
+        s.C[a] = (int*)take(cap * 4);
+        s.O[a] = (T*)take(cap * sizeof(T));
         s.V[a] = (T*)take(cap * sizeof(T));
-        s.Xs[a] = (double*)take(cap * sizeof(double));
+        s.Cs[a] = (int*)take(cap * 4);
+        s.Os[a] = (T*)take(cap * sizeof(T));
         s.Vs[a] = (T*)take(cap * sizeof(T));
     }
     s.H = (T*)take(cap * sizeof(T));
@@ -171,9 +175,11 @@ template <typename T> size_t layout(sph_mesh* m, char* base, bool assign) {
     s.bsum = (int*)take((size_t)SCAN_TILE * 4);
     s.perm = (int*)take(cap * 4);
     s.partials = (double*)take(nblk * MAXF * sizeof(double));
+    s.occ = (unsigned*)take(nocc * 4);
     if (assign) {
         s.n = 0;
         s.nblk = 0;
+        s.nocc = (int)nocc;
         s.ctrl = m->d_ctrl;
         s.dom = m->d_dom;
         s.siz = m->d_siz;
@@ -198,7 +204,7 @@ template <typename T> void ctrl_inf_bits(Ctrl* c) {
 
 template <typename T, int D> void enqueue_rebuild(sph_mesh* m, const State<T>& s, cudaStream_t stream) {
     launch_hash<T, D>(m->grid, s, stream);
-    launch_scan(m->grid.ncell, s.count, s.cell_start, s.bsum, stream);
+    launch_scan(m->grid.ncell, s.count, s.cell_start, s.bsum, stream, s.occ, s.nocc);
     launch_scatter<T>(s, stream);
     launch_cellsort(m->grid.ncell, s.n, s.cell_start, s.perm, s.count, stream);
     launch_gather<T, D>(m->grid, s, stream);
@@ -207,7 +213,8 @@ template <typename T, int D> void enqueue_rebuild(sph_mesh* m, const State<T>& s
 template <typename T> Out<T> out_stored(const State<T>& s) {
     Out<T> o;
     for (int a = 0; a < 3; ++a) {
-        o.X[a] = s.X[a];
+        o.C[a] = s.C[a];
+        o.O[a] = s.O[a];
         o.V[a] = s.V[a];
         o.av[a] = nullptr;
     }
@@ -286,18 +293,28 @@ template <typename T, int D> sph_status step_impl(sph_mesh* m, int32_t n_steps) 
 
 // state in device memory -> host arrays in original order (from an Out-like set of arrays)
 template <typename T>
-sph_status download(sph_mesh* m, double* const X[3], T* const V[3], T* H, unsigned* G, int* ID, double* x_out,
-                    int32_t* group_out, double* v_out, double* h_out) {
+sph_status download(sph_mesh* m, int* const Cd[3], T* const Od[3], T* const V[3], T* H, unsigned* G, int* ID,
+                    double* x_out, int32_t* group_out, double* v_out, double* h_out) {
     const int n = m->n, D = m->D;
     std::vector<int> id(n);
     CK(cudaMemcpyAsync(id.data(), ID, sizeof(int) * n, cudaMemcpyDeviceToHost, m->stream));
-    std::vector<double> xs(x_out ? (size_t)n * 3 : 0);
+    std::vector<int> cs(x_out ? (size_t)n * 3 : 0);
+    std::vector<T> os(x_out ? (size_t)n * 3 : 0);
     std::vector<T> vs(v_out ? (size_t)n * 3 : 0), hs(h_out ? n : 0);
     std::vector<unsigned> gs(group_out ? n : 0);
     for (int a = 0; a < D; ++a) {
-        if (x_out) CK(cudaMemcpyAsync(xs.data() + (size_t)a * n, X[a], sizeof(double) * n, cudaMemcpyDeviceToHost, m->stream));
+        if (x_out) {
+            CK(cudaMemcpyAsync(cs.data() + (size_t)a * n, Cd[a], sizeof(int) * n, cudaMemcpyDeviceToHost, m->stream));
+            CK(cudaMemcpyAsync(os.data() + (size_t)a * n, Od[a], sizeof(T) * n, cudaMemcpyDeviceToHost, m->stream));
+        }
         if (v_out) CK(cudaMemcpyAsync(vs.data() + (size_t)a * n, V[a], sizeof(T) * n, cudaMemcpyDeviceToHost, m->stream));
     }
+    // FP64 position = origin + cell * c0 + offset
+    std::vector<double> xs(x_out ? (size_t)n * 3 : 0);
+    for (int a = 0; x_out && a < D; ++a)
+        for (int k = 0; k < n; ++k)
+            xs[(size_t)a * n + k] = ((double)m->grid.origin[a] + (double)cs[(size_t)a * n + k] * m->grid.c[0]) +
+                                    (double)os[(size_t)a * n + k];
     if (h_out) CK(cudaMemcpyAsync(hs.data(), H, sizeof(T) * n, cudaMemcpyDeviceToHost, m->stream));
     if (group_out) CK(cudaMemcpyAsync(gs.data(), G, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, m->stream));
     CK(cudaStreamSynchronize(m->stream));
@@ -318,14 +335,21 @@ template <typename T, int D> sph_status set_state_impl(sph_mesh* m, int64_t n, c
                                                        const double* v, const double* h) {
     State<T>& s = st<T>(m);
     const int nn = (int)n;
-    std::vector<double> xs((size_t)std::max(nn, 1) * 3);
-    std::vector<T> vs((size_t)std::max(nn, 1) * 3, T(0)), hs(std::max(nn, 1));
+    std::vector<int> cs((size_t)std::max(nn, 1) * 3);
+    std::vector<T> os((size_t)std::max(nn, 1) * 3), vs((size_t)std::max(nn, 1) * 3, T(0)), hs(std::max(nn, 1));
     std::vector<unsigned> gs(std::max(nn, 1));
     std::vector<int> ids(std::max(nn, 1));
+    const double c0 = m->grid.c[0], inv_c0 = m->grid.inv_c[0];
     for (int i = 0; i < nn; ++i) {
         const int gi = group[i];
         for (int a = 0; a < D; ++a) {
-            xs[(size_t)a * nn + i] = x[(size_t)i * 3 + a];
+            // finest cell and offset: c = floor((x - origin) * (1/c0)), o = (x - origin) - c*c0
+            const double rel = x[(size_t)i * 3 + a] - (double)m->grid.origin[a];
+            double t = std::floor(rel * inv_c0);
+            int ca = (int)std::fmax(std::fmin(t, 2.0e9), -2.0e9);
+            ca = std::min(std::max(ca, 0), m->grid.dims[0][a] - 1);
+            cs[(size_t)a * nn + i] = ca;
+            os[(size_t)a * nn + i] = (T)(rel - (double)ca * c0);
             if (v) vs[(size_t)a * nn + i] = (T)v[(size_t)i * 3 + a];
         }
         if (h) hs[i] = (T)h[i];
@@ -334,16 +358,17 @@ template <typename T, int D> sph_status set_state_impl(sph_mesh* m, int64_t n, c
     }
     CK(cudaSetDevice(m->device));
     for (int a = 0; a < D; ++a) {
-        CK(cudaMemcpyAsync(s.X[a], xs.data() + (size_t)a * nn, sizeof(double) * nn, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(s.C[a], cs.data() + (size_t)a * nn, sizeof(int) * nn, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(s.O[a], os.data() + (size_t)a * nn, sizeof(T) * nn, cudaMemcpyHostToDevice, m->stream));
         CK(cudaMemcpyAsync(s.V[a], vs.data() + (size_t)a * nn, sizeof(T) * nn, cudaMemcpyHostToDevice, m->stream));
     }
     CK(cudaMemcpyAsync(s.G, gs.data(), 4 * (size_t)nn, cudaMemcpyHostToDevice, m->stream));
     CK(cudaMemcpyAsync(s.ID, ids.data(), 4 * (size_t)nn, cudaMemcpyHostToDevice, m->stream));
     s.n = nn;
-    s.nblk = div_up(nn, BLOCK);
+    s.nblk = div_up((long long)nn * Lpp<D>::v, BLOCK);   // blocks of the pair passes
     m->n = nn;
     if (h) CK(cudaMemcpyAsync(s.H, hs.data(), sizeof(T) * nn, cudaMemcpyHostToDevice, m->stream));
-    else if (nn > 0) launch_init_h<T, D>(s, m->stream);
+    else if (nn > 0) launch_init_h<T, D>(m->grid, s, m->stream);
     Ctrl c;
     host_ctrl_init(&c);
     ctrl_inf_bits<T>(&c);
@@ -379,7 +404,7 @@ template <typename T, int D> sph_status dbg_rebuild_impl(sph_mesh* m, int64_t* k
     if (r != SPH_OK) return r;
     const int n = m->n, nc = m->grid.ncell;
     launch_hash<T, D>(m->grid, s, m->stream);
-    launch_scan(nc, s.count, s.cell_start, s.bsum, m->stream);
+    launch_scan(nc, s.count, s.cell_start, s.bsum, m->stream, s.occ, s.nocc);
     launch_scatter<T>(s, m->stream);
     launch_cellsort(nc, s.n, s.cell_start, s.perm, s.count, m->stream);
     CK(cudaGetLastError());
@@ -531,7 +556,7 @@ sph_status dbg_update_impl(sph_mesh* m, const double* dt, const int32_t* reset, 
     Out<T> o;
     void* buf = nullptr;
     const size_t nn = (size_t)std::max(n, 1);
-    const size_t bytes = nn * (3 * sizeof(double) + 6 * sizeof(T) + sizeof(T) + 8) + 4096;
+    const size_t bytes = 16 * ((nn * (3 * 4 + 9 * sizeof(T) + sizeof(T) + 8) + 4096 + 15) / 16) + 16 * 256;
     CK(cudaMalloc(&buf, bytes));
     char* p = (char*)buf;
     auto take = [&](size_t b) {
@@ -539,7 +564,8 @@ sph_status dbg_update_impl(sph_mesh* m, const double* dt, const int32_t* reset, 
         p += (b + 255) & ~(size_t)255;
         return q;
     };
-    for (int a = 0; a < 3; ++a) o.X[a] = (double*)take(nn * sizeof(double));
+    for (int a = 0; a < 3; ++a) o.C[a] = (int*)take(nn * 4);
+    for (int a = 0; a < 3; ++a) o.O[a] = (T*)take(nn * sizeof(T));
     for (int a = 0; a < 3; ++a) o.V[a] = (T*)take(nn * sizeof(T));
     for (int a = 0; a < 3; ++a) o.av[a] = (T*)take(nn * sizeof(T));
     o.H = (T*)take(nn * sizeof(T));
@@ -547,11 +573,10 @@ sph_status dbg_update_impl(sph_mesh* m, const double* dt, const int32_t* reset, 
     o.ID = (int*)take(nn * 4);
     launch_integrate<T, D>(m->grid, m->params, s, m->d_ctrl_dbg, o, m->stream);
     CK(cudaGetLastError());
-    r = download<T>(m, o.X, o.V, o.H, o.G, o.ID, x_out, nullptr, v_out, h_out);
+    r = download<T>(m, o.C, o.O, o.V, o.H, o.G, o.ID, x_out, nullptr, v_out, h_out);
     if (r == SPH_OK && a_v) {
-        std::vector<double> tmp((size_t)n * 3);
         T* const avs[3] = {o.av[0], o.av[1], o.av[2]};
-        r = download<T>(m, o.X, avs, o.H, o.G, o.ID, nullptr, nullptr, a_v, nullptr);
+        r = download<T>(m, o.C, o.O, avs, o.H, o.G, o.ID, nullptr, nullptr, a_v, nullptr);
     }
     cudaFree(buf);
     return r;
@@ -577,7 +602,7 @@ template <typename T, int D> sph_status pair_counts_impl(sph_mesh* m, int64_t* c
 template <typename T, int D>
 sph_status positions_impl(sph_mesh* m, double* x_out, int32_t* group_out, double* v_out, double* h_out) {
     State<T>& s = st<T>(m);
-    return download<T>(m, s.X, s.V, s.H, s.G, s.ID, x_out, group_out, v_out, h_out);
+    return download<T>(m, s.C, s.O, s.V, s.H, s.G, s.ID, x_out, group_out, v_out, h_out);
 }
 
 sph_status check_status(sph_mesh* m) {
@@ -757,6 +782,26 @@ sph_status sph_mesh_create(const sph_domain_desc* dd, const sph_sizing_desc* sz,
     for (int k = 0; k < sz->n_ref; ++k) {
         for (int a = 0; a < 3; ++a) zs.rc[k][a] = sz->ref_center[k][a];
         zs.rr[k] = sz->ref_radius[k];
+    }
+    // float copies used by the FP32 evaluation of h_t and of the level set
+    zs.fa = (float)zs.a;
+    zs.fb = (float)zs.b;
+    zs.flo = (float)zs.lo;
+    zs.fhi = (float)zs.hi;
+    for (int a = 0; a < 3; ++a) zs.fq[a] = (float)zs.q[a];
+    for (int k = 0; k < MAXH; ++k) {
+        for (int a = 0; a < 3; ++a) zs.frc[k][a] = (float)zs.rc[k][a];
+        zs.frr[k] = (float)zs.rr[k];
+    }
+    for (int a = 0; a < 3; ++a) {
+        dm.flo[a] = (float)dm.lo[a];
+        dm.fhi[a] = (float)dm.hi[a];
+        dm.fbc[a] = (float)dm.bc[a];
+    }
+    dm.fbr = (float)dm.br;
+    for (int k = 0; k < MAXH; ++k) {
+        for (int a = 0; a < 3; ++a) dm.fhc[k][a] = (float)dm.hc[k][a];
+        dm.fhr[k] = (float)dm.hr[k];
     }
 
     auto cleanup = [&](sph_status s) {

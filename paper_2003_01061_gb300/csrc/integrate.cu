@@ -141,107 +141,215 @@ template <typename T> __global__ void __launch_bounds__(256) k_control(Params p,
     c->sample_now = (c->n % p.sample_every) == 0 ? 1 : 0;
 }
 
+// h_t(x) and the level set in the working precision, from the position in that precision and
+// constants stored in it (no FP64 instruction in the FP32 build): the FP32 build stores h as a
+// float, and the level set only decides whether a particle is clearly inside.
+template <typename T> __device__ __forceinline__ T wp(double d, float f);
+template <> __device__ __forceinline__ float wp<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double wp<double>(double d, float) { return d; }
+
+template <typename T> __device__ __forceinline__ T sizing_h_t(const Sizing& s, const T x[3]) {
+    if (s.kind == 0) return wp<T>(s.a, s.fa);
+    T h;
+    if (s.kind == 1) {
+        T dmin = T(1e30);
+        for (int k = 0; k < s.nref; ++k) {
+            const T d0 = x[0] - wp<T>(s.rc[k][0], s.frc[k][0]), d1 = x[1] - wp<T>(s.rc[k][1], s.frc[k][1]),
+                    d2 = x[2] - wp<T>(s.rc[k][2], s.frc[k][2]);
+            const T dk = fabs(t_sqrt(d0 * d0 + d1 * d1 + d2 * d2) - wp<T>(s.rr[k], s.frr[k]));
+            dmin = dk < dmin ? dk : dmin;
+        }
+        h = wp<T>(s.a, s.fa) + wp<T>(s.b, s.fb) * dmin;
+    } else {
+        const T d0 = x[0] - wp<T>(s.q[0], s.fq[0]), d1 = x[1] - wp<T>(s.q[1], s.fq[1]),
+                d2 = x[2] - wp<T>(s.q[2], s.fq[2]);
+        h = wp<T>(s.a, s.fa) + wp<T>(s.b, s.fb) * t_sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    }
+    const T lo = wp<T>(s.lo, s.flo), hi = wp<T>(s.hi, s.fhi);
+    h = h < lo ? lo : h;
+    return h > hi ? hi : h;
+}
+
+template <typename T> __device__ __forceinline__ T domain_phi_t(const Domain& dom, const T x[3]) {
+    T phi;
+    if (dom.base == 0) {
+        phi = T(1e30);
+        for (int a = 0; a < dom.D; ++a) {
+            const T dlo = x[a] - wp<T>(dom.lo[a], dom.flo[a]), dhi = wp<T>(dom.hi[a], dom.fhi[a]) - x[a];
+            phi = dlo < phi ? dlo : phi;
+            phi = dhi < phi ? dhi : phi;
+        }
+    } else {
+        const T d0 = x[0] - wp<T>(dom.bc[0], dom.fbc[0]), d1 = x[1] - wp<T>(dom.bc[1], dom.fbc[1]);
+        const T d2 = dom.D == 3 ? x[2] - wp<T>(dom.bc[2], dom.fbc[2]) : T(0);
+        phi = wp<T>(dom.br, dom.fbr) - t_sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    }
+    for (int k = 0; k < dom.nh; ++k) {
+        const T d0 = x[0] - wp<T>(dom.hc[k][0], dom.fhc[k][0]), d1 = x[1] - wp<T>(dom.hc[k][1], dom.fhc[k][1]);
+        const T d2 = dom.D == 3 ? x[2] - wp<T>(dom.hc[k][2], dom.fhc[k][2]) : T(0);
+        const T pk = t_sqrt(d0 * d0 + d1 * d1 + d2 * d2) - wp<T>(dom.hr[k], dom.fhr[k]);
+        phi = pk < phi ? pk : phi;
+    }
+    return phi;
+}
+
 // Viscous pass + update, one thread per sorted particle, writing the new state in sorted order:
 //   v'_i = 0 (nullified) or f v_i;  v~_i = v'_i + dt (a_p,i - eps v'_i)                       (Eq. 23)
 //   a_v,i = Pi_i sum_{j in g, j != i} [2 eta_i eta_j/(eta_i+eta_j)] (rho_i^-2 + rho_j^-2)
 //                 W_d'(r_ij, h_ij) (v~_i - v~_j) / r_ij,  eta = rho nu, nu = visc r_c |v~|    (Eq. 7, Eq. 8)
-//   v+ = v~ + dt a_v;  x+ = x + dt v+  (FP64);  curves/surfaces: x+ onto the feature, v+ <- Pi(x+) v+;
-//   volume: phi(x+) < 0 -> back to phi = 0.01 h along grad phi, v+ = 0, escape counted;  h+ = h_t(x+).
+//   v+ = v~ + dt a_v;  x+ = x + dt v+  (FP64);  curves/surfaces: x+ onto the feature in FP64,
+//   v+ <- Pi(x+) v+;  volume: phi(x+) < 0 -> back to phi = 0.01 h along grad phi (FP64),
+//   v+ = 0, escape counted;  h+ = h_t(x+).
+// The neighbour sum uses the walk of the pressure pass (same pairs, same predicate), with LPP
+// lanes per particle; the lead lane does the update.
 template <typename T, int D>
 __global__ void __launch_bounds__(BLOCK) k_integrate(Grid g, Params p, State<T> s, const Ctrl* cu, Out<T> o) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= s.n) return;
-    T offi[3], hi;
-    unsigned mi;
-    Rec<T, D>::load(s.P, s.Ms, k, offi, hi, mi);
-    const int gi = meta_group(mi), di = meta_dim(mi);
-    double x[3] = {s.Xs[0][k], s.Xs[1][k], D == 3 ? s.Xs[2][k] : 0.0};
-    T v[3] = {s.Vs[0][k], s.Vs[1][k], D == 3 ? s.Vs[2][k] : T(0)};
+    constexpr int LPP = Lpp<D>::v;
+    __shared__ int2 sbuf[BUF_CAP * BLOCK];
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) / LPP;
+    const bool lead = (threadIdx.x % LPP) == 0;
+    const bool inrange = k < s.n;
+    T offi[3] = {T(0), T(0), T(0)}, hi = T(1);
+    unsigned mi = 0;
+    int c[3] = {0, 0, 0};            // stored position: finest cell + offset
+    T o3[3] = {T(0), T(0), T(0)};
+    T v[3] = {T(0), T(0), T(0)};
+    if (inrange) {
+        Rec<T, D>::load(s.P, s.Ms, k, offi, hi, mi);
+        for (int a = 0; a < D; ++a) {
+            c[a] = s.Cs[a][k];
+            o3[a] = s.Os[a][k];
+            v[a] = s.Vs[a][k];
+        }
+    }
+    const int gi = inrange ? meta_group(mi) : -1, di = inrange ? meta_dim(mi) : 0;
+    const bool done = cu->phase == PH_DONE;          // the same for every thread
+    const bool moving = inrange && di > 0 && !done;
     T av[3] = {T(0), T(0), T(0)};
     T hnew = hi;
-    if (di == 0 || cu->phase == PH_DONE) {
-        if (di == 0) v[0] = v[1] = v[2] = T(0);
-    } else {
-        const T dt = (T)cu->dt[gi];
-        const bool rs = cu->reset[gi] != 0;
-        const T f = (T)cu->f, eps = (T)cu->eps;
+    T dt = T(0), f = T(1), eps = T(0);
+    bool rs = true;
+    T vt[3] = {T(0), T(0), T(0)};
+    T tg[3] = {T(0), T(0), T(0)};
+    if (moving) {
+        dt = (T)cu->dt[gi];
+        rs = cu->reset[gi] != 0;
+        f = (T)cu->f;
+        eps = (T)cu->eps;
         const Vec4<T> ai = s.A[k];
         const T api[3] = {ai.x, ai.y, ai.z};
-        T vt[3];
         for (int a = 0; a < 3; ++a) {
-            T vp = rs ? T(0) : f * v[a];
+            const T vp = rs ? T(0) : f * v[a];
             vt[a] = vp + dt * (api[a] - eps * vp);
         }
-        const Feat& fi = s.dom->f[gi];
-        T tg[3] = {T(0), T(0), T(0)};
         if (di < D) {
-            T xi[3] = {(T)x[0], (T)x[1], (T)x[2]};
-            feature_tangent<T>(fi, xi, tg);
+            T xi[3];
+            pos_t<T, D>(g, c, o3, xi);
+            feature_tangent<T>(s.dom->f[gi], xi, tg);
         }
-        if (p.visc > 0.0) {
-            const T kappa = (T)p.kappa, hk = T(0.5) * kappa, visc = (T)p.visc;
-            const T ri2 = ipow(hi, 2 * di);
-            const T eta_i = visc * kappa * hi * t_sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]) / ipow(hi, di);
-            int li, ci[3];
-            decode_key(g, s.Ks[k], li, ci);
-            walk<T, D>(g, s.cell_start, s.n, s.P, s.Ms, li, ci, offi, hi, kappa,
-                       [&](int j, const T dx[3], T r2, T hj, unsigned mj, const T*, int, int, int, int) {
-                           if (meta_group(mj) != gi || j == k || !(r2 < pair_rc2(hi, hj, hk))) return;
-                           T r = t_sqrt(r2);
-                           if (!(r > T(0))) return;
-                           const Vec4<T> aj = s.A[j];
-                           const T apj[3] = {aj.x, aj.y, aj.z};
-                           T vtj[3];
-                           for (int a = 0; a < D; ++a) {
-                               T vp = rs ? T(0) : f * s.Vs[a][j];
-                               vtj[a] = vp + dt * (apj[a] - eps * vp);
-                           }
-                           if (D == 2) vtj[2] = T(0);
-                           T eta_j = visc * kappa * hj * t_sqrt(vtj[0] * vtj[0] + vtj[1] * vtj[1] + vtj[2] * vtj[2]) /
-                                     ipow(hj, di);
-                           T es = eta_i + eta_j;
-                           if (!(es > T(0))) return;
-                           T eb = T(2) * eta_i * eta_j / es;
-                           T invR = T(2) / (kappa * (hi + hj));
-                           T q = r * invR;
-                           T t = T(1) - q;
-                           T dW = wendland_alpha<T>(di, invR) * (T(-20) * q * t * t * t) * invR;
-                           T coef = eb * (ri2 + ipow(hj, 2 * di)) * dW / r;
-                           for (int a = 0; a < D; ++a) av[a] += coef * (vt[a] - vtj[a]);
-                       });
-            tangent_map<T>(di, D, tg, av);
-        }
+    }
+    if (p.visc > 0.0 && !done) {
+        const T kappa = (T)p.kappa, hk = T(0.5) * kappa, visc = (T)p.visc;
+        const T ri2 = ipow(hi, 2 * di);
+        const T eta_i = visc * kappa * hi * t_sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]) *
+                        fast_rcp(ipow(hi, di));
+        int li = 0, ci[3] = {0, 0, 0};
+        if (inrange) decode_key(g, s.Ks[k], li, ci);
+        walk_sub<T, D, LPP, BUF_CAP>(
+            g, s.cell_start, s.occ, s.n, s.P, s.Ms, sbuf + threadIdx.x, moving, li, ci, offi, hi, kappa,
+            [&](int j, const T*, T r2, T hj, unsigned mj) -> bool {
+                return meta_group(mj) == gi && j != k && r2 < pair_rc2(hi, hj, hk) && r2 > T(0);
+            },
+            [&](int j, const T dx[3], T r2, T hj, unsigned, const T*, int, int, int, int) {
+                const T invr = fast_rsqrt(r2);
+                const T r = r2 * invr;
+                const Vec4<T> aj = s.A[j];
+                const T apj[3] = {aj.x, aj.y, aj.z};
+                T vtj[3] = {T(0), T(0), T(0)};
+                for (int a = 0; a < D; ++a) {
+                    const T vp = rs ? T(0) : f * s.Vs[a][j];
+                    vtj[a] = vp + dt * (apj[a] - eps * vp);
+                }
+                const T eta_j = visc * kappa * hj * t_sqrt(vtj[0] * vtj[0] + vtj[1] * vtj[1] + vtj[2] * vtj[2]) *
+                                fast_rcp(ipow(hj, di));
+                const T es = eta_i + eta_j;
+                if (!(es > T(0))) return;
+                const T eb = T(2) * eta_i * eta_j / es;
+                const T invR = fast_rcp(hk * (hi + hj));
+                const T q = r * invR;
+                const T t = T(1) - q;
+                const T dW = wendland_alpha<T>(di, invR) * (T(-20) * q * t * t * t) * invR;
+                const T coef = eb * (ri2 + ipow(hj, 2 * di)) * dW * invr;
+                for (int a = 0; a < D; ++a) av[a] += coef * (vt[a] - vtj[a]);
+            });
+        for (int a = 0; a < D; ++a) av[a] = sub_sum<LPP>(av[a]);
+        if (moving) tangent_map<T>(di, D, tg, av);
+    }
+    if (!lead) return;
+    if (moving) {
+        const Feat& fi = s.dom->f[gi];
+        // x+ = x + dt v+, advanced on the offset and re-normalised into the finest cell
+        const T c0 = (T)g.c0, inv_c0 = T(1) / c0;
+        bool clamped = false;
         for (int a = 0; a < 3; ++a) {
             v[a] = vt[a] + dt * av[a];
-            if (a < D) x[a] = x[a] + (double)dt * (double)v[a];
+            if (a >= D) continue;
+            T oa = o3[a] + dt * v[a];
+            const T q = t_floor(oa * inv_c0);
+            if (q != T(0)) {
+                c[a] += (int)q;
+                oa -= q * c0;
+            }
+            if (c[a] < 0 || c[a] > g.dims[0][a] - 1) {
+                clamped = true;
+                c[a] = min(max(c[a], 0), g.dims[0][a] - 1);
+            }
+            o3[a] = oa;
         }
+        if (clamped) atomicOr(&s.ctrl->status, ST_OUTSIDE_GRID);
+        T xt[3];
+        pos_t<T, D>(g, c, o3, xt);
         if (fi.kind == K_VOLUME) {
-            double gph[3];
-            double ph = domain_phi(*s.dom, x, gph);
-            if (ph < 0.0) {
-                const double target = 0.01 * (double)hi;
-                for (int it = 0; it < 3 && ph < 0.5 * target; ++it) {
-                    double g2 = gph[0] * gph[0] + gph[1] * gph[1] + gph[2] * gph[2];
-                    for (int a = 0; a < D; ++a) x[a] += (target - ph) * gph[a] / g2;
-                    ph = domain_phi(*s.dom, x, gph);
+            // working-precision pre-check; the FP64 level set only close to or outside the boundary
+            if (!(domain_phi_t<T>(*s.dom, xt) > T(1e-3) * hi)) {
+                double x[3], gph[3];
+                pos64<T, D>(g, c, o3, x);
+                double ph = domain_phi(*s.dom, x, gph);
+                if (ph < 0.0) {
+                    const double target = 0.01 * (double)hi;
+                    for (int it = 0; it < 3 && ph < 0.5 * target; ++it) {
+                        double g2 = gph[0] * gph[0] + gph[1] * gph[1] + gph[2] * gph[2];
+                        for (int a = 0; a < D; ++a) x[a] += (target - ph) * gph[a] / g2;
+                        ph = domain_phi(*s.dom, x, gph);
+                    }
+                    v[0] = v[1] = v[2] = T(0);
+                    atomicAdd(&s.ctrl->escapes, 1ull);
+                    fine_of<T, D>(g, x, c, o3);
+                    pos_t<T, D>(g, c, o3, xt);
                 }
-                v[0] = v[1] = v[2] = T(0);
-                atomicAdd(&s.ctrl->escapes, 1ull);
             }
         } else {
+            // projection onto the feature in FP64 (Algorithm 1: map r_{n+1} onto feature k)
+            double x[3];
+            pos64<T, D>(g, c, o3, x);
             project_feature(fi, D, x);
             double t64[3], v64[3] = {(double)v[0], (double)v[1], (double)v[2]};
             feature_tangent<double>(fi, x, t64);
             tangent_map<double>(di, D, t64, v64);
             for (int a = 0; a < 3; ++a) v[a] = (T)v64[a];
+            fine_of<T, D>(g, x, c, o3);
+            pos_t<T, D>(g, c, o3, xt);
         }
-        hnew = (T)sizing_h(*s.siz, x);
+        hnew = sizing_h_t<T>(*s.siz, xt);
         bool fin = true;
-        for (int a = 0; a < D; ++a) fin = fin && isfinite(x[a]) && isfinite((double)v[a]);
+        for (int a = 0; a < D; ++a) fin = fin && isfinite(o3[a]) && isfinite(v[a]);
         if (!fin) atomicOr(&s.ctrl->status, ST_NONFINITE);
     }
+    if (!inrange) return;
+    if (di == 0) v[0] = v[1] = v[2] = T(0);
     for (int a = 0; a < D; ++a) {
-        o.X[a][k] = x[a];
+        o.C[a][k] = c[a];
+        o.O[a][k] = o3[a];
         o.V[a][k] = v[a];
         if (o.av[a]) o.av[a][k] = av[a];
     }
@@ -256,7 +364,7 @@ template <typename T> void launch_control(const Params& p, const State<T>& s, cu
 template <typename T, int D>
 void launch_integrate(const Grid& g, const Params& p, const State<T>& s, const Ctrl* use, const Out<T>& o,
                       cudaStream_t st) {
-    k_integrate<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(g, p, s, use, o);
+    k_integrate<T, D><<<div_up((long long)s.n * Lpp<D>::v, BLOCK), BLOCK, 0, st>>>(g, p, s, use, o);
 }
 
 template void launch_control<float>(const Params&, const State<float>&, cudaStream_t);

@@ -1,6 +1,7 @@
 // interact.cu -- the fused pressure pass of one relaxation step (Algorithm 1: renormalisation
 // gamma_i, pressure force with the feature-boundary correction, map onto the feature, step-size
-// candidates), one thread per particle in sorted order.
+// candidates).  LPP consecutive lanes handle one particle (sorted order) and split its
+// neighbour candidates; their partial sums are combined with a fixed shuffle butterfly.
 //
 // For particle i of group g (intrinsic dimension d, kernel W_d, rho = h^-d, P = p0 h^(2d)):
 //   sigma_i = sum_{j in g, r < kappa h_i} W_d(r_ij, h_i)             (Eq. 20 denominator, j = i included)
@@ -16,8 +17,10 @@ namespace sph {
 
 template <typename T, int D>
 __global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s, T* dbg_sigma, T* dbg_gamma) {
+    constexpr int LPP = Lpp<D>::v;
     __shared__ unsigned long long sh_dta[MAXF], sh_dtv[MAXF];
     __shared__ double sh_part[BLOCK / 32][MAXF];
+    __shared__ int2 sbuf[BUF_CAP * BLOCK];
     const int G = p.G;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int t = threadIdx.x; t < G; t += blockDim.x) {
@@ -29,96 +32,106 @@ __global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s
         for (int t = threadIdx.x; t < (BLOCK / 32) * MAXF; t += blockDim.x) (&sh_part[0][0])[t] = 0.0;
     __syncthreads();
 
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    int gi = -1, di = 0;
-    T vtil = T(0);
-    if (k < s.n) {
-        T offi[3], hi;
-        unsigned mi;
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) / LPP;
+    const bool lead = (threadIdx.x % LPP) == 0;
+    const bool inrange = k < s.n;
+    T offi[3] = {T(0), T(0), T(0)}, hi = T(1);
+    unsigned mi = 0;
+    int li = 0, ci[3] = {0, 0, 0};
+    if (inrange) {
         Rec<T, D>::load(s.P, s.Ms, k, offi, hi, mi);
-        gi = meta_group(mi);
-        di = meta_dim(mi);
-        T ap[3] = {T(0), T(0), T(0)};
-        T sig = T(0), gam = T(0);
-        if (di > 0) {
-            int li, ci[3];
-            decode_key(g, s.Ks[k], li, ci);
-            const Feat& fi = s.dom->f[gi];
-            T tg[3] = {T(0), T(0), T(0)};
-            if (di < D) {
-                T xi[3] = {(T)s.Xs[0][k], (T)s.Xs[1][k], D == 3 ? (T)s.Xs[2][k] : T(0)};
-                feature_tangent<T>(fi, xi, tg);
+        decode_key(g, s.Ks[k], li, ci);
+    }
+    const int gi = inrange ? meta_group(mi) : -1;
+    const int di = inrange ? meta_dim(mi) : 0;
+    const bool active = inrange && di > 0;
+    T tg[3] = {T(0), T(0), T(0)};
+    if (active && di < D) {
+        T xi[3] = {T(0), T(0), T(0)};
+        for (int a = 0; a < D; ++a) xi[a] = (T)g.origin[a] + (T)(ci[a] << li) * (T)g.c0 + offi[a];
+        feature_tangent<T>(s.dom->f[gi], xi, tg);
+    }
+    const T kappa = (T)p.kappa, hk = T(0.5) * kappa, p0 = (T)p.p0;
+    const T rci2 = self_rc2(hi, kappa);
+    const T invRi = fast_rcp(kappa * hi);
+    const T alpha_i = wendland_alpha<T>(di > 0 ? di : 1, invRi);
+    const T Pi = p0 * ipow(hi, 2 * di);
+    const bool brho = p.boundary_rho != 0;
+    const T c0 = (T)g.c0;
+    const T org[3] = {(T)g.origin[0], (T)g.origin[1], (T)g.origin[2]};
+    T F[3] = {T(0), T(0), T(0)};
+    T sig = T(0), gam = T(0);
+
+    walk_sub<T, D, LPP, BUF_CAP>(
+        g, s.cell_start, s.occ, s.n, s.P, s.Ms, sbuf + threadIdx.x, active, li, ci, offi, hi, kappa,
+        [&](int j, const T*, T r2, T hj, unsigned mj) -> bool {
+            if (meta_group(mj) == gi) return r2 < rci2 || (j != k && r2 < pair_rc2(hi, hj, hk));
+            return meta_dim(mj) < di && r2 < pair_rc2(hi, hj, hk);
+        },
+        [&](int j, const T dx[3], T r2, T hj, unsigned mj, const T offj[3], int l, int cxj, int cy, int cz) {
+            const T invr = r2 > T(0) ? fast_rsqrt(r2) : T(0);
+            const T r = r2 * invr;
+            if (meta_group(mj) == gi) {
+                if (r2 < rci2) {
+                    const T q = r * invRi;
+                    const T t = T(1) - q;
+                    const T w = alpha_i * (t * t) * (t * t) * (T(1) + T(4) * q);
+                    sig += w;
+                    gam += w * ipow(hj, di);
+                }
+                if (j != k && r2 < pair_rc2(hi, hj, hk) && r2 > T(0)) {
+                    const T invR = fast_rcp(hk * (hi + hj));
+                    const T q = r * invR;
+                    const T t = T(1) - q;
+                    const T dW = wendland_alpha<T>(di, invR) * (T(-20) * q * t * t * t) * invR;
+                    const T c1 = (Pi + p0 * ipow(hj, 2 * di)) * dW * invr;
+                    F[0] += c1 * dx[0];
+                    F[1] += c1 * dx[1];
+                    if (D == 3) F[2] += c1 * dx[2];
+                }
+            } else {
+                const T invR = fast_rcp(hk * (hi + hj));
+                const T q = r * invR;
+                const T t = T(1) - q;
+                const T w = wendland_alpha<T>(di, invR) * (t * t) * (t * t) * (T(1) + T(4) * q);
+                const int cj[3] = {cxj, cy, cz};
+                T xb[3] = {T(0), T(0), T(0)};
+                for (int a = 0; a < D; ++a) xb[a] = org[a] + (T)(cj[a] << l) * c0 + offj[a];
+                T nb[3];
+                boundary_normal<T>(s.dom->f[meta_group(mj)], xb, nb);
+                tangent_map<T>(di, D, tg, nb);
+                const T nn2 = nb[0] * nb[0] + nb[1] * nb[1] + nb[2] * nb[2];
+                if (nn2 > T(1e-12)) {
+                    const T Ab = brho ? fast_rcp(hj) : ipow(hj, di - 1);
+                    const T c2 = Ab * (Pi + p0 * ipow(hj, 2 * di)) * w * fast_rsqrt(nn2);
+                    F[0] += c2 * nb[0];
+                    F[1] += c2 * nb[1];
+                    if (D == 3) F[2] += c2 * nb[2];
+                }
             }
-            const T kappa = (T)p.kappa, hk = T(0.5) * kappa, p0 = (T)p.p0;
-            const T rci2 = self_rc2(hi, kappa);
-            const T invRi = T(1) / (kappa * hi);
-            const T alpha_i = wendland_alpha<T>(di, invRi);
-            const T Pi = p0 * ipow(hi, 2 * di);
-            const bool brho = p.boundary_rho != 0;
-            const T c0 = (T)g.c0;
-            const T org[3] = {(T)g.origin[0], (T)g.origin[1], (T)g.origin[2]};
-            T F[3] = {T(0), T(0), T(0)};
-            walk<T, D>(g, s.cell_start, s.n, s.P, s.Ms, li, ci, offi, hi, kappa,
-                       [&](int j, const T dx[3], T r2, T hj, unsigned mj, const T offj[3], int l, int cxj, int cy,
-                           int cz) {
-                           const int gj = meta_group(mj);
-                           if (gj == gi) {
-                               if (r2 < rci2) {
-                                   T q = t_sqrt(r2) * invRi;
-                                   T t = T(1) - q;
-                                   T w = alpha_i * (t * t) * (t * t) * (T(1) + T(4) * q);
-                                   sig += w;
-                                   gam += w * ipow(hj, di);
-                               }
-                               if (j != k && r2 < pair_rc2(hi, hj, hk)) {
-                                   T r = t_sqrt(r2);
-                                   if (r > T(0)) {
-                                       T invR = T(2) / (kappa * (hi + hj));
-                                       T q = r * invR;
-                                       T t = T(1) - q;
-                                       T dW = wendland_alpha<T>(di, invR) * (T(-20) * q * t * t * t) * invR;
-                                       T c1 = (Pi + p0 * ipow(hj, 2 * di)) * dW / r;
-                                       F[0] += c1 * dx[0];
-                                       F[1] += c1 * dx[1];
-                                       if (D == 3) F[2] += c1 * dx[2];
-                                   }
-                               }
-                           } else if (meta_dim(mj) < di && r2 < pair_rc2(hi, hj, hk)) {
-                               T r = t_sqrt(r2);
-                               T invR = T(2) / (kappa * (hi + hj));
-                               T q = r * invR;
-                               T t = T(1) - q;
-                               T w = wendland_alpha<T>(di, invR) * (t * t) * (t * t) * (T(1) + T(4) * q);
-                               const int cj[3] = {cxj, cy, cz};
-                               T xb[3] = {T(0), T(0), T(0)};
-                               for (int a = 0; a < D; ++a) xb[a] = org[a] + (T)(cj[a] << l) * c0 + offj[a];
-                               T nb[3];
-                               boundary_normal<T>(s.dom->f[gj], xb, nb);
-                               tangent_map<T>(di, D, tg, nb);
-                               T nn = t_sqrt(nb[0] * nb[0] + nb[1] * nb[1] + nb[2] * nb[2]);
-                               if (nn > T(1e-6)) {
-                                   T Ab = brho ? T(1) / hj : ipow(hj, di - 1);
-                                   T c2 = Ab * (Pi + p0 * ipow(hj, 2 * di)) * w / nn;
-                                   F[0] += c2 * nb[0];
-                                   F[1] += c2 * nb[1];
-                                   if (D == 3) F[2] += c2 * nb[2];
-                               }
-                           }
-                       });
-            const T ig = T(1) / gam;
-            for (int a = 0; a < 3; ++a) ap[a] = -F[a] * ig;
-            tangent_map<T>(di, D, tg, ap);
-            vtil = T(1) / sig;
-            const T rc = kappa * hi;
-            T an = t_sqrt(ap[0] * ap[0] + ap[1] * ap[1] + ap[2] * ap[2]);
-            T v0 = s.Vs[0][k], v1 = s.Vs[1][k], v2 = D == 3 ? s.Vs[2][k] : T(0);
-            T vn = t_sqrt(v0 * v0 + v1 * v1 + v2 * v2);
-            T dta = an > T(0) ? (T)p.cfl_a * t_sqrt(rc / an) : (T)CUDART_INF;
-            T dtv = vn > T(0) ? (T)p.cfl_v * rc / vn : (T)CUDART_INF;
-            if (!(an == an) || !isfinite(an)) atomicOr(&s.ctrl->status, ST_NONFINITE);
-            atomicMin(&sh_dta[gi], min_bits(dta));
-            atomicMin(&sh_dtv[gi], min_bits(dtv));
-        }
+        });
+    for (int a = 0; a < D; ++a) F[a] = sub_sum<LPP>(F[a]);
+    sig = sub_sum<LPP>(sig);
+    gam = sub_sum<LPP>(gam);
+
+    T ap[3] = {T(0), T(0), T(0)};
+    T vtil = T(0);
+    if (active && lead) {
+        const T ig = T(1) / gam;
+        for (int a = 0; a < 3; ++a) ap[a] = -F[a] * ig;
+        tangent_map<T>(di, D, tg, ap);
+        vtil = T(1) / sig;
+        const T rc = kappa * hi;
+        const T an = t_sqrt(ap[0] * ap[0] + ap[1] * ap[1] + ap[2] * ap[2]);
+        const T v0 = s.Vs[0][k], v1 = s.Vs[1][k], v2 = D == 3 ? s.Vs[2][k] : T(0);
+        const T vn = t_sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+        const T dta = an > T(0) ? (T)p.cfl_a * t_sqrt(rc / an) : (T)CUDART_INF;
+        const T dtv = vn > T(0) ? (T)p.cfl_v * rc / vn : (T)CUDART_INF;
+        if (!(an == an) || !isfinite(an)) atomicOr(&s.ctrl->status, ST_NONFINITE);
+        atomicMin(&sh_dta[gi], min_bits(dta));
+        atomicMin(&sh_dtv[gi], min_bits(dtv));
+    }
+    if (inrange && lead) {
         Vec4<T> a4;
         a4.x = ap[0];
         a4.y = ap[1];
@@ -131,7 +144,7 @@ __global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s
     if (sample) {
         // deterministic per-warp, per-group sums of V~: one fixed shuffle tree per group present
         const unsigned full = 0xffffffffu;
-        const int gk = (k < s.n && di > 0) ? gi : -1;
+        const int gk = (active && lead) ? gi : -1;
         unsigned pending = __ballot_sync(full, gk >= 0);
         while (pending) {
             int leader = __ffs(pending) - 1;
@@ -155,55 +168,63 @@ __global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s
     }
 }
 
-// neighbour sets for inspection: mode 0 pair predicate (j != i), mode 1 self predicate (j = i
-// included), over all groups.  lists == nullptr: count only.
+// neighbour sets for inspection, through the same walk as the pair passes (one lane per
+// particle): mode 0 pair predicate (j != i), mode 1 self predicate (j = i included), over all
+// groups.  lists == nullptr: count only.
 template <typename T, int D>
 __global__ void __launch_bounds__(BLOCK) k_neighbors(Grid g, Params p, State<T> s, int mode, int* counts,
                                                      const long long* offsets, int* lists) {
+    __shared__ int2 sbuf[BUF_CAP * BLOCK];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= s.n) return;
-    T offi[3], hi;
-    unsigned mi;
-    Rec<T, D>::load(s.P, s.Ms, k, offi, hi, mi);
-    int li, ci[3];
-    decode_key(g, s.Ks[k], li, ci);
+    const bool active = k < s.n;
+    T offi[3] = {T(0), T(0), T(0)}, hi = T(1);
+    unsigned mi = 0;
+    int li = 0, ci[3] = {0, 0, 0};
+    if (active) {
+        Rec<T, D>::load(s.P, s.Ms, k, offi, hi, mi);
+        decode_key(g, s.Ks[k], li, ci);
+    }
     const T kappa = (T)p.kappa, hk = T(0.5) * kappa;
     const T rci2 = self_rc2(hi, kappa);
     int cnt = 0;
-    long long base = lists ? offsets[k] : 0;
-    walk<T, D>(g, s.cell_start, s.n, s.P, s.Ms, li, ci, offi, hi, kappa,
-               [&](int j, const T*, T r2, T hj, unsigned, const T*, int, int, int, int) {
-                   bool acc = mode == 0 ? (j != k && r2 < pair_rc2(hi, hj, hk)) : (r2 < rci2);
-                   if (acc) {
-                       if (lists) lists[base + cnt] = j;
-                       ++cnt;
-                   }
-               });
-    if (!lists) counts[k] = cnt;
+    const long long base = (lists && active) ? offsets[k] : 0;
+    walk_sub<T, D, 1, BUF_CAP>(
+        g, s.cell_start, s.occ, s.n, s.P, s.Ms, sbuf + threadIdx.x, active, li, ci, offi, hi, kappa,
+        [&](int j, const T*, T r2, T hj, unsigned) -> bool {
+            return mode == 0 ? (j != k && r2 < pair_rc2(hi, hj, hk)) : (r2 < rci2);
+        },
+        [&](int j, const T*, T, T, unsigned, const T*, int, int, int, int) {
+            if (lists) lists[base + cnt] = j;
+            ++cnt;
+        });
+    if (active && !lists) counts[k] = cnt;
 }
 
-// candidate pairs visited and pairs inside the interaction support, summed over all particles
+// candidate pairs examined and pairs inside the interaction support of the pressure pass,
+// summed over all particles (one lane per particle)
 template <typename T, int D>
 __global__ void __launch_bounds__(BLOCK) k_pair_counts(Grid g, Params p, State<T> s, unsigned long long* out2) {
+    __shared__ int2 sbuf[BUF_CAP * BLOCK];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long cand = 0, accd = 0;
-    if (k < s.n) {
-        T offi[3], hi;
-        unsigned mi;
+    const bool inrange = k < s.n;
+    T offi[3] = {T(0), T(0), T(0)}, hi = T(1);
+    unsigned mi = 0;
+    int li = 0, ci[3] = {0, 0, 0};
+    if (inrange) {
         Rec<T, D>::load(s.P, s.Ms, k, offi, hi, mi);
-        const int gi = meta_group(mi), di = meta_dim(mi);
-        if (di > 0) {
-            int li, ci[3];
-            decode_key(g, s.Ks[k], li, ci);
-            const T kappa = (T)p.kappa, hk = T(0.5) * kappa;
-            walk<T, D>(g, s.cell_start, s.n, s.P, s.Ms, li, ci, offi, hi, kappa,
-                       [&](int j, const T*, T r2, T hj, unsigned mj, const T*, int, int, int, int) {
-                           ++cand;
-                           int gj = meta_group(mj);
-                           if ((gj == gi || meta_dim(mj) < di) && j != k && r2 < pair_rc2(hi, hj, hk)) ++accd;
-                       });
-        }
+        decode_key(g, s.Ks[k], li, ci);
     }
+    const int gi = inrange ? meta_group(mi) : -1, di = inrange ? meta_dim(mi) : 0;
+    const bool active = inrange && di > 0;
+    const T kappa = (T)p.kappa, hk = T(0.5) * kappa;
+    unsigned long long cand = 0, accd = 0;
+    walk_sub<T, D, 1, BUF_CAP>(
+        g, s.cell_start, s.occ, s.n, s.P, s.Ms, sbuf + threadIdx.x, active, li, ci, offi, hi, kappa,
+        [&](int j, const T*, T r2, T hj, unsigned mj) -> bool {
+            ++cand;
+            return (meta_group(mj) == gi || meta_dim(mj) < di) && j != k && r2 < pair_rc2(hi, hj, hk);
+        },
+        [&](int, const T*, T, T, unsigned, const T*, int, int, int, int) { ++accd; });
     for (int o = 16; o > 0; o >>= 1) {
         cand += __shfl_down_sync(0xffffffffu, cand, o);
         accd += __shfl_down_sync(0xffffffffu, accd, o);

@@ -54,9 +54,10 @@ __global__ void __launch_bounds__(BLOCK) k_na_hash(Grid g, int n, const double* 
     if (i >= n) return;
     double x[3] = {x0[i], x1[i], D == 3 ? x2[i] : 0.0};
     int l = level_of(g, h[i]);
-    int cell[3];
-    float off[3];
-    cell_of<float, D>(g, l, x, cell, off);
+    int c[3], cell[3];
+    float o[3], off[3];
+    fine_of<float, D>(g, x, c, o);              // finest cell, then the level's cell (c >> l)
+    level_repr<float, D>(g, l, c, o, cell, off);
     int k = key_of(g, l, cell);
     key[i] = k;
     atomicAdd(count + k, 1);

@@ -10,16 +10,11 @@ namespace sph {
 template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_hash(Grid g, State<T> s) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
-    double x[3] = {s.X[0][i], s.X[1][i], D == 3 ? s.X[2][i] : 0.0};
-    T h = s.H[i];
-    int l = level_of(g, h);
-    int cell[3];
-    T off[3];
-    bool clamped = cell_of<T, D>(g, l, x, cell, off);
-    int key = key_of(g, l, cell);
+    const int l = level_of(g, s.H[i]);
+    int cell[3] = {s.C[0][i] >> l, s.C[1][i] >> l, D == 3 ? s.C[2][i] >> l : 0};
+    const int key = key_of(g, l, cell);
     s.K[i] = key;
     atomicAdd(s.count + key, 1);
-    if (clamped) atomicOr(&s.ctrl->status, ST_OUTSIDE_GRID);
 }
 
 // ---- exclusive scan of the per-cell counts: three passes over tiles of SCAN_TILE cells ----
@@ -62,8 +57,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(int ncell, const i
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(int nb, int ncell, int* __restrict__ bsum,
-                                                           int* __restrict__ cell_start) {
+                                                           int* __restrict__ cell_start, unsigned* __restrict__ occ,
+                                                           int nocc) {
     __shared__ int ws[32];
+    for (int t = threadIdx.x; t < nocc; t += blockDim.x) occ[t] = 0u;   // rebuilt by the gather
     int base = threadIdx.x * SCAN_ITEMS;
     int loc[SCAN_ITEMS];
     int v = 0;
@@ -141,39 +138,52 @@ template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_gather(G
         atomicOr(&s.ctrl->status, ST_NONFINITE);
         i = 0;
     }
-    double x[3] = {s.X[0][i], s.X[1][i], D == 3 ? s.X[2][i] : 0.0};
-    T h = s.H[i];
-    unsigned meta = s.G[i];
+    int c[3] = {0, 0, 0};
+    T o[3] = {T(0), T(0), T(0)};
+    const T h = s.H[i];
+    const unsigned meta = s.G[i];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-        s.Xs[a][k] = x[a];
+        c[a] = s.C[a][i];
+        o[a] = s.O[a][i];
+        s.Cs[a][k] = c[a];
+        s.Os[a][k] = o[a];
         s.Vs[a][k] = s.V[a][i];
     }
     s.Hs[k] = h;
     s.IDs[k] = s.ID[i];
     s.Ks[k] = s.K[i];
-    int l = level_of(g, h);
+    const int l = level_of(g, h);
     int cell[3];
     T off[3];
-    cell_of<T, D>(g, l, x, cell, off);
+    level_repr<T, D>(g, l, c, o, cell, off);
     Rec<T, D>::store(s.P, s.Ms, k, off, h, (meta & 255u) | ((unsigned)cell[0] << 8));
+    if (s.occ) {   // level occupancy of the top-level cell holding the particle
+        const int t = g.L - 1;
+        int ct[3] = {0, 0, 0};
+        for (int a = 0; a < D; ++a) ct[a] = min((cell[a] << l) >> t, g.dims[t][a] - 1);
+        atomicOr(s.occ + (ct[2] * g.dims[t][1] + ct[1]) * g.dims[t][0] + ct[0], 1u << l);
+    }
 }
 
 // ---- initial smoothing lengths h = h_t(x) ----
-template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_init_h(State<T> s) {
+template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_init_h(Grid g, State<T> s) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
-    double x[3] = {s.X[0][i], s.X[1][i], D == 3 ? s.X[2][i] : 0.0};
+    int c[3] = {s.C[0][i], s.C[1][i], D == 3 ? s.C[2][i] : 0};
+    T o[3] = {s.O[0][i], s.O[1][i], D == 3 ? s.O[2][i] : T(0)};
+    double x[3];
+    pos64<T, D>(g, c, o, x);
     s.H[i] = (T)sizing_h(*s.siz, x);
 }
 
 template <typename T, int D> void launch_hash(const Grid& g, const State<T>& s, cudaStream_t st) {
     k_hash<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(g, s);
 }
-void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t st) {
+void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t st, unsigned* occ, int nocc) {
     int nb = div_up(ncell, SCAN_TILE);
     k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(ncell, count, bsum);
-    k_scan_top<<<1, SCAN_THREADS, 0, st>>>(nb, ncell, bsum, cell_start);
+    k_scan_top<<<1, SCAN_THREADS, 0, st>>>(nb, ncell, bsum, cell_start, occ, nocc);
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(ncell, count, bsum, cell_start);
 }
 template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st) {
@@ -185,14 +195,14 @@ void launch_cellsort(int ncell, int n, const int* cell_start, int* perm, int* co
 template <typename T, int D> void launch_gather(const Grid& g, const State<T>& s, cudaStream_t st) {
     k_gather<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(g, s);
 }
-template <typename T, int D> void launch_init_h(const State<T>& s, cudaStream_t st) {
-    k_init_h<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s);
+template <typename T, int D> void launch_init_h(const Grid& g, const State<T>& s, cudaStream_t st) {
+    k_init_h<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(g, s);
 }
 
 #define SPH_INST(T, D)                                                          \
     template void launch_hash<T, D>(const Grid&, const State<T>&, cudaStream_t);   \
     template void launch_gather<T, D>(const Grid&, const State<T>&, cudaStream_t); \
-    template void launch_init_h<T, D>(const State<T>&, cudaStream_t);
+    template void launch_init_h<T, D>(const Grid&, const State<T>&, cudaStream_t);
 SPH_INST(float, 2)
 SPH_INST(float, 3)
 SPH_INST(double, 2)

@@ -14,6 +14,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <math_constants.h>
+#include <climits>
 #include <stdint.h>
 
 namespace sph {
@@ -44,6 +45,8 @@ struct Domain {
     int nh;
     double hc[MAXH][3];
     double hr[MAXH];
+    float flo[3], fhi[3], fbc[3], fbr;   // float copies for the FP32 level-set pre-check
+    float fhc[MAXH][3], fhr[MAXH];
     int nf;
     Feat f[MAXF];
 };
@@ -55,6 +58,8 @@ struct Sizing {
     int nref;
     double rc[MAXH][3];
     double rr[MAXH];
+    float fa, fb, flo, fhi, fq[3];       // float copies for the FP32 evaluation of h_t
+    float frc[MAXH][3], frr[MAXH];
 };
 
 struct Grid {
@@ -175,22 +180,46 @@ template <typename T> __device__ __forceinline__ int level_of(const Grid& g, T h
     return l;
 }
 
-// cell coordinates and cell-relative offset of an FP64 position at level l:
-//   cell = floor((x - origin) * inv_c_l), off = (x - origin) - cell * c_l  (rounded to T)
+// Positions are stored as the finest-level cell (integers) and the offset from that cell's
+// origin in the working precision.  From an FP64 position:
+//   c = floor((x - origin) * inv_c0) (clamped into the finest grid), o = (x - origin) - c * c0
 template <typename T, int D>
-__device__ __forceinline__ bool cell_of(const Grid& g, int l, const double x[3], int cell[3], T off[3]) {
+__device__ __forceinline__ bool fine_of(const Grid& g, const double x[3], int c[3], T o[3]) {
     bool clamped = false;
     for (int a = 0; a < 3; ++a) {
-        if (a >= D) { cell[a] = 0; off[a] = T(0); continue; }
+        if (a >= D) { c[a] = 0; o[a] = T(0); continue; }
         double rel = __dsub_rn(x[a], (double)g.origin[a]);
-        double t = floor(__dmul_rn(rel, g.inv_c[l]));
-        int c = (int)fmax(fmin(t, 2.0e9), -2.0e9);
-        if (c < 0) { c = 0; clamped = true; }
-        if (c > g.dims[l][a] - 1) { c = g.dims[l][a] - 1; clamped = true; }
-        cell[a] = c;
-        off[a] = (T)__dsub_rn(rel, __dmul_rn((double)c, g.c[l]));
+        double t = floor(__dmul_rn(rel, g.inv_c[0]));
+        int ca = (int)fmax(fmin(t, 2.0e9), -2.0e9);
+        if (ca < 0) { ca = 0; clamped = true; }
+        if (ca > g.dims[0][a] - 1) { ca = g.dims[0][a] - 1; clamped = true; }
+        c[a] = ca;
+        o[a] = (T)__dsub_rn(rel, __dmul_rn((double)ca, g.c[0]));
     }
     return clamped;
+}
+
+// the FP64 position of a stored (finest cell, offset) pair
+template <typename T, int D> __device__ __forceinline__ void pos64(const Grid& g, const int c[3], const T o[3], double x[3]) {
+    for (int a = 0; a < 3; ++a)
+        x[a] = a < D ? __dadd_rn(__dadd_rn((double)g.origin[a], __dmul_rn((double)c[a], g.c[0])), (double)o[a]) : 0.0;
+}
+
+// the same position in the working precision (for the sizing function, the level-set
+// pre-check and tangent directions; absolute error ~ the precision of |x|)
+template <typename T, int D> __device__ __forceinline__ void pos_t(const Grid& g, const int c[3], const T o[3], T x[3]) {
+    for (int a = 0; a < 3; ++a) x[a] = a < D ? (T)g.origin[a] + (T)c[a] * (T)g.c0 + o[a] : T(0);
+}
+
+// level-l representation derived from the stored one, each operation rounded in T:
+//   cell = c >> l, off = o + (c - (cell << l)) * c0
+template <typename T, int D>
+__device__ __forceinline__ void level_repr(const Grid& g, int l, const int c[3], const T o[3], int cell[3], T off[3]) {
+    for (int a = 0; a < 3; ++a) {
+        if (a >= D) { cell[a] = 0; off[a] = T(0); continue; }
+        cell[a] = c[a] >> l;
+        off[a] = rn_add(o[a], rn_mul((T)(c[a] - (cell[a] << l)), (T)g.c0));
+    }
 }
 
 __device__ __forceinline__ int key_of(const Grid& g, int l, const int cell[3]) {
@@ -413,6 +442,131 @@ template <typename T> __device__ __forceinline__ T pair_rc2(T hi, T hj, T half_k
 template <typename T> __device__ __forceinline__ T self_rc2(T hi, T kappa) {
     T rc = rn_mul(hi, kappa);
     return rn_mul(rc, rc);
+}
+
+// ---- reciprocal / reciprocal square root for the pair arithmetic (not the predicate) ----
+__device__ __forceinline__ float fast_rcp(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double fast_rcp(double v) { return 1.0 / v; }
+__device__ __forceinline__ float fast_rsqrt(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double fast_rsqrt(double v) { return 1.0 / sqrt(v); }
+
+// ---- sub-warp stencil walk ----
+// LPP consecutive lanes handle one particle.  They share the particle's stencil (the same as in
+// `walk`) and split the candidates of every stencil row between them (lane r takes s+r,
+// s+r+LPP, ...).  A candidate j for which accept(j, dx, r2, h_j, meta_j) holds is kept in the
+// lane's slice of `buf` (CAP entries of (j, level | row), stride BLOCK, in shared memory); the
+// kept candidates are handed to fn(j, dx, r2, h_j, meta_j, off_j, l, cx_j, cy, cz) when the
+// buffer is full and at the end, so the per-pair work runs with the lanes mostly converged.
+// Levels with no particle in the 3^D top-level cells around i (bit l of `occ`, built by the
+// gather) are skipped.  dx and r2 are computed exactly as in `walk`, so a candidate is
+// accepted or rejected identically by both.  No warp-synchronous operation is used inside.
+template <typename T, int D>
+__device__ __forceinline__ int candidate_dx(const Vec4<T>* __restrict__ P, const unsigned* __restrict__ M, int j,
+                                            const int Pi[3], const T offi[3], T c0, int l, int cy, int cz, T offj[3],
+                                            T& hj, unsigned& mj, T dx[3], T& r2) {
+    Rec<T, D>::load(P, M, j, offj, hj, mj);
+    const int cxj = meta_cx(mj);
+    dx[0] = rn_add(rn_sub(offi[0], offj[0]), rn_mul((T)(Pi[0] - (cxj << l)), c0));
+    dx[1] = rn_add(rn_sub(offi[1], offj[1]), rn_mul((T)(Pi[1] - (cy << l)), c0));
+    if (D == 3) dx[2] = rn_add(rn_sub(offi[2], offj[2]), rn_mul((T)(Pi[2] - (cz << l)), c0));
+    else dx[2] = T(0);
+    r2 = rn_add(rn_mul(dx[0], dx[0]), rn_mul(dx[1], dx[1]));
+    if (D == 3) r2 = rn_add(r2, rn_mul(dx[2], dx[2]));
+    return cxj;
+}
+
+// bit l set: some particle of level l lies in the 3^D top-level cells around the particle
+template <int D>
+__device__ __forceinline__ unsigned level_mask(const Grid& g, const unsigned* __restrict__ occ, const int Pi[3],
+                                               const int fl[3]) {
+    if (!occ) return (1u << g.L) - 1u;
+    const int T_ = g.L - 1;
+    int ct[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) ct[a] = (Pi[a] + fl[a]) >> T_;
+    unsigned m = 0;
+    const int z0 = D == 3 ? max(ct[2] - 1, 0) : 0, z1 = D == 3 ? min(ct[2] + 1, g.dims[T_][2] - 1) : 0;
+    const int y0 = max(ct[1] - 1, 0), y1 = min(ct[1] + 1, g.dims[T_][1] - 1);
+    const int x0 = max(ct[0] - 1, 0), x1 = min(ct[0] + 1, g.dims[T_][0] - 1);
+    for (int z = z0; z <= z1; ++z)
+        for (int y = y0; y <= y1; ++y)
+            for (int x = x0; x <= x1; ++x) m |= __ldg(occ + (z * g.dims[T_][1] + y) * g.dims[T_][0] + x);
+    return m;
+}
+
+template <typename T, int D, int LPP, int CAP, typename A, typename F>
+__device__ __forceinline__ void walk_sub(const Grid& g, const int* __restrict__ cell_start,
+                                         const unsigned* __restrict__ occ, int n, const Vec4<T>* __restrict__ P,
+                                         const unsigned* __restrict__ M, int2* __restrict__ buf, bool active, int li,
+                                         const int ci[3], const T offi[3], T hi, T kappa, A&& accept, F&& fn) {
+    if (!active) return;
+    const int sub = (int)(threadIdx.x % LPP);
+    const T c0 = (T)g.c0;
+    const T inv_c0 = T(1) / c0;
+    int Pi[3], fl[3];
+    T fi[3];
+    for (int a = 0; a < 3; ++a) {
+        Pi[a] = ci[a] << li;
+        fi[a] = offi[a] * inv_c0;
+        fl[a] = (int)t_floor(fi[a]);
+    }
+    const unsigned lmask = level_mask<D>(g, occ, Pi, fl);
+    const T rhi = kappa * hi;
+    int cnt = 0;
+    auto flush = [&]() {
+        for (int t = 0; t < cnt; ++t) {
+            const int2 e = buf[t * BLOCK];
+            const int l = e.y >> 28, rid = e.y & 0x0fffffff;
+            const int cz = rid / g.dims[l][1], cy = rid - cz * g.dims[l][1];
+            T offj[3], hj, dx[3], r2;
+            unsigned mj;
+            const int cxj = candidate_dx<T, D>(P, M, e.x, Pi, offi, c0, l, cy, cz, offj, hj, mj, dx, r2);
+            fn(e.x, dx, r2, hj, mj, offj, l, cxj, cy, cz);
+        }
+        cnt = 0;
+    };
+    for (int l = 0; l < g.L; ++l) {
+        if (!((lmask >> l) & 1u)) continue;
+        const T cl = (T)g.c[l];
+        T R = T(0.5) * (rhi + cl);
+        R = (R > rhi ? R : rhi) * T(1.0 + 1.0 / 1024.0);
+        const T Rc = R * inv_c0;
+        int lo[3] = {0, 0, 0}, hb[3] = {0, 0, 0};
+        bool empty = false;
+        for (int a = 0; a < D; ++a) {
+            const int a0 = (Pi[a] + (int)t_floor(fi[a] - Rc)) >> l;
+            const int a1 = (Pi[a] + (int)t_floor(fi[a] + Rc)) >> l;
+            lo[a] = a0 < 0 ? 0 : a0;
+            hb[a] = a1 > g.dims[l][a] - 1 ? g.dims[l][a] - 1 : a1;
+            empty = empty || lo[a] > hb[a];
+        }
+        if (empty) continue;
+        const int dxl = g.dims[l][0], dyl = g.dims[l][1];
+        for (int cz = lo[2]; cz <= hb[2]; ++cz) {
+            for (int cy = lo[1]; cy <= hb[1]; ++cy) {
+                const int rid = cz * dyl + cy;
+                const int row = g.base[l] + rid * dxl;
+                const int s = max(__ldg(cell_start + row + lo[0]), 0);
+                const int e = min(__ldg(cell_start + row + hb[0] + 1), n);
+                for (int j = s + sub; j < e; j += LPP) {
+                    T offj[3], hj, dx[3], r2;
+                    unsigned mj;
+                    candidate_dx<T, D>(P, M, j, Pi, offi, c0, l, cy, cz, offj, hj, mj, dx, r2);
+                    if (accept(j, dx, r2, hj, mj)) {
+                        buf[cnt * BLOCK] = make_int2(j, (l << 28) | rid);
+                        if (++cnt == CAP) flush();
+                    }
+                }
+            }
+        }
+    }
+    flush();
+}
+
+// sum over the LPP lanes of one particle (xor butterfly: every lane gets the same bits)
+template <int LPP, typename T> __device__ __forceinline__ T sub_sum(T v) {
+#pragma unroll
+    for (int o = 1; o < LPP; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 }  // namespace sph

@@ -7,15 +7,17 @@ namespace sph {
 
 template <typename T> struct State {
     int n;
-    // stored state (order of the previous sort)
-    double* X[3];
+    // stored state (order of the previous sort): position = finest cell C + offset O
+    int* C[3];
+    T* O[3];
     T* V[3];
     T* H;
     unsigned* G;
     int* ID;
     int* K;            // cell key of every stored particle (written by the hash)
     // sorted state
-    double* Xs[3];
+    int* Cs[3];
+    T* Os[3];
     T* Vs[3];
     T* Hs;
     unsigned* Ms;
@@ -29,7 +31,10 @@ template <typename T> struct State {
     int* cell_start;
     int* bsum;
     int* perm;
-    // per-block, per-group partial sums of V~ (sample steps)
+    // per top-level cell: bit l set when a particle of level l lies in it (built by the gather)
+    unsigned* occ;
+    int nocc;
+    // per-block, per-group partial sums of V~ (sample steps); nblk = blocks of the pair passes
     double* partials;
     int nblk;
     Ctrl* ctrl;
@@ -39,7 +44,8 @@ template <typename T> struct State {
 
 // output set of the update kernel (the stored state, or scratch for inspection calls)
 template <typename T> struct Out {
-    double* X[3];
+    int* C[3];
+    T* O[3];
     T* V[3];
     T* H;
     unsigned* G;
@@ -47,7 +53,12 @@ template <typename T> struct Out {
     T* av[3];          // optional: viscous acceleration (inspection only)
 };
 
-constexpr int BUF_CAP = 32;   // kept candidates per lane between flushes of the warp walk (shared memory)
+constexpr int BUF_CAP = 16;   // kept candidates per lane between flushes of the walk (shared memory)
+// lanes per particle in the pair passes
+template <int D> struct Lpp {
+    static constexpr int v = D == 2 ? 4 : 8;
+};
+constexpr int LPP_MAX = 8;
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -56,11 +67,12 @@ inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // rebuild.cu
 template <typename T, int D> void launch_hash(const Grid& g, const State<T>& s, cudaStream_t st);
-void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t st);
+void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t st, unsigned* occ = nullptr,
+                 int nocc = 0);
 template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st);
 void launch_cellsort(int ncell, int n, const int* cell_start, int* perm, int* count, cudaStream_t st);
 template <typename T, int D> void launch_gather(const Grid& g, const State<T>& s, cudaStream_t st);
-template <typename T, int D> void launch_init_h(const State<T>& s, cudaStream_t st);
+template <typename T, int D> void launch_init_h(const Grid& g, const State<T>& s, cudaStream_t st);
 
 // interact.cu
 template <typename T, int D>

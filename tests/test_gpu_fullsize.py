@@ -104,11 +104,14 @@ def test_disk_full_run_invariants(disk):
     phi = WL.domain_phi(w["domain"], p["x"])
     vol = p["group"] == 0
     assert phi[vol].min() >= -1e-12
+    # positions are stored as finest cell + FP32 offset: a projected point is exact to the
+    # offset's precision (a few ulp of a cell edge ~ 2 h_lo)
     for k, f in enumerate(w["domain"]["features"]):
         if f["kind"] == "circle":
             sel = p["group"] == k
             r = np.linalg.norm(p["x"][sel, :2] - np.asarray(f["c"][:2]), axis=1)
-            assert np.abs(r - f["r"]).max() < 1e-12
-    assert np.allclose(p["h"], f32(WL.sizing_eval(w["sizing"], p["x"])), rtol=2e-6)
+            assert np.abs(r - f["r"]).max() < 1e-6 * w["h_lo"]
+    # the FP32 build evaluates h_t in FP32 from the FP32 absolute position (error ~ ulp(|x|) b / h)
+    assert np.allclose(p["h"], f32(WL.sizing_eval(w["sizing"], p["x"])), rtol=1e-5)
     assert np.array_equal(p["group"], w["group"])
     m.close()

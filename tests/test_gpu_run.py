@@ -122,12 +122,12 @@ def test_disk_statistics_fp32():
     assert np.abs(hg - ho).sum() <= 0.05
     qg, qo = quality_2d(w, got["x"]), quality_2d(w, o.x)
     assert abs(qg[0] - qo[0]) <= 0.5 and abs(qg[1] - qo[1]) <= 0.01
-    # every curve particle stays on its circle
+    # every curve particle stays on its circle (to the precision of the stored FP32 offset)
     for k, f in enumerate(w["domain"]["features"]):
         if f["kind"] == "circle":
             sel = got["group"] == k
             r = np.linalg.norm(got["x"][sel, :2] - np.asarray(f["c"][:2]), axis=1)
-            assert np.abs(r - f["r"]).max() < 1e-12
+            assert np.abs(r - f["r"]).max() < 1e-6 * w["h_lo"]
 
 
 def test_run_until_converged_reaches_done():
