@@ -36,6 +36,8 @@ METRIC = "particle-steps/s"
 WORKLOAD = "disk_holes_2d_120k"
 FLOP_PER_PAIR = 50.0       # FP32 operations per interacting pair of the pressure pass (see design notes)
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# one step: hash, three scan passes, scatter, gather, pressure pass, controller, update
+KERNELS_PER_STEP = 9
 
 
 def parse():
@@ -305,7 +307,7 @@ def run_ours(args):
         "stages_ms": {k: v["avg_ms"] for k, v in stages.items()},
         "pairs_per_particle": {"candidates": cand / n, "interacting": accd / n},
         "clocks": clocks,
-        "gpu_launches": 10 * args.steps,
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
         "e2e": e2e,
         "cpu_baseline": cpu,
     }

@@ -95,7 +95,7 @@ struct KTime {
     const char* name;
     int kernels;   // kernel launches per step in this stage
 };
-const KTime kStages[4] = {{"rebuild", 7}, {"interact", 1}, {"control", 1}, {"integrate", 1}};
+const KTime kStages[4] = {{"rebuild", 6}, {"interact", 1}, {"control", 1}, {"integrate", 1}};
 
 }  // namespace
 
@@ -174,8 +174,13 @@ template <typename T> size_t layout(sph_mesh* m, char* base, bool assign) {
     s.cell_start = (int*)take((ncell + 1) * 4);
     s.bsum = (int*)take((size_t)SCAN_TILE * 4);
     s.perm = (int*)take(cap * 4);
+    s.sperm = (int*)take(cap * 4);
     s.partials = (double*)take(nblk * MAXF * sizeof(double));
     s.occ = (unsigned*)take(nocc * 4);
+    const size_t nlanes = cap * LPP_MAX;
+    s.vj = (int*)take(nlanes * VCAP_MAX * 4);
+    s.vr = (T*)take(nlanes * VCAP_MAX * sizeof(T));
+    s.vcnt = (int*)take(nlanes * 4);
     if (assign) {
         s.n = 0;
         s.nblk = 0;
@@ -193,6 +198,7 @@ void host_ctrl_init(Ctrl* c) {
     c->phase = PH1;
     c->sample_now = 1;
     c->f = 1.0;
+    c->f_f = 1.0f;
 }
 
 template <typename T> void ctrl_inf_bits(Ctrl* c) {
@@ -204,9 +210,8 @@ template <typename T> void ctrl_inf_bits(Ctrl* c) {
 
 template <typename T, int D> void enqueue_rebuild(sph_mesh* m, const State<T>& s, cudaStream_t stream) {
     launch_hash<T, D>(m->grid, s, stream);
-    launch_scan(m->grid.ncell, s.count, s.cell_start, s.bsum, stream, s.occ, s.nocc);
+    launch_scan(m->grid.ncell, s.count, s.cell_start, s.bsum, stream, s.occ, s.nocc, true);
     launch_scatter<T>(s, stream);
-    launch_cellsort(m->grid.ncell, s.n, s.cell_start, s.perm, s.count, stream);
     launch_gather<T, D>(m->grid, s, stream);
 }
 
@@ -403,15 +408,12 @@ template <typename T, int D> sph_status dbg_rebuild_impl(sph_mesh* m, int64_t* k
     sph_status r = dbg_state<T>(m, s, nullptr);
     if (r != SPH_OK) return r;
     const int n = m->n, nc = m->grid.ncell;
-    launch_hash<T, D>(m->grid, s, m->stream);
-    launch_scan(nc, s.count, s.cell_start, s.bsum, m->stream, s.occ, s.nocc);
-    launch_scatter<T>(s, m->stream);
-    launch_cellsort(nc, s.n, s.cell_start, s.perm, s.count, m->stream);
+    enqueue_rebuild<T, D>(m, s, m->stream);     // the same kernels as a step's rebuild
     CK(cudaGetLastError());
     std::vector<int> k(n), cs(nc + 1), p(n);
     CK(cudaMemcpyAsync(k.data(), s.K, 4 * (size_t)n, cudaMemcpyDeviceToHost, m->stream));
     CK(cudaMemcpyAsync(cs.data(), s.cell_start, 4 * (size_t)(nc + 1), cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaMemcpyAsync(p.data(), s.perm, 4 * (size_t)n, cudaMemcpyDeviceToHost, m->stream));
+    CK(cudaMemcpyAsync(p.data(), s.sperm, 4 * (size_t)n, cudaMemcpyDeviceToHost, m->stream));
     CK(cudaStreamSynchronize(m->stream));
     for (int i = 0; i < n; ++i) {
         if (key_out) key_out[i] = k[i];
@@ -544,10 +546,13 @@ sph_status dbg_update_impl(sph_mesh* m, const double* dt, const int32_t* reset, 
     host_ctrl_init(&c);
     for (int g = 0; g < G; ++g) {
         c.dt[g] = dt[g];
+        c.dt_f[g] = (float)dt[g];
         c.reset[g] = reset[g];
     }
     c.eps = eps;
     c.f = f;
+    c.eps_f = (float)eps;
+    c.f_f = (float)f;
     State<T> s;
     sph_status r = dbg_prepare<T, D>(m, s, &c);
     if (r != SPH_OK) return r;
@@ -688,7 +693,8 @@ sph_status sph_mesh_create(const sph_domain_desc* dd, const sph_sizing_desc* sz,
         return fail(SPH_E_INVALID, "grid: %lld cells is more than the %lld the cell scan supports", (long long)gi.n_cells,
                     (long long)SCAN_TILE * SCAN_TILE);
     for (int l = 0; l < gi.levels; ++l)
-        if (gi.dims[l][0] >= ((int64_t)1 << 23)) return fail(SPH_E_INVALID, "grid: too many cells along x");
+        if (gi.dims[l][0] >= ((int64_t)1 << 23) || gi.dims[l][1] >= ((int64_t)1 << 14) || gi.dims[l][2] >= ((int64_t)1 << 14))
+            return fail(SPH_E_INVALID, "grid: too many cells (x < 2^23, y and z < 2^14 per level)");
 
     sph_mesh* m = new sph_mesh();
     m->D = D;
@@ -705,6 +711,7 @@ sph_status sph_mesh_create(const sph_domain_desc* dd, const sph_sizing_desc* sz,
     for (int l = 0; l < MAXL; ++l) {
         g.c[l] = std::ldexp((double)gi.c0, l);
         g.inv_c[l] = 1.0 / g.c[l];
+        g.cf[l] = (float)g.c[l];
         g.thr[l] = gi.thr[l];
         for (int a = 0; a < 3; ++a) g.dims[l][a] = l < gi.levels ? (int)gi.dims[l][a] : 1;
         g.base[l] = l < gi.levels ? (int)gi.base[l] : (int)gi.n_cells;
@@ -726,7 +733,13 @@ sph_status sph_mesh_create(const sph_domain_desc* dd, const sph_sizing_desc* sz,
     p.window = pp->window;
     p.ramp_len = pp->ramp_len;
     p.boundary_rho = pp->boundary_rho;
+    p.kappa_f = (float)p.kappa;
+    p.p0_f = (float)p.p0;
+    p.visc_f = (float)p.visc;
+    p.cfl_a_f = (float)p.cfl_a;
+    p.cfl_v_f = (float)p.cfl_v;
     p.G = dd->n_features;
+    for (int k = 0; k < MAXF; ++k) p.gdim[k] = k < dd->n_features ? dd->features[k].dim : 0;
     Domain& dm = m->hdom;
     std::memset(&dm, 0, sizeof dm);
     dm.D = D;

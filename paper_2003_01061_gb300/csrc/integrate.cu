@@ -20,8 +20,9 @@ __device__ inline void window_reset(Ctrl* c) {
     }
 }
 
-// One block.  Reduces the per-block V~ sums of a sampling step in a fixed order, then thread 0
-// runs the controller for step n:
+// One block of 256 threads.  The controller state is copied into shared memory at once, the
+// per-block V~ sums of a sampling step are reduced in a fixed order, and the controller for
+// step n runs with one thread per group (thread 0 keeps the scalar state):
 //  1. RAMP -> PHASE2 after ramp_len steps (windows restart);
 //  2. in PHASE1 / PHASE2 on steps n % sample_every == 0: V-bar_g enters the open window; a full
 //     window closes with its mean; with two closed windows E_t = max_g |V-bar - A_last|/|A_last|,
@@ -32,13 +33,20 @@ __device__ inline void window_reset(Ctrl* c) {
 //     nullify every step (Sec. 3.4.3, 3.4.4);
 //  4. per group dt = min(dta, dtv/f), nullified (dt = dta) on the schedule or when dt falls
 //     below dt_collapse times the group's previous step; dt <= dt_cap (Eq. 24).
+// DONE freezes the state (dt = 0, the step counter stops).
 template <typename T> __global__ void __launch_bounds__(256) k_control(Params p, State<T> s) {
-    __shared__ double vs[MAXF];
-    Ctrl* c = s.ctrl;
-    const int G = p.G;
-    const bool sample = c->sample_now != 0;
-    if (sample) {
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __shared__ double vs[MAXF], et[MAXF], ea[MAXF];
+    __shared__ Ctrl sc;
+    __shared__ int fl[4];          // 0: done, 1: sampling step, 2: window closes, 3: reset windows
+    __shared__ double par[3];      // eps, f, periodic
+    constexpr int NW = (int)(sizeof(Ctrl) / sizeof(unsigned));
+    unsigned* scw = reinterpret_cast<unsigned*>(&sc);
+    unsigned* gw = reinterpret_cast<unsigned*>(s.ctrl);
+    const int t = threadIdx.x, G = p.G;
+    for (int k = t; k < NW; k += blockDim.x) scw[k] = gw[k];
+    __syncthreads();
+    if (sc.sample_now != 0) {
+        const int lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
         for (int g = wid; g < G; g += nw) {
             double acc = 0.0;
             for (int b = lane; b < s.nblk; b += 32) acc += s.partials[(size_t)b * G + g];
@@ -47,106 +55,143 @@ template <typename T> __global__ void __launch_bounds__(256) k_control(Params p,
             if (lane == 0) vs[g] = acc;
         }
     }
+    if (t == 0) {
+        const bool done = sc.phase == PH_DONE;
+        bool reset = false;
+        if (!done && sc.phase == PH_RAMP && sc.n - sc.ramp_start >= p.ramp_len) {
+            sc.phase = PH2;
+            sc.wcount = 0;
+            sc.nwin = 0;
+            reset = true;
+        }
+        const bool smp = !done && (sc.phase == PH1 || sc.phase == PH2) && sc.n % p.sample_every == 0;
+        fl[0] = done;
+        fl[1] = smp;
+        fl[2] = smp && sc.wcount + 1 == p.window;
+        fl[3] = reset;
+    }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-
-    double dta[MAXF], dtv[MAXF];
-    for (int g = 0; g < G; ++g) {
-        dta[g] = (double)from_bits<T>(c->dta_bits[g]);
-        dtv[g] = (double)from_bits<T>(c->dtv_bits[g]);
-        c->dta_bits[g] = inf_bits<T>();
-        c->dtv_bits[g] = inf_bits<T>();
+    if (fl[3] && t < MAXF) {
+        sc.wsum[t] = 0.0;
+        sc.A_last[t] = 0.0;
+        sc.A_prev[t] = 0.0;
     }
-    bool done = c->phase == PH_DONE;
-    if (!done && c->phase == PH_RAMP && c->n - c->ramp_start >= p.ramp_len) {
-        c->phase = PH2;
-        window_reset(c);
+    __syncthreads();
+    if (fl[1] && t < G) {
+        sc.Vbar[t] = p.gdim[t] > 0 ? vs[t] : 0.0;
+        sc.wsum[t] += sc.Vbar[t];
+        if (fl[2]) {
+            sc.A_prev[t] = sc.A_last[t];
+            sc.A_last[t] = sc.wsum[t] / p.window;
+            sc.wsum[t] = 0.0;
+        }
     }
-    if (!done && (c->phase == PH1 || c->phase == PH2) && c->n % p.sample_every == 0) {
-        for (int g = 0; g < G; ++g) {
-            c->Vbar[g] = s.dom->f[g].dim > 0 ? vs[g] : 0.0;
-            c->wsum[g] += c->Vbar[g];
+    if (t == 0 && fl[1]) {
+        sc.wcount += 1;
+        if (fl[2]) {
+            sc.wcount = 0;
+            sc.nwin += 1;
         }
-        c->wcount += 1;
-        if (c->wcount == p.window) {
+    }
+    __syncthreads();
+    const bool evaluate = fl[1] && sc.nwin >= 2;
+    if (evaluate && t < MAXF) {
+        const bool use = t < G && p.gdim[t] >= 1;
+        et[t] = use ? rel_err(sc.Vbar[t], sc.A_last[t]) : 0.0;
+        ea[t] = use ? rel_err(sc.A_last[t], sc.A_prev[t]) : 0.0;
+    }
+    __syncthreads();
+    if (t == 0) {
+        bool reset = false;
+        if (evaluate) {
+            double e1 = 0.0, e2 = 0.0;
             for (int g = 0; g < G; ++g) {
-                c->A_prev[g] = c->A_last[g];
-                c->A_last[g] = c->wsum[g] / p.window;
-                c->wsum[g] = 0.0;
+                e1 = fmax(e1, et[g]);
+                e2 = fmax(e2, ea[g]);
             }
-            c->wcount = 0;
-            c->nwin += 1;
-        }
-        if (c->nwin >= 2) {
-            double et = 0.0, ea = 0.0;
-            for (int g = 0; g < G; ++g) {
-                if (s.dom->f[g].dim < 1) continue;
-                et = fmax(et, rel_err(c->Vbar[g], c->A_last[g]));
-                ea = fmax(ea, rel_err(c->A_last[g], c->A_prev[g]));
-            }
-            c->E_t = et;
-            c->E_avg = ea;
-            c->E_sys = fmax(et, ea);
-            if (c->E_sys < p.threshold) {
-                if (c->phase == PH1) {
-                    c->phase = PH_RAMP;
-                    c->ramp_start = c->n;
-                    window_reset(c);
+            sc.E_t = e1;
+            sc.E_avg = e2;
+            sc.E_sys = fmax(e1, e2);
+            if (sc.E_sys < p.threshold) {
+                if (sc.phase == PH1) {
+                    sc.phase = PH_RAMP;
+                    sc.ramp_start = sc.n;
+                    sc.wcount = 0;
+                    sc.nwin = 0;
+                    reset = true;
                 } else {
-                    c->phase = PH_DONE;
-                    done = true;
+                    sc.phase = PH_DONE;
+                    fl[0] = 1;
                 }
             }
         }
-    }
-    if (done) {
-        c->phase = PH_DONE;
-        for (int g = 0; g < G; ++g) {
-            c->dt[g] = 0.0;
-            c->reset[g] = 1;
+        fl[3] = reset;
+        double eps = p.eps1, f = 1.0;
+        bool periodic = (sc.n % p.reset_period) == 0;
+        if (sc.phase == PH_RAMP) {
+            const double sr = (double)(sc.n - sc.ramp_start) / (double)p.ramp_len;
+            eps = p.eps1 * (1.0 - sr);
+            f = 0.5 * (1.0 + cos(CUDART_PI * sr));
+        } else if (sc.phase == PH2) {
+            eps = 0.0;
+            periodic = true;
         }
-        c->eps = 0.0;
-        c->f = 0.0;
-        c->sample_now = 0;
-        return;
+        par[0] = eps;
+        par[1] = f;
+        par[2] = periodic ? 1.0 : 0.0;
     }
-    double eps = p.eps1, f = 1.0;
-    bool periodic = (c->n % p.reset_period) == 0;
-    if (c->phase == PH_RAMP) {
-        double sr = (double)(c->n - c->ramp_start) / (double)p.ramp_len;
-        eps = p.eps1 * (1.0 - sr);
-        f = 0.5 * (1.0 + cos(CUDART_PI * sr));
-    } else if (c->phase == PH2) {
-        eps = 0.0;
-        periodic = true;
+    __syncthreads();
+    if (fl[3] && t < MAXF) {
+        sc.wsum[t] = 0.0;
+        sc.A_last[t] = 0.0;
+        sc.A_prev[t] = 0.0;
     }
-    for (int g = 0; g < G; ++g) {
-        if (s.dom->f[g].dim < 1) {
-            c->dt[g] = 0.0;
-            c->reset[g] = 1;
-            continue;
+    if (t < G) {
+        const double dta = (double)from_bits<T>(sc.dta_bits[t]);
+        const double dtv = (double)from_bits<T>(sc.dtv_bits[t]);
+        if (fl[0] || p.gdim[t] < 1) {
+            sc.dt[t] = 0.0;
+            sc.dt_f[t] = 0.0f;
+            sc.reset[t] = 1;
+        } else {
+            const double f = par[1];
+            const double dv = f > 0.0 ? dtv / f : CUDART_INF;
+            const double cand = fmin(dta, dv);
+            const bool rs = par[2] != 0.0 || (sc.dt_prev[t] > 0.0 && cand < p.dt_collapse * sc.dt_prev[t]);
+            double dt = rs ? dta : cand;
+            dt = fmin(dt, p.dt_cap);
+            sc.dt_prev[t] = dt;
+            sc.dt[t] = dt;
+            sc.dt_f[t] = (float)dt;
+            sc.reset[t] = rs ? 1 : 0;
         }
-        double dv = f > 0.0 ? dtv[g] / f : CUDART_INF;
-        double cand = fmin(dta[g], dv);
-        bool rs = periodic || (c->dt_prev[g] > 0.0 && cand < p.dt_collapse * c->dt_prev[g]);
-        double dt = rs ? dta[g] : cand;
-        dt = fmin(dt, p.dt_cap);
-        c->dt_prev[g] = dt;
-        c->dt[g] = dt;
-        c->reset[g] = rs ? 1 : 0;
     }
-    c->eps = eps;
-    c->f = f;
-    c->n += 1;
-    c->sample_now = (c->n % p.sample_every) == 0 ? 1 : 0;
+    if (t < MAXF) {
+        sc.dta_bits[t] = inf_bits<T>();
+        sc.dtv_bits[t] = inf_bits<T>();
+    }
+    if (t == 0) {
+        if (fl[0]) {
+            sc.phase = PH_DONE;
+            sc.eps = 0.0;
+            sc.f = 0.0;
+            sc.sample_now = 0;
+        } else {
+            sc.eps = par[0];
+            sc.f = par[1];
+            sc.n += 1;
+            sc.sample_now = (sc.n % p.sample_every) == 0 ? 1 : 0;
+        }
+        sc.eps_f = (float)sc.eps;
+        sc.f_f = (float)sc.f;
+    }
+    __syncthreads();
+    for (int k = t; k < NW; k += blockDim.x) gw[k] = scw[k];
 }
 
 // h_t(x) and the level set in the working precision, from the position in that precision and
 // constants stored in it (no FP64 instruction in the FP32 build): the FP32 build stores h as a
 // float, and the level set only decides whether a particle is clearly inside.
-template <typename T> __device__ __forceinline__ T wp(double d, float f);
-template <> __device__ __forceinline__ float wp<float>(double, float f) { return f; }
-template <> __device__ __forceinline__ double wp<double>(double d, float) { return d; }
 
 template <typename T> __device__ __forceinline__ T sizing_h_t(const Sizing& s, const T x[3]) {
     if (s.kind == 0) return wp<T>(s.a, s.fa);
@@ -232,10 +277,10 @@ __global__ void __launch_bounds__(BLOCK) k_integrate(Grid g, Params p, State<T> 
     T vt[3] = {T(0), T(0), T(0)};
     T tg[3] = {T(0), T(0), T(0)};
     if (moving) {
-        dt = (T)cu->dt[gi];
+        dt = wp<T>(cu->dt[gi], cu->dt_f[gi]);
         rs = cu->reset[gi] != 0;
-        f = (T)cu->f;
-        eps = (T)cu->eps;
+        f = wp<T>(cu->f, cu->f_f);
+        eps = wp<T>(cu->eps, cu->eps_f);
         const Vec4<T> ai = s.A[k];
         const T api[3] = {ai.x, ai.y, ai.z};
         for (int a = 0; a < 3; ++a) {
@@ -249,38 +294,53 @@ __global__ void __launch_bounds__(BLOCK) k_integrate(Grid g, Params p, State<T> 
         }
     }
     if (p.visc > 0.0 && !done) {
-        const T kappa = (T)p.kappa, hk = T(0.5) * kappa, visc = (T)p.visc;
-        const T ri2 = ipow(hi, 2 * di);
-        const T eta_i = visc * kappa * hi * t_sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]) *
-                        fast_rcp(ipow(hi, di));
+        const T kappa = wp<T>(p.kappa, p.kappa_f), hk = T(0.5) * kappa, visc = wp<T>(p.visc, p.visc_f);
+        T hid, hi2d;
+        hpow(hi, di > 0 ? di : 1, hid, hi2d);
+        const T eta_i = visc * kappa * hi * t_sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]) * fast_rcp(hid);
+        // one same-group pair (j at distance r): the viscous term of Eq. 7
+        auto pair = [&](int j, T r, T hj) {
+            const T invr = fast_rcp(r);
+            const Vec4<T> aj = s.A[j];
+            const T apj[3] = {aj.x, aj.y, aj.z};
+            T vtj[3] = {T(0), T(0), T(0)};
+            for (int a = 0; a < D; ++a) {
+                const T vp = rs ? T(0) : f * s.Vs[a][j];
+                vtj[a] = vp + dt * (apj[a] - eps * vp);
+            }
+            T hjd, hj2d;
+            hpow(hj, di, hjd, hj2d);
+            const T eta_j = visc * kappa * hj * t_sqrt(vtj[0] * vtj[0] + vtj[1] * vtj[1] + vtj[2] * vtj[2]) *
+                            fast_rcp(hjd);
+            const T es = eta_i + eta_j;
+            if (!(es > T(0))) return;
+            const T eb = T(2) * eta_i * eta_j / es;
+            const T invR = fast_rcp(hk * (hi + hj));
+            const T q = r * invR;
+            const T t = T(1) - q;
+            const T dW = wendland_alpha<T>(di, invR) * (T(-20) * q * t * t * t) * invR;
+            const T coef = eb * (hi2d + hj2d) * dW * invr;
+            for (int a = 0; a < D; ++a) av[a] += coef * (vt[a] - vtj[a]);
+        };
+        // the pairs the pressure pass found (list), or the cell walk where the list overflowed
+        constexpr int VCAP = Vcap<D>::v;
+        const int NL = s.n * LPP, lg = blockIdx.x * blockDim.x + threadIdx.x;
+        const int vc = moving ? s.vcnt[lg] : 0;
+        const bool ov = sub_sum<LPP>(vc > VCAP ? 1 : 0) != 0;   // overflow in any lane of the particle
+        if (moving && !ov)
+            for (int e = 0; e < vc; ++e) {
+                const int j = s.vj[(size_t)e * NL + lg];
+                pair(j, s.vr[(size_t)e * NL + lg], s.Hs[j]);
+            }
         int li = 0, ci[3] = {0, 0, 0};
-        if (inrange) decode_key(g, s.Ks[k], li, ci);
+        if (moving && ov) decode_key(g, s.Ks[k], li, ci);
         walk_sub<T, D, LPP, BUF_CAP>(
-            g, s.cell_start, s.occ, s.n, s.P, s.Ms, sbuf + threadIdx.x, moving, li, ci, offi, hi, kappa,
+            g, s.cell_start, s.occ, s.n, s.P, s.Ms, sbuf + threadIdx.x, moving && ov, li, ci, offi, hi, kappa,
             [&](int j, const T*, T r2, T hj, unsigned mj) -> bool {
                 return meta_group(mj) == gi && j != k && r2 < pair_rc2(hi, hj, hk) && r2 > T(0);
             },
-            [&](int j, const T dx[3], T r2, T hj, unsigned, const T*, int, int, int, int) {
-                const T invr = fast_rsqrt(r2);
-                const T r = r2 * invr;
-                const Vec4<T> aj = s.A[j];
-                const T apj[3] = {aj.x, aj.y, aj.z};
-                T vtj[3] = {T(0), T(0), T(0)};
-                for (int a = 0; a < D; ++a) {
-                    const T vp = rs ? T(0) : f * s.Vs[a][j];
-                    vtj[a] = vp + dt * (apj[a] - eps * vp);
-                }
-                const T eta_j = visc * kappa * hj * t_sqrt(vtj[0] * vtj[0] + vtj[1] * vtj[1] + vtj[2] * vtj[2]) *
-                                fast_rcp(ipow(hj, di));
-                const T es = eta_i + eta_j;
-                if (!(es > T(0))) return;
-                const T eb = T(2) * eta_i * eta_j / es;
-                const T invR = fast_rcp(hk * (hi + hj));
-                const T q = r * invR;
-                const T t = T(1) - q;
-                const T dW = wendland_alpha<T>(di, invR) * (T(-20) * q * t * t * t) * invR;
-                const T coef = eb * (ri2 + ipow(hj, 2 * di)) * dW * invr;
-                for (int a = 0; a < D; ++a) av[a] += coef * (vt[a] - vtj[a]);
+            [&](int j, const T*, T r2, T hj, unsigned, const T*, int, int, int, int) {
+                pair(j, r2 * fast_rsqrt(r2), hj);
             });
         for (int a = 0; a < D; ++a) av[a] = sub_sum<LPP>(av[a]);
         if (moving) tangent_map<T>(di, D, tg, av);

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s
         for (int a = 0; a < D; ++a) xi[a] = (T)g.origin[a] + (T)(ci[a] << li) * (T)g.c0 + offi[a];
         feature_tangent<T>(s.dom->f[gi], xi, tg);
     }
-    const T kappa = (T)p.kappa, hk = T(0.5) * kappa, p0 = (T)p.p0;
+    const T kappa = wp<T>(p.kappa, p.kappa_f), hk = T(0.5) * kappa, p0 = wp<T>(p.p0, p.p0_f);
     const T rci2 = self_rc2(hi, kappa);
     const T invRi = fast_rcp(kappa * hi);
     const T alpha_i = wendland_alpha<T>(di > 0 ? di : 1, invRi);
@@ -61,6 +61,10 @@ __global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s
     const T org[3] = {(T)g.origin[0], (T)g.origin[1], (T)g.origin[2]};
     T F[3] = {T(0), T(0), T(0)};
     T sig = T(0), gam = T(0);
+    constexpr int VCAP = Vcap<D>::v;
+    const int NL = s.n * LPP;                              // lanes of the hand-over list
+    const int lg = blockIdx.x * blockDim.x + threadIdx.x;  // this lane's column in it
+    int vc = 0;
 
     walk_sub<T, D, LPP, BUF_CAP>(
         g, s.cell_start, s.occ, s.n, s.P, s.Ms, sbuf + threadIdx.x, active, li, ci, offi, hi, kappa,
@@ -71,23 +75,30 @@ __global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s
         [&](int j, const T dx[3], T r2, T hj, unsigned mj, const T offj[3], int l, int cxj, int cy, int cz) {
             const T invr = r2 > T(0) ? fast_rsqrt(r2) : T(0);
             const T r = r2 * invr;
+            T hjd, hj2d;
+            hpow(hj, di, hjd, hj2d);
             if (meta_group(mj) == gi) {
                 if (r2 < rci2) {
                     const T q = r * invRi;
                     const T t = T(1) - q;
                     const T w = alpha_i * (t * t) * (t * t) * (T(1) + T(4) * q);
                     sig += w;
-                    gam += w * ipow(hj, di);
+                    gam += w * hjd;
                 }
                 if (j != k && r2 < pair_rc2(hi, hj, hk) && r2 > T(0)) {
                     const T invR = fast_rcp(hk * (hi + hj));
                     const T q = r * invR;
                     const T t = T(1) - q;
                     const T dW = wendland_alpha<T>(di, invR) * (T(-20) * q * t * t * t) * invR;
-                    const T c1 = (Pi + p0 * ipow(hj, 2 * di)) * dW * invr;
+                    const T c1 = (Pi + p0 * hj2d) * dW * invr;
                     F[0] += c1 * dx[0];
                     F[1] += c1 * dx[1];
                     if (D == 3) F[2] += c1 * dx[2];
+                    if (vc < VCAP) {   // the pair again in the viscous sum (Eq. 7, second term)
+                        s.vj[(size_t)vc * NL + lg] = j;
+                        s.vr[(size_t)vc * NL + lg] = r;
+                    }
+                    ++vc;
                 }
             } else {
                 const T invR = fast_rcp(hk * (hi + hj));
@@ -102,14 +113,15 @@ __global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s
                 tangent_map<T>(di, D, tg, nb);
                 const T nn2 = nb[0] * nb[0] + nb[1] * nb[1] + nb[2] * nb[2];
                 if (nn2 > T(1e-12)) {
-                    const T Ab = brho ? fast_rcp(hj) : ipow(hj, di - 1);
-                    const T c2 = Ab * (Pi + p0 * ipow(hj, 2 * di)) * w * fast_rsqrt(nn2);
+                    const T Ab = brho ? fast_rcp(hj) : hjd * fast_rcp(hj);
+                    const T c2 = Ab * (Pi + p0 * hj2d) * w * fast_rsqrt(nn2);
                     F[0] += c2 * nb[0];
                     F[1] += c2 * nb[1];
                     if (D == 3) F[2] += c2 * nb[2];
                 }
             }
         });
+    if (inrange) s.vcnt[lg] = vc;
     for (int a = 0; a < D; ++a) F[a] = sub_sum<LPP>(F[a]);
     sig = sub_sum<LPP>(sig);
     gam = sub_sum<LPP>(gam);
@@ -125,8 +137,8 @@ __global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s
         const T an = t_sqrt(ap[0] * ap[0] + ap[1] * ap[1] + ap[2] * ap[2]);
         const T v0 = s.Vs[0][k], v1 = s.Vs[1][k], v2 = D == 3 ? s.Vs[2][k] : T(0);
         const T vn = t_sqrt(v0 * v0 + v1 * v1 + v2 * v2);
-        const T dta = an > T(0) ? (T)p.cfl_a * t_sqrt(rc / an) : (T)CUDART_INF;
-        const T dtv = vn > T(0) ? (T)p.cfl_v * rc / vn : (T)CUDART_INF;
+        const T dta = an > T(0) ? wp<T>(p.cfl_a, p.cfl_a_f) * t_sqrt(rc / an) : T(CUDART_INF_F);
+        const T dtv = vn > T(0) ? wp<T>(p.cfl_v, p.cfl_v_f) * rc / vn : T(CUDART_INF_F);
         if (!(an == an) || !isfinite(an)) atomicOr(&s.ctrl->status, ST_NONFINITE);
         atomicMin(&sh_dta[gi], min_bits(dta));
         atomicMin(&sh_dtv[gi], min_bits(dtv));
@@ -184,7 +196,7 @@ __global__ void __launch_bounds__(BLOCK) k_neighbors(Grid g, Params p, State<T> 
         Rec<T, D>::load(s.P, s.Ms, k, offi, hi, mi);
         decode_key(g, s.Ks[k], li, ci);
     }
-    const T kappa = (T)p.kappa, hk = T(0.5) * kappa;
+    const T kappa = wp<T>(p.kappa, p.kappa_f), hk = T(0.5) * kappa;
     const T rci2 = self_rc2(hi, kappa);
     int cnt = 0;
     const long long base = (lists && active) ? offsets[k] : 0;
@@ -216,7 +228,7 @@ __global__ void __launch_bounds__(BLOCK) k_pair_counts(Grid g, Params p, State<T
     }
     const int gi = inrange ? meta_group(mi) : -1, di = inrange ? meta_dim(mi) : 0;
     const bool active = inrange && di > 0;
-    const T kappa = (T)p.kappa, hk = T(0.5) * kappa;
+    const T kappa = wp<T>(p.kappa, p.kappa_f), hk = T(0.5) * kappa;
     unsigned long long cand = 0, accd = 0;
     walk_sub<T, D, 1, BUF_CAP>(
         g, s.cell_start, s.occ, s.n, s.P, s.Ms, sbuf + threadIdx.x, active, li, ci, offi, hi, kappa,

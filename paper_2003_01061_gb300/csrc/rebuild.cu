@@ -43,14 +43,25 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_sums, int& 
     return before + x - v;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(int ncell, const int* __restrict__ count,
+// relative: the counters were not reset since the previous rebuild, where the scatter left
+// count[c] = cell_start[c+1]; the new per-cell count is count[c] - cell_start[c+1] (and is
+// stored back into count for the down-sweep), so no pass over all cells resets them.
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(int ncell, int* __restrict__ count,
+                                                              const int* __restrict__ cell_start, bool relative,
                                                               int* __restrict__ bsum) {
     __shared__ int ws[32];
     int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
     int v = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k)
-        if (base + k < ncell) v += count[base + k];
+        if (base + k < ncell) {
+            int nk = count[base + k];
+            if (relative) {
+                nk -= cell_start[base + k + 1];
+                count[base + k] = nk;
+            }
+            v += nk;
+        }
     int total;
     block_exclusive_scan(v, ws, total);
     if (threadIdx.x == 0) bsum[blockIdx.x] = total;
@@ -130,6 +141,10 @@ __global__ void __launch_bounds__(BLOCK) k_cellsort(int ncell, int n, const int*
 }
 
 // ---- gather into sorted order + cell-relative offsets ----
+// The scatter fills each cell's slots in arbitrary order; slot k of cell c takes the particle
+// whose stored index has rank (k - start_c) among the cell's particles, which makes the
+// counting sort stable.  Usually a cell's particles were consecutive in the stored order (it
+// is the previous step's sorted order), and the rank is found from the cell's minimum.
 template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_gather(Grid g, State<T> s) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= s.n) return;
@@ -137,6 +152,30 @@ template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_gather(G
     if ((unsigned)i >= (unsigned)s.n) {   // defensive: a broken permutation is reported, not followed
         atomicOr(&s.ctrl->status, ST_NONFINITE);
         i = 0;
+    }
+    {
+        const int key = s.K[i];
+        const int c0s = max(s.cell_start[key], 0), c0e = min(s.cell_start[key + 1], s.n);
+        const int m = c0e - c0s, r = k - c0s;
+        if (m > 1 && r >= 0 && r < m) {
+            int mn = INT_MAX, mx = INT_MIN;
+            for (int t = c0s; t < c0e; ++t) {
+                const int v = s.perm[t];
+                mn = min(mn, v);
+                mx = max(mx, v);
+            }
+            if (mx - mn + 1 == m) {
+                i = mn + r;
+            } else {
+                for (int t = c0s; t < c0e; ++t) {
+                    const int v = s.perm[t];
+                    int below = 0;
+                    for (int u = c0s; u < c0e; ++u) below += s.perm[u] < v;
+                    if (below == r) i = v;
+                }
+            }
+        }
+        s.sperm[k] = i;
     }
     int c[3] = {0, 0, 0};
     T o[3] = {T(0), T(0), T(0)};
@@ -180,9 +219,10 @@ template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_init_h(G
 template <typename T, int D> void launch_hash(const Grid& g, const State<T>& s, cudaStream_t st) {
     k_hash<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(g, s);
 }
-void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t st, unsigned* occ, int nocc) {
+void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t st, unsigned* occ, int nocc,
+                 bool relative) {
     int nb = div_up(ncell, SCAN_TILE);
-    k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(ncell, count, bsum);
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(ncell, count, cell_start, relative, bsum);
     k_scan_top<<<1, SCAN_THREADS, 0, st>>>(nb, ncell, bsum, cell_start, occ, nocc);
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(ncell, count, bsum, cell_start);
 }

@@ -68,6 +68,7 @@ struct Grid {
     float origin[3];
     double c[MAXL];      // c0 * 2^l
     double inv_c[MAXL];  // 1 / c_l rounded once in FP64
+    float cf[MAXL];      // c0 * 2^l as float (exact)
     float thr[MAXL];
     int dims[MAXL][3];
     int base[MAXL + 1];
@@ -78,6 +79,8 @@ struct Params {
     double kappa, p0, visc, cfl_a, cfl_v, eps1, dt_cap, dt_collapse, threshold;
     int reset_period, sample_every, window, ramp_len, boundary_rho;
     int G;
+    int gdim[MAXF];      // intrinsic dimension of every group (feature)
+    float kappa_f, p0_f, visc_f, cfl_a_f, cfl_v_f;   // float copies for the FP32 kernels
 };
 
 // controller state + per-step accumulators (one per instance, in device memory)
@@ -90,6 +93,7 @@ struct Ctrl {
     double wsum[MAXF], A_last[MAXF], A_prev[MAXF], Vbar[MAXF], dt_prev[MAXF], dt[MAXF];
     int reset[MAXF];
     double E_t, E_avg, E_sys, eps, f;
+    float dt_f[MAXF], eps_f, f_f;      // float copies of dt, eps, f for the FP32 update
     unsigned long long dta_bits[MAXF], dtv_bits[MAXF];   // per-group minima of Eq. 24 terms
 };
 
@@ -119,11 +123,24 @@ template <typename T> __device__ __forceinline__ T t_floor(T v);
 template <> __device__ __forceinline__ float t_floor<float>(float v) { return floorf(v); }
 template <> __device__ __forceinline__ double t_floor<double>(double v) { return floor(v); }
 
+// a constant in the working precision: the float copy in the FP32 build (a double-to-float
+// conversion runs on the FP64 pipe, which is narrow on this GPU), the double in the FP64 build
+template <typename T> __device__ __forceinline__ T wp(double d, float f);
+template <> __device__ __forceinline__ float wp<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double wp<double>(double d, float) { return d; }
+
 // h^k for small non-negative integer k
 template <typename T> __device__ __forceinline__ T ipow(T h, int k) {
     T r = T(1);
     for (int i = 0; i < k; ++i) r *= h;
     return r;
+}
+
+// h^d and h^(2d) for an intrinsic dimension d in {1, 2, 3}
+template <typename T> __device__ __forceinline__ void hpow(T h, int d, T& hd, T& h2d) {
+    const T h2 = h * h;
+    hd = d == 1 ? h : (d == 2 ? h2 : h2 * h);
+    h2d = hd * hd;
 }
 
 // Wendland C2 normalisation alpha_d / (its R-dependence): alpha_1 = 3/(2R), alpha_2 = 7/(pi R^2),
@@ -391,7 +408,7 @@ __device__ __forceinline__ void walk(const Grid& g, const int* __restrict__ cell
     }
     const T rhi = kappa * hi;
     for (int l = 0; l < g.L; ++l) {
-        T cl = (T)g.c[l];
+        T cl = wp<T>(g.c[l], g.cf[l]);
         T R = T(0.5) * (rhi + cl);
         R = (R > rhi ? R : rhi) * T(1.0 + 1.0 / 1024.0);
         T Rc = R * inv_c0;
@@ -515,8 +532,7 @@ __device__ __forceinline__ void walk_sub(const Grid& g, const int* __restrict__ 
     auto flush = [&]() {
         for (int t = 0; t < cnt; ++t) {
             const int2 e = buf[t * BLOCK];
-            const int l = e.y >> 28, rid = e.y & 0x0fffffff;
-            const int cz = rid / g.dims[l][1], cy = rid - cz * g.dims[l][1];
+            const int l = e.y >> 28, cz = (e.y >> 14) & 0x3fff, cy = e.y & 0x3fff;
             T offj[3], hj, dx[3], r2;
             unsigned mj;
             const int cxj = candidate_dx<T, D>(P, M, e.x, Pi, offi, c0, l, cy, cz, offj, hj, mj, dx, r2);
@@ -526,7 +542,7 @@ __device__ __forceinline__ void walk_sub(const Grid& g, const int* __restrict__ 
     };
     for (int l = 0; l < g.L; ++l) {
         if (!((lmask >> l) & 1u)) continue;
-        const T cl = (T)g.c[l];
+        const T cl = wp<T>(g.c[l], g.cf[l]);
         T R = T(0.5) * (rhi + cl);
         R = (R > rhi ? R : rhi) * T(1.0 + 1.0 / 1024.0);
         const T Rc = R * inv_c0;
@@ -552,7 +568,7 @@ __device__ __forceinline__ void walk_sub(const Grid& g, const int* __restrict__ 
                     unsigned mj;
                     candidate_dx<T, D>(P, M, j, Pi, offi, c0, l, cy, cz, offj, hj, mj, dx, r2);
                     if (accept(j, dx, r2, hj, mj)) {
-                        buf[cnt * BLOCK] = make_int2(j, (l << 28) | rid);
+                        buf[cnt * BLOCK] = make_int2(j, (l << 28) | (cz << 14) | cy);
                         if (++cnt == CAP) flush();
                     }
                 }

@@ -30,10 +30,17 @@ template <typename T> struct State {
     int* count;
     int* cell_start;
     int* bsum;
-    int* perm;
+    int* perm;         // slot -> stored index as left by the scatter (unordered inside a cell)
+    int* sperm;        // slot -> stored index, stable (ordered inside a cell; written by the gather)
     // per top-level cell: bit l set when a particle of level l lies in it (built by the gather)
     unsigned* occ;
     int nocc;
+    // same-group pairs found by the pressure pass, handed to the viscous pass: for lane
+    // g = k*LPP + r of particle k, entry c is (vj, vr)[c * n*LPP + g] (index, distance);
+    // vcnt[g] counts them (> VCAP: the list overflowed and the viscous pass walks the cells)
+    int* vj;
+    T* vr;
+    int* vcnt;
     // per-block, per-group partial sums of V~ (sample steps); nblk = blocks of the pair passes
     double* partials;
     int nblk;
@@ -59,6 +66,11 @@ template <int D> struct Lpp {
     static constexpr int v = D == 2 ? 4 : 8;
 };
 constexpr int LPP_MAX = 8;
+// same-group pair slots per lane in the pressure-to-viscous hand-over list
+template <int D> struct Vcap {
+    static constexpr int v = D == 2 ? 8 : 12;
+};
+constexpr int VCAP_MAX = 12;
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
@@ -68,7 +80,7 @@ inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 // rebuild.cu
 template <typename T, int D> void launch_hash(const Grid& g, const State<T>& s, cudaStream_t st);
 void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t st, unsigned* occ = nullptr,
-                 int nocc = 0);
+                 int nocc = 0, bool relative = false);
 template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st);
 void launch_cellsort(int ncell, int n, const int* cell_start, int* perm, int* count, cudaStream_t st);
 template <typename T, int D> void launch_gather(const Grid& g, const State<T>& s, cudaStream_t st);
