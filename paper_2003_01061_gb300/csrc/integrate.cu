@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(BLOCK) k_integrate(Grid g, Params p, State<T> 
                 pair(j, s.vr[(size_t)e * NL + lg], s.Hs[j]);
             }
         int li = 0, ci[3] = {0, 0, 0};
-        if (moving && ov) decode_key(g, s.Ks[k], li, ci);
+        if (moving && ov) own_cell<T, D>(g, s, k, hi, li, ci);
         walk_sub<T, D, LPP, BUF_CAP>(
             g, s.cell_start, s.occ, s.n, s.P, s.Ms, sbuf + threadIdx.x, moving && ov, li, ci, offi, hi, kappa,
             [&](int j, const T*, T r2, T hj, unsigned mj) -> bool {

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s
     int li = 0, ci[3] = {0, 0, 0};
     if (inrange) {
         Rec<T, D>::load(s.P, s.Ms, k, offi, hi, mi);
-        decode_key(g, s.Ks[k], li, ci);
+        own_cell<T, D>(g, s, k, hi, li, ci);
     }
     const int gi = inrange ? meta_group(mi) : -1;
     const int di = inrange ? meta_dim(mi) : 0;
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(BLOCK) k_neighbors(Grid g, Params p, State<T> 
     int li = 0, ci[3] = {0, 0, 0};
     if (active) {
         Rec<T, D>::load(s.P, s.Ms, k, offi, hi, mi);
-        decode_key(g, s.Ks[k], li, ci);
+        own_cell<T, D>(g, s, k, hi, li, ci);
     }
     const T kappa = wp<T>(p.kappa, p.kappa_f), hk = T(0.5) * kappa;
     const T rci2 = self_rc2(hi, kappa);
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(BLOCK) k_pair_counts(Grid g, Params p, State<T
     int li = 0, ci[3] = {0, 0, 0};
     if (inrange) {
         Rec<T, D>::load(s.P, s.Ms, k, offi, hi, mi);
-        decode_key(g, s.Ks[k], li, ci);
+        own_cell<T, D>(g, s, k, hi, li, ci);
     }
     const int gi = inrange ? meta_group(mi) : -1, di = inrange ? meta_dim(mi) : 0;
     const bool active = inrange && di > 0;

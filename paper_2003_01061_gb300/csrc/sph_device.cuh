@@ -556,18 +556,28 @@ __device__ __forceinline__ void walk_sub(const Grid& g, const int* __restrict__ 
             empty = empty || lo[a] > hb[a];
         }
         if (empty) continue;
+        // every radius the callers test at this level is below R: candidates beyond it are
+        // rejected on the distance alone
+        const T R2 = R * R;
         const int dxl = g.dims[l][0], dyl = g.dims[l][1];
         for (int cz = lo[2]; cz <= hb[2]; ++cz) {
+            const T mcz = D == 3 ? rn_mul((T)(Pi[2] - (cz << l)), c0) : T(0);
             for (int cy = lo[1]; cy <= hb[1]; ++cy) {
+                const T mcy = rn_mul((T)(Pi[1] - (cy << l)), c0);
                 const int rid = cz * dyl + cy;
                 const int row = g.base[l] + rid * dxl;
                 const int s = max(__ldg(cell_start + row + lo[0]), 0);
                 const int e = min(__ldg(cell_start + row + hb[0] + 1), n);
                 for (int j = s + sub; j < e; j += LPP) {
-                    T offj[3], hj, dx[3], r2;
+                    T offj[3], hj, dx[3];
                     unsigned mj;
-                    candidate_dx<T, D>(P, M, j, Pi, offi, c0, l, cy, cz, offj, hj, mj, dx, r2);
-                    if (accept(j, dx, r2, hj, mj)) {
+                    Rec<T, D>::load(P, M, j, offj, hj, mj);
+                    dx[0] = rn_add(rn_sub(offi[0], offj[0]), rn_mul((T)(Pi[0] - (meta_cx(mj) << l)), c0));
+                    dx[1] = rn_add(rn_sub(offi[1], offj[1]), mcy);
+                    dx[2] = D == 3 ? rn_add(rn_sub(offi[2], offj[2]), mcz) : T(0);
+                    T r2 = rn_add(rn_mul(dx[0], dx[0]), rn_mul(dx[1], dx[1]));
+                    if (D == 3) r2 = rn_add(r2, rn_mul(dx[2], dx[2]));
+                    if (r2 < R2 && accept(j, dx, r2, hj, mj)) {
                         buf[cnt * BLOCK] = make_int2(j, (l << 28) | (cz << 14) | cy);
                         if (++cnt == CAP) flush();
                     }

@@ -71,6 +71,14 @@ template <int D> struct Vcap {
     static constexpr int v = D == 2 ? 8 : 12;
 };
 constexpr int VCAP_MAX = 12;
+// level and level-cell of sorted particle k (from its h and stored finest cell; the same as
+// decoding its key, without the integer divisions)
+template <typename T, int D>
+__device__ __forceinline__ void own_cell(const Grid& g, const State<T>& s, int k, T h, int& l, int c[3]) {
+    l = level_of(g, h);
+    for (int a = 0; a < 3; ++a) c[a] = a < D ? (s.Cs[a][k] >> l) : 0;
+}
+
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
