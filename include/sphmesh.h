@@ -271,6 +271,168 @@ sph_status sph_mesh_kernel_times(sph_mesh* m, sph_kernel_time* out, int32_t cap,
 sph_status sph_debug_pair_counts(sph_mesh* m, int64_t* candidates, int64_t* accepted);
 
 /* ------------------------------------------------------------------------------------------
+ * Batches: many independent relaxation problems advanced together.  Every problem ("instance")
+ * runs Algorithm 1 with its own domain, sizing, parameters and two-phase controller (Sec. 3.4),
+ * exactly as a sph_mesh would; the batch packs all instances into one particle array and one
+ * cell-key range so that each kernel of a step serves every instance in one launch.  This is
+ * how small problems fill the GPU (the paper relaxes one problem at a time).
+ *
+ * All instances of a batch share the ambient dimension and the precision.  The batch allocates
+ * particle slots for the sum of the max_particles given at creation (each rounded up to 64);
+ * any instance may hold any count as long as the loaded instances' counts, each rounded up to
+ * 64, fit that total.  Loaded instances occupy consecutive slot ranges; loading or emptying
+ * one moves the others on the device and makes the next step re-capture its graph.  A freshly
+ * created instance is empty and idle (controller DONE).  An empty instance costs nothing per
+ * step; a converged (DONE) one costs a pass over its slots and no pair work.  Instance results
+ * do not depend on the other instances of the batch: a particle only interacts with particles
+ * of its own instance, and every sum runs in the same order as for the instance alone.
+ * Indices `inst` run from 0 to n_inst-1; out-of-range indices give SPH_E_INVALID.
+ * ------------------------------------------------------------------------------------------ */
+#define SPH_MAX_INSTANCES 4096
+typedef struct sph_batch sph_batch;
+
+/* Creates a batch of n_inst instances; domains, sizings, params and max_particles are arrays of
+ * n_inst entries, validated as by sph_mesh_create.  stream as for sph_mesh_create.
+ * Errors: SPH_E_INVALID (a descriptor, mixed dims or precisions, too many cells or slots in
+ * total), SPH_E_NOMEM, SPH_E_CUDA. */
+sph_status sph_batch_create(int32_t n_inst, const sph_domain_desc* domains, const sph_sizing_desc* sizings,
+                            const sph_params* params, const int64_t* max_particles, void* stream,
+                            sph_batch** out);
+
+/* Number of instances, particle slots in use (the work of one step is proportional to it) and
+ * slots allocated.  Any pointer may be NULL. */
+sph_status sph_batch_size(const sph_batch* b, int32_t* n_inst, int64_t* n_slots, int64_t* slot_capacity);
+
+/* Replaces the problem of instance inst (domain, sizing, parameters; same dim and precision)
+ * and leaves it empty and idle.  Waits for the batch's stream.  The other instances keep their
+ * state. */
+sph_status sph_batch_set_problem(sph_batch* b, int32_t inst, const sph_domain_desc* domain,
+                                 const sph_sizing_desc* sizing, const sph_params* params);
+
+/* sph_mesh_set_state for instance inst: loads its particles and resets its controller to
+ * Phase One, step 0; n = 0 empties the instance (controller DONE).  Waits for the batch's
+ * stream.  The other instances keep their state.  Errors: those of sph_mesh_set_state, and
+ * SPH_E_NOMEM when the loaded instances would not fit the batch's slots (nothing changes). */
+sph_status sph_batch_set_state(sph_batch* b, int32_t inst, int64_t n, const double* x,
+                               const int32_t* group, const double* v, const double* h);
+
+/* Enqueues n_steps steps of every instance (idle and DONE instances stay frozen). */
+sph_status sph_batch_step(sph_batch* b, int32_t n_steps);
+
+/* Waits for the batch's stream and checks every instance's status word; the first instance
+ * with a problem names itself in the message.  Errors as for sph_mesh_sync. */
+sph_status sph_batch_sync(sph_batch* b);
+
+/* Steps until every loaded instance is DONE or has run max_iters steps (checking every
+ * sample_every steps); iters_out receives the largest step count.  Errors as for
+ * sph_mesh_run_until_converged (SPH_E_NOT_CONVERGED names the first unfinished instance). */
+sph_status sph_batch_run_until_converged(sph_batch* b, int64_t max_iters, int64_t* iters_out);
+
+/* sph_mesh_positions for instance inst (original order of its last sph_batch_set_state). */
+sph_status sph_batch_positions(sph_batch* b, int32_t inst, double* x_out, int32_t* group_out,
+                               double* v_out, double* h_out, int64_t capacity, int64_t* n_out);
+
+/* Controller reports of all instances (out: cap >= n_inst entries), from one device copy. */
+sph_status sph_batch_reports(sph_batch* b, sph_report* out, int32_t cap);
+
+/* Per-stage timing over the whole batch, as sph_mesh_set_timing / sph_mesh_kernel_times. */
+sph_status sph_batch_set_timing(sph_batch* b, int32_t enable);
+sph_status sph_batch_kernel_times(sph_batch* b, sph_kernel_time* out, int32_t cap, int32_t* n_out);
+
+/* Releases the batch and its device memory.  NULL is ignored. */
+void sph_batch_destroy(sph_batch* b);
+
+/* Device bytes per particle slot of a batch of the given dimension and precision (the
+ * per-cell arrays, which grow with the loaded problems' grids, come on top).  For sizing a
+ * batch or a server from the free device memory. */
+sph_status sph_batch_slot_bytes(int32_t dim, int32_t precision, int64_t* bytes_per_slot);
+
+/* ------------------------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop over two batches (2D and 3D jobs, on two CUDA
+ * streams so that their steps overlap).  The paper has no counterpart (it relaxes one problem
+ * at a time).  A job is a problem (domain, sizing, parameters) with its initial particles and
+ * an iteration limit.  sph_server_poll runs one scheduling round:
+ *   1. retire every resident job whose controller is DONE (SPH_JOB_DONE), whose iteration count
+ *      reached its max_iters (SPH_JOB_NOT_CONVERGED) or whose status word shows a non-finite
+ *      value or a particle outside the grid (SPH_JOB_FAILED): its particles are copied to host
+ *      memory and its instance and slots are freed;
+ *   2. admit queued jobs in arrival order while an instance is free and the job's particles
+ *      (rounded up to 64) fit the free slots -- a job that does not fit waits, later smaller
+ *      jobs may pass it;
+ *   3. advance every resident job by steps_per_poll steps and wait for them.
+ * A job's result does not depend on the other jobs resident with it: it equals the result of
+ * the same problem run alone through sph_mesh_run_until_converged with the same limit, as long
+ * as steps_per_poll divides the number of steps the job needs (otherwise the job runs up to
+ * steps_per_poll - 1 steps past its end, with its state frozen once it is DONE).
+ * Times are seconds since sph_server_create (host steady clock).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct sph_server sph_server;
+
+typedef enum {
+    SPH_JOB_QUEUED = 1,
+    SPH_JOB_RUNNING = 2,
+    SPH_JOB_DONE = 3,           /* both phases finished (Sec. 3.4)                              */
+    SPH_JOB_NOT_CONVERGED = 4,  /* max_iters reached first; the result is the state at that step */
+    SPH_JOB_FAILED = 5          /* non-finite value or particle outside the grid; or admission
+                                   failed for a reason other than memory                       */
+} sph_job_state;
+
+typedef struct {
+    int32_t precision;          /* 32 or 64, for every job                                       */
+    int32_t max_jobs;           /* resident jobs per dimension (1..SPH_MAX_INSTANCES)            */
+    int64_t slot_capacity[2];   /* particle slots for 2D and 3D jobs (0: no jobs of that
+                                   dimension; -1: hbm_fraction of the free device memory,
+                                   shared by the dimensions asking for it)                     */
+    double hbm_fraction;        /* used with slot_capacity -1, in (0, 1)                         */
+    int32_t steps_per_poll;     /* steps per scheduling round (20 = the paper's sample period)   */
+} sph_server_config;
+
+typedef struct {
+    int32_t state;              /* sph_job_state                                                 */
+    int32_t dim;
+    int64_t n;                  /* particles                                                     */
+    int64_t iterations;         /* steps run (at retirement)                                     */
+    int32_t phase;              /* controller phase at retirement                                */
+    uint32_t status_word;       /* device status word at retirement (sph_report.status)         */
+    int64_t escapes;
+    double E_sys;
+    double t_submit, t_admit, t_finish;
+} sph_job_info;
+
+typedef struct {
+    int64_t submitted, finished, running, queued, rounds;
+    double particle_steps;      /* sum over rounds of resident particles x steps_per_poll        */
+} sph_server_stats;
+
+/* Creates the server and allocates its batches.  Errors: SPH_E_INVALID, SPH_E_NOMEM, SPH_E_CUDA. */
+sph_status sph_server_create(const sph_server_config* cfg, sph_server** out);
+
+/* Queues a job (inputs are copied; h may be NULL for h_t(x)); job_id receives its id.
+ * Errors: SPH_E_INVALID (no capacity for its dimension, other precision, n < 1, more
+ * particles than the server's slots).  Problem descriptors are validated at admission: a job
+ * whose descriptors are invalid ends as SPH_JOB_FAILED. */
+sph_status sph_server_submit(sph_server* s, const sph_domain_desc* domain, const sph_sizing_desc* sizing,
+                             const sph_params* params, int64_t n, const double* x, const int32_t* group,
+                             const double* h, int64_t max_iters, int64_t* job_id);
+
+/* One scheduling round (see above); stats (may be NULL) receives the counters after it. */
+sph_status sph_server_poll(sph_server* s, sph_server_stats* stats);
+
+/* Polls until no job is queued or resident, at most max_rounds rounds.
+ * Errors: SPH_E_NOT_CONVERGED when work is left after max_rounds, plus those of poll. */
+sph_status sph_server_drain(sph_server* s, int64_t max_rounds, sph_server_stats* stats);
+
+/* State and timing of a job; for a finished job also its particles in submission order
+ * (x_out [n][3], group_out [n], h_out [n]; any may be NULL; capacity >= n). */
+sph_status sph_server_job(sph_server* s, int64_t job_id, sph_job_info* info, double* x_out,
+                          int32_t* group_out, double* h_out, int64_t capacity);
+
+/* Forgets a finished job (its results are freed). */
+sph_status sph_server_release(sph_server* s, int64_t job_id);
+
+void sph_server_destroy(sph_server* s);
+
+/* ------------------------------------------------------------------------------------------
  * Cell-list rebuild that allocates nothing.  The paper has no counterpart: this entry point
  * serves callers that are not allowed to allocate device memory -- for example an application
  * that reserves all of the GPU's memory for its own pool at start-up and forbids libraries from

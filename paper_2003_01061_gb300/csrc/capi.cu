@@ -1,6 +1,14 @@
 // capi.cu -- host side of libsphmesh.so: descriptor validation, the cell-grid specification,
-// device memory, the per-step launch sequence (captured once into a CUDA graph), and the
-// inspection entry points.  See include/sphmesh.h for the contract of every function.
+// the layout of a batch of instances in device memory, the per-step launch sequence (captured
+// once into a CUDA graph), and the inspection entry points.  See include/sphmesh.h for the
+// contract of every function.
+//
+// Every handle is a batch: NI independent instances, each with its own domain, sizing,
+// parameters and controller, packed into one particle array and one cell-key range.  The loaded
+// instances occupy consecutive slot ranges in index order (each its particle count rounded up
+// to CHUNK); loading or emptying an instance re-packs the others (a device-side move) and
+// re-captures the step graph.  Every kernel serves all instances in one launch.  A sph_mesh is
+// a batch of one.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -97,30 +105,52 @@ struct KTime {
 };
 const KTime kStages[4] = {{"rebuild", 6}, {"interact", 1}, {"control", 1}, {"integrate", 1}};
 
+// host copy of one instance
+struct Inst {
+    Grid grid;            // base[] and occ_base are global (set by relayout)
+    int lbase[MAXL];      // first key of each level within the instance
+    int ncell = 0;        // cells of the instance
+    int nocc = 0;         // its top-level cells
+    Params params;
+    Domain dom;
+    Sizing siz;
+    double h_lo = 0, h_hi = 0;
+    int64_t cap = 0;      // max_particles given at creation
+    int off = 0, slots = 0;   // current slot range [off, off + slots) (slots = 0 while empty)
+    int n = 0;            // particles loaded
+};
+
 }  // namespace
 
-struct sph_mesh {
-    int D = 2, prec = 32;
-    int64_t cap = 0;
-    int n = 0;
-    Grid grid;
-    Params params;
-    Domain hdom;
-    Sizing hsiz;
-    double h_lo = 0, h_hi = 0;
+struct sph_batch {
+    int D = 2, prec = 32, NI = 0;
+    std::vector<Inst> in;
+    int nslots = 0;                   // slots in use (all loaded instances)
+    int slot_cap = 0;                 // slots allocated
+    int ncell = 0, nocc = 0;          // keys (cells + one dummy key per loaded instance), top-level cells
+    size_t cell_cap = 0, occ_cap = 0; // allocated entries of the cell arrays
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;
-    void* pool = nullptr;
+    void* pool = nullptr;             // per-slot arrays
+    void* cpool = nullptr;            // per-cell arrays
     State<float> sf;
     State<double> sd;
-    Domain* d_dom = nullptr;
-    Sizing* d_siz = nullptr;
+    Grid* d_grids = nullptr;
+    Params* d_params = nullptr;
+    Domain* d_doms = nullptr;
+    Sizing* d_sizs = nullptr;
     Ctrl* d_ctrl = nullptr;
     Ctrl* d_ctrl_dbg = nullptr;
-    // CUDA graph of one step
+    int* d_inst_off = nullptr;
+    int* d_inst_n = nullptr;
+    int* d_chunk_inst = nullptr;
+    int* d_old_off = nullptr;         // re-packing: previous offsets and slots to move, per instance
+    int* d_move_n = nullptr;
+    bool mesh = false;                // created by sph_mesh_create
+    // CUDA graph of one step; rebuilt when the layout or the timing mode changes
     cudaGraphExec_t gexec = nullptr;
-    int graph_n = -1;
+    long long layout_version = 0, graph_version = -1;
     bool graph_timed = false;
     // stage timing
     bool timing = false;
@@ -130,19 +160,213 @@ struct sph_mesh {
     int64_t stage_steps = 0;
 };
 
+struct sph_mesh : sph_batch {};
+
 namespace {
 
-template <typename T> State<T>& st(sph_mesh* m);
-template <> State<float>& st<float>(sph_mesh* m) { return m->sf; }
-template <> State<double>& st<double>(sph_mesh* m) { return m->sd; }
+#define DISPATCH(b, fn, ...)                                              \
+    ((b)->prec == 32 ? ((b)->D == 2 ? fn<float, 2>(__VA_ARGS__) : fn<float, 3>(__VA_ARGS__)) \
+                     : ((b)->D == 2 ? fn<double, 2>(__VA_ARGS__) : fn<double, 3>(__VA_ARGS__)))
 
-// carve every device array out of one allocation (256-byte aligned pieces)
-template <typename T> size_t layout(sph_mesh* m, char* base, bool assign) {
-    const size_t cap = (size_t)std::max<int64_t>(m->cap, 1);
-    const size_t ncell = (size_t)m->grid.ncell;
-    const size_t nblk = (size_t)div_up((long long)cap * LPP_MAX, BLOCK);
-    const int t = m->grid.L - 1;
-    const size_t nocc = (size_t)m->grid.dims[t][0] * m->grid.dims[t][1] * m->grid.dims[t][2];
+template <typename T> State<T>& st(sph_batch* b);
+template <> State<float>& st<float>(sph_batch* b) { return b->sf; }
+template <> State<double>& st<double>(sph_batch* b) { return b->sd; }
+
+int lpp_of(int D) { return D == 2 ? Lpp<2>::v : Lpp<3>::v; }
+int vcap_of(int D) { return D == 2 ? Vcap<2>::v : Vcap<3>::v; }
+
+// Validates one instance's descriptors and fills its host copy (grid bases instance-relative).
+sph_status make_instance(const sph_domain_desc* dd, const sph_sizing_desc* sz, const sph_params* pp,
+                         int64_t max_particles, Inst& I) {
+    if (!dd || !sz || !pp) return fail(SPH_E_INVALID, "create: NULL argument");
+    if (dd->dim != 2 && dd->dim != 3) return fail(SPH_E_INVALID, "domain: dim must be 2 or 3");
+    if (dd->n_features < 1 || dd->n_features > SPH_MAX_FEATURES) return fail(SPH_E_INVALID, "domain: n_features out of range");
+    if (dd->n_holes < 0 || dd->n_holes > SPH_MAX_HOLES) return fail(SPH_E_INVALID, "domain: n_holes out of range");
+    if (dd->base != 0 && dd->base != 1) return fail(SPH_E_INVALID, "domain: base must be 0 (box) or 1 (ball)");
+    if (pp->precision != 32 && pp->precision != 64) return fail(SPH_E_INVALID, "params: precision must be 32 or 64");
+    if (!(pp->kappa > 0) || !(pp->p0 > 0) || pp->visc < 0 || !(pp->cfl_a > 0) || !(pp->cfl_v > 0) || pp->eps1 < 0 ||
+        !(pp->dt_cap > 0) || pp->dt_collapse < 0 || !(pp->threshold > 0) || pp->reset_period < 1 ||
+        pp->sample_every < 1 || pp->window < 1 || pp->ramp_len < 1)
+        return fail(SPH_E_INVALID, "params: value out of range");
+    if (max_particles < 0 || max_particles > (int64_t)1 << 30) return fail(SPH_E_INVALID, "max_particles out of range");
+    if (sz->kind < 0 || sz->kind > 2 || !(sz->lo > 0) || !(sz->hi >= sz->lo) || sz->n_ref < 0 || sz->n_ref > SPH_MAX_HOLES)
+        return fail(SPH_E_INVALID, "sizing: need kind 0..2, 0 < lo <= hi, n_ref <= %d", SPH_MAX_HOLES);
+    if (sz->kind == 0 && !(sz->a >= sz->lo && sz->a <= sz->hi)) return fail(SPH_E_INVALID, "sizing: constant h outside [lo, hi]");
+    const int D = dd->dim;
+    for (int k = 0; k < dd->n_features; ++k) {
+        const sph_feature& f = dd->features[k];
+        int want = -1;
+        switch (f.kind) {
+            case SPH_FEAT_VOLUME: want = D; break;
+            case SPH_FEAT_POINT: want = 0; break;
+            case SPH_FEAT_SEGMENT: want = 1; break;
+            case SPH_FEAT_CIRCLE: want = D == 2 ? 1 : -1; break;
+            case SPH_FEAT_RECT: want = D == 3 ? 2 : -1; break;
+            case SPH_FEAT_SPHERE: want = D == 3 ? 2 : -1; break;
+            default: break;
+        }
+        if (want < 0 || f.dim != want) return fail(SPH_E_INVALID, "feature %d: kind/dim mismatch for a %dD domain", k, D);
+        if (f.kind == SPH_FEAT_SEGMENT) {
+            const double d0 = f.geom[3] - f.geom[0], d1 = f.geom[4] - f.geom[1], d2 = f.geom[5] - f.geom[2];
+            if (!(d0 * d0 + d1 * d1 + d2 * d2 > 0)) return fail(SPH_E_INVALID, "feature %d: zero-length segment", k);
+        }
+    }
+    sph_grid_info gi;
+    sph_status r = grid_spec(D, dd->bbox_lo, dd->bbox_hi, sz->lo, sz->hi, pp->kappa, &gi);
+    if (r != SPH_OK) return r;
+    if (gi.n_cells > (int64_t)SCAN_TILE * SCAN_TILE)
+        return fail(SPH_E_INVALID, "grid: %lld cells is more than the %lld the cell scan supports", (long long)gi.n_cells,
+                    (long long)SCAN_TILE * SCAN_TILE);
+    for (int l = 0; l < gi.levels; ++l)
+        if (gi.dims[l][0] >= ((int64_t)1 << 23) || gi.dims[l][1] >= ((int64_t)1 << 14) || gi.dims[l][2] >= ((int64_t)1 << 14))
+            return fail(SPH_E_INVALID, "grid: too many cells (x < 2^23, y and z < 2^14 per level)");
+
+    I = Inst();
+    I.cap = max_particles;
+    I.h_lo = sz->lo;
+    I.h_hi = sz->hi;
+    Grid& g = I.grid;
+    std::memset(&g, 0, sizeof g);
+    g.D = D;
+    g.L = gi.levels;
+    g.c0 = gi.c0;
+    for (int a = 0; a < 3; ++a) g.origin[a] = gi.origin[a];
+    for (int l = 0; l < MAXL; ++l) {
+        g.c[l] = std::ldexp((double)gi.c0, l);
+        g.inv_c[l] = 1.0 / g.c[l];
+        g.cf[l] = (float)g.c[l];
+        g.thr[l] = gi.thr[l];
+        for (int a = 0; a < 3; ++a) g.dims[l][a] = l < gi.levels ? (int)gi.dims[l][a] : 1;
+        I.lbase[l] = l < gi.levels ? (int)gi.base[l] : (int)gi.n_cells;
+    }
+    I.ncell = (int)gi.n_cells;
+    g.ncell = I.ncell;
+    const int t = gi.levels - 1;
+    I.nocc = (int)(gi.dims[t][0] * gi.dims[t][1] * gi.dims[t][2]);
+    Params& p = I.params;
+    std::memset(&p, 0, sizeof p);
+    p.kappa = pp->kappa;
+    p.p0 = pp->p0;
+    p.visc = pp->visc;
+    p.cfl_a = pp->cfl_a;
+    p.cfl_v = pp->cfl_v;
+    p.eps1 = pp->eps1;
+    p.dt_cap = pp->dt_cap;
+    p.dt_collapse = pp->dt_collapse;
+    p.threshold = pp->threshold;
+    p.reset_period = pp->reset_period;
+    p.sample_every = pp->sample_every;
+    p.window = pp->window;
+    p.ramp_len = pp->ramp_len;
+    p.boundary_rho = pp->boundary_rho;
+    p.kappa_f = (float)p.kappa;
+    p.p0_f = (float)p.p0;
+    p.visc_f = (float)p.visc;
+    p.cfl_a_f = (float)p.cfl_a;
+    p.cfl_v_f = (float)p.cfl_v;
+    p.G = dd->n_features;
+    for (int k = 0; k < MAXF; ++k) p.gdim[k] = k < dd->n_features ? dd->features[k].dim : 0;
+    Domain& dm = I.dom;
+    std::memset(&dm, 0, sizeof dm);
+    dm.D = D;
+    dm.base = dd->base;
+    for (int a = 0; a < 3; ++a) {
+        dm.lo[a] = dd->bbox_lo[a];
+        dm.hi[a] = dd->bbox_hi[a];
+        dm.bc[a] = dd->ball_center[a];
+    }
+    dm.br = dd->ball_radius;
+    dm.nh = dd->n_holes;
+    for (int k = 0; k < dd->n_holes; ++k) {
+        for (int a = 0; a < 3; ++a) dm.hc[k][a] = dd->hole_center[k][a];
+        dm.hr[k] = dd->hole_radius[k];
+    }
+    dm.nf = dd->n_features;
+    for (int k = 0; k < dd->n_features; ++k) {
+        const sph_feature& f = dd->features[k];
+        Feat& F = dm.f[k];
+        F.kind = f.kind;
+        F.dim = f.dim;
+        for (int a = 0; a < 12; ++a) F.g[a] = f.geom[a];
+        for (int a = 0; a < 3; ++a) {
+            F.nb[a] = f.normal[a];
+            F.fnb[a] = (float)f.normal[a];
+        }
+        F.orient = f.orient;
+        F.forient = (float)f.orient;
+        if (f.kind == SPH_FEAT_SEGMENT) {
+            double ab[3] = {f.geom[3] - f.geom[0], f.geom[4] - f.geom[1], f.geom[5] - f.geom[2]};
+            double L = std::sqrt(ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2]);
+            for (int a = 0; a < 3; ++a) F.ftg[a] = (float)(ab[a] / L);
+        } else if (f.kind == SPH_FEAT_RECT) {
+            for (int a = 0; a < 3; ++a) F.ftg[a] = (float)f.normal[a];
+        }
+        if (f.kind == SPH_FEAT_CIRCLE || f.kind == SPH_FEAT_SPHERE)
+            for (int a = 0; a < 3; ++a) F.fc[a] = (float)f.geom[a];
+        if (f.kind == SPH_FEAT_CIRCLE) F.fc[2] = 0.0f;
+    }
+    Sizing& zs = I.siz;
+    std::memset(&zs, 0, sizeof zs);
+    zs.kind = sz->kind;
+    zs.a = sz->a;
+    zs.b = sz->b;
+    zs.lo = sz->lo;
+    zs.hi = sz->hi;
+    for (int a = 0; a < 3; ++a) zs.q[a] = sz->center[a];
+    zs.nref = sz->n_ref;
+    for (int k = 0; k < sz->n_ref; ++k) {
+        for (int a = 0; a < 3; ++a) zs.rc[k][a] = sz->ref_center[k][a];
+        zs.rr[k] = sz->ref_radius[k];
+    }
+    // float copies used by the FP32 evaluation of h_t and of the level set
+    zs.fa = (float)zs.a;
+    zs.fb = (float)zs.b;
+    zs.flo = (float)zs.lo;
+    zs.fhi = (float)zs.hi;
+    for (int a = 0; a < 3; ++a) zs.fq[a] = (float)zs.q[a];
+    for (int k = 0; k < MAXH; ++k) {
+        for (int a = 0; a < 3; ++a) zs.frc[k][a] = (float)zs.rc[k][a];
+        zs.frr[k] = (float)zs.rr[k];
+    }
+    for (int a = 0; a < 3; ++a) {
+        dm.flo[a] = (float)dm.lo[a];
+        dm.fhi[a] = (float)dm.hi[a];
+        dm.fbc[a] = (float)dm.bc[a];
+    }
+    dm.fbr = (float)dm.br;
+    for (int k = 0; k < MAXH; ++k) {
+        for (int a = 0; a < 3; ++a) dm.fhc[k][a] = (float)dm.hc[k][a];
+        dm.fhr[k] = (float)dm.hr[k];
+    }
+    return SPH_OK;
+}
+
+void host_ctrl_init(Ctrl* c) {
+    std::memset(c, 0, sizeof *c);
+    c->phase = PH1;
+    c->sample_now = 1;
+    c->f = 1.0;
+    c->f_f = 1.0f;
+}
+
+template <typename T> void ctrl_inf_bits(Ctrl* c) {
+    for (int g = 0; g < MAXF; ++g) {
+        c->dta_bits[g] = inf_bits<T>();
+        c->dtv_bits[g] = inf_bits<T>();
+    }
+}
+
+void ctrl_inf_bits(int prec, Ctrl* c) {
+    if (prec == 32) ctrl_inf_bits<float>(c);
+    else ctrl_inf_bits<double>(c);
+}
+
+// carve the per-slot arrays out of one allocation (256-byte aligned pieces)
+template <typename T> size_t slot_layout(sph_batch* b, char* base, bool assign) {
+    const size_t cap = (size_t)std::max(b->slot_cap, 1);
+    const size_t nlanes = cap * (size_t)lpp_of(b->D);
+    const size_t nblk = (size_t)div_up((long long)nlanes, BLOCK);
+    const size_t vcap = (size_t)vcap_of(b->D);
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         off = (off + 255) & ~(size_t)255;
@@ -170,49 +394,248 @@ template <typename T> size_t layout(sph_mesh* m, char* base, bool assign) {
     s.Ks = (int*)take(cap * 4);
     s.P = (Vec4<T>*)take(cap * sizeof(Vec4<T>));
     s.A = (Vec4<T>*)take(cap * sizeof(Vec4<T>));
-    s.count = (int*)take(ncell * 4);
-    s.cell_start = (int*)take((ncell + 1) * 4);
-    s.bsum = (int*)take((size_t)SCAN_TILE * 4);
     s.perm = (int*)take(cap * 4);
     s.sperm = (int*)take(cap * 4);
     s.partials = (double*)take(nblk * MAXF * sizeof(double));
-    s.occ = (unsigned*)take(nocc * 4);
-    const size_t nlanes = cap * LPP_MAX;
-    s.vj = (int*)take(nlanes * VCAP_MAX * 4);
-    s.vr = (T*)take(nlanes * VCAP_MAX * sizeof(T));
+    s.vj = (int*)take(nlanes * vcap * 4);
+    s.vr = (T*)take(nlanes * vcap * sizeof(T));
     s.vcnt = (int*)take(nlanes * 4);
     if (assign) {
-        s.n = 0;
-        s.nblk = 0;
-        s.nocc = (int)nocc;
-        s.ctrl = m->d_ctrl;
-        s.dom = m->d_dom;
-        s.siz = m->d_siz;
-        st<T>(m) = s;
+        s.n = b->nslots;
+        s.NI = b->NI;
+        s.nblk = div_up((long long)b->nslots * lpp_of(b->D), BLOCK);
+        s.inst_off = b->d_inst_off;
+        s.inst_n = b->d_inst_n;
+        s.chunk_inst = b->d_chunk_inst;
+        s.grids = b->d_grids;
+        s.params = b->d_params;
+        s.doms = b->d_doms;
+        s.sizs = b->d_sizs;
+        s.ctrls = b->d_ctrl;
+        st<T>(b) = s;
     }
     return off + 256;
 }
 
-void host_ctrl_init(Ctrl* c) {
-    std::memset(c, 0, sizeof *c);
-    c->phase = PH1;
-    c->sample_now = 1;
-    c->f = 1.0;
-    c->f_f = 1.0f;
+template <typename T> void set_cell_arrays(sph_batch* b) {
+    State<T>& s = st<T>(b);
+    char* base = (char*)b->cpool;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        off = (off + 255) & ~(size_t)255;
+        char* p = base + off;
+        off += bytes;
+        return p;
+    };
+    s.count = (int*)take(b->cell_cap * 4);
+    s.cell_start = (int*)take((b->cell_cap + 1) * 4);
+    s.bsum = (int*)take((size_t)SCAN_TILE * 4);
+    s.occ = (unsigned*)take(b->occ_cap * 4);
+    s.ncell = b->ncell;
+    s.nocc = b->nocc;
 }
 
-template <typename T> void ctrl_inf_bits(Ctrl* c) {
-    for (int g = 0; g < MAXF; ++g) {
-        c->dta_bits[g] = inf_bits<T>();
-        c->dtv_bits[g] = inf_bits<T>();
+template <typename T, int D> void repack(sph_batch* b) { launch_repack<T, D>(st<T>(b), b->d_old_off, b->d_move_n, b->stream); }
+template <typename T> void set_slots(sph_batch* b) {
+    State<T>& s = st<T>(b);
+    s.n = b->nslots;
+    s.nblk = div_up((long long)b->nslots * lpp_of(b->D), BLOCK);
+}
+
+// Lays the batch out again after instance `changed` gets `new_n` particles (changed < 0: no
+// count changes).  Slot ranges: the loaded instances in index order, each its count rounded up
+// to CHUNK; the stored state of every other loaded instance is moved to its new range on the
+// device.  Key ranges: each loaded instance's cells and its dummy key.  The per-cell arrays are
+// reallocated if too small and cleared (the relative scan then starts from zero counts).
+// Uploads the grids and the descriptors of instance `desc` (all instances for desc < 0).
+// Fails with SPH_E_NOMEM, changing nothing, when the slots do not fit the allocation.
+sph_status relayout(sph_batch* b, int changed, int new_n, int desc) {
+    const int NI = b->NI;
+    std::vector<int> old_off(NI), move(NI, 0), noff(NI + 1), nsl(NI), nn(NI);
+    long long total = 0;
+    for (int i = 0; i < NI; ++i) {
+        const Inst& I = b->in[i];
+        nn[i] = i == changed ? new_n : I.n;
+        nsl[i] = (nn[i] + CHUNK - 1) / CHUNK * CHUNK;
+        noff[i] = (int)total;
+        total += nsl[i];
+        old_off[i] = I.off;
+        if (i != changed && I.slots > 0 && I.off != noff[i]) move[i] = I.slots;
     }
+    noff[NI] = (int)total;
+    if (total > b->slot_cap)
+        return fail(SPH_E_NOMEM, "batch: %lld particle slots needed, %d allocated", total, b->slot_cap);
+    long long keys = 0, occ = 0;
+    for (int i = 0; i < NI; ++i)
+        if (nn[i] > 0) {
+            keys += b->in[i].ncell + 1;
+            occ += b->in[i].nocc;
+        }
+    if (keys > (long long)SCAN_TILE * SCAN_TILE)
+        return fail(SPH_E_INVALID, "batch: %lld cell keys is more than the %lld the cell scan supports", keys,
+                    (long long)SCAN_TILE * SCAN_TILE);
+    if (!b->cpool || (size_t)keys > b->cell_cap || (size_t)occ > b->occ_cap) {
+        const size_t kc = std::max({(size_t)keys, b->cell_cap, (size_t)1});
+        const size_t oc = std::max({(size_t)occ, b->occ_cap, (size_t)1});
+        const size_t bytes = kc * 4 + (kc + 1) * 4 + (size_t)SCAN_TILE * 4 + oc * 4 + 4 * 256;
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess)
+            return fail(SPH_E_NOMEM, "device allocation of %zu bytes of cell arrays failed", bytes);
+        if (b->cpool) {
+            CK(cudaStreamSynchronize(b->stream));
+            cudaFree(b->cpool);
+        }
+        b->cpool = p;
+        b->cell_cap = kc;
+        b->occ_cap = oc;
+    }
+    // slots: chunk table, offsets, counts; then the moves
+    std::vector<int> chunk((size_t)(total / CHUNK));
+    for (int i = 0; i < NI; ++i)
+        for (int c = noff[i] / CHUNK; c < (noff[i] + nsl[i]) / CHUNK; ++c) chunk[c] = i;
+    if (!chunk.empty())
+        CK(cudaMemcpyAsync(b->d_chunk_inst, chunk.data(), 4 * chunk.size(), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->d_inst_off, noff.data(), 4 * (size_t)(NI + 1), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->d_inst_n, nn.data(), 4 * (size_t)NI, cudaMemcpyHostToDevice, b->stream));
+    b->nslots = (int)total;
+    if (b->prec == 32) set_slots<float>(b);
+    else set_slots<double>(b);
+    if (std::any_of(move.begin(), move.end(), [](int v) { return v > 0; })) {
+        CK(cudaMemcpyAsync(b->d_old_off, old_off.data(), 4 * (size_t)NI, cudaMemcpyHostToDevice, b->stream));
+        CK(cudaMemcpyAsync(b->d_move_n, move.data(), 4 * (size_t)NI, cudaMemcpyHostToDevice, b->stream));
+        DISPATCH(b, repack, b);
+        CK(cudaGetLastError());
+    }
+    for (int i = 0; i < NI; ++i) {
+        Inst& I = b->in[i];
+        I.off = noff[i];
+        I.slots = nsl[i];
+        I.n = nn[i];
+    }
+    // keys
+    long long kb = 0, ob = 0;
+    for (Inst& I : b->in) {
+        const bool loaded = I.n > 0;
+        for (int l = 0; l < MAXL; ++l) I.grid.base[l] = (int)kb + (loaded ? I.lbase[l] : 0);
+        I.grid.base[MAXL] = (int)kb + (loaded ? I.ncell : 0);   // the instance's dummy key (padding slots)
+        I.grid.ncell = loaded ? I.ncell : 0;
+        I.grid.occ_base = (int)ob;
+        if (loaded) {
+            kb += I.ncell + 1;
+            ob += I.nocc;
+        }
+    }
+    b->ncell = (int)keys;
+    b->nocc = (int)occ;
+    if (b->prec == 32) set_cell_arrays<float>(b);
+    else set_cell_arrays<double>(b);
+    const State<float>& sf = b->sf;
+    const State<double>& sd = b->sd;
+    CK(cudaMemsetAsync(b->prec == 32 ? sf.count : sd.count, 0, (size_t)std::max<long long>(keys, 1) * 4, b->stream));
+    CK(cudaMemsetAsync(b->prec == 32 ? sf.cell_start : sd.cell_start, 0, (size_t)(keys + 1) * 4, b->stream));
+    CK(cudaMemsetAsync(b->prec == 32 ? sf.occ : sd.occ, 0, (size_t)std::max<long long>(occ, 1) * 4, b->stream));
+    std::vector<Grid> g(NI);
+    for (int i = 0; i < NI; ++i) g[i] = b->in[i].grid;
+    CK(cudaMemcpyAsync(b->d_grids, g.data(), sizeof(Grid) * NI, cudaMemcpyHostToDevice, b->stream));
+    std::vector<Params> p;
+    std::vector<Domain> d;
+    std::vector<Sizing> z;
+    const int d0 = desc < 0 ? 0 : desc, d1 = desc < 0 ? NI : desc + 1;
+    for (int i = d0; i < d1; ++i) {
+        p.push_back(b->in[i].params);
+        d.push_back(b->in[i].dom);
+        z.push_back(b->in[i].siz);
+    }
+    const size_t nd = (size_t)(d1 - d0);
+    CK(cudaMemcpyAsync(b->d_params + d0, p.data(), sizeof(Params) * nd, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->d_doms + d0, d.data(), sizeof(Domain) * nd, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->d_sizs + d0, z.data(), sizeof(Sizing) * nd, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));   // the host vectors above go out of scope
+    b->layout_version += 1;
+    return SPH_OK;
 }
 
-template <typename T, int D> void enqueue_rebuild(sph_mesh* m, const State<T>& s, cudaStream_t stream) {
-    launch_hash<T, D>(m->grid, s, stream);
-    launch_scan(m->grid.ncell, s.count, s.cell_start, s.bsum, stream, s.occ, s.nocc, true);
+void batch_free(sph_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (int k = 0; k < 5; ++k)
+        if (b->ev[k]) cudaEventDestroy(b->ev[k]);
+    cudaFree(b->pool);
+    cudaFree(b->cpool);
+    cudaFree(b->d_grids);
+    cudaFree(b->d_params);
+    cudaFree(b->d_doms);
+    cudaFree(b->d_sizs);
+    cudaFree(b->d_ctrl);
+    cudaFree(b->d_ctrl_dbg);
+    cudaFree(b->d_inst_off);
+    cudaFree(b->d_inst_n);
+    cudaFree(b->d_chunk_inst);
+    cudaFree(b->d_old_off);
+    cudaFree(b->d_move_n);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+// Device side of a batch whose host instances are filled in: allocations for the sum of the
+// instances' max_particles (each rounded up to CHUNK), descriptors, every instance empty.
+sph_status batch_init(sph_batch* b, void* stream) {
+    b->NI = (int)b->in.size();
+    long long cap = 0;
+    for (Inst& I : b->in) {
+        I.off = 0;
+        I.slots = 0;
+        I.n = 0;
+        cap += std::max<int64_t>(CHUNK, (I.cap + CHUNK - 1) / CHUNK * CHUNK);
+    }
+    if (cap * 12 >= ((long long)1 << 31))   // lane-indexed arrays hold slots * LPP * VCAP entries
+        return fail(SPH_E_INVALID, "batch: %lld particle slots in total is too many", cap);
+    b->slot_cap = (int)cap;
+    b->nslots = 0;
+    if (cudaGetDevice(&b->device) != cudaSuccess) return fail(SPH_E_CUDA, "no CUDA device");
+    if (stream) b->stream = (cudaStream_t)stream;
+    else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(SPH_E_CUDA, "cudaStreamCreate failed");
+        b->own_stream = true;
+    }
+    const int NI = b->NI;
+    if (cudaMalloc(&b->d_grids, sizeof(Grid) * NI) != cudaSuccess ||
+        cudaMalloc(&b->d_params, sizeof(Params) * NI) != cudaSuccess ||
+        cudaMalloc(&b->d_doms, sizeof(Domain) * NI) != cudaSuccess ||
+        cudaMalloc(&b->d_sizs, sizeof(Sizing) * NI) != cudaSuccess ||
+        cudaMalloc(&b->d_ctrl, sizeof(Ctrl) * NI) != cudaSuccess ||
+        cudaMalloc(&b->d_ctrl_dbg, sizeof(Ctrl) * NI) != cudaSuccess ||
+        cudaMalloc(&b->d_inst_off, sizeof(int) * (NI + 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_inst_n, sizeof(int) * NI) != cudaSuccess ||
+        cudaMalloc(&b->d_old_off, sizeof(int) * NI) != cudaSuccess ||
+        cudaMalloc(&b->d_move_n, sizeof(int) * NI) != cudaSuccess ||
+        cudaMalloc(&b->d_chunk_inst, sizeof(int) * (size_t)(b->slot_cap / CHUNK)) != cudaSuccess)
+        return fail(SPH_E_NOMEM, "device allocation of descriptors failed");
+    const size_t bytes = b->prec == 32 ? slot_layout<float>(b, nullptr, false) : slot_layout<double>(b, nullptr, false);
+    if (cudaMalloc(&b->pool, bytes) != cudaSuccess)
+        return fail(SPH_E_NOMEM, "device allocation of %zu bytes failed", bytes);
+    if (b->prec == 32) slot_layout<float>(b, (char*)b->pool, true);
+    else slot_layout<double>(b, (char*)b->pool, true);
+    CK(cudaMemsetAsync(b->pool, 0, bytes, b->stream));
+    std::vector<Ctrl> c(NI);
+    for (int i = 0; i < NI; ++i) {
+        host_ctrl_init(&c[i]);
+        ctrl_inf_bits(b->prec, &c[i]);
+    }
+    CK(cudaMemcpyAsync(b->d_ctrl, c.data(), sizeof(Ctrl) * NI, cudaMemcpyHostToDevice, b->stream));
+    sph_status r = relayout(b, -1, 0, -1);   // synchronises the stream
+    if (r != SPH_OK) return r;
+    for (int k = 0; k < 5; ++k)
+        if (cudaEventCreate(&b->ev[k]) != cudaSuccess) return fail(SPH_E_CUDA, "cudaEventCreate failed");
+    return SPH_OK;
+}
+
+template <typename T, int D> void enqueue_rebuild(const State<T>& s, cudaStream_t stream) {
+    launch_hash<T, D>(s, stream);
+    launch_scan(s.ncell, s.count, s.cell_start, s.bsum, stream, s.occ, s.nocc, true);
     launch_scatter<T>(s, stream);
-    launch_gather<T, D>(m->grid, s, stream);
+    launch_gather<T, D>(s, stream);
 }
 
 template <typename T> Out<T> out_stored(const State<T>& s) {
@@ -229,192 +652,242 @@ template <typename T> Out<T> out_stored(const State<T>& s) {
     return o;
 }
 
-template <typename T, int D> void enqueue_step(sph_mesh* m, bool timed) {
-    const State<T>& s = st<T>(m);
-    cudaStream_t stream = m->stream;
-    if (timed) cudaEventRecordWithFlags(m->ev[0], stream, cudaEventRecordExternal);
-    enqueue_rebuild<T, D>(m, s, stream);
-    if (timed) cudaEventRecordWithFlags(m->ev[1], stream, cudaEventRecordExternal);
-    launch_interact<T, D>(m->grid, m->params, s, nullptr, nullptr, stream);
-    if (timed) cudaEventRecordWithFlags(m->ev[2], stream, cudaEventRecordExternal);
-    launch_control<T>(m->params, s, stream);
-    if (timed) cudaEventRecordWithFlags(m->ev[3], stream, cudaEventRecordExternal);
-    launch_integrate<T, D>(m->grid, m->params, s, s.ctrl, out_stored<T>(s), stream);
-    if (timed) cudaEventRecordWithFlags(m->ev[4], stream, cudaEventRecordExternal);
+template <typename T, int D> void enqueue_step(sph_batch* b, bool timed) {
+    const State<T>& s = st<T>(b);
+    cudaStream_t stream = b->stream;
+    if (timed) cudaEventRecordWithFlags(b->ev[0], stream, cudaEventRecordExternal);
+    enqueue_rebuild<T, D>(s, stream);
+    if (timed) cudaEventRecordWithFlags(b->ev[1], stream, cudaEventRecordExternal);
+    launch_interact<T, D>(s, nullptr, nullptr, stream);
+    if (timed) cudaEventRecordWithFlags(b->ev[2], stream, cudaEventRecordExternal);
+    launch_control<T, D>(s, stream);
+    if (timed) cudaEventRecordWithFlags(b->ev[3], stream, cudaEventRecordExternal);
+    launch_integrate<T, D>(s, s.ctrls, out_stored<T>(s), stream);
+    if (timed) cudaEventRecordWithFlags(b->ev[4], stream, cudaEventRecordExternal);
 }
 
-sph_status collect_timing(sph_mesh* m) {
-    if (!m->ev_pending) return SPH_OK;
-    CK(cudaEventSynchronize(m->ev[4]));
+sph_status collect_timing(sph_batch* b) {
+    if (!b->ev_pending) return SPH_OK;
+    CK(cudaEventSynchronize(b->ev[4]));
     for (int k = 0; k < 4; ++k) {
         float ms = 0;
-        CK(cudaEventElapsedTime(&ms, m->ev[k], m->ev[k + 1]));
-        m->stage_ms[k] += ms;
+        CK(cudaEventElapsedTime(&ms, b->ev[k], b->ev[k + 1]));
+        b->stage_ms[k] += ms;
     }
-    m->stage_steps += 1;
-    m->ev_pending = false;
+    b->stage_steps += 1;
+    b->ev_pending = false;
     return SPH_OK;
 }
 
-template <typename T, int D> sph_status build_graph(sph_mesh* m) {
-    if (m->gexec) {
-        cudaGraphExecDestroy(m->gexec);
-        m->gexec = nullptr;
+template <typename T, int D> sph_status build_graph(sph_batch* b) {
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
     }
     cudaGraph_t graph;
-    CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_step<T, D>(m, m->timing);
-    cudaError_t e = cudaStreamEndCapture(m->stream, &graph);
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_step<T, D>(b, b->timing);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
     if (e != cudaSuccess) return fail(SPH_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&m->gexec, graph, 0);
+    e = cudaGraphInstantiate(&b->gexec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(SPH_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    m->graph_n = m->n;
-    m->graph_timed = m->timing;
+    b->graph_version = b->layout_version;
+    b->graph_timed = b->timing;
     return SPH_OK;
 }
 
-template <typename T, int D> sph_status step_impl(sph_mesh* m, int32_t n_steps) {
-    if (m->n == 0) return SPH_OK;
-    CK(cudaSetDevice(m->device));
-    if (!m->gexec || m->graph_n != m->n || m->graph_timed != m->timing) {
-        sph_status r = build_graph<T, D>(m);
+template <typename T, int D> sph_status step_impl(sph_batch* b, int32_t n_steps) {
+    if (b->nslots == 0) return SPH_OK;   // nothing loaded
+    CK(cudaSetDevice(b->device));
+    if (!b->gexec || b->graph_version != b->layout_version || b->graph_timed != b->timing) {
+        sph_status r = build_graph<T, D>(b);
         if (r != SPH_OK) return r;
     }
     for (int i = 0; i < n_steps; ++i) {
-        if (m->timing) {
-            sph_status r = collect_timing(m);
+        if (b->timing) {
+            sph_status r = collect_timing(b);
             if (r != SPH_OK) return r;
         }
-        CK(cudaGraphLaunch(m->gexec, m->stream));
-        if (m->timing) m->ev_pending = true;
+        CK(cudaGraphLaunch(b->gexec, b->stream));
+        if (b->timing) b->ev_pending = true;
     }
     return SPH_OK;
 }
 
-#define DISPATCH(m, fn, ...)                                              \
-    ((m)->prec == 32 ? ((m)->D == 2 ? fn<float, 2>(__VA_ARGS__) : fn<float, 3>(__VA_ARGS__)) \
-                     : ((m)->D == 2 ? fn<double, 2>(__VA_ARGS__) : fn<double, 3>(__VA_ARGS__)))
 
-// state in device memory -> host arrays in original order (from an Out-like set of arrays)
+// one instance's slots in device memory -> host arrays in its original order (arrays indexed
+// by global slot; the instance's range is read)
 template <typename T>
-sph_status download(sph_mesh* m, int* const Cd[3], T* const Od[3], T* const V[3], T* H, unsigned* G, int* ID,
-                    double* x_out, int32_t* group_out, double* v_out, double* h_out) {
-    const int n = m->n, D = m->D;
-    std::vector<int> id(n);
-    CK(cudaMemcpyAsync(id.data(), ID, sizeof(int) * n, cudaMemcpyDeviceToHost, m->stream));
-    std::vector<int> cs(x_out ? (size_t)n * 3 : 0);
-    std::vector<T> os(x_out ? (size_t)n * 3 : 0);
-    std::vector<T> vs(v_out ? (size_t)n * 3 : 0), hs(h_out ? n : 0);
-    std::vector<unsigned> gs(group_out ? n : 0);
+sph_status download(sph_batch* b, int inst, int* const Cd[3], T* const Od[3], T* const V[3], T* H, unsigned* G,
+                    int* ID, double* x_out, int32_t* group_out, double* v_out, double* h_out) {
+    const Inst& I = b->in[inst];
+    const int ns = I.slots, o0 = I.off, n = I.n, D = b->D;
+    std::vector<int> id(ns);
+    CK(cudaMemcpyAsync(id.data(), ID + o0, sizeof(int) * ns, cudaMemcpyDeviceToHost, b->stream));
+    std::vector<int> cs(x_out ? (size_t)ns * 3 : 0);
+    std::vector<T> os(x_out ? (size_t)ns * 3 : 0);
+    std::vector<T> vs(v_out ? (size_t)ns * 3 : 0), hs(h_out ? ns : 0);
+    std::vector<unsigned> gs(group_out ? ns : 0);
     for (int a = 0; a < D; ++a) {
         if (x_out) {
-            CK(cudaMemcpyAsync(cs.data() + (size_t)a * n, Cd[a], sizeof(int) * n, cudaMemcpyDeviceToHost, m->stream));
-            CK(cudaMemcpyAsync(os.data() + (size_t)a * n, Od[a], sizeof(T) * n, cudaMemcpyDeviceToHost, m->stream));
+            CK(cudaMemcpyAsync(cs.data() + (size_t)a * ns, Cd[a] + o0, sizeof(int) * ns, cudaMemcpyDeviceToHost, b->stream));
+            CK(cudaMemcpyAsync(os.data() + (size_t)a * ns, Od[a] + o0, sizeof(T) * ns, cudaMemcpyDeviceToHost, b->stream));
         }
-        if (v_out) CK(cudaMemcpyAsync(vs.data() + (size_t)a * n, V[a], sizeof(T) * n, cudaMemcpyDeviceToHost, m->stream));
+        if (v_out) CK(cudaMemcpyAsync(vs.data() + (size_t)a * ns, V[a] + o0, sizeof(T) * ns, cudaMemcpyDeviceToHost, b->stream));
     }
-    // FP64 position = origin + cell * c0 + offset
-    std::vector<double> xs(x_out ? (size_t)n * 3 : 0);
-    for (int a = 0; x_out && a < D; ++a)
-        for (int k = 0; k < n; ++k)
-            xs[(size_t)a * n + k] = ((double)m->grid.origin[a] + (double)cs[(size_t)a * n + k] * m->grid.c[0]) +
-                                    (double)os[(size_t)a * n + k];
-    if (h_out) CK(cudaMemcpyAsync(hs.data(), H, sizeof(T) * n, cudaMemcpyDeviceToHost, m->stream));
-    if (group_out) CK(cudaMemcpyAsync(gs.data(), G, sizeof(unsigned) * n, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
-    for (int k = 0; k < n; ++k) {
+    if (h_out) CK(cudaMemcpyAsync(hs.data(), H + o0, sizeof(T) * ns, cudaMemcpyDeviceToHost, b->stream));
+    if (group_out) CK(cudaMemcpyAsync(gs.data(), G + o0, sizeof(unsigned) * ns, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    const Grid& g = I.grid;
+    int seen = 0;
+    for (int k = 0; k < ns; ++k) {
         const int i = id[k];
-        if (i < 0 || i >= n) return fail(SPH_E_CUDA, "corrupt particle index on the device");
+        if (i < 0) continue;   // padding
+        if (i >= n) return fail(SPH_E_CUDA, "corrupt particle index on the device");
+        ++seen;
         for (int a = 0; a < 3; ++a) {
-            if (x_out) x_out[(size_t)i * 3 + a] = a < D ? xs[(size_t)a * n + k] : 0.0;
-            if (v_out) v_out[(size_t)i * 3 + a] = a < D ? (double)vs[(size_t)a * n + k] : 0.0;
+            // FP64 position = origin + cell * c0 + offset
+            if (x_out)
+                x_out[(size_t)i * 3 + a] =
+                    a < D ? ((double)g.origin[a] + (double)cs[(size_t)a * ns + k] * g.c[0]) + (double)os[(size_t)a * ns + k]
+                          : 0.0;
+            if (v_out) v_out[(size_t)i * 3 + a] = a < D ? (double)vs[(size_t)a * ns + k] : 0.0;
         }
         if (h_out) h_out[i] = (double)hs[k];
         if (group_out) group_out[i] = (int32_t)(gs[k] & 63u);
     }
+    if (seen != n) return fail(SPH_E_CUDA, "corrupt particle index on the device");
     return SPH_OK;
 }
 
-template <typename T, int D> sph_status set_state_impl(sph_mesh* m, int64_t n, const double* x, const int32_t* group,
-                                                       const double* v, const double* h) {
-    State<T>& s = st<T>(m);
+sph_status check_args(const sph_batch* b, int inst, int64_t n, const double* x, const int32_t* group, const double* v,
+                      const double* h) {
+    const Inst& I = b->in[inst];
+    const int64_t cap = b->mesh ? I.cap : (int64_t)b->slot_cap;
+    if (n < 0 || n > cap) return fail(SPH_E_INVALID, "set_state: n=%lld outside [0, %lld]", (long long)n, (long long)cap);
+    if (n > 0 && (!x || !group)) return fail(SPH_E_INVALID, "set_state: x and group are required");
+    const int D = b->D;
+    for (int64_t i = 0; i < n; ++i) {
+        if (group[i] < 0 || group[i] >= I.params.G)
+            return fail(SPH_E_INVALID, "set_state: particle %lld has group %d", (long long)i, group[i]);
+        for (int a = 0; a < D; ++a) {
+            const double xa = x[i * 3 + a], lo = I.dom.lo[a], hi = I.dom.hi[a];
+            if (!(xa >= lo - 1e-9 * (1 + std::fabs(lo)) && xa <= hi + 1e-9 * (1 + std::fabs(hi))))
+                return fail(SPH_E_INVALID, "set_state: particle %lld outside the bounding box", (long long)i);
+        }
+        // the grid's top level covers kappa*h_hi*(1+2^-10); allow h up to h_hi*(1+2^-11) so that
+        // values rounded to the working precision are accepted
+        if (h && !(h[i] > 0 && h[i] <= I.h_hi * (1 + 1.0 / 2048.0)))
+            return fail(SPH_E_INVALID, "set_state: h of particle %lld outside [lo, hi]", (long long)i);
+        if (v)
+            for (int a = 0; a < D; ++a)
+                if (!std::isfinite(v[i * 3 + a])) return fail(SPH_E_INVALID, "set_state: non-finite velocity");
+    }
+    return SPH_OK;
+}
+
+// Loads one instance's particles into its slots (live first, padding after) and resets its
+// controller: Phase One at step 0, or, for an empty batch instance, the idle state DONE.
+template <typename T, int D> sph_status set_state_impl(sph_batch* b, int inst, int64_t n, const double* x,
+                                                       const int32_t* group, const double* v, const double* h,
+                                                       bool idle_when_empty) {
+    State<T>& s = st<T>(b);
+    Inst& I = b->in[inst];
     const int nn = (int)n;
-    std::vector<int> cs((size_t)std::max(nn, 1) * 3);
-    std::vector<T> os((size_t)std::max(nn, 1) * 3), vs((size_t)std::max(nn, 1) * 3, T(0)), hs(std::max(nn, 1));
-    std::vector<unsigned> gs(std::max(nn, 1));
-    std::vector<int> ids(std::max(nn, 1));
-    const double c0 = m->grid.c[0], inv_c0 = m->grid.inv_c[0];
+    CK(cudaSetDevice(b->device));
+    sph_status r = relayout(b, inst, nn, inst);   // makes room (moving the other instances)
+    if (r != SPH_OK) return r;
+    const int ns = I.slots, o0 = I.off;
+    std::vector<int> cs((size_t)ns * 3, 0);
+    std::vector<T> os((size_t)ns * 3, T(0)), vs((size_t)ns * 3, T(0)), hs(ns, T(0));
+    std::vector<unsigned> gs(ns, 0u);
+    std::vector<int> ids(ns, -1);
+    const Grid& g = I.grid;
+    const double c0 = g.c[0], inv_c0 = g.inv_c[0];
     for (int i = 0; i < nn; ++i) {
         const int gi = group[i];
         for (int a = 0; a < D; ++a) {
             // finest cell and offset: c = floor((x - origin) * (1/c0)), o = (x - origin) - c*c0
-            const double rel = x[(size_t)i * 3 + a] - (double)m->grid.origin[a];
+            const double rel = x[(size_t)i * 3 + a] - (double)g.origin[a];
             double t = std::floor(rel * inv_c0);
             int ca = (int)std::fmax(std::fmin(t, 2.0e9), -2.0e9);
-            ca = std::min(std::max(ca, 0), m->grid.dims[0][a] - 1);
-            cs[(size_t)a * nn + i] = ca;
-            os[(size_t)a * nn + i] = (T)(rel - (double)ca * c0);
-            if (v) vs[(size_t)a * nn + i] = (T)v[(size_t)i * 3 + a];
+            ca = std::min(std::max(ca, 0), g.dims[0][a] - 1);
+            cs[(size_t)a * ns + i] = ca;
+            os[(size_t)a * ns + i] = (T)(rel - (double)ca * c0);
+            if (v) vs[(size_t)a * ns + i] = (T)v[(size_t)i * 3 + a];
         }
         if (h) hs[i] = (T)h[i];
-        gs[i] = (unsigned)gi | ((unsigned)m->hdom.f[gi].dim << 6);
+        gs[i] = (unsigned)gi | ((unsigned)I.dom.f[gi].dim << 6);
         ids[i] = i;
     }
-    CK(cudaSetDevice(m->device));
     for (int a = 0; a < D; ++a) {
-        CK(cudaMemcpyAsync(s.C[a], cs.data() + (size_t)a * nn, sizeof(int) * nn, cudaMemcpyHostToDevice, m->stream));
-        CK(cudaMemcpyAsync(s.O[a], os.data() + (size_t)a * nn, sizeof(T) * nn, cudaMemcpyHostToDevice, m->stream));
-        CK(cudaMemcpyAsync(s.V[a], vs.data() + (size_t)a * nn, sizeof(T) * nn, cudaMemcpyHostToDevice, m->stream));
+        CK(cudaMemcpyAsync(s.C[a] + o0, cs.data() + (size_t)a * ns, sizeof(int) * ns, cudaMemcpyHostToDevice, b->stream));
+        CK(cudaMemcpyAsync(s.O[a] + o0, os.data() + (size_t)a * ns, sizeof(T) * ns, cudaMemcpyHostToDevice, b->stream));
+        CK(cudaMemcpyAsync(s.V[a] + o0, vs.data() + (size_t)a * ns, sizeof(T) * ns, cudaMemcpyHostToDevice, b->stream));
     }
-    CK(cudaMemcpyAsync(s.G, gs.data(), 4 * (size_t)nn, cudaMemcpyHostToDevice, m->stream));
-    CK(cudaMemcpyAsync(s.ID, ids.data(), 4 * (size_t)nn, cudaMemcpyHostToDevice, m->stream));
-    s.n = nn;
-    s.nblk = div_up((long long)nn * Lpp<D>::v, BLOCK);   // blocks of the pair passes
-    m->n = nn;
-    if (h) CK(cudaMemcpyAsync(s.H, hs.data(), sizeof(T) * nn, cudaMemcpyHostToDevice, m->stream));
-    else if (nn > 0) launch_init_h<T, D>(m->grid, s, m->stream);
+    CK(cudaMemcpyAsync(s.G + o0, gs.data(), 4 * (size_t)ns, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(s.ID + o0, ids.data(), 4 * (size_t)ns, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(s.H + o0, hs.data(), sizeof(T) * ns, cudaMemcpyHostToDevice, b->stream));
+    if (!h && nn > 0) launch_init_h<T, D>(s, inst, b->stream);
     Ctrl c;
     host_ctrl_init(&c);
     ctrl_inf_bits<T>(&c);
-    CK(cudaMemcpyAsync(m->d_ctrl, &c, sizeof c, cudaMemcpyHostToDevice, m->stream));
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(m->stream));
-    m->stage_steps = 0;
-    for (double& t : m->stage_ms) t = 0;
-    m->ev_pending = false;
-    return SPH_OK;
-}
-
-// a copy of the state whose controller is the scratch controller (inspection calls never
-// touch the real controller)
-template <typename T> sph_status dbg_state(sph_mesh* m, State<T>& out, const Ctrl* init) {
-    out = st<T>(m);
-    Ctrl c;
-    if (init) c = *init;
-    else {
-        CK(cudaMemcpyAsync(&c, m->d_ctrl, sizeof c, cudaMemcpyDeviceToHost, m->stream));
-        CK(cudaStreamSynchronize(m->stream));
+    if (nn == 0 && idle_when_empty) {
+        c.phase = PH_DONE;
+        c.sample_now = 0;
+        c.f = 0.0;
+        c.f_f = 0.0f;
     }
-    ctrl_inf_bits<T>(&c);
-    c.sample_now = 0;
-    CK(cudaMemcpyAsync(m->d_ctrl_dbg, &c, sizeof c, cudaMemcpyHostToDevice, m->stream));
-    out.ctrl = m->d_ctrl_dbg;
+    CK(cudaMemcpyAsync(b->d_ctrl + inst, &c, sizeof c, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(b->stream));
+    b->stage_steps = 0;
+    for (double& t : b->stage_ms) t = 0;
+    b->ev_pending = false;
     return SPH_OK;
 }
 
-template <typename T, int D> sph_status dbg_rebuild_impl(sph_mesh* m, int64_t* key_out, int64_t* cs_out, int64_t* perm_out) {
-    State<T> s;
-    sph_status r = dbg_state<T>(m, s, nullptr);
+// a copy of the state whose controllers are the scratch controllers (inspection calls never
+// touch the real ones)
+template <typename T> sph_status dbg_state(sph_batch* b, State<T>& out, const Ctrl* init) {
+    out = st<T>(b);
+    std::vector<Ctrl> c(b->NI);
+    if (init) std::fill(c.begin(), c.end(), *init);
+    else {
+        CK(cudaMemcpyAsync(c.data(), b->d_ctrl, sizeof(Ctrl) * b->NI, cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+    }
+    for (Ctrl& x : c) {
+        ctrl_inf_bits<T>(&x);
+        x.sample_now = 0;
+        if (!init && x.phase == PH_DONE) x.phase = PH2;   // inspect a converged state as well
+    }
+    CK(cudaMemcpyAsync(b->d_ctrl_dbg, c.data(), sizeof(Ctrl) * b->NI, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    out.ctrls = b->d_ctrl_dbg;
+    return SPH_OK;
+}
+
+template <typename T, int D> sph_status dbg_prepare(sph_batch* b, State<T>& s, const Ctrl* init) {
+    sph_status r = dbg_state<T>(b, s, init);
     if (r != SPH_OK) return r;
-    const int n = m->n, nc = m->grid.ncell;
-    enqueue_rebuild<T, D>(m, s, m->stream);     // the same kernels as a step's rebuild
+    enqueue_rebuild<T, D>(s, b->stream);
     CK(cudaGetLastError());
+    return SPH_OK;
+}
+
+// The inspection entry points serve a mesh (a batch of one: instance 0, slots from 0).
+template <typename T, int D> sph_status dbg_rebuild_impl(sph_batch* b, int64_t* key_out, int64_t* cs_out, int64_t* perm_out) {
+    State<T> s;
+    sph_status r = dbg_prepare<T, D>(b, s, nullptr);
+    if (r != SPH_OK) return r;
+    const int n = b->in[0].n, nc = b->in[0].ncell;
     std::vector<int> k(n), cs(nc + 1), p(n);
-    CK(cudaMemcpyAsync(k.data(), s.K, 4 * (size_t)n, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaMemcpyAsync(cs.data(), s.cell_start, 4 * (size_t)(nc + 1), cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaMemcpyAsync(p.data(), s.sperm, 4 * (size_t)n, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
+    CK(cudaMemcpyAsync(k.data(), s.K, 4 * (size_t)n, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(cs.data(), s.cell_start, 4 * (size_t)(nc + 1), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(p.data(), s.sperm, 4 * (size_t)n, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
     for (int i = 0; i < n; ++i) {
         if (key_out) key_out[i] = k[i];
         if (perm_out) perm_out[i] = p[i];
@@ -424,50 +897,44 @@ template <typename T, int D> sph_status dbg_rebuild_impl(sph_mesh* m, int64_t* k
     return SPH_OK;
 }
 
-template <typename T, int D> sph_status dbg_prepare(sph_mesh* m, State<T>& s, const Ctrl* init) {
-    sph_status r = dbg_state<T>(m, s, init);
-    if (r != SPH_OK) return r;
-    enqueue_rebuild<T, D>(m, s, m->stream);
-    CK(cudaGetLastError());
-    return SPH_OK;
-}
-
 template <typename T, int D>
-sph_status dbg_neighbors_impl(sph_mesh* m, int32_t mode, int64_t* counts_out, int32_t* lists_out, int64_t cap,
+sph_status dbg_neighbors_impl(sph_batch* b, int32_t mode, int64_t* counts_out, int32_t* lists_out, int64_t cap,
                               int64_t* total_out) {
     State<T> s;
-    sph_status r = dbg_prepare<T, D>(m, s, nullptr);
+    sph_status r = dbg_prepare<T, D>(b, s, nullptr);
     if (r != SPH_OK) return r;
-    const int n = m->n;
+    const int ns = s.n, n = b->in[0].n;
     int* d_counts = nullptr;
     long long* d_off = nullptr;
     int* d_lists = nullptr;
-    CK(cudaMalloc(&d_counts, 4 * (size_t)std::max(n, 1)));
-    launch_neighbors<T, D>(m->grid, m->params, s, mode, d_counts, nullptr, nullptr, m->stream);
-    std::vector<int> cnt(n), ids(n);
-    CK(cudaMemcpyAsync(cnt.data(), d_counts, 4 * (size_t)n, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaMemcpyAsync(ids.data(), s.IDs, 4 * (size_t)n, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
-    std::vector<long long> off(n + 1, 0);
-    for (int k = 0; k < n; ++k) off[k + 1] = off[k] + cnt[k];
-    const long long total = off[n];
-    CK(cudaMalloc(&d_off, sizeof(long long) * (size_t)(n + 1)));
+    CK(cudaMalloc(&d_counts, 4 * (size_t)std::max(ns, 1)));
+    launch_neighbors<T, D>(s, mode, d_counts, nullptr, nullptr, b->stream);
+    std::vector<int> cnt(ns), ids(ns);
+    CK(cudaMemcpyAsync(cnt.data(), d_counts, 4 * (size_t)ns, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(ids.data(), s.IDs, 4 * (size_t)ns, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    std::vector<long long> off(ns + 1, 0);
+    for (int k = 0; k < ns; ++k) off[k + 1] = off[k] + cnt[k];
+    const long long total = off[ns];
+    CK(cudaMalloc(&d_off, sizeof(long long) * (size_t)(ns + 1)));
     CK(cudaMalloc(&d_lists, 4 * (size_t)std::max<long long>(total, 1)));
-    CK(cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * (size_t)(n + 1), cudaMemcpyHostToDevice, m->stream));
-    launch_neighbors<T, D>(m->grid, m->params, s, mode, d_counts, d_off, d_lists, m->stream);
+    CK(cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * (size_t)(ns + 1), cudaMemcpyHostToDevice, b->stream));
+    launch_neighbors<T, D>(s, mode, d_counts, d_off, d_lists, b->stream);
     std::vector<int> lists((size_t)std::max<long long>(total, 1));
-    CK(cudaMemcpyAsync(lists.data(), d_lists, 4 * (size_t)total, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
+    CK(cudaMemcpyAsync(lists.data(), d_lists, 4 * (size_t)total, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
     cudaFree(d_counts);
     cudaFree(d_off);
     cudaFree(d_lists);
     // regroup by original index, map sorted slots to original indices, ascending
-    std::vector<int> slot_of(n);
-    for (int k = 0; k < n; ++k) slot_of[ids[k]] = k;
+    std::vector<int> slot_of(n, -1);
+    for (int k = 0; k < ns; ++k)
+        if (ids[k] >= 0 && ids[k] < n) slot_of[ids[k]] = k;
     long long w = 0;
     bool overflow = false;
     for (int i = 0; i < n; ++i) {
         const int k = slot_of[i];
+        if (k < 0) return fail(SPH_E_CUDA, "corrupt particle index on the device");
         std::vector<int> li(lists.begin() + off[k], lists.begin() + off[k + 1]);
         for (int& j : li) j = ids[j];
         std::sort(li.begin(), li.end());
@@ -484,30 +951,31 @@ sph_status dbg_neighbors_impl(sph_mesh* m, int32_t mode, int64_t* counts_out, in
 }
 
 template <typename T, int D>
-sph_status dbg_interact_impl(sph_mesh* m, double* a_p, double* sigma, double* gamma, double* dta, double* dtv) {
+sph_status dbg_interact_impl(sph_batch* b, double* a_p, double* sigma, double* gamma, double* dta, double* dtv) {
     State<T> s;
-    sph_status r = dbg_prepare<T, D>(m, s, nullptr);
+    sph_status r = dbg_prepare<T, D>(b, s, nullptr);
     if (r != SPH_OK) return r;
-    const int n = m->n, G = m->params.G;
+    const int ns = s.n, n = b->in[0].n, G = b->in[0].params.G;
     T *d_sig = nullptr, *d_gam = nullptr;
-    CK(cudaMalloc(&d_sig, sizeof(T) * (size_t)std::max(n, 1)));
-    CK(cudaMalloc(&d_gam, sizeof(T) * (size_t)std::max(n, 1)));
-    launch_interact<T, D>(m->grid, m->params, s, d_sig, d_gam, m->stream);
+    CK(cudaMalloc(&d_sig, sizeof(T) * (size_t)std::max(ns, 1)));
+    CK(cudaMalloc(&d_gam, sizeof(T) * (size_t)std::max(ns, 1)));
+    launch_interact<T, D>(s, d_sig, d_gam, b->stream);
     CK(cudaGetLastError());
-    std::vector<Vec4<T>> A(n);
-    std::vector<T> sg(n), gm(n);
-    std::vector<int> ids(n);
+    std::vector<Vec4<T>> A(ns);
+    std::vector<T> sg(ns), gm(ns);
+    std::vector<int> ids(ns);
     Ctrl c;
-    CK(cudaMemcpyAsync(A.data(), s.A, sizeof(Vec4<T>) * (size_t)n, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaMemcpyAsync(sg.data(), d_sig, sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaMemcpyAsync(gm.data(), d_gam, sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaMemcpyAsync(ids.data(), s.IDs, 4 * (size_t)n, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaMemcpyAsync(&c, m->d_ctrl_dbg, sizeof c, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
+    CK(cudaMemcpyAsync(A.data(), s.A, sizeof(Vec4<T>) * (size_t)ns, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(sg.data(), d_sig, sizeof(T) * (size_t)ns, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(gm.data(), d_gam, sizeof(T) * (size_t)ns, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(ids.data(), s.IDs, 4 * (size_t)ns, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(&c, b->d_ctrl_dbg, sizeof c, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
     cudaFree(d_sig);
     cudaFree(d_gam);
-    for (int k = 0; k < n; ++k) {
+    for (int k = 0; k < ns; ++k) {
         const int i = ids[k];
+        if (i < 0 || i >= n) continue;
         if (a_p) {
             a_p[(size_t)i * 3 + 0] = (double)A[k].x;
             a_p[(size_t)i * 3 + 1] = (double)A[k].y;
@@ -517,31 +985,31 @@ sph_status dbg_interact_impl(sph_mesh* m, double* a_p, double* sigma, double* ga
         if (gamma) gamma[i] = (double)gm[k];
     }
     for (int g = 0; g < G; ++g) {
-        T a, b;
+        T a, bb;
         if (sizeof(T) == 4) {
             unsigned ua = (unsigned)c.dta_bits[g], ub = (unsigned)c.dtv_bits[g];
             float fa, fb;
             std::memcpy(&fa, &ua, 4);
             std::memcpy(&fb, &ub, 4);
             a = (T)fa;
-            b = (T)fb;
+            bb = (T)fb;
         } else {
             double fa, fb;
             std::memcpy(&fa, &c.dta_bits[g], 8);
             std::memcpy(&fb, &c.dtv_bits[g], 8);
             a = (T)fa;
-            b = (T)fb;
+            bb = (T)fb;
         }
         if (dta) dta[g] = (double)a;
-        if (dtv) dtv[g] = (double)b;
+        if (dtv) dtv[g] = (double)bb;
     }
     return SPH_OK;
 }
 
 template <typename T, int D>
-sph_status dbg_update_impl(sph_mesh* m, const double* dt, const int32_t* reset, double eps, double f, double* x_out,
+sph_status dbg_update_impl(sph_batch* b, const double* dt, const int32_t* reset, double eps, double f, double* x_out,
                            double* v_out, double* h_out, double* a_v) {
-    const int n = m->n, G = m->params.G;
+    const int G = b->in[0].params.G;
     Ctrl c;
     host_ctrl_init(&c);
     for (int g = 0; g < G; ++g) {
@@ -554,19 +1022,19 @@ sph_status dbg_update_impl(sph_mesh* m, const double* dt, const int32_t* reset, 
     c.eps_f = (float)eps;
     c.f_f = (float)f;
     State<T> s;
-    sph_status r = dbg_prepare<T, D>(m, s, &c);
+    sph_status r = dbg_prepare<T, D>(b, s, &c);
     if (r != SPH_OK) return r;
-    launch_interact<T, D>(m->grid, m->params, s, nullptr, nullptr, m->stream);
+    launch_interact<T, D>(s, nullptr, nullptr, b->stream);
     // scratch output arrays
     Out<T> o;
     void* buf = nullptr;
-    const size_t nn = (size_t)std::max(n, 1);
-    const size_t bytes = 16 * ((nn * (3 * 4 + 9 * sizeof(T) + sizeof(T) + 8) + 4096 + 15) / 16) + 16 * 256;
+    const size_t nn = (size_t)std::max(s.n, 1);
+    const size_t bytes = nn * (3 * 4 + 9 * sizeof(T) + sizeof(T) + 8) + 20 * 256;
     CK(cudaMalloc(&buf, bytes));
     char* p = (char*)buf;
-    auto take = [&](size_t b) {
+    auto take = [&](size_t sz) {
         char* q = p;
-        p += (b + 255) & ~(size_t)255;
+        p += (sz + 255) & ~(size_t)255;
         return q;
     };
     for (int a = 0; a < 3; ++a) o.C[a] = (int*)take(nn * 4);
@@ -576,28 +1044,28 @@ sph_status dbg_update_impl(sph_mesh* m, const double* dt, const int32_t* reset, 
     o.H = (T*)take(nn * sizeof(T));
     o.G = (unsigned*)take(nn * 4);
     o.ID = (int*)take(nn * 4);
-    launch_integrate<T, D>(m->grid, m->params, s, m->d_ctrl_dbg, o, m->stream);
+    launch_integrate<T, D>(s, b->d_ctrl_dbg, o, b->stream);
     CK(cudaGetLastError());
-    r = download<T>(m, o.C, o.O, o.V, o.H, o.G, o.ID, x_out, nullptr, v_out, h_out);
+    r = download<T>(b, 0, o.C, o.O, o.V, o.H, o.G, o.ID, x_out, nullptr, v_out, h_out);
     if (r == SPH_OK && a_v) {
         T* const avs[3] = {o.av[0], o.av[1], o.av[2]};
-        r = download<T>(m, o.C, o.O, avs, o.H, o.G, o.ID, nullptr, nullptr, a_v, nullptr);
+        r = download<T>(b, 0, o.C, o.O, avs, o.H, o.G, o.ID, nullptr, nullptr, a_v, nullptr);
     }
     cudaFree(buf);
     return r;
 }
 
-template <typename T, int D> sph_status pair_counts_impl(sph_mesh* m, int64_t* cand, int64_t* accd) {
+template <typename T, int D> sph_status pair_counts_impl(sph_batch* b, int64_t* cand, int64_t* accd) {
     State<T> s;
-    sph_status r = dbg_prepare<T, D>(m, s, nullptr);
+    sph_status r = dbg_prepare<T, D>(b, s, nullptr);
     if (r != SPH_OK) return r;
     unsigned long long* d = nullptr;
     CK(cudaMalloc(&d, 16));
-    CK(cudaMemsetAsync(d, 0, 16, m->stream));
-    launch_pair_counts<T, D>(m->grid, m->params, s, d, m->stream);
+    CK(cudaMemsetAsync(d, 0, 16, b->stream));
+    launch_pair_counts<T, D>(s, d, b->stream);
     unsigned long long h[2];
-    CK(cudaMemcpyAsync(h, d, 16, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
+    CK(cudaMemcpyAsync(h, d, 16, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
     cudaFree(d);
     if (cand) *cand = (int64_t)h[0];
     if (accd) *accd = (int64_t)h[1];
@@ -605,17 +1073,121 @@ template <typename T, int D> sph_status pair_counts_impl(sph_mesh* m, int64_t* c
 }
 
 template <typename T, int D>
-sph_status positions_impl(sph_mesh* m, double* x_out, int32_t* group_out, double* v_out, double* h_out) {
-    State<T>& s = st<T>(m);
-    return download<T>(m, s.C, s.O, s.V, s.H, s.G, s.ID, x_out, group_out, v_out, h_out);
+sph_status positions_impl(sph_batch* b, int inst, double* x_out, int32_t* group_out, double* v_out, double* h_out) {
+    State<T>& s = st<T>(b);
+    return download<T>(b, inst, s.C, s.O, s.V, s.H, s.G, s.ID, x_out, group_out, v_out, h_out);
 }
 
-sph_status check_status(sph_mesh* m) {
-    Ctrl c;
-    CK(cudaMemcpyAsync(&c, m->d_ctrl, sizeof c, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
-    if (c.status & ST_NONFINITE) return fail(SPH_E_DIVERGED, "non-finite acceleration or position at step %lld", c.n);
-    if (c.status & ST_OUTSIDE_GRID) return fail(SPH_E_OVERFLOW, "a particle left the cell grid (step %lld)", c.n);
+sph_status read_ctrls(sph_batch* b, std::vector<Ctrl>& c) {
+    c.resize(b->NI);
+    CK(cudaMemcpyAsync(c.data(), b->d_ctrl, sizeof(Ctrl) * b->NI, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return SPH_OK;
+}
+
+sph_status status_of(const Ctrl& c, int inst, bool named) {
+    const char* who = named ? "instance " : "";
+    char tag[32] = "";
+    if (named) std::snprintf(tag, sizeof tag, "%d: ", inst);
+    if (c.status & ST_NONFINITE)
+        return fail(SPH_E_DIVERGED, "%s%snon-finite acceleration or position at step %lld", who, tag, c.n);
+    if (c.status & ST_OUTSIDE_GRID)
+        return fail(SPH_E_OVERFLOW, "%s%sa particle left the cell grid (step %lld)", who, tag, c.n);
+    return SPH_OK;
+}
+
+sph_status check_status(sph_batch* b) {
+    std::vector<Ctrl> c;
+    sph_status r = read_ctrls(b, c);
+    if (r != SPH_OK) return r;
+    for (int i = 0; i < b->NI; ++i) {
+        r = status_of(c[i], i, !b->mesh);
+        if (r != SPH_OK) return r;
+    }
+    return SPH_OK;
+}
+
+void fill_report(const sph_batch* b, int inst, const Ctrl& c, sph_report* out) {
+    std::memset(out, 0, sizeof *out);
+    const int G = b->in[inst].params.G;
+    out->phase = c.phase;
+    out->n_groups = G;
+    out->iteration = c.n;
+    out->ramp_start = c.ramp_start;
+    out->escapes = (int64_t)c.escapes;
+    out->status = c.status;
+    out->E_t = c.E_t;
+    out->E_avg = c.E_avg;
+    out->E_sys = c.E_sys;
+    for (int g = 0; g < G; ++g) {
+        out->vbar[g] = c.Vbar[g];
+        out->dt[g] = c.dt[g];
+        out->reset[g] = c.reset[g];
+    }
+}
+
+// Steps until every instance's controller is DONE or has run max_iters steps, checking every
+// `every` steps.
+sph_status run_impl(sph_batch* b, int64_t max_iters, int64_t* iters_out) {
+    int every = 1 << 30;
+    for (const Inst& I : b->in) every = std::min(every, I.params.sample_every);
+    std::vector<Ctrl> c;
+    sph_status r = read_ctrls(b, c);
+    if (r != SPH_OK) return r;
+    auto pending = [&](int64_t& nmin) {
+        bool any = false;
+        nmin = INT64_MAX;
+        for (int i = 0; i < b->NI; ++i)
+            if (c[i].phase != PH_DONE && c[i].n < max_iters && !(c[i].status & ST_NONFINITE) && b->in[i].n > 0) {
+                any = true;
+                nmin = std::min<int64_t>(nmin, c[i].n);
+            }
+        return any;
+    };
+    int64_t nmin = 0;
+    while (pending(nmin)) {
+        const int64_t chunk = std::min<int64_t>(every, max_iters - nmin);
+        r = DISPATCH(b, step_impl, b, (int32_t)chunk);
+        if (r != SPH_OK) return r;
+        r = read_ctrls(b, c);
+        if (r != SPH_OK) return r;
+    }
+    int64_t it = 0;
+    for (const Ctrl& x : c) it = std::max<int64_t>(it, x.n);
+    if (iters_out) *iters_out = it;
+    r = check_status(b);
+    if (r != SPH_OK) return r;
+    for (int i = 0; i < b->NI; ++i)
+        if (c[i].phase != PH_DONE) {
+            if (b->mesh) return fail(SPH_E_NOT_CONVERGED, "not converged after %lld steps", (long long)c[i].n);
+            return fail(SPH_E_NOT_CONVERGED, "instance %d not converged after %lld steps", i, (long long)c[i].n);
+        }
+    return SPH_OK;
+}
+
+sph_status kernel_times_impl(sph_batch* b, sph_kernel_time* out, int32_t cap, int32_t* n_out) {
+    sph_status r = collect_timing(b);
+    if (r != SPH_OK) return r;
+    int k = 0;
+    for (; k < 4 && k < cap; ++k) {
+        std::memset(out[k].name, 0, sizeof out[k].name);
+        std::snprintf(out[k].name, sizeof out[k].name, "%s", kStages[k].name);
+        out[k].launches = b->stage_steps * kStages[k].kernels;
+        out[k].total_ms = b->stage_ms[k];
+    }
+    if (n_out) *n_out = k;
+    return SPH_OK;
+}
+
+sph_status set_timing_impl(sph_batch* b, int32_t enable) {
+    if (b->timing) {
+        sph_status r = collect_timing(b);
+        if (r != SPH_OK) return r;
+    }
+    b->timing = enable != 0;
+    b->stage_steps = 0;
+    for (double& t : b->stage_ms) t = 0;
+    b->ev_pending = false;
     return SPH_OK;
 }
 
@@ -654,201 +1226,26 @@ sph_status sph_grid_spec(int32_t dim, const double* lo, const double* hi, double
     return grid_spec(dim, lo, hi, h_lo, h_hi, kappa, out);
 }
 
+// ---- single instance ----
+
 sph_status sph_mesh_create(const sph_domain_desc* dd, const sph_sizing_desc* sz, const sph_params* pp,
                            int64_t max_particles, void* stream, sph_mesh** out) {
     if (!dd || !sz || !pp || !out) return fail(SPH_E_INVALID, "create: NULL argument");
     *out = nullptr;
-    if (dd->dim != 2 && dd->dim != 3) return fail(SPH_E_INVALID, "domain: dim must be 2 or 3");
-    if (dd->n_features < 1 || dd->n_features > SPH_MAX_FEATURES) return fail(SPH_E_INVALID, "domain: n_features out of range");
-    if (dd->n_holes < 0 || dd->n_holes > SPH_MAX_HOLES) return fail(SPH_E_INVALID, "domain: n_holes out of range");
-    if (dd->base != 0 && dd->base != 1) return fail(SPH_E_INVALID, "domain: base must be 0 (box) or 1 (ball)");
-    if (pp->precision != 32 && pp->precision != 64) return fail(SPH_E_INVALID, "params: precision must be 32 or 64");
-    if (!(pp->kappa > 0) || !(pp->p0 > 0) || pp->visc < 0 || !(pp->cfl_a > 0) || !(pp->cfl_v > 0) || pp->eps1 < 0 ||
-        !(pp->dt_cap > 0) || pp->dt_collapse < 0 || !(pp->threshold > 0) || pp->reset_period < 1 ||
-        pp->sample_every < 1 || pp->window < 1 || pp->ramp_len < 1)
-        return fail(SPH_E_INVALID, "params: value out of range");
-    if (max_particles < 0 || max_particles > (int64_t)1 << 30) return fail(SPH_E_INVALID, "max_particles out of range");
-    if (sz->kind < 0 || sz->kind > 2 || !(sz->lo > 0) || !(sz->hi >= sz->lo) || sz->n_ref < 0 || sz->n_ref > SPH_MAX_HOLES)
-        return fail(SPH_E_INVALID, "sizing: need kind 0..2, 0 < lo <= hi, n_ref <= %d", SPH_MAX_HOLES);
-    if (sz->kind == 0 && !(sz->a >= sz->lo && sz->a <= sz->hi)) return fail(SPH_E_INVALID, "sizing: constant h outside [lo, hi]");
-    const int D = dd->dim;
-    for (int k = 0; k < dd->n_features; ++k) {
-        const sph_feature& f = dd->features[k];
-        int want = -1;
-        switch (f.kind) {
-            case SPH_FEAT_VOLUME: want = D; break;
-            case SPH_FEAT_POINT: want = 0; break;
-            case SPH_FEAT_SEGMENT: want = 1; break;
-            case SPH_FEAT_CIRCLE: want = D == 2 ? 1 : -1; break;
-            case SPH_FEAT_RECT: want = D == 3 ? 2 : -1; break;
-            case SPH_FEAT_SPHERE: want = D == 3 ? 2 : -1; break;
-            default: break;
-        }
-        if (want < 0 || f.dim != want) return fail(SPH_E_INVALID, "feature %d: kind/dim mismatch for a %dD domain", k, D);
-    }
-    sph_grid_info gi;
-    sph_status r = grid_spec(D, dd->bbox_lo, dd->bbox_hi, sz->lo, sz->hi, pp->kappa, &gi);
+    Inst I;
+    sph_status r = make_instance(dd, sz, pp, max_particles, I);
     if (r != SPH_OK) return r;
-    if (gi.n_cells > (int64_t)SCAN_TILE * SCAN_TILE)
-        return fail(SPH_E_INVALID, "grid: %lld cells is more than the %lld the cell scan supports", (long long)gi.n_cells,
-                    (long long)SCAN_TILE * SCAN_TILE);
-    for (int l = 0; l < gi.levels; ++l)
-        if (gi.dims[l][0] >= ((int64_t)1 << 23) || gi.dims[l][1] >= ((int64_t)1 << 14) || gi.dims[l][2] >= ((int64_t)1 << 14))
-            return fail(SPH_E_INVALID, "grid: too many cells (x < 2^23, y and z < 2^14 per level)");
-
     sph_mesh* m = new sph_mesh();
-    m->D = D;
+    m->mesh = true;
+    m->D = dd->dim;
     m->prec = pp->precision;
-    m->cap = max_particles;
-    m->h_lo = sz->lo;
-    m->h_hi = sz->hi;
-    Grid& g = m->grid;
-    std::memset(&g, 0, sizeof g);
-    g.D = D;
-    g.L = gi.levels;
-    g.c0 = gi.c0;
-    for (int a = 0; a < 3; ++a) g.origin[a] = gi.origin[a];
-    for (int l = 0; l < MAXL; ++l) {
-        g.c[l] = std::ldexp((double)gi.c0, l);
-        g.inv_c[l] = 1.0 / g.c[l];
-        g.cf[l] = (float)g.c[l];
-        g.thr[l] = gi.thr[l];
-        for (int a = 0; a < 3; ++a) g.dims[l][a] = l < gi.levels ? (int)gi.dims[l][a] : 1;
-        g.base[l] = l < gi.levels ? (int)gi.base[l] : (int)gi.n_cells;
+    m->in.push_back(I);
+    r = batch_init(m, stream);
+    if (r != SPH_OK) {
+        batch_free(m);
+        delete m;
+        return r;
     }
-    g.base[MAXL] = (int)gi.n_cells;
-    g.ncell = (int)gi.n_cells;
-    Params& p = m->params;
-    p.kappa = pp->kappa;
-    p.p0 = pp->p0;
-    p.visc = pp->visc;
-    p.cfl_a = pp->cfl_a;
-    p.cfl_v = pp->cfl_v;
-    p.eps1 = pp->eps1;
-    p.dt_cap = pp->dt_cap;
-    p.dt_collapse = pp->dt_collapse;
-    p.threshold = pp->threshold;
-    p.reset_period = pp->reset_period;
-    p.sample_every = pp->sample_every;
-    p.window = pp->window;
-    p.ramp_len = pp->ramp_len;
-    p.boundary_rho = pp->boundary_rho;
-    p.kappa_f = (float)p.kappa;
-    p.p0_f = (float)p.p0;
-    p.visc_f = (float)p.visc;
-    p.cfl_a_f = (float)p.cfl_a;
-    p.cfl_v_f = (float)p.cfl_v;
-    p.G = dd->n_features;
-    for (int k = 0; k < MAXF; ++k) p.gdim[k] = k < dd->n_features ? dd->features[k].dim : 0;
-    Domain& dm = m->hdom;
-    std::memset(&dm, 0, sizeof dm);
-    dm.D = D;
-    dm.base = dd->base;
-    for (int a = 0; a < 3; ++a) {
-        dm.lo[a] = dd->bbox_lo[a];
-        dm.hi[a] = dd->bbox_hi[a];
-        dm.bc[a] = dd->ball_center[a];
-    }
-    dm.br = dd->ball_radius;
-    dm.nh = dd->n_holes;
-    for (int k = 0; k < dd->n_holes; ++k) {
-        for (int a = 0; a < 3; ++a) dm.hc[k][a] = dd->hole_center[k][a];
-        dm.hr[k] = dd->hole_radius[k];
-    }
-    dm.nf = dd->n_features;
-    for (int k = 0; k < dd->n_features; ++k) {
-        const sph_feature& f = dd->features[k];
-        Feat& F = dm.f[k];
-        F.kind = f.kind;
-        F.dim = f.dim;
-        for (int a = 0; a < 12; ++a) F.g[a] = f.geom[a];
-        for (int a = 0; a < 3; ++a) {
-            F.nb[a] = f.normal[a];
-            F.fnb[a] = (float)f.normal[a];
-        }
-        F.orient = f.orient;
-        F.forient = (float)f.orient;
-        if (f.kind == SPH_FEAT_SEGMENT) {
-            double ab[3] = {f.geom[3] - f.geom[0], f.geom[4] - f.geom[1], f.geom[5] - f.geom[2]};
-            double L = std::sqrt(ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2]);
-            if (!(L > 0)) {
-                delete m;
-                return fail(SPH_E_INVALID, "feature %d: zero-length segment", k);
-            }
-            for (int a = 0; a < 3; ++a) F.ftg[a] = (float)(ab[a] / L);
-        } else if (f.kind == SPH_FEAT_RECT) {
-            for (int a = 0; a < 3; ++a) F.ftg[a] = (float)f.normal[a];
-        }
-        if (f.kind == SPH_FEAT_CIRCLE || f.kind == SPH_FEAT_SPHERE)
-            for (int a = 0; a < 3; ++a) F.fc[a] = (float)f.geom[a];
-        if (f.kind == SPH_FEAT_CIRCLE) F.fc[2] = 0.0f;
-    }
-    Sizing& zs = m->hsiz;
-    std::memset(&zs, 0, sizeof zs);
-    zs.kind = sz->kind;
-    zs.a = sz->a;
-    zs.b = sz->b;
-    zs.lo = sz->lo;
-    zs.hi = sz->hi;
-    for (int a = 0; a < 3; ++a) zs.q[a] = sz->center[a];
-    zs.nref = sz->n_ref;
-    for (int k = 0; k < sz->n_ref; ++k) {
-        for (int a = 0; a < 3; ++a) zs.rc[k][a] = sz->ref_center[k][a];
-        zs.rr[k] = sz->ref_radius[k];
-    }
-    // float copies used by the FP32 evaluation of h_t and of the level set
-    zs.fa = (float)zs.a;
-    zs.fb = (float)zs.b;
-    zs.flo = (float)zs.lo;
-    zs.fhi = (float)zs.hi;
-    for (int a = 0; a < 3; ++a) zs.fq[a] = (float)zs.q[a];
-    for (int k = 0; k < MAXH; ++k) {
-        for (int a = 0; a < 3; ++a) zs.frc[k][a] = (float)zs.rc[k][a];
-        zs.frr[k] = (float)zs.rr[k];
-    }
-    for (int a = 0; a < 3; ++a) {
-        dm.flo[a] = (float)dm.lo[a];
-        dm.fhi[a] = (float)dm.hi[a];
-        dm.fbc[a] = (float)dm.bc[a];
-    }
-    dm.fbr = (float)dm.br;
-    for (int k = 0; k < MAXH; ++k) {
-        for (int a = 0; a < 3; ++a) dm.fhc[k][a] = (float)dm.hc[k][a];
-        dm.fhr[k] = (float)dm.hr[k];
-    }
-
-    auto cleanup = [&](sph_status s) {
-        sph_mesh_destroy(m);
-        return s;
-    };
-    if (cudaGetDevice(&m->device) != cudaSuccess) return cleanup(fail(SPH_E_CUDA, "no CUDA device"));
-    if (stream) m->stream = (cudaStream_t)stream;
-    else {
-        if (cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking) != cudaSuccess)
-            return cleanup(fail(SPH_E_CUDA, "cudaStreamCreate failed"));
-        m->own_stream = true;
-    }
-    if (cudaMalloc(&m->d_dom, sizeof(Domain)) != cudaSuccess || cudaMalloc(&m->d_siz, sizeof(Sizing)) != cudaSuccess ||
-        cudaMalloc(&m->d_ctrl, sizeof(Ctrl)) != cudaSuccess || cudaMalloc(&m->d_ctrl_dbg, sizeof(Ctrl)) != cudaSuccess)
-        return cleanup(fail(SPH_E_NOMEM, "device allocation of descriptors failed"));
-    size_t bytes = m->prec == 32 ? layout<float>(m, nullptr, false) : layout<double>(m, nullptr, false);
-    if (cudaMalloc(&m->pool, bytes) != cudaSuccess)
-        return cleanup(fail(SPH_E_NOMEM, "device allocation of %zu bytes failed", bytes));
-    if (m->prec == 32) layout<float>(m, (char*)m->pool, true);
-    else layout<double>(m, (char*)m->pool, true);
-    if (cudaMemsetAsync(m->pool, 0, bytes, m->stream) != cudaSuccess ||
-        cudaMemcpyAsync(m->d_dom, &m->hdom, sizeof(Domain), cudaMemcpyHostToDevice, m->stream) != cudaSuccess ||
-        cudaMemcpyAsync(m->d_siz, &m->hsiz, sizeof(Sizing), cudaMemcpyHostToDevice, m->stream) != cudaSuccess)
-        return cleanup(fail(SPH_E_CUDA, "device initialisation failed"));
-    Ctrl c;
-    host_ctrl_init(&c);
-    if (m->prec == 32) ctrl_inf_bits<float>(&c);
-    else ctrl_inf_bits<double>(&c);
-    if (cudaMemcpyAsync(m->d_ctrl, &c, sizeof c, cudaMemcpyHostToDevice, m->stream) != cudaSuccess ||
-        cudaStreamSynchronize(m->stream) != cudaSuccess)
-        return cleanup(fail(SPH_E_CUDA, "device initialisation failed"));
-    for (int k = 0; k < 5; ++k)
-        if (cudaEventCreate(&m->ev[k]) != cudaSuccess) return cleanup(fail(SPH_E_CUDA, "cudaEventCreate failed"));
     *out = m;
     return SPH_OK;
 }
@@ -856,30 +1253,15 @@ sph_status sph_mesh_create(const sph_domain_desc* dd, const sph_sizing_desc* sz,
 sph_status sph_mesh_set_state(sph_mesh* m, int64_t n, const double* x, const int32_t* group, const double* v,
                               const double* h) {
     if (!m) return fail(SPH_E_INVALID, "set_state: NULL handle");
-    if (n < 0 || n > m->cap) return fail(SPH_E_INVALID, "set_state: n=%lld outside [0, %lld]", (long long)n, (long long)m->cap);
-    if (n > 0 && (!x || !group)) return fail(SPH_E_INVALID, "set_state: x and group are required");
-    const int D = m->D;
-    for (int64_t i = 0; i < n; ++i) {
-        if (group[i] < 0 || group[i] >= m->params.G) return fail(SPH_E_INVALID, "set_state: particle %lld has group %d", (long long)i, group[i]);
-        for (int a = 0; a < D; ++a) {
-            double xa = x[i * 3 + a];
-            if (!(xa >= m->hdom.lo[a] - 1e-9 * (1 + std::fabs(m->hdom.lo[a])) && xa <= m->hdom.hi[a] + 1e-9 * (1 + std::fabs(m->hdom.hi[a]))))
-                return fail(SPH_E_INVALID, "set_state: particle %lld outside the bounding box", (long long)i);
-        }
-        // the grid's top level covers kappa*h_hi*(1+2^-10); allow h up to h_hi*(1+2^-11) so that
-        // values rounded to the working precision are accepted
-        if (h && !(h[i] > 0 && h[i] <= m->h_hi * (1 + 1.0 / 2048.0)))
-            return fail(SPH_E_INVALID, "set_state: h of particle %lld outside [lo, hi]", (long long)i);
-        if (v)
-            for (int a = 0; a < D; ++a)
-                if (!std::isfinite(v[i * 3 + a])) return fail(SPH_E_INVALID, "set_state: non-finite velocity");
-    }
-    return DISPATCH(m, set_state_impl, m, n, x, group, v, h);
+    sph_status r = check_args(m, 0, n, x, group, v, h);
+    if (r != SPH_OK) return r;
+    return DISPATCH(m, set_state_impl, m, 0, n, x, group, v, h, false);
 }
 
 sph_status sph_mesh_step(sph_mesh* m, int32_t n_steps) {
     if (!m) return fail(SPH_E_INVALID, "step: NULL handle");
     if (n_steps < 0) return fail(SPH_E_INVALID, "step: n_steps < 0");
+    if (m->in[0].n == 0) return SPH_OK;
     return DISPATCH(m, step_impl, m, n_steps);
 }
 
@@ -892,80 +1274,43 @@ sph_status sph_mesh_sync(sph_mesh* m) {
 sph_status sph_mesh_run_until_converged(sph_mesh* m, int64_t max_iters, int64_t* iters_out) {
     if (!m) return fail(SPH_E_INVALID, "run: NULL handle");
     if (max_iters < 0) return fail(SPH_E_INVALID, "run: max_iters < 0");
-    Ctrl c;
-    CK(cudaMemcpyAsync(&c, m->d_ctrl, sizeof c, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
-    while (c.phase != PH_DONE && c.n < max_iters) {
-        int64_t chunk = std::min<int64_t>(m->params.sample_every, max_iters - c.n);
-        sph_status r = sph_mesh_step(m, (int32_t)chunk);
-        if (r != SPH_OK) return r;
-        CK(cudaMemcpyAsync(&c, m->d_ctrl, sizeof c, cudaMemcpyDeviceToHost, m->stream));
-        CK(cudaStreamSynchronize(m->stream));
-        if (c.status & ST_NONFINITE) break;
-        if (m->n == 0) break;
-    }
-    if (iters_out) *iters_out = c.n;
-    sph_status r = check_status(m);
-    if (r != SPH_OK) return r;
-    if (c.phase != PH_DONE) return fail(SPH_E_NOT_CONVERGED, "not converged after %lld steps", (long long)c.n);
-    return SPH_OK;
+    return run_impl(m, max_iters, iters_out);
 }
 
 sph_status sph_mesh_positions(sph_mesh* m, double* x_out, int32_t* group_out, double* v_out, double* h_out,
                               int64_t capacity, int64_t* n_out) {
     if (!m) return fail(SPH_E_INVALID, "positions: NULL handle");
-    if (n_out) *n_out = m->n;
-    if (capacity < m->n) return fail(SPH_E_INVALID, "positions: capacity %lld < n %d", (long long)capacity, m->n);
-    if (m->n == 0) return SPH_OK;
-    return DISPATCH(m, positions_impl, m, x_out, group_out, v_out, h_out);
+    const int n = m->in[0].n;
+    if (n_out) *n_out = n;
+    if (capacity < n) return fail(SPH_E_INVALID, "positions: capacity %lld < n %d", (long long)capacity, n);
+    if (n == 0) return SPH_OK;
+    return DISPATCH(m, positions_impl, m, 0, x_out, group_out, v_out, h_out);
 }
 
 sph_status sph_mesh_report(sph_mesh* m, sph_report* out) {
     if (!m || !out) return fail(SPH_E_INVALID, "report: NULL argument");
-    Ctrl c;
-    CK(cudaMemcpyAsync(&c, m->d_ctrl, sizeof c, cudaMemcpyDeviceToHost, m->stream));
-    CK(cudaStreamSynchronize(m->stream));
-    std::memset(out, 0, sizeof *out);
-    out->phase = c.phase;
-    out->n_groups = m->params.G;
-    out->iteration = c.n;
-    out->ramp_start = c.ramp_start;
-    out->escapes = (int64_t)c.escapes;
-    out->status = c.status;
-    out->E_t = c.E_t;
-    out->E_avg = c.E_avg;
-    out->E_sys = c.E_sys;
-    for (int g = 0; g < m->params.G; ++g) {
-        out->vbar[g] = c.Vbar[g];
-        out->dt[g] = c.dt[g];
-        out->reset[g] = c.reset[g];
-    }
+    std::vector<Ctrl> c;
+    sph_status r = read_ctrls(m, c);
+    if (r != SPH_OK) return r;
+    fill_report(m, 0, c[0], out);
     return SPH_OK;
 }
 
 void sph_mesh_destroy(sph_mesh* m) {
     if (!m) return;
-    if (m->stream) cudaStreamSynchronize(m->stream);
-    if (m->gexec) cudaGraphExecDestroy(m->gexec);
-    for (int k = 0; k < 5; ++k)
-        if (m->ev[k]) cudaEventDestroy(m->ev[k]);
-    cudaFree(m->pool);
-    cudaFree(m->d_dom);
-    cudaFree(m->d_siz);
-    cudaFree(m->d_ctrl);
-    cudaFree(m->d_ctrl_dbg);
-    if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+    batch_free(m);
     delete m;
 }
 
 sph_status sph_mesh_grid(const sph_mesh* m, sph_grid_info* out) {
     if (!m || !out) return fail(SPH_E_INVALID, "grid: NULL argument");
-    return grid_spec(m->D, m->hdom.lo, m->hdom.hi, m->h_lo, m->h_hi, m->params.kappa, out);
+    const Inst& I = m->in[0];
+    return grid_spec(m->D, I.dom.lo, I.dom.hi, I.h_lo, I.h_hi, I.params.kappa, out);
 }
 
 sph_status sph_debug_rebuild(sph_mesh* m, int64_t* key_out, int64_t* cs_out, int64_t* perm_out) {
     if (!m) return fail(SPH_E_INVALID, "debug_rebuild: NULL handle");
-    if (m->n == 0) return SPH_OK;
+    if (m->in[0].n == 0) return SPH_OK;
     return DISPATCH(m, dbg_rebuild_impl, m, key_out, cs_out, perm_out);
 }
 
@@ -973,7 +1318,7 @@ sph_status sph_debug_neighbors(sph_mesh* m, int32_t mode, int64_t* counts_out, i
                                int64_t list_capacity, int64_t* total_out) {
     if (!m) return fail(SPH_E_INVALID, "debug_neighbors: NULL handle");
     if (mode != 0 && mode != 1) return fail(SPH_E_INVALID, "debug_neighbors: mode must be 0 or 1");
-    if (m->n == 0) {
+    if (m->in[0].n == 0) {
         if (total_out) *total_out = 0;
         return SPH_OK;
     }
@@ -982,20 +1327,20 @@ sph_status sph_debug_neighbors(sph_mesh* m, int32_t mode, int64_t* counts_out, i
 
 sph_status sph_debug_interact(sph_mesh* m, double* a_p, double* sigma, double* gamma, double* dta, double* dtv) {
     if (!m) return fail(SPH_E_INVALID, "debug_interact: NULL handle");
-    if (m->n == 0) return SPH_OK;
+    if (m->in[0].n == 0) return SPH_OK;
     return DISPATCH(m, dbg_interact_impl, m, a_p, sigma, gamma, dta, dtv);
 }
 
 sph_status sph_debug_update(sph_mesh* m, const double* dt, const int32_t* reset, double eps, double f, double* x_out,
                             double* v_out, double* h_out, double* a_v) {
     if (!m || !dt || !reset) return fail(SPH_E_INVALID, "debug_update: NULL argument");
-    if (m->n == 0) return SPH_OK;
+    if (m->in[0].n == 0) return SPH_OK;
     return DISPATCH(m, dbg_update_impl, m, dt, reset, eps, f, x_out, v_out, h_out, a_v);
 }
 
 sph_status sph_debug_pair_counts(sph_mesh* m, int64_t* candidates, int64_t* accepted) {
     if (!m) return fail(SPH_E_INVALID, "pair_counts: NULL handle");
-    if (m->n == 0) {
+    if (m->in[0].n == 0) {
         if (candidates) *candidates = 0;
         if (accepted) *accepted = 0;
         return SPH_OK;
@@ -1005,30 +1350,166 @@ sph_status sph_debug_pair_counts(sph_mesh* m, int64_t* candidates, int64_t* acce
 
 sph_status sph_mesh_set_timing(sph_mesh* m, int32_t enable) {
     if (!m) return fail(SPH_E_INVALID, "set_timing: NULL handle");
-    if (m->timing) {
-        sph_status r = collect_timing(m);
-        if (r != SPH_OK) return r;
-    }
-    m->timing = enable != 0;
-    m->stage_steps = 0;
-    for (double& t : m->stage_ms) t = 0;
-    m->ev_pending = false;
-    return SPH_OK;
+    return set_timing_impl(m, enable);
 }
 
 sph_status sph_mesh_kernel_times(sph_mesh* m, sph_kernel_time* out, int32_t cap, int32_t* n_out) {
     if (!m) return fail(SPH_E_INVALID, "kernel_times: NULL handle");
-    sph_status r = collect_timing(m);
-    if (r != SPH_OK) return r;
-    int k = 0;
-    for (; k < 4 && k < cap; ++k) {
-        std::memset(out[k].name, 0, sizeof out[k].name);
-        std::snprintf(out[k].name, sizeof out[k].name, "%s", kStages[k].name);
-        out[k].launches = m->stage_steps * kStages[k].kernels;
-        out[k].total_ms = m->stage_ms[k];
+    if (cap > 0 && !out) return fail(SPH_E_INVALID, "kernel_times: NULL output");
+    return kernel_times_impl(m, out, cap, n_out);
+}
+
+// ---- batch ----
+
+sph_status sph_batch_create(int32_t n_inst, const sph_domain_desc* domains, const sph_sizing_desc* sizings,
+                            const sph_params* params, const int64_t* max_particles, void* stream, sph_batch** out) {
+    if (!domains || !sizings || !params || !max_particles || !out) return fail(SPH_E_INVALID, "batch_create: NULL argument");
+    *out = nullptr;
+    if (n_inst < 1 || n_inst > SPH_MAX_INSTANCES)
+        return fail(SPH_E_INVALID, "batch_create: n_inst must be in [1, %d]", SPH_MAX_INSTANCES);
+    std::vector<Inst> in(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+        sph_status r = make_instance(domains + i, sizings + i, params + i, max_particles[i], in[i]);
+        if (r != SPH_OK) return fail(r, "instance %d: %s", i, g_err.c_str());
+        if (domains[i].dim != domains[0].dim || params[i].precision != params[0].precision)
+            return fail(SPH_E_INVALID, "instance %d: every instance needs the same dim and precision", i);
     }
-    if (n_out) *n_out = k;
+    sph_batch* b = new sph_batch();
+    b->D = domains[0].dim;
+    b->prec = params[0].precision;
+    b->in = in;
+    sph_status r = batch_init(b, stream);
+    if (r != SPH_OK) {
+        batch_free(b);
+        delete b;
+        return r;
+    }
+    // every instance starts idle (no particles, controller DONE)
+    std::vector<Ctrl> c(b->NI);
+    for (Ctrl& x : c) {
+        host_ctrl_init(&x);
+        ctrl_inf_bits(b->prec, &x);
+        x.phase = PH_DONE;
+        x.sample_now = 0;
+        x.f = 0.0;
+        x.f_f = 0.0f;
+    }
+    if (cudaMemcpyAsync(b->d_ctrl, c.data(), sizeof(Ctrl) * b->NI, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        batch_free(b);
+        delete b;
+        return fail(SPH_E_CUDA, "device initialisation failed");
+    }
+    *out = b;
     return SPH_OK;
+}
+
+sph_status sph_batch_size(const sph_batch* b, int32_t* n_inst, int64_t* n_slots, int64_t* slot_capacity) {
+    if (!b) return fail(SPH_E_INVALID, "batch_size: NULL handle");
+    if (n_inst) *n_inst = b->NI;
+    if (n_slots) *n_slots = b->nslots;
+    if (slot_capacity) *slot_capacity = b->slot_cap;
+    return SPH_OK;
+}
+
+sph_status sph_batch_set_problem(sph_batch* b, int32_t inst, const sph_domain_desc* dd, const sph_sizing_desc* sz,
+                                 const sph_params* pp) {
+    if (!b || !dd || !sz || !pp) return fail(SPH_E_INVALID, "set_problem: NULL argument");
+    if (inst < 0 || inst >= b->NI) return fail(SPH_E_INVALID, "set_problem: instance %d out of range", inst);
+    if (dd->dim != b->D || pp->precision != b->prec)
+        return fail(SPH_E_INVALID, "set_problem: dim and precision must match the batch");
+    Inst I;
+    sph_status r = make_instance(dd, sz, pp, b->in[inst].cap, I);
+    if (r != SPH_OK) return r;
+    CK(cudaSetDevice(b->device));
+    CK(cudaStreamSynchronize(b->stream));
+    const Inst old = b->in[inst];
+    I.off = old.off;
+    I.slots = old.slots;
+    I.n = old.n;
+    b->in[inst] = I;
+    r = DISPATCH(b, set_state_impl, b, inst, 0, nullptr, nullptr, nullptr, nullptr, true);
+    if (r != SPH_OK) b->in[inst] = old;
+    return r;
+}
+
+sph_status sph_batch_set_state(sph_batch* b, int32_t inst, int64_t n, const double* x, const int32_t* group,
+                               const double* v, const double* h) {
+    if (!b) return fail(SPH_E_INVALID, "set_state: NULL handle");
+    if (inst < 0 || inst >= b->NI) return fail(SPH_E_INVALID, "set_state: instance %d out of range", inst);
+    sph_status r = check_args(b, inst, n, x, group, v, h);
+    if (r != SPH_OK) return r;
+    return DISPATCH(b, set_state_impl, b, inst, n, x, group, v, h, true);
+}
+
+sph_status sph_batch_step(sph_batch* b, int32_t n_steps) {
+    if (!b) return fail(SPH_E_INVALID, "step: NULL handle");
+    if (n_steps < 0) return fail(SPH_E_INVALID, "step: n_steps < 0");
+    return DISPATCH(b, step_impl, b, n_steps);
+}
+
+sph_status sph_batch_sync(sph_batch* b) {
+    if (!b) return fail(SPH_E_INVALID, "sync: NULL handle");
+    CK(cudaStreamSynchronize(b->stream));
+    return check_status(b);
+}
+
+sph_status sph_batch_run_until_converged(sph_batch* b, int64_t max_iters, int64_t* iters_out) {
+    if (!b) return fail(SPH_E_INVALID, "run: NULL handle");
+    if (max_iters < 0) return fail(SPH_E_INVALID, "run: max_iters < 0");
+    return run_impl(b, max_iters, iters_out);
+}
+
+sph_status sph_batch_positions(sph_batch* b, int32_t inst, double* x_out, int32_t* group_out, double* v_out,
+                               double* h_out, int64_t capacity, int64_t* n_out) {
+    if (!b) return fail(SPH_E_INVALID, "positions: NULL handle");
+    if (inst < 0 || inst >= b->NI) return fail(SPH_E_INVALID, "positions: instance %d out of range", inst);
+    const int n = b->in[inst].n;
+    if (n_out) *n_out = n;
+    if (capacity < n) return fail(SPH_E_INVALID, "positions: capacity %lld < n %d", (long long)capacity, n);
+    if (n == 0) return SPH_OK;
+    return DISPATCH(b, positions_impl, b, inst, x_out, group_out, v_out, h_out);
+}
+
+sph_status sph_batch_reports(sph_batch* b, sph_report* out, int32_t cap) {
+    if (!b || !out) return fail(SPH_E_INVALID, "reports: NULL argument");
+    if (cap < b->NI) return fail(SPH_E_INVALID, "reports: capacity %d < %d instances", cap, b->NI);
+    std::vector<Ctrl> c;
+    sph_status r = read_ctrls(b, c);
+    if (r != SPH_OK) return r;
+    for (int i = 0; i < b->NI; ++i) fill_report(b, i, c[i], out + i);
+    return SPH_OK;
+}
+
+sph_status sph_batch_set_timing(sph_batch* b, int32_t enable) {
+    if (!b) return fail(SPH_E_INVALID, "set_timing: NULL handle");
+    return set_timing_impl(b, enable);
+}
+
+sph_status sph_batch_kernel_times(sph_batch* b, sph_kernel_time* out, int32_t cap, int32_t* n_out) {
+    if (!b) return fail(SPH_E_INVALID, "kernel_times: NULL handle");
+    if (cap > 0 && !out) return fail(SPH_E_INVALID, "kernel_times: NULL output");
+    return kernel_times_impl(b, out, cap, n_out);
+}
+
+sph_status sph_batch_slot_bytes(int32_t dim, int32_t precision, int64_t* bytes_per_slot) {
+    if (!bytes_per_slot) return fail(SPH_E_INVALID, "slot_bytes: NULL argument");
+    if (dim != 2 && dim != 3) return fail(SPH_E_INVALID, "slot_bytes: dim must be 2 or 3");
+    if (precision != 32 && precision != 64) return fail(SPH_E_INVALID, "slot_bytes: precision must be 32 or 64");
+    sph_batch b;
+    b.D = dim;
+    b.prec = precision;
+    b.slot_cap = 1 << 20;
+    const size_t bytes = precision == 32 ? slot_layout<float>(&b, nullptr, false) : slot_layout<double>(&b, nullptr, false);
+    // plus the chunk table
+    *bytes_per_slot = (int64_t)((bytes + (size_t)b.slot_cap - 1) / (size_t)b.slot_cap) + 1;
+    return SPH_OK;
+}
+
+void sph_batch_destroy(sph_batch* b) {
+    if (!b) return;
+    batch_free(b);
+    delete b;
 }
 
 }  // extern "C"

@@ -20,7 +20,7 @@ __device__ inline void window_reset(Ctrl* c) {
     }
 }
 
-// One block of 256 threads.  The controller state is copied into shared memory at once, the
+// One block of 256 threads per instance.  The controller state is copied into shared memory at once, the
 // per-block V~ sums of a sampling step are reduced in a fixed order, and the controller for
 // step n runs with one thread per group (thread 0 keeps the scalar state):
 //  1. RAMP -> PHASE2 after ramp_len steps (windows restart);
@@ -34,22 +34,29 @@ __device__ inline void window_reset(Ctrl* c) {
 //  4. per group dt = min(dta, dtv/f), nullified (dt = dta) on the schedule or when dt falls
 //     below dt_collapse times the group's previous step; dt <= dt_cap (Eq. 24).
 // DONE freezes the state (dt = 0, the step counter stops).
-template <typename T> __global__ void __launch_bounds__(256) k_control(Params p, State<T> s) {
+template <typename T, int D> __global__ void __launch_bounds__(256) k_control(State<T> s) {
     __shared__ double vs[MAXF], et[MAXF], ea[MAXF];
     __shared__ Ctrl sc;
+    __shared__ Params p;
     __shared__ int fl[4];          // 0: done, 1: sampling step, 2: window closes, 3: reset windows
     __shared__ double par[3];      // eps, f, periodic
+    const int inst = blockIdx.x;
     constexpr int NW = (int)(sizeof(Ctrl) / sizeof(unsigned));
     unsigned* scw = reinterpret_cast<unsigned*>(&sc);
-    unsigned* gw = reinterpret_cast<unsigned*>(s.ctrl);
-    const int t = threadIdx.x, G = p.G;
+    unsigned* gw = reinterpret_cast<unsigned*>(s.ctrls + inst);
+    const int t = threadIdx.x;
     for (int k = t; k < NW; k += blockDim.x) scw[k] = gw[k];
+    block_copy(&p, s.params + inst);
     __syncthreads();
+    const int G = p.G;
     if (sc.sample_now != 0) {
+        // the pair-pass blocks of this instance (BLOCK/LPP slots each)
+        constexpr int PB = BLOCK / Lpp<D>::v;
+        const int b0 = __ldg(s.inst_off + inst) / PB, b1 = __ldg(s.inst_off + inst + 1) / PB;
         const int lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
         for (int g = wid; g < G; g += nw) {
             double acc = 0.0;
-            for (int b = lane; b < s.nblk; b += 32) acc += s.partials[(size_t)b * G + g];
+            for (int b = b0 + lane; b < b1; b += 32) acc += s.partials[(size_t)b * MAXF + g];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
             if (lane == 0) vs[g] = acc;
@@ -246,14 +253,37 @@ template <typename T> __device__ __forceinline__ T domain_phi_t(const Domain& do
 //   v+ <- Pi(x+) v+;  volume: phi(x+) < 0 -> back to phi = 0.01 h along grad phi (FP64),
 //   v+ = 0, escape counted;  h+ = h_t(x+).
 // The neighbour sum uses the walk of the pressure pass (same pairs, same predicate), with LPP
-// lanes per particle; the lead lane does the update.
+// lanes per particle; the lead lane does the update.  As in the pressure pass, a block lies in
+// one instance.  Padding slots are copied through unchanged.
 template <typename T, int D>
-__global__ void __launch_bounds__(BLOCK) k_integrate(Grid g, Params p, State<T> s, const Ctrl* cu, Out<T> o) {
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 2) k_integrate(State<T> s, const Ctrl* use, Out<T> o) {
     constexpr int LPP = Lpp<D>::v;
     __shared__ int2 sbuf[BUF_CAP * BLOCK];
+    __shared__ Grid g;
+    __shared__ Params p;
+    const int inst = __ldg(s.chunk_inst + (blockIdx.x * (BLOCK / LPP)) / CHUNK);
+    const Ctrl* const cu = use + inst;
+    Ctrl* const ctrl = s.ctrls + inst;
+    const Domain& dom = s.doms[inst];
+    block_copy(&g, s.grids + inst);
+    block_copy(&p, s.params + inst);
+    __syncthreads();
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) / LPP;
     const bool lead = (threadIdx.x % LPP) == 0;
-    const bool inrange = k < s.n;
+    if (k < s.n && !live(s, inst, k)) {   // padding: keep the slot as it is
+        if (lead) {
+            for (int a = 0; a < D; ++a) {
+                o.C[a][k] = s.Cs[a][k];
+                o.O[a][k] = s.Os[a][k];
+                o.V[a][k] = s.Vs[a][k];
+                if (o.av[a]) o.av[a][k] = T(0);
+            }
+            o.H[k] = s.Hs[k];
+            o.G[k] = 0u;
+            o.ID[k] = s.IDs[k];
+        }
+    }
+    const bool inrange = k < s.n && live(s, inst, k);
     T offi[3] = {T(0), T(0), T(0)}, hi = T(1);
     unsigned mi = 0;
     int c[3] = {0, 0, 0};            // stored position: finest cell + offset
@@ -290,7 +320,7 @@ __global__ void __launch_bounds__(BLOCK) k_integrate(Grid g, Params p, State<T> 
         if (di < D) {
             T xi[3];
             pos_t<T, D>(g, c, o3, xi);
-            feature_tangent<T>(s.dom->f[gi], xi, tg);
+            feature_tangent<T>(dom.f[gi], xi, tg);
         }
     }
     if (p.visc > 0.0 && !done) {
@@ -347,7 +377,7 @@ __global__ void __launch_bounds__(BLOCK) k_integrate(Grid g, Params p, State<T> 
     }
     if (!lead) return;
     if (moving) {
-        const Feat& fi = s.dom->f[gi];
+        const Feat& fi = dom.f[gi];
         // x+ = x + dt v+, advanced on the offset and re-normalised into the finest cell
         const T c0 = (T)g.c0, inv_c0 = T(1) / c0;
         bool clamped = false;
@@ -366,24 +396,24 @@ __global__ void __launch_bounds__(BLOCK) k_integrate(Grid g, Params p, State<T> 
             }
             o3[a] = oa;
         }
-        if (clamped) atomicOr(&s.ctrl->status, ST_OUTSIDE_GRID);
+        if (clamped) atomicOr(&ctrl->status, ST_OUTSIDE_GRID);
         T xt[3];
         pos_t<T, D>(g, c, o3, xt);
         if (fi.kind == K_VOLUME) {
             // working-precision pre-check; the FP64 level set only close to or outside the boundary
-            if (!(domain_phi_t<T>(*s.dom, xt) > T(1e-3) * hi)) {
+            if (!(domain_phi_t<T>(dom, xt) > T(1e-3) * hi)) {
                 double x[3], gph[3];
                 pos64<T, D>(g, c, o3, x);
-                double ph = domain_phi(*s.dom, x, gph);
+                double ph = domain_phi(dom, x, gph);
                 if (ph < 0.0) {
                     const double target = 0.01 * (double)hi;
                     for (int it = 0; it < 3 && ph < 0.5 * target; ++it) {
                         double g2 = gph[0] * gph[0] + gph[1] * gph[1] + gph[2] * gph[2];
                         for (int a = 0; a < D; ++a) x[a] += (target - ph) * gph[a] / g2;
-                        ph = domain_phi(*s.dom, x, gph);
+                        ph = domain_phi(dom, x, gph);
                     }
                     v[0] = v[1] = v[2] = T(0);
-                    atomicAdd(&s.ctrl->escapes, 1ull);
+                    atomicAdd(&ctrl->escapes, 1ull);
                     fine_of<T, D>(g, x, c, o3);
                     pos_t<T, D>(g, c, o3, xt);
                 }
@@ -400,10 +430,10 @@ __global__ void __launch_bounds__(BLOCK) k_integrate(Grid g, Params p, State<T> 
             fine_of<T, D>(g, x, c, o3);
             pos_t<T, D>(g, c, o3, xt);
         }
-        hnew = sizing_h_t<T>(*s.siz, xt);
+        hnew = sizing_h_t<T>(s.sizs[inst], xt);
         bool fin = true;
         for (int a = 0; a < D; ++a) fin = fin && isfinite(o3[a]) && isfinite(v[a]);
-        if (!fin) atomicOr(&s.ctrl->status, ST_NONFINITE);
+        if (!fin) atomicOr(&ctrl->status, ST_NONFINITE);
     }
     if (!inrange) return;
     if (di == 0) v[0] = v[1] = v[2] = T(0);
@@ -418,20 +448,16 @@ __global__ void __launch_bounds__(BLOCK) k_integrate(Grid g, Params p, State<T> 
     o.ID[k] = s.IDs[k];
 }
 
-template <typename T> void launch_control(const Params& p, const State<T>& s, cudaStream_t st) {
-    k_control<T><<<1, 256, 0, st>>>(p, s);
+template <typename T, int D> void launch_control(const State<T>& s, cudaStream_t st) {
+    k_control<T, D><<<s.NI, 256, 0, st>>>(s);
 }
-template <typename T, int D>
-void launch_integrate(const Grid& g, const Params& p, const State<T>& s, const Ctrl* use, const Out<T>& o,
-                      cudaStream_t st) {
-    k_integrate<T, D><<<div_up((long long)s.n * Lpp<D>::v, BLOCK), BLOCK, 0, st>>>(g, p, s, use, o);
+template <typename T, int D> void launch_integrate(const State<T>& s, const Ctrl* use, const Out<T>& o, cudaStream_t st) {
+    k_integrate<T, D><<<div_up((long long)s.n * Lpp<D>::v, BLOCK), BLOCK, 0, st>>>(s, use, o);
 }
 
-template void launch_control<float>(const Params&, const State<float>&, cudaStream_t);
-template void launch_control<double>(const Params&, const State<double>&, cudaStream_t);
-#define SPH_INST(T, D)                                                                                          \
-    template void launch_integrate<T, D>(const Grid&, const Params&, const State<T>&, const Ctrl*, const Out<T>&, \
-                                         cudaStream_t);
+#define SPH_INST(T, D)                                                      \
+    template void launch_control<T, D>(const State<T>&, cudaStream_t);      \
+    template void launch_integrate<T, D>(const State<T>&, const Ctrl*, const Out<T>&, cudaStream_t);
 SPH_INST(float, 2)
 SPH_INST(float, 3)
 SPH_INST(double, 2)

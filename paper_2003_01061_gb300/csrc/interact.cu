@@ -11,30 +11,40 @@
 //   a_p,i   = Pi_i(-F_i / gamma_i),  V~_i = 1 / sigma_i
 // and the Eq. 24 candidates 0.25 sqrt(r_c/|a_p|), r_c/(40 |v|), reduced to per-group minima.
 // On sampling steps each block also writes its per-group sums of V~ (Eq. 22) in a fixed order.
+//
+// A block serves BLOCK/LPP consecutive slots, which lie in one chunk and so in one instance:
+// the instance's grid and parameters are copied into shared memory once per block.
 #include "sph_internal.cuh"
 
 namespace sph {
 
 template <typename T, int D>
-__global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s, T* dbg_sigma, T* dbg_gamma) {
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTERACT_MINB : 2) k_interact(State<T> s, T* dbg_sigma, T* dbg_gamma) {
     constexpr int LPP = Lpp<D>::v;
     __shared__ unsigned long long sh_dta[MAXF], sh_dtv[MAXF];
     __shared__ double sh_part[BLOCK / 32][MAXF];
     __shared__ int2 sbuf[BUF_CAP * BLOCK];
-    const int G = p.G;
+    __shared__ Grid g;
+    __shared__ Params p;
+    const int inst = __ldg(s.chunk_inst + (blockIdx.x * (BLOCK / LPP)) / CHUNK);
+    Ctrl* const ctrl = s.ctrls + inst;
+    const Domain& dom = s.doms[inst];
+    block_copy(&g, s.grids + inst);
+    block_copy(&p, s.params + inst);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int t = threadIdx.x; t < G; t += blockDim.x) {
+    for (int t = threadIdx.x; t < MAXF; t += blockDim.x) {
         sh_dta[t] = inf_bits<T>();
         sh_dtv[t] = inf_bits<T>();
     }
-    const bool sample = s.ctrl->sample_now != 0;
+    const bool sample = ctrl->sample_now != 0;
     if (sample)
         for (int t = threadIdx.x; t < (BLOCK / 32) * MAXF; t += blockDim.x) (&sh_part[0][0])[t] = 0.0;
     __syncthreads();
+    const int G = p.G;
 
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) / LPP;
     const bool lead = (threadIdx.x % LPP) == 0;
-    const bool inrange = k < s.n;
+    const bool inrange = k < s.n && live(s, inst, k);
     T offi[3] = {T(0), T(0), T(0)}, hi = T(1);
     unsigned mi = 0;
     int li = 0, ci[3] = {0, 0, 0};
@@ -44,12 +54,13 @@ __global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s
     }
     const int gi = inrange ? meta_group(mi) : -1;
     const int di = inrange ? meta_dim(mi) : 0;
-    const bool active = inrange && di > 0;
+    // a converged (DONE) instance is frozen: no pair work
+    const bool active = inrange && di > 0 && ctrl->phase != PH_DONE;
     T tg[3] = {T(0), T(0), T(0)};
     if (active && di < D) {
         T xi[3] = {T(0), T(0), T(0)};
         for (int a = 0; a < D; ++a) xi[a] = (T)g.origin[a] + (T)(ci[a] << li) * (T)g.c0 + offi[a];
-        feature_tangent<T>(s.dom->f[gi], xi, tg);
+        feature_tangent<T>(dom.f[gi], xi, tg);
     }
     const T kappa = wp<T>(p.kappa, p.kappa_f), hk = T(0.5) * kappa, p0 = wp<T>(p.p0, p.p0_f);
     const T rci2 = self_rc2(hi, kappa);
@@ -109,7 +120,7 @@ __global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s
                 T xb[3] = {T(0), T(0), T(0)};
                 for (int a = 0; a < D; ++a) xb[a] = org[a] + (T)(cj[a] << l) * c0 + offj[a];
                 T nb[3];
-                boundary_normal<T>(s.dom->f[meta_group(mj)], xb, nb);
+                boundary_normal<T>(dom.f[meta_group(mj)], xb, nb);
                 tangent_map<T>(di, D, tg, nb);
                 const T nn2 = nb[0] * nb[0] + nb[1] * nb[1] + nb[2] * nb[2];
                 if (nn2 > T(1e-12)) {
@@ -139,7 +150,7 @@ __global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s
         const T vn = t_sqrt(v0 * v0 + v1 * v1 + v2 * v2);
         const T dta = an > T(0) ? wp<T>(p.cfl_a, p.cfl_a_f) * t_sqrt(rc / an) : T(CUDART_INF_F);
         const T dtv = vn > T(0) ? wp<T>(p.cfl_v, p.cfl_v_f) * rc / vn : T(CUDART_INF_F);
-        if (!(an == an) || !isfinite(an)) atomicOr(&s.ctrl->status, ST_NONFINITE);
+        if (!(an == an) || !isfinite(an)) atomicOr(&ctrl->status, ST_NONFINITE);
         atomicMin(&sh_dta[gi], min_bits(dta));
         atomicMin(&sh_dtv[gi], min_bits(dtv));
     }
@@ -170,25 +181,29 @@ __global__ void __launch_bounds__(BLOCK) k_interact(Grid g, Params p, State<T> s
     }
     __syncthreads();
     for (int t = threadIdx.x; t < G; t += blockDim.x) {
-        if (sh_dta[t] != inf_bits<T>()) atomicMin(&s.ctrl->dta_bits[t], sh_dta[t]);
-        if (sh_dtv[t] != inf_bits<T>()) atomicMin(&s.ctrl->dtv_bits[t], sh_dtv[t]);
+        if (sh_dta[t] != inf_bits<T>()) atomicMin(&ctrl->dta_bits[t], sh_dta[t]);
+        if (sh_dtv[t] != inf_bits<T>()) atomicMin(&ctrl->dtv_bits[t], sh_dtv[t]);
         if (sample) {
             double acc = 0.0;
             for (int w = 0; w < BLOCK / 32; ++w) acc += sh_part[w][t];
-            s.partials[(size_t)blockIdx.x * G + t] = acc;
+            s.partials[(size_t)blockIdx.x * MAXF + t] = acc;
         }
     }
 }
 
 // neighbour sets for inspection, through the same walk as the pair passes (one lane per
 // particle): mode 0 pair predicate (j != i), mode 1 self predicate (j = i included), over all
-// groups.  lists == nullptr: count only.
+// groups.  lists == nullptr: count only.  (A block spans several chunks: the instance is
+// looked up per slot.)
 template <typename T, int D>
-__global__ void __launch_bounds__(BLOCK) k_neighbors(Grid g, Params p, State<T> s, int mode, int* counts,
-                                                     const long long* offsets, int* lists) {
+__global__ void __launch_bounds__(BLOCK) k_neighbors(State<T> s, int mode, int* counts, const long long* offsets,
+                                                     int* lists) {
     __shared__ int2 sbuf[BUF_CAP * BLOCK];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = k < s.n;
+    const int inst = k < s.n ? inst_of(s, k) : 0;
+    const Grid& g = s.grids[inst];
+    const Params& p = s.params[inst];
+    const bool active = k < s.n && live(s, inst, k);
     T offi[3] = {T(0), T(0), T(0)}, hi = T(1);
     unsigned mi = 0;
     int li = 0, ci[3] = {0, 0, 0};
@@ -209,16 +224,19 @@ __global__ void __launch_bounds__(BLOCK) k_neighbors(Grid g, Params p, State<T> 
             if (lists) lists[base + cnt] = j;
             ++cnt;
         });
-    if (active && !lists) counts[k] = cnt;
+    if (k < s.n && !lists) counts[k] = cnt;
 }
 
 // candidate pairs examined and pairs inside the interaction support of the pressure pass,
 // summed over all particles (one lane per particle)
 template <typename T, int D>
-__global__ void __launch_bounds__(BLOCK) k_pair_counts(Grid g, Params p, State<T> s, unsigned long long* out2) {
+__global__ void __launch_bounds__(BLOCK) k_pair_counts(State<T> s, unsigned long long* out2) {
     __shared__ int2 sbuf[BUF_CAP * BLOCK];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool inrange = k < s.n;
+    const int inst = k < s.n ? inst_of(s, k) : 0;
+    const Grid& g = s.grids[inst];
+    const Params& p = s.params[inst];
+    const bool inrange = k < s.n && live(s, inst, k);
     T offi[3] = {T(0), T(0), T(0)}, hi = T(1);
     unsigned mi = 0;
     int li = 0, ci[3] = {0, 0, 0};
@@ -247,26 +265,21 @@ __global__ void __launch_bounds__(BLOCK) k_pair_counts(Grid g, Params p, State<T
     }
 }
 
-template <typename T, int D>
-void launch_interact(const Grid& g, const Params& p, const State<T>& s, T* dbg_sigma, T* dbg_gamma, cudaStream_t st) {
-    k_interact<T, D><<<s.nblk, BLOCK, 0, st>>>(g, p, s, dbg_sigma, dbg_gamma);
+template <typename T, int D> void launch_interact(const State<T>& s, T* dbg_sigma, T* dbg_gamma, cudaStream_t st) {
+    k_interact<T, D><<<s.nblk, BLOCK, 0, st>>>(s, dbg_sigma, dbg_gamma);
 }
 template <typename T, int D>
-void launch_neighbors(const Grid& g, const Params& p, const State<T>& s, int mode, int* counts,
-                      const long long* offsets, int* lists, cudaStream_t st) {
-    k_neighbors<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(g, p, s, mode, counts, offsets, lists);
+void launch_neighbors(const State<T>& s, int mode, int* counts, const long long* offsets, int* lists, cudaStream_t st) {
+    k_neighbors<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s, mode, counts, offsets, lists);
 }
-template <typename T, int D>
-void launch_pair_counts(const Grid& g, const Params& p, const State<T>& s, unsigned long long* out2, cudaStream_t st) {
-    k_pair_counts<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(g, p, s, out2);
+template <typename T, int D> void launch_pair_counts(const State<T>& s, unsigned long long* out2, cudaStream_t st) {
+    k_pair_counts<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s, out2);
 }
 
 #define SPH_INST(T, D)                                                                                        \
-    template void launch_interact<T, D>(const Grid&, const Params&, const State<T>&, T*, T*, cudaStream_t);     \
-    template void launch_neighbors<T, D>(const Grid&, const Params&, const State<T>&, int, int*,              \
-                                         const long long*, int*, cudaStream_t);                               \
-    template void launch_pair_counts<T, D>(const Grid&, const Params&, const State<T>&, unsigned long long*,  \
-                                           cudaStream_t);
+    template void launch_interact<T, D>(const State<T>&, T*, T*, cudaStream_t);                               \
+    template void launch_neighbors<T, D>(const State<T>&, int, int*, const long long*, int*, cudaStream_t);   \
+    template void launch_pair_counts<T, D>(const State<T>&, unsigned long long*, cudaStream_t);
 SPH_INST(float, 2)
 SPH_INST(float, 3)
 SPH_INST(double, 2)

@@ -1,18 +1,26 @@
 // rebuild.cu -- cell-list rebuild (Algorithm 1: "update the multi-level data structure",
-// "construct Verlet neighbour list"): cell key per particle, per-cell histogram, exclusive scan,
-// scatter, per-cell ordering by stored index (which makes the counting sort stable and
-// deterministic), and the gather of the state into sorted order with cell-relative offsets.
+// "construct Verlet neighbour list") for every instance of a batch at once: cell key per
+// particle, per-cell histogram, exclusive scan, scatter, and the gather of the state into
+// sorted order with cell-relative offsets; the gather also orders each cell by stored index,
+// which makes the counting sort stable and deterministic.
 #include "sph_internal.cuh"
 
 namespace sph {
 
 // ---- key + histogram ----
-template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_hash(Grid g, State<T> s) {
+template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_hash(State<T> s) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
-    const int l = level_of(g, s.H[i]);
-    int cell[3] = {s.C[0][i] >> l, s.C[1][i] >> l, D == 3 ? s.C[2][i] >> l : 0};
-    const int key = key_of(g, l, cell);
+    const int inst = inst_of(s, i);
+    const Grid& g = s.grids[inst];
+    int key;
+    if (!live(s, inst, i)) {
+        key = g.base[MAXL];                      // padding: the instance's dummy cell
+    } else {
+        const int l = level_of(g, s.H[i]);
+        int cell[3] = {s.C[0][i] >> l, s.C[1][i] >> l, D == 3 ? s.C[2][i] >> l : 0};
+        key = key_of(g, l, cell);
+    }
     s.K[i] = key;
     atomicAdd(s.count + key, 1);
 }
@@ -145,12 +153,12 @@ __global__ void __launch_bounds__(BLOCK) k_cellsort(int ncell, int n, const int*
 // whose stored index has rank (k - start_c) among the cell's particles, which makes the
 // counting sort stable.  Usually a cell's particles were consecutive in the stored order (it
 // is the previous step's sorted order), and the rank is found from the cell's minimum.
-template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_gather(Grid g, State<T> s) {
+template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_gather(State<T> s) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= s.n) return;
     int i = s.perm[k];
     if ((unsigned)i >= (unsigned)s.n) {   // defensive: a broken permutation is reported, not followed
-        atomicOr(&s.ctrl->status, ST_NONFINITE);
+        atomicOr(&s.ctrls[0].status, ST_NONFINITE);
         i = 0;
     }
     {
@@ -192,6 +200,9 @@ template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_gather(G
     s.Hs[k] = h;
     s.IDs[k] = s.ID[i];
     s.Ks[k] = s.K[i];
+    const int inst = inst_of(s, k);
+    if (!live(s, inst, k)) return;               // padding slot (sorted last in its instance)
+    const Grid& g = s.grids[inst];
     const int l = level_of(g, h);
     int cell[3];
     T off[3];
@@ -201,23 +212,64 @@ template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_gather(G
         const int t = g.L - 1;
         int ct[3] = {0, 0, 0};
         for (int a = 0; a < D; ++a) ct[a] = min((cell[a] << l) >> t, g.dims[t][a] - 1);
-        atomicOr(s.occ + (ct[2] * g.dims[t][1] + ct[1]) * g.dims[t][0] + ct[0], 1u << l);
+        atomicOr(s.occ + g.occ_base + (ct[2] * g.dims[t][1] + ct[1]) * g.dims[t][0] + ct[0], 1u << l);
     }
 }
 
-// ---- initial smoothing lengths h = h_t(x) ----
-template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_init_h(Grid g, State<T> s) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= s.n) return;
+// ---- initial smoothing lengths h = h_t(x) of one instance ----
+template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_init_h(State<T> s, int inst) {
+    const int i = __ldg(s.inst_off + inst) + blockIdx.x * blockDim.x + threadIdx.x;
+    if (!live(s, inst, i) || i >= __ldg(s.inst_off + inst + 1)) return;
+    const Grid& g = s.grids[inst];
     int c[3] = {s.C[0][i], s.C[1][i], D == 3 ? s.C[2][i] : 0};
     T o[3] = {s.O[0][i], s.O[1][i], D == 3 ? s.O[2][i] : T(0)};
     double x[3];
     pos64<T, D>(g, c, o, x);
-    s.H[i] = (T)sizing_h(*s.siz, x);
+    s.H[i] = (T)sizing_h(s.sizs[inst], x);
 }
 
-template <typename T, int D> void launch_hash(const Grid& g, const State<T>& s, cudaStream_t st) {
-    k_hash<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(g, s);
+// ---- batch re-packing: instance i's stored state moves from slot old_off[i] to its new offset
+// s.inst_off[i] (the first move_n[i] slots).  Pass 0 copies the stored arrays into the sorted
+// arrays (scratch here: the next gather rewrites them), pass 1 copies them back, so moves
+// between overlapping ranges never read a slot that was already overwritten.
+template <typename T, int D>
+__global__ void __launch_bounds__(BLOCK) k_repack(State<T> s, const int* __restrict__ old_off,
+                                                  const int* __restrict__ move_n, int pass) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= s.n) return;
+    const int i = inst_of(s, k);
+    const int r = k - __ldg(s.inst_off + i);
+    if (r >= __ldg(move_n + i)) return;
+    if (pass == 0) {
+        const int src = __ldg(old_off + i) + r;
+        for (int a = 0; a < D; ++a) {
+            s.Cs[a][k] = s.C[a][src];
+            s.Os[a][k] = s.O[a][src];
+            s.Vs[a][k] = s.V[a][src];
+        }
+        s.Hs[k] = s.H[src];
+        s.Ms[k] = s.G[src];
+        s.IDs[k] = s.ID[src];
+    } else {
+        for (int a = 0; a < D; ++a) {
+            s.C[a][k] = s.Cs[a][k];
+            s.O[a][k] = s.Os[a][k];
+            s.V[a][k] = s.Vs[a][k];
+        }
+        s.H[k] = s.Hs[k];
+        s.G[k] = s.Ms[k];
+        s.ID[k] = s.IDs[k];
+    }
+}
+
+template <typename T, int D> void launch_repack(const State<T>& s, const int* old_off, const int* move_n, cudaStream_t st) {
+    if (s.n == 0) return;
+    k_repack<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s, old_off, move_n, 0);
+    k_repack<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s, old_off, move_n, 1);
+}
+
+template <typename T, int D> void launch_hash(const State<T>& s, cudaStream_t st) {
+    k_hash<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s);
 }
 void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t st, unsigned* occ, int nocc,
                  bool relative) {
@@ -232,17 +284,18 @@ template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st) {
 void launch_cellsort(int ncell, int n, const int* cell_start, int* perm, int* count, cudaStream_t st) {
     k_cellsort<<<div_up(ncell, BLOCK), BLOCK, 0, st>>>(ncell, n, cell_start, perm, count);
 }
-template <typename T, int D> void launch_gather(const Grid& g, const State<T>& s, cudaStream_t st) {
-    k_gather<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(g, s);
+template <typename T, int D> void launch_gather(const State<T>& s, cudaStream_t st) {
+    k_gather<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s);
 }
-template <typename T, int D> void launch_init_h(const Grid& g, const State<T>& s, cudaStream_t st) {
-    k_init_h<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(g, s);
+template <typename T, int D> void launch_init_h(const State<T>& s, int inst, cudaStream_t st) {
+    k_init_h<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s, inst);   // threads past the instance exit
 }
 
-#define SPH_INST(T, D)                                                          \
-    template void launch_hash<T, D>(const Grid&, const State<T>&, cudaStream_t);   \
-    template void launch_gather<T, D>(const Grid&, const State<T>&, cudaStream_t); \
-    template void launch_init_h<T, D>(const Grid&, const State<T>&, cudaStream_t);
+#define SPH_INST(T, D)                                                    \
+    template void launch_hash<T, D>(const State<T>&, cudaStream_t);        \
+    template void launch_gather<T, D>(const State<T>&, cudaStream_t);      \
+    template void launch_init_h<T, D>(const State<T>&, int, cudaStream_t);  \
+    template void launch_repack<T, D>(const State<T>&, const int*, const int*, cudaStream_t);
 SPH_INST(float, 2)
 SPH_INST(float, 3)
 SPH_INST(double, 2)

@@ -71,8 +71,9 @@ struct Grid {
     float cf[MAXL];      // c0 * 2^l as float (exact)
     float thr[MAXL];
     int dims[MAXL][3];
-    int base[MAXL + 1];
-    int ncell;
+    int base[MAXL + 1];  // first key of each level; base[MAXL]: the instance's dummy key
+    int ncell;           // cells of the instance (its keys are base[0] .. base[0]+ncell-1)
+    int occ_base;        // first entry of the instance's top-level cells in the occupancy array
 };
 
 struct Params {
@@ -506,7 +507,8 @@ __device__ __forceinline__ unsigned level_mask(const Grid& g, const unsigned* __
     const int x0 = max(ct[0] - 1, 0), x1 = min(ct[0] + 1, g.dims[T_][0] - 1);
     for (int z = z0; z <= z1; ++z)
         for (int y = y0; y <= y1; ++y)
-            for (int x = x0; x <= x1; ++x) m |= __ldg(occ + (z * g.dims[T_][1] + y) * g.dims[T_][0] + x);
+            for (int x = x0; x <= x1; ++x)
+                m |= __ldg(occ + g.occ_base + (z * g.dims[T_][1] + y) * g.dims[T_][0] + x);
     return m;
 }
 

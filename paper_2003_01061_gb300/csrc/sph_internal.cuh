@@ -1,19 +1,38 @@
-// sph_internal.cuh -- device pointers of one instance and the kernel launchers shared by the
-// translation units of libsphmesh.so.  Not part of the public ABI.
+// sph_internal.cuh -- device pointers of a batch of instances and the kernel launchers shared by
+// the translation units of libsphmesh.so.  Not part of the public ABI.
+//
+// A batch packs NI independent instances (same dimension and precision) into one particle
+// array.  Instance i owns the slots [inst_off[i], inst_off[i+1]) -- its particle count rounded up
+// to a multiple of CHUNK, none while it is empty -- of which the first inst_n[i] hold its
+// particles in the current order; the rest are padding (hashed to the instance's dummy cell,
+// which sorts last and is never searched).  Its cells are the global keys grids[i].base[0] ..
+// grids[i].base[MAXL]-1, followed by its dummy key grids[i].base[MAXL].  Every kernel serves all
+// instances in one launch over the n slots in use.
 #pragma once
 #include "sph_device.cuh"
 
 namespace sph {
 
+constexpr int CHUNK = 64;      // slot alignment of instances (a multiple of every pair-pass block)
+
 template <typename T> struct State {
-    int n;
+    int n;             // total slots of the batch
+    int NI;            // instances
+    const int* inst_off;    // [NI+1]
+    const int* inst_n;      // [NI]
+    const int* chunk_inst;  // [n / CHUNK] instance of every chunk of slots
+    const Grid* grids;      // [NI]
+    const Params* params;   // [NI]
+    const Domain* doms;     // [NI]
+    const Sizing* sizs;     // [NI]
+    Ctrl* ctrls;            // [NI]
     // stored state (order of the previous sort): position = finest cell C + offset O
     int* C[3];
     T* O[3];
     T* V[3];
     T* H;
     unsigned* G;
-    int* ID;
+    int* ID;           // index of the particle in its instance's input order (-1: padding)
     int* K;            // cell key of every stored particle (written by the hash)
     // sorted state
     int* Cs[3];
@@ -32,6 +51,7 @@ template <typename T> struct State {
     int* bsum;
     int* perm;         // slot -> stored index as left by the scatter (unordered inside a cell)
     int* sperm;        // slot -> stored index, stable (ordered inside a cell; written by the gather)
+    int ncell;         // total keys (all instances' cells and dummy cells)
     // per top-level cell: bit l set when a particle of level l lies in it (built by the gather)
     unsigned* occ;
     int nocc;
@@ -44,9 +64,6 @@ template <typename T> struct State {
     // per-block, per-group partial sums of V~ (sample steps); nblk = blocks of the pair passes
     double* partials;
     int nblk;
-    Ctrl* ctrl;
-    const Domain* dom;
-    const Sizing* siz;
 };
 
 // output set of the update kernel (the stored state, or scratch for inspection calls)
@@ -71,6 +88,31 @@ template <int D> struct Vcap {
     static constexpr int v = D == 2 ? 8 : 12;
 };
 constexpr int VCAP_MAX = 12;
+
+// minimum resident blocks per SM asked of the compiler for the two pair passes (FP32 build;
+// the FP64 build asks for 2): it bounds the registers per thread, trading spills for occupancy
+#ifndef SPH_INTERACT_MINB
+#define SPH_INTERACT_MINB 4
+#endif
+#ifndef SPH_INTEGRATE_MINB
+#define SPH_INTEGRATE_MINB 3
+#endif
+
+// instance of slot k, and whether the slot holds a particle
+template <typename T> __device__ __forceinline__ int inst_of(const State<T>& s, int k) {
+    return __ldg(s.chunk_inst + k / CHUNK);
+}
+template <typename T> __device__ __forceinline__ bool live(const State<T>& s, int i, int k) {
+    return k - __ldg(s.inst_off + i) < __ldg(s.inst_n + i);
+}
+
+// copy a struct into shared memory with the whole block (one round trip)
+template <typename S> __device__ __forceinline__ void block_copy(S* dst, const S* src) {
+    const unsigned* a = reinterpret_cast<const unsigned*>(src);
+    unsigned* b = reinterpret_cast<unsigned*>(dst);
+    for (int t = threadIdx.x; t < (int)(sizeof(S) / 4); t += blockDim.x) b[t] = a[t];
+}
+
 // level and level-cell of sorted particle k (from its h and stored finest cell; the same as
 // decoding its key, without the integer divisions)
 template <typename T, int D>
@@ -86,32 +128,26 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // rebuild.cu
-template <typename T, int D> void launch_hash(const Grid& g, const State<T>& s, cudaStream_t st);
+template <typename T, int D> void launch_hash(const State<T>& s, cudaStream_t st);
 void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t st, unsigned* occ = nullptr,
                  int nocc = 0, bool relative = false);
 template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st);
 void launch_cellsort(int ncell, int n, const int* cell_start, int* perm, int* count, cudaStream_t st);
-template <typename T, int D> void launch_gather(const Grid& g, const State<T>& s, cudaStream_t st);
-template <typename T, int D> void launch_init_h(const Grid& g, const State<T>& s, cudaStream_t st);
+template <typename T, int D> void launch_gather(const State<T>& s, cudaStream_t st);
+template <typename T, int D> void launch_init_h(const State<T>& s, int inst, cudaStream_t st);
+template <typename T, int D> void launch_repack(const State<T>& s, const int* old_off, const int* move_n, cudaStream_t st);
 
 // interact.cu
+template <typename T, int D> void launch_interact(const State<T>& s, T* dbg_sigma, T* dbg_gamma, cudaStream_t st);
 template <typename T, int D>
-void launch_interact(const Grid& g, const Params& p, const State<T>& s, T* dbg_sigma, T* dbg_gamma, cudaStream_t st);
-template <typename T, int D>
-void launch_neighbors(const Grid& g, const Params& p, const State<T>& s, int mode, int* counts,
-                      const long long* offsets, int* lists, cudaStream_t st);
-template <typename T, int D>
-void launch_pair_counts(const Grid& g, const Params& p, const State<T>& s, unsigned long long* out2, cudaStream_t st);
+void launch_neighbors(const State<T>& s, int mode, int* counts, const long long* offsets, int* lists, cudaStream_t st);
+template <typename T, int D> void launch_pair_counts(const State<T>& s, unsigned long long* out2, cudaStream_t st);
 
 // integrate.cu
-template <typename T> void launch_control(const Params& p, const State<T>& s, cudaStream_t st);
-template <typename T, int D>
-void launch_integrate(const Grid& g, const Params& p, const State<T>& s, const Ctrl* use, const Out<T>& o,
-                      cudaStream_t st);
+template <typename T, int D> void launch_control(const State<T>& s, cudaStream_t st);
+template <typename T, int D> void launch_integrate(const State<T>& s, const Ctrl* use, const Out<T>& o, cudaStream_t st);
 
-}  // namespace sph
-
-namespace sph {
 // sets the message returned by sph_last_error() on the calling thread (capi.cu)
 void set_last_error(const char* msg);
+
 }  // namespace sph

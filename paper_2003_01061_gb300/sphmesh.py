@@ -70,11 +70,35 @@ class sph_kernel_time(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
 
+class sph_server_config(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_jobs", C.c_int32), ("slot_capacity", C.c_int64 * 2),
+                ("hbm_fraction", C.c_double), ("steps_per_poll", C.c_int32)]
+
+
+class sph_job_info(C.Structure):
+    _fields_ = [("state", C.c_int32), ("dim", C.c_int32), ("n", C.c_int64), ("iterations", C.c_int64),
+                ("phase", C.c_int32), ("status_word", C.c_uint32), ("escapes", C.c_int64), ("E_sys", C.c_double),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_finish", C.c_double)]
+
+
+class sph_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("finished", C.c_int64), ("running", C.c_int64), ("queued", C.c_int64),
+                ("rounds", C.c_int64), ("particle_steps", C.c_double)]
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_NOT_CONVERGED, JOB_FAILED = 1, 2, 3, 4, 5
+
+
 EXPORTS = ["sph_params_default", "sph_mesh_create", "sph_mesh_set_state", "sph_mesh_step", "sph_mesh_sync",
            "sph_mesh_run_until_converged", "sph_mesh_positions", "sph_mesh_report", "sph_mesh_destroy",
            "sph_last_error", "sph_grid_spec", "sph_mesh_grid", "sph_debug_rebuild", "sph_debug_neighbors",
            "sph_debug_interact", "sph_debug_update", "sph_mesh_set_timing", "sph_mesh_kernel_times",
-           "sph_debug_pair_counts", "sph_cell_sort_noalloc"]
+           "sph_debug_pair_counts", "sph_cell_sort_noalloc", "sph_batch_create", "sph_batch_size",
+           "sph_batch_set_problem", "sph_batch_set_state", "sph_batch_step", "sph_batch_sync",
+           "sph_batch_run_until_converged", "sph_batch_positions", "sph_batch_reports", "sph_batch_set_timing",
+           "sph_batch_kernel_times", "sph_batch_destroy", "sph_batch_slot_bytes", "sph_server_create",
+           "sph_server_submit", "sph_server_poll", "sph_server_drain", "sph_server_job", "sph_server_release",
+           "sph_server_destroy"]
 
 _lib = None
 
@@ -106,13 +130,32 @@ def lib():
             "sph_mesh_kernel_times": [vp, vp, i32, vp],
             "sph_debug_pair_counts": [vp, vp, vp],
             "sph_cell_sort_noalloc": [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp],
+            "sph_batch_create": [i32, vp, vp, vp, vp, vp, vp],
+            "sph_batch_size": [vp, vp, vp, vp],
+            "sph_batch_set_problem": [vp, i32, vp, vp, vp],
+            "sph_batch_set_state": [vp, i32, i64, vp, vp, vp, vp],
+            "sph_batch_step": [vp, i32],
+            "sph_batch_sync": [vp],
+            "sph_batch_run_until_converged": [vp, i64, vp],
+            "sph_batch_positions": [vp, i32, vp, vp, vp, vp, i64, vp],
+            "sph_batch_reports": [vp, vp, i32],
+            "sph_batch_set_timing": [vp, i32],
+            "sph_batch_kernel_times": [vp, vp, i32, vp],
+            "sph_batch_slot_bytes": [i32, i32, vp],
+            "sph_server_create": [vp, vp],
+            "sph_server_submit": [vp, vp, vp, vp, i64, vp, vp, vp, i64, vp],
+            "sph_server_poll": [vp, vp],
+            "sph_server_drain": [vp, i64, vp],
+            "sph_server_job": [vp, i64, vp, vp, vp, vp, i64],
+            "sph_server_release": [vp, i64],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = C.c_int
-        L.sph_mesh_destroy.argtypes = [vp]
-        L.sph_mesh_destroy.restype = None
+        for name in ("sph_mesh_destroy", "sph_batch_destroy", "sph_server_destroy"):
+            getattr(L, name).argtypes = [vp]
+            getattr(L, name).restype = None
         L.sph_last_error.argtypes = []
         L.sph_last_error.restype = C.c_char_p
         _lib = L
@@ -322,6 +365,140 @@ def sph_cell_sort_noalloc(grid: sph_grid_info, n, x_ptr, y_ptr, z_ptr, h_ptr, ke
                                        cell_start_ptr, perm_ptr, stream))
 
 
+def sph_batch_create(domains, sizings, params, max_particles, stream: int | None = None):
+    n = len(domains)
+    D = (sph_domain_desc * n)(*domains)
+    Z = (sph_sizing_desc * n)(*sizings)
+    P = (sph_params * n)(*params)
+    M = np.ascontiguousarray(max_particles, dtype=np.int64)
+    h = C.c_void_p()
+    _check(lib().sph_batch_create(n, D, Z, P, _p(M), stream, C.addressof(h)))
+    return h
+
+
+def sph_batch_size(b):
+    ni, ns, cap = C.c_int32(0), C.c_int64(0), C.c_int64(0)
+    _check(lib().sph_batch_size(b, C.addressof(ni), C.addressof(ns), C.addressof(cap)))
+    return ni.value, ns.value, cap.value
+
+
+def sph_batch_set_problem(b, inst, domain: sph_domain_desc, sizing: sph_sizing_desc, params: sph_params):
+    _check(lib().sph_batch_set_problem(b, int(inst), C.addressof(domain), C.addressof(sizing), C.addressof(params)))
+
+
+def sph_batch_set_state(b, inst, x, group, v=None, h=None):
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    group = np.ascontiguousarray(group, dtype=np.int32)
+    v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+    h = None if h is None else np.ascontiguousarray(h, dtype=np.float64)
+    _check(lib().sph_batch_set_state(b, int(inst), len(x), _p(x), _p(group), _p(v), _p(h)))
+
+
+def sph_batch_step(b, n_steps=1):
+    _check(lib().sph_batch_step(b, int(n_steps)))
+
+
+def sph_batch_sync(b):
+    _check(lib().sph_batch_sync(b))
+
+
+def sph_batch_run_until_converged(b, max_iters):
+    it = C.c_int64(0)
+    st = lib().sph_batch_run_until_converged(b, int(max_iters), C.addressof(it))
+    if st not in (SPH_OK, SPH_E_NOT_CONVERGED):
+        _check(st)
+    return st == SPH_OK, it.value
+
+
+def sph_batch_positions(b, inst, n):
+    x = np.zeros((n, 3))
+    g = np.zeros(n, np.int32)
+    v = np.zeros((n, 3))
+    h = np.zeros(n)
+    got = C.c_int64(0)
+    _check(lib().sph_batch_positions(b, int(inst), _p(x), _p(g), _p(v), _p(h), n, C.addressof(got)))
+    return dict(x=x, group=g, v=v, h=h)
+
+
+def sph_batch_reports(b, n_inst):
+    arr = (sph_report * n_inst)()
+    _check(lib().sph_batch_reports(b, arr, n_inst))
+    return list(arr)
+
+
+def sph_batch_set_timing(b, enable):
+    _check(lib().sph_batch_set_timing(b, int(bool(enable))))
+
+
+def sph_batch_kernel_times(b):
+    arr = (sph_kernel_time * 16)()
+    n = C.c_int32(0)
+    _check(lib().sph_batch_kernel_times(b, arr, 16, C.addressof(n)))
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(n.value)}
+
+
+def sph_batch_destroy(b):
+    if b:
+        lib().sph_batch_destroy(b)
+
+
+def sph_batch_slot_bytes(dim, precision=32):
+    v = C.c_int64(0)
+    _check(lib().sph_batch_slot_bytes(int(dim), int(precision), C.addressof(v)))
+    return v.value
+
+
+def sph_server_create(precision=32, max_jobs=64, slot_capacity=(-1, -1), hbm_fraction=0.5, steps_per_poll=20):
+    cfg = sph_server_config()
+    cfg.precision, cfg.max_jobs, cfg.hbm_fraction, cfg.steps_per_poll = precision, max_jobs, hbm_fraction, steps_per_poll
+    cfg.slot_capacity[0], cfg.slot_capacity[1] = int(slot_capacity[0]), int(slot_capacity[1])
+    h = C.c_void_p()
+    _check(lib().sph_server_create(C.addressof(cfg), C.addressof(h)))
+    return h
+
+
+def sph_server_submit(s, domain: sph_domain_desc, sizing: sph_sizing_desc, params: sph_params, x, group, h=None,
+                      max_iters=1000):
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    group = np.ascontiguousarray(group, dtype=np.int32)
+    h = None if h is None else np.ascontiguousarray(h, dtype=np.float64)
+    jid = C.c_int64(0)
+    _check(lib().sph_server_submit(s, C.addressof(domain), C.addressof(sizing), C.addressof(params), len(x), _p(x),
+                                   _p(group), _p(h), int(max_iters), C.addressof(jid)))
+    return jid.value
+
+
+def sph_server_poll(s) -> sph_server_stats:
+    st = sph_server_stats()
+    _check(lib().sph_server_poll(s, C.addressof(st)))
+    return st
+
+
+def sph_server_drain(s, max_rounds=100000) -> sph_server_stats:
+    st = sph_server_stats()
+    _check(lib().sph_server_drain(s, int(max_rounds), C.addressof(st)))
+    return st
+
+
+def sph_server_job(s, job_id, n=0):
+    info = sph_job_info()
+    if n > 0:
+        x, g, h = np.zeros((n, 3)), np.zeros(n, np.int32), np.zeros(n)
+        _check(lib().sph_server_job(s, int(job_id), C.addressof(info), _p(x), _p(g), _p(h), n))
+        return info, dict(x=x, group=g, h=h)
+    _check(lib().sph_server_job(s, int(job_id), C.addressof(info), None, None, None, 0))
+    return info, None
+
+
+def sph_server_release(s, job_id):
+    _check(lib().sph_server_release(s, int(job_id)))
+
+
+def sph_server_destroy(s):
+    if s:
+        lib().sph_server_destroy(s)
+
+
 class Mesh:
     """Owning handle: create from a workload dictionary, destroy on close / garbage collection."""
 
@@ -356,6 +533,99 @@ class Mesh:
     def close(self):
         if self.h:
             sph_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owning batch handle over a list of workload dictionaries (one instance each)."""
+
+    def __init__(self, ws: list, precision: int = 32, max_particles: list | None = None,
+                 stream: int | None = None, params: list | None = None):
+        self.ws = list(ws)
+        self.precision = precision
+        doms = [domain_desc(w["domain"]) for w in ws]
+        sizs = [sizing_desc(w["sizing"]) for w in ws]
+        prms = [params_struct((params[i] if params else None) or w["params"], precision) for i, w in enumerate(ws)]
+        caps = max_particles or [len(w["x"]) for w in ws]
+        self.caps = list(caps)
+        self.h = sph_batch_create(doms, sizs, prms, caps, stream)
+        self.n_inst = len(ws)
+        self.n = [0] * self.n_inst
+
+    def set_problem(self, inst, w, params: dict | None = None):
+        sph_batch_set_problem(self.h, inst, domain_desc(w["domain"]), sizing_desc(w["sizing"]),
+                              params_struct(params or w["params"], self.precision))
+        self.ws[inst] = w
+        self.n[inst] = 0
+
+    def set_state(self, inst, x=None, group=None, v=None, h=None):
+        w = self.ws[inst]
+        x = w["x"] if x is None else x
+        group = w["group"] if group is None else group
+        sph_batch_set_state(self.h, inst, x, group, v, h)
+        self.n[inst] = len(x)
+
+    def step(self, k=1):
+        sph_batch_step(self.h, k)
+
+    def sync(self):
+        sph_batch_sync(self.h)
+
+    def positions(self, inst):
+        return sph_batch_positions(self.h, inst, self.n[inst])
+
+    def reports(self):
+        return sph_batch_reports(self.h, self.n_inst)
+
+    def close(self):
+        if self.h:
+            sph_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owning server handle; jobs are workload dictionaries."""
+
+    def __init__(self, precision=32, max_jobs=64, slot_capacity=(-1, -1), hbm_fraction=0.5, steps_per_poll=20):
+        self.precision = precision
+        self.h = sph_server_create(precision, max_jobs, slot_capacity, hbm_fraction, steps_per_poll)
+        self.n_of = {}
+
+    def submit(self, w, max_iters, params: dict | None = None, h=None):
+        jid = sph_server_submit(self.h, domain_desc(w["domain"]), sizing_desc(w["sizing"]),
+                                params_struct(params or w["params"], self.precision), w["x"], w["group"], h,
+                                max_iters)
+        self.n_of[jid] = len(w["x"])
+        return jid
+
+    def poll(self):
+        return sph_server_poll(self.h)
+
+    def drain(self, max_rounds=100000):
+        return sph_server_drain(self.h, max_rounds)
+
+    def job(self, jid, with_result=True):
+        return sph_server_job(self.h, jid, self.n_of[jid] if with_result else 0)
+
+    def release(self, jid):
+        sph_server_release(self.h, jid)
+        self.n_of.pop(jid, None)
+
+    def close(self):
+        if self.h:
+            sph_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

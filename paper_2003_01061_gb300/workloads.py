@@ -206,11 +206,13 @@ def _disk_holes_geometry(rng, n_holes=3):
     return holes
 
 
-def disk_holes(n_target: int | None = 120_000, seed: int = 2, params: dict | None = None):
+def disk_holes(n_target: int | None = 120_000, seed: int = 2, params: dict | None = None,
+               mc_samples: int = 2_000_000):
     """Unit disk minus 3 seeded holes; h linear in the distance to the nearest hole (0.004-0.04).
 
     ``n_target=None`` keeps the literal sizing; otherwise every length of h is scaled by one
-    factor c chosen so that the integral of rho_t over all features is about n_target.
+    factor c chosen so that the integral of rho_t over all features is about n_target
+    (volume part by Monte Carlo with ``mc_samples`` points).
     """
     rng = np.random.default_rng(seed)
     holes = _disk_holes_geometry(rng)
@@ -236,7 +238,7 @@ def disk_holes(n_target: int | None = 120_000, seed: int = 2, params: dict | Non
         return lambda s: np.stack([cc[0] + R * np.cos(s / R), cc[1] + R * np.sin(s / R), np.zeros_like(s)], axis=1)
 
     def counts(siz):
-        nv = _mc_volume_count(np.random.default_rng(seed + 100), dom, siz)
+        nv = _mc_volume_count(np.random.default_rng(seed + 100), dom, siz, mc_samples)
         nc = [_count_curve(2 * math.pi * R, circ_at(cc, R), siz) for cc, R, _ in circles]
         return nv, nc
 
@@ -260,7 +262,8 @@ def disk_holes(n_target: int | None = 120_000, seed: int = 2, params: dict | Non
     return _finish("disk_holes", dom, siz, feats, xs, gs, params or PAPER_PARAMS, scale=scale, h_lo=siz["lo"], h_hi=siz["hi"])
 
 
-def cube_sphere(n_target: int | None = 1_200_000, seed: int = 3, params: dict | None = None, sphere_r: float = 0.3):
+def cube_sphere(n_target: int | None = 1_200_000, seed: int = 3, params: dict | None = None, sphere_r: float = 0.3,
+                mc_samples: int = 2_000_000):
     """[0,1]^3 minus a centred sphere; h = min(0.008 + 0.04 |d_sphere|, 0.05), optionally scaled."""
     rng = np.random.default_rng(seed)
     cs = np.array([0.5, 0.5, 0.5])
@@ -311,7 +314,7 @@ def cube_sphere(n_target: int | None = 1_200_000, seed: int = 3, params: dict | 
         return float(np.sum(sizing_eval(siz, p) ** -2.0) / m / m)
 
     def counts(siz):
-        nv = _mc_volume_count(np.random.default_rng(seed + 100), dom, siz)
+        nv = _mc_volume_count(np.random.default_rng(seed + 100), dom, siz, mc_samples)
         nf = [face_count(f, siz) for f in faces]
         ns = 4 * math.pi * sphere_r ** 2 / siz["lo"] ** 2 if siz["hi"] > 0 else 0
         ne = [_count_curve(1.0, seg_at(e), siz) for e in edges]
@@ -357,4 +360,43 @@ def subset(w: dict, keep: np.ndarray) -> dict:
     out = dict(w)
     out["x"] = w["x"][keep].copy()
     out["group"] = w["group"][keep].copy()
+    return out
+
+
+def _log_uniform(rng, lo, hi):
+    return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+
+def batch_mix(n_inst: int = 64, seed: int = 4, n_lo: int = 1_000, n_hi: int = 200_000, mc_samples: int = 100_000):
+    """Independent instances for a batch: half 2D disks with holes (seeded hole layouts), half
+    3D cubes minus a sphere (seeded radius 0.2-0.35), particle counts log-uniform over
+    [n_lo, n_hi].  Returns (2D workloads, 3D workloads)."""
+    rng = np.random.default_rng(seed)
+    w2, w3 = [], []
+    for k in range(n_inst):
+        n = _log_uniform(rng, n_lo, n_hi)
+        s = int(rng.integers(1 << 30))
+        if k % 2 == 0:
+            w2.append(disk_holes(n_target=n, seed=s, mc_samples=mc_samples))
+        else:
+            w3.append(cube_sphere(n_target=n, seed=s, sphere_r=float(rng.uniform(0.2, 0.35)), mc_samples=mc_samples))
+    return w2, w3
+
+
+def request_stream(n_jobs: int = 48, rate: float = 50.0, seed: int = 5, n_lo: int = 1_000, n_hi: int = 200_000,
+                   frac_3d: float = 0.5, mc_samples: int = 100_000):
+    """A Poisson stream of meshing jobs: arrival times (seconds, exponential gaps of mean
+    1/rate), each job a 2D disk with holes or a 3D cube minus a sphere (probability frac_3d)
+    with a log-uniform particle count over [n_lo, n_hi].  Returns a list of (t_arrival, w)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    for _ in range(n_jobs):
+        t += float(rng.exponential(1.0 / rate))
+        n = _log_uniform(rng, n_lo, n_hi)
+        s = int(rng.integers(1 << 30))
+        if rng.random() < frac_3d:
+            w = cube_sphere(n_target=n, seed=s, sphere_r=float(rng.uniform(0.2, 0.35)), mc_samples=mc_samples)
+        else:
+            w = disk_holes(n_target=n, seed=s, mc_samples=mc_samples)
+        out.append((t, w))
     return out

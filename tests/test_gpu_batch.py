@@ -1,0 +1,168 @@
+"""Batched instances against the same instances run alone (needs a GB300).
+
+A batch packs independent problems into one particle array and one cell-key range; a particle
+only ever meets particles of its own instance, every per-instance sum runs over the same
+candidates in the same order, and the per-block partial sums of V~ cover the same slots
+relative to the instance's start.  So an instance advanced inside a batch must give results
+bit-identical to the same problem advanced alone, whatever the other instances do: idle, loaded
+later, replaced by another problem, or converged.
+"""
+import numpy as np
+import pytest
+
+from paper_2003_01061_gb300 import build as B
+from paper_2003_01061_gb300 import sphmesh as S
+from paper_2003_01061_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def alone(w, steps, prec, params=None):
+    m = S.Mesh(w, precision=prec, params=params)
+    m.set_state()
+    m.step(steps)
+    m.sync()
+    p, r = m.positions(), m.report()
+    m.close()
+    return p, r
+
+
+def same(pa, pb):
+    for k in ("x", "v", "h", "group"):
+        assert np.array_equal(pa[k], pb[k]), k
+
+
+def same_report(ra, rb):
+    assert ra.iteration == rb.iteration and ra.phase == rb.phase
+    assert ra.E_sys == rb.E_sys and ra.escapes == rb.escapes
+    assert list(ra.dt)[: ra.n_groups] == list(rb.dt)[: rb.n_groups]
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_batch_2d_matches_alone_bitwise(prec):
+    ws = [WL.square2d(h=0.05, seed=1), WL.disk_holes(n_target=6000, seed=5), WL.square2d(h=0.03, seed=7)]
+    b = S.Batch(ws, precision=prec)
+    for i in range(len(ws)):
+        b.set_state(i)
+    b.step(60)
+    b.sync()
+    reps = b.reports()
+    for i, w in enumerate(ws):
+        pa, ra = alone(w, 60, prec)
+        same(pa, b.positions(i))
+        same_report(ra, reps[i])
+    b.close()
+
+
+def test_batch_3d_matches_alone_bitwise():
+    ws = [WL.cube_sphere(n_target=12000, seed=3), WL.cube_sphere(n_target=8000, seed=4, sphere_r=0.25)]
+    b = S.Batch(ws, precision=32)
+    for i in range(len(ws)):
+        b.set_state(i)
+    b.step(25)
+    b.sync()
+    reps = b.reports()
+    for i, w in enumerate(ws):
+        pa, ra = alone(w, 25, 32)
+        same(pa, b.positions(i))
+        same_report(ra, reps[i])
+    b.close()
+
+
+def test_idle_late_and_replaced_instances():
+    # instance 0 runs throughout; 1 stays idle; 2 is loaded after 20 steps; 3 gets a new
+    # problem (another grid) after 30 steps and is loaded then
+    w0, w2 = WL.square2d(h=0.04, seed=11), WL.square2d(h=0.05, seed=12)
+    w3a, w3b = WL.square2d(h=0.05, seed=13), WL.disk_holes(n_target=3000, seed=14)
+    caps = [len(w0["x"]), 500, len(w2["x"]), max(len(w3a["x"]), len(w3b["x"]))]
+    b = S.Batch([w0, w0, w2, w3a], precision=32, max_particles=caps)
+    b.set_state(0)
+    b.set_state(3)
+    b.step(20)
+    b.set_state(2)
+    b.step(10)
+    b.set_problem(3, w3b)
+    b.set_state(3)
+    b.step(40)
+    b.sync()
+    reps = b.reports()
+    pa, ra = alone(w0, 70, 32)
+    same(pa, b.positions(0))
+    same_report(ra, reps[0])
+    assert reps[1].phase == S.DONE and reps[1].iteration == 0 and b.positions(1)["x"].shape == (0, 3)
+    pa, ra = alone(w2, 50, 32)
+    same(pa, b.positions(2))
+    same_report(ra, reps[2])
+    pa, ra = alone(w3b, 40, 32)
+    same(pa, b.positions(3))
+    same_report(ra, reps[3])
+    b.close()
+
+
+def test_batch_run_until_converged_matches_alone():
+    # scaled controller (short windows) so that both phases finish within a few hundred steps
+    ws = [WL.square2d(h=0.05, seed=21), WL.square2d(h=0.06, seed=22)]
+    prm = [WL.scaled_controller(dict(w["params"], threshold=2e-2)) for w in ws]
+    b = S.Batch(ws, precision=32, params=prm)
+    for i in range(len(ws)):
+        b.set_state(i)
+    ok, iters = S.sph_batch_run_until_converged(b.h, 4000)
+    reps = b.reports()
+    for i, w in enumerate(ws):
+        m = S.Mesh(w, precision=32, params=prm[i])
+        m.set_state()
+        ok_i, it_i = S.sph_mesh_run_until_converged(m.h, 4000)
+        assert ok_i == (reps[i].phase == S.DONE)
+        assert reps[i].iteration == it_i
+        same(m.positions(), b.positions(i))
+        m.close()
+    assert ok == all(r.phase == S.DONE for r in reps)
+    assert iters == max(r.iteration for r in reps)
+    b.close()
+
+
+def test_batch_rejects_bad_arguments():
+    w2, w3 = WL.square2d(h=0.05, seed=1), WL.cube_sphere(n_target=3000, seed=3)
+    with pytest.raises(S.SphError):
+        S.Batch([w2, w3])                       # mixed dimensions
+    b = S.Batch([w2], precision=32)
+    with pytest.raises(S.SphError):
+        S.sph_batch_set_state(b.h, 1, w2["x"], w2["group"])   # no such instance
+    cap = (len(w2["x"]) + 63) // 64 * 64
+    with pytest.raises(S.SphError):             # more particles than the batch holds
+        S.sph_batch_set_state(b.h, 0, np.tile(w2["x"], (2, 1)), np.tile(w2["group"], 2))
+    with pytest.raises(S.SphError):
+        b.set_problem(0, w3)                    # other dimension
+    assert S.sph_batch_size(b.h) == (1, 0, cap)
+    b.set_state(0)
+    assert S.sph_batch_size(b.h) == (1, cap, cap)
+    b.close()
+
+
+def test_batch_capacity_is_shared_between_instances():
+    # two instances with room for 2 x 1000 particles: one may take more than its own share
+    # while the other is empty, and the second load is refused until the first shrinks
+    w = WL.square2d(h=0.05, seed=31)
+    n = len(w["x"])
+    b = S.Batch([w, w], precision=32, max_particles=[n, n])
+    _, _, cap = S.sph_batch_size(b.h)
+    big = WL.square2d(h=0.037, seed=32)
+    assert (n + 63) // 64 * 64 < (len(big["x"]) + 63) // 64 * 64 <= cap
+    b.set_problem(0, big)
+    b.set_state(0)
+    with pytest.raises(S.SphError) as e:
+        b.set_state(1)
+    assert e.value.status == S.SPH_E_NOMEM
+    b.step(30)
+    b.set_state(0, x=np.zeros((0, 3)), group=np.zeros(0, np.int32))
+    b.set_state(1)
+    b.step(30)
+    b.sync()
+    pa, ra = alone(w, 30, 32)
+    same(pa, b.positions(1))
+    b.close()
