@@ -14,6 +14,13 @@ hole (0.004-0.04 scaled to ~120k particles), FP32 pair sums with FP64 projection
           read-back of the final positions -- all inside the host-timed region.
 * roofline: the dominant kernel's achieved rate from its live CUDA-event times.
 * cpu_baseline / --impl reference: the FP64 CPU oracle on the host cores (bounded sample).
+* batched: 64 independent instances (half 2D disks with holes, half 3D cubes minus a sphere,
+          particle counts log-uniform over 1k-200k, seeded), one batch per dimension on its own
+          stream, each step one CUDA graph per batch; particle-steps/s over all instances.
+* serving: a seeded Poisson stream of jobs of the same two kinds through the server (admitted
+          by memory, retired on convergence or at the iteration limit), p50/p99 job latency and
+          aggregate particle-steps/s, beside the same jobs served one at a time by the plain
+          FP64 single-instance path (FIFO on the measured service times).
 Multi-GPU (torchrun): every rank runs an independent replica (weak scaling, no collective on
 the data path); value = particles of all ranks x K / max rank time.
 """
@@ -49,6 +56,13 @@ def parse():
     ap.add_argument("--n", type=int, default=120_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--serve-jobs", type=int, default=32)
+    ap.add_argument("--serve-iters", type=int, default=600)
+    ap.add_argument("--serve-max-n", type=int, default=200_000)
+    ap.add_argument("--no-fp64", action="store_true")
     return ap.parse_args()
 
 
@@ -134,6 +148,39 @@ def make_workload(n):
     return WL.disk_holes(n_target=n, seed=2)
 
 
+def _gen_one(spec):
+    from paper_2003_01061_gb300 import workloads as WL
+
+    kind, n, seed, r = spec
+    if kind == 2:
+        return WL.disk_holes(n_target=n, seed=seed, mc_samples=100_000)
+    return WL.cube_sphere(n_target=n, seed=seed, sphere_r=r, mc_samples=100_000)
+
+
+def _specs(n_items, seed, n_lo, n_hi, alternate, rate=None, frac_3d=0.5):
+    """Seeded (kind, n, seed, sphere radius) per item (+ Poisson arrival times when rate)."""
+    rng = np.random.default_rng(seed)
+    t, out, times = 0.0, [], []
+    for k in range(n_items):
+        if rate:
+            t += float(rng.exponential(1.0 / rate))
+        n = int(round(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi)))))
+        s = int(rng.integers(1 << 30))
+        kind = (2 if k % 2 == 0 else 3) if alternate else (3 if rng.random() < frac_3d else 2)
+        out.append((kind, n, s, float(rng.uniform(0.2, 0.35))))
+        times.append(t)
+    return out, times
+
+
+def generate(specs):
+    """Workloads built in a process pool started with spawn (never forked after GPU use)."""
+    import multiprocessing as mp
+
+    procs = max(1, min(16, (os.cpu_count() or 2) - 1, len(specs)))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_gen_one, specs, chunksize=1)
+
+
 # ----------------------------------------------------------------------------------------
 # CPU oracle timing (the reference arm and the cpu_baseline leg)
 # ----------------------------------------------------------------------------------------
@@ -207,6 +254,14 @@ def run_ours(args):
     import torch
 
     ws, rank, local = dist_env()
+    # batch and serving inputs, generated before the first GPU call
+    batch_ws, serve_ws, serve_t = None, None, None
+    if rank == 0 and not args.no_batch:
+        specs, _ = _specs(64, 4, 1_000, 200_000, alternate=True)
+        batch_ws = generate(specs)
+    if rank == 0 and not args.no_serve:
+        specs, serve_t = _specs(args.serve_jobs, 5, 1_000, args.serve_max_n, alternate=False, rate=50.0)
+        serve_ws = generate(specs)
     if ws > 1:
         import torch.distributed as dist
 
@@ -287,6 +342,22 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = e2e_run(S, w, stream, args.steps)
 
+    batched = None
+    if batch_ws is not None:
+        batched = batched_run(S, torch, dev, batch_ws, args.batch_steps)
+        batched["config"] = {"workload": "64 instances, half disk_holes_2d / half cube_sphere_3d, "
+                                         "n log-uniform 1k-200k (seed 4)",
+                             "l2": "working set larger than L2 (no flush)"}
+    serving = None
+    if serve_ws is not None:
+        serving = serving_run(S, serve_ws, serve_t, args.serve_iters)
+        serving["config"] = {"workload": f"{args.serve_jobs} jobs, Poisson 50 jobs/s (seed 5), half 2D disks "
+                                         f"with holes / half 3D cubes minus a sphere, n log-uniform "
+                                         f"1k-{args.serve_max_n // 1000}k, paper controller, "
+                                         f"max {args.serve_iters} iterations, 20 steps per round"}
+        if not args.no_fp64:
+            serving["fp64_one_at_a_time"] = fp64_one_at_a_time(S, serve_ws, serve_t, args.serve_iters)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         from oracle import oracle as O
@@ -310,6 +381,8 @@ def run_ours(args):
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "batched": batched,
+        "serving": serving,
     }
     m.close()
     if rank == 0:
@@ -347,6 +420,118 @@ def e2e_run(S, w, stream, steps):
     return {"value": n * steps / (t1 - t0), "unit": METRIC, "h2d_bytes_per_step": h2d / steps,
             "d2h_bytes_per_step": d2h, "wall_s": t1 - t0,
             "job": f"upload of {n} particles, {steps} steps each with a controller-report read, final download"}
+
+
+def batched_run(S, torch, dev, ws, steps):
+    """All instances of each dimension in one batch; the two batches on two streams."""
+    groups = [[w for w in ws if w["domain"]["D"] == d] for d in (2, 3)]
+    streams = [torch.cuda.Stream(device=dev) for _ in groups]
+    batches = []
+    for g, st in zip(groups, streams):
+        if not g:
+            continue
+        b = S.Batch(g, precision=32, stream=st.cuda_stream)
+        for i in range(len(g)):
+            b.set_state(i)
+        batches.append((b, st, sum(len(w["x"]) for w in g)))
+    for b, _, _ in batches:
+        b.step(3)
+    for b, _, _ in batches:
+        b.sync()
+        S.sph_batch_set_timing(b.h, 1)
+        b.step(1)
+        b.sync()
+        S.sph_batch_set_timing(b.h, 1)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    start.record(torch.cuda.current_stream(dev))
+    ends = []
+    for b, st, _ in batches:
+        st.wait_event(start)
+    for b, st, _ in batches:
+        b.step(steps)
+    for b, st, _ in batches:
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(st)
+        ends.append(e)
+    torch.cuda.synchronize()
+    ms = max(start.elapsed_time(e) for e in ends)
+    parts = sum(n for _, _, n in batches)
+    out = {"value": parts * steps / (ms / 1e3), "unit": METRIC, "steps": steps, "ms_per_step": ms / steps,
+           "instances": len(ws), "particles": parts,
+           "per_dim": {}}
+    for (b, _, n), d in zip(batches, (2, 3)):
+        t = S.sph_batch_kernel_times(b.h)
+        _, slots, _ = S.sph_batch_size(b.h)
+        out["per_dim"][f"{d}d"] = {"instances": b.n_inst, "particles": n, "slots": slots,
+                                   "stages_ms": {k: (v[1] / max(steps, 1)) for k, v in t.items()}}
+        S.sph_batch_set_timing(b.h, 0)
+        b.sync()
+        b.close()
+    return out
+
+
+def serving_run(S, jobs, times, max_iters, steps_per_poll=20):
+    """Real-time Poisson arrivals into the server; latency from the scheduled arrival."""
+    srv = S.Server(precision=32, max_jobs=64, slot_capacity=(-1, -1), hbm_fraction=0.3,
+                   steps_per_poll=steps_per_poll)
+    # warm the step graphs with one small job of each dimension
+    for w in {w["domain"]["D"]: w for w in jobs}.values():
+        srv.submit(w, steps_per_poll)
+    srv.drain()
+    ids, py_sub = [], []
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        now = time.perf_counter() - t0
+        while k < len(jobs) and times[k] <= now:
+            ids.append(srv.submit(jobs[k], max_iters))
+            py_sub.append(time.perf_counter() - t0)
+            k += 1
+        st = srv.poll()
+        if k == len(jobs) and st.running == 0 and st.queued == 0:
+            break
+        if st.running == 0 and st.queued == 0 and k < len(jobs):
+            time.sleep(max(0.0, times[k] - (time.perf_counter() - t0)))
+    wall = time.perf_counter() - t0
+    lat, psteps, states = [], 0.0, {}
+    t_end = 0.0
+    for i, jid in enumerate(ids):
+        info, _ = srv.job(jid, with_result=False)
+        delay = py_sub[i] - times[i]
+        lat.append(info.t_finish - info.t_submit + delay)
+        psteps += info.n * info.iterations
+        states[int(info.state)] = states.get(int(info.state), 0) + 1
+        t_end = max(t_end, times[i] + lat[-1])
+    srv.close()
+    lat = np.array(lat)
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "value": psteps / (t_end - times[0]), "unit": METRIC,
+            "wall_s": wall, "jobs": len(jobs), "particle_steps": psteps,
+            "done": states.get(S.JOB_DONE, 0), "not_converged": states.get(S.JOB_NOT_CONVERGED, 0),
+            "failed": states.get(S.JOB_FAILED, 0)}
+
+
+def fp64_one_at_a_time(S, jobs, times, max_iters):
+    """The same jobs served one at a time by the plain FP64 single-instance path (FIFO)."""
+    service, psteps = [], 0.0
+    for w in jobs:
+        t = time.perf_counter()
+        m = S.Mesh(w, precision=64)
+        m.set_state()
+        ok, it = S.sph_mesh_run_until_converged(m.h, max_iters)
+        m.positions()
+        m.close()
+        service.append(time.perf_counter() - t)
+        psteps += len(w["x"]) * it
+    fin, lat = 0.0, []
+    for a, sv in zip(times, service):
+        fin = max(fin, a) + sv
+        lat.append(fin - a)
+    lat = np.array(lat)
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "value": psteps / (fin - times[0]), "unit": METRIC,
+            "service_s_total": float(sum(service)), "queueing": "FIFO on measured service times"}
 
 
 def main():

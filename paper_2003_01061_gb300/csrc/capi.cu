@@ -147,6 +147,7 @@ struct sph_batch {
     int* d_chunk_inst = nullptr;
     int* d_old_off = nullptr;         // re-packing: previous offsets and slots to move, per instance
     int* d_move_n = nullptr;
+    One one;                          // descriptors passed by value when NI == 1
     bool mesh = false;                // created by sph_mesh_create
     // CUDA graph of one step; rebuilt when the layout or the timing mode changes
     cudaGraphExec_t gexec = nullptr;
@@ -382,13 +383,12 @@ template <typename T> size_t slot_layout(sph_batch* b, char* base, bool assign) 
         s.V[a] = (T*)take(cap * sizeof(T));
         s.Cs[a] = (int*)take(cap * 4);
         s.Os[a] = (T*)take(cap * sizeof(T));
-        s.Vs[a] = (T*)take(cap * sizeof(T));
     }
+    s.VH = (Vec4<T>*)take(cap * sizeof(Vec4<T>));
     s.H = (T*)take(cap * sizeof(T));
     s.G = (unsigned*)take(cap * 4);
     s.ID = (int*)take(cap * 4);
     s.K = (int*)take(cap * 4);
-    s.Hs = (T*)take(cap * sizeof(T));
     s.Ms = (unsigned*)take(cap * 4);
     s.IDs = (int*)take(cap * 4);
     s.Ks = (int*)take(cap * 4);
@@ -527,6 +527,8 @@ sph_status relayout(sph_batch* b, int changed, int new_n, int desc) {
     }
     b->ncell = (int)keys;
     b->nocc = (int)occ;
+    b->one.g = b->in[0].grid;
+    b->one.p = b->in[0].params;
     if (b->prec == 32) set_cell_arrays<float>(b);
     else set_cell_arrays<double>(b);
     const State<float>& sf = b->sf;
@@ -631,11 +633,13 @@ sph_status batch_init(sph_batch* b, void* stream) {
     return SPH_OK;
 }
 
-template <typename T, int D> void enqueue_rebuild(const State<T>& s, cudaStream_t stream) {
-    launch_hash<T, D>(s, stream);
+const One* one_of(const sph_batch* b) { return b->NI == 1 ? &b->one : nullptr; }
+
+template <typename T, int D> void enqueue_rebuild(const sph_batch* b, const State<T>& s, cudaStream_t stream) {
+    launch_hash<T, D>(s, one_of(b), stream);
     launch_scan(s.ncell, s.count, s.cell_start, s.bsum, stream, s.occ, s.nocc, true);
     launch_scatter<T>(s, stream);
-    launch_gather<T, D>(s, stream);
+    launch_gather<T, D>(s, one_of(b), stream);
 }
 
 template <typename T> Out<T> out_stored(const State<T>& s) {
@@ -656,13 +660,13 @@ template <typename T, int D> void enqueue_step(sph_batch* b, bool timed) {
     const State<T>& s = st<T>(b);
     cudaStream_t stream = b->stream;
     if (timed) cudaEventRecordWithFlags(b->ev[0], stream, cudaEventRecordExternal);
-    enqueue_rebuild<T, D>(s, stream);
+    enqueue_rebuild<T, D>(b, s, stream);
     if (timed) cudaEventRecordWithFlags(b->ev[1], stream, cudaEventRecordExternal);
-    launch_interact<T, D>(s, nullptr, nullptr, stream);
+    launch_interact<T, D>(s, one_of(b), nullptr, nullptr, stream);
     if (timed) cudaEventRecordWithFlags(b->ev[2], stream, cudaEventRecordExternal);
-    launch_control<T, D>(s, stream);
+    launch_control<T, D>(s, one_of(b), stream);
     if (timed) cudaEventRecordWithFlags(b->ev[3], stream, cudaEventRecordExternal);
-    launch_integrate<T, D>(s, s.ctrls, out_stored<T>(s), stream);
+    launch_integrate<T, D>(s, one_of(b), s.ctrls, out_stored<T>(s), stream);
     if (timed) cudaEventRecordWithFlags(b->ev[4], stream, cudaEventRecordExternal);
 }
 
@@ -872,7 +876,7 @@ template <typename T> sph_status dbg_state(sph_batch* b, State<T>& out, const Ct
 template <typename T, int D> sph_status dbg_prepare(sph_batch* b, State<T>& s, const Ctrl* init) {
     sph_status r = dbg_state<T>(b, s, init);
     if (r != SPH_OK) return r;
-    enqueue_rebuild<T, D>(s, b->stream);
+    enqueue_rebuild<T, D>(b, s, b->stream);
     CK(cudaGetLastError());
     return SPH_OK;
 }
@@ -959,7 +963,7 @@ sph_status dbg_interact_impl(sph_batch* b, double* a_p, double* sigma, double* g
     T *d_sig = nullptr, *d_gam = nullptr;
     CK(cudaMalloc(&d_sig, sizeof(T) * (size_t)std::max(ns, 1)));
     CK(cudaMalloc(&d_gam, sizeof(T) * (size_t)std::max(ns, 1)));
-    launch_interact<T, D>(s, d_sig, d_gam, b->stream);
+    launch_interact<T, D>(s, one_of(b), d_sig, d_gam, b->stream);
     CK(cudaGetLastError());
     std::vector<Vec4<T>> A(ns);
     std::vector<T> sg(ns), gm(ns);
@@ -1024,7 +1028,7 @@ sph_status dbg_update_impl(sph_batch* b, const double* dt, const int32_t* reset,
     State<T> s;
     sph_status r = dbg_prepare<T, D>(b, s, &c);
     if (r != SPH_OK) return r;
-    launch_interact<T, D>(s, nullptr, nullptr, b->stream);
+    launch_interact<T, D>(s, one_of(b), nullptr, nullptr, b->stream);
     // scratch output arrays
     Out<T> o;
     void* buf = nullptr;
@@ -1044,7 +1048,7 @@ sph_status dbg_update_impl(sph_batch* b, const double* dt, const int32_t* reset,
     o.H = (T*)take(nn * sizeof(T));
     o.G = (unsigned*)take(nn * 4);
     o.ID = (int*)take(nn * 4);
-    launch_integrate<T, D>(s, b->d_ctrl_dbg, o, b->stream);
+    launch_integrate<T, D>(s, one_of(b), b->d_ctrl_dbg, o, b->stream);
     CK(cudaGetLastError());
     r = download<T>(b, 0, o.C, o.O, o.V, o.H, o.G, o.ID, x_out, nullptr, v_out, h_out);
     if (r == SPH_OK && a_v) {

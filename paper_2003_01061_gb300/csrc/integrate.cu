@@ -34,10 +34,10 @@ __device__ inline void window_reset(Ctrl* c) {
 //  4. per group dt = min(dta, dtv/f), nullified (dt = dta) on the schedule or when dt falls
 //     below dt_collapse times the group's previous step; dt <= dt_cap (Eq. 24).
 // DONE freezes the state (dt = 0, the step counter stops).
-template <typename T, int D> __global__ void __launch_bounds__(256) k_control(State<T> s) {
+template <typename T, int D, bool ONE> __global__ void __launch_bounds__(256) k_control(State<T> s, One one) {
     __shared__ double vs[MAXF], et[MAXF], ea[MAXF];
     __shared__ Ctrl sc;
-    __shared__ Params p;
+    __shared__ Params psh;
     __shared__ int fl[4];          // 0: done, 1: sampling step, 2: window closes, 3: reset windows
     __shared__ double par[3];      // eps, f, periodic
     const int inst = blockIdx.x;
@@ -46,7 +46,8 @@ template <typename T, int D> __global__ void __launch_bounds__(256) k_control(St
     unsigned* gw = reinterpret_cast<unsigned*>(s.ctrls + inst);
     const int t = threadIdx.x;
     for (int k = t; k < NW; k += blockDim.x) scw[k] = gw[k];
-    block_copy(&p, s.params + inst);
+    if (!ONE) block_copy(&psh, s.params + inst);
+    const Params& p = ONE ? one.p : psh;
     __syncthreads();
     const int G = p.G;
     if (sc.sample_now != 0) {
@@ -255,30 +256,37 @@ template <typename T> __device__ __forceinline__ T domain_phi_t(const Domain& do
 // The neighbour sum uses the walk of the pressure pass (same pairs, same predicate), with LPP
 // lanes per particle; the lead lane does the update.  As in the pressure pass, a block lies in
 // one instance.  Padding slots are copied through unchanged.
-template <typename T, int D>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 2) k_integrate(State<T> s, const Ctrl* use, Out<T> o) {
+template <typename T, int D, bool ONE>
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 2)
+    k_integrate(State<T> s, One one, const Ctrl* use, Out<T> o) {
     constexpr int LPP = Lpp<D>::v;
     __shared__ int2 sbuf[BUF_CAP * BLOCK];
-    __shared__ Grid g;
-    __shared__ Params p;
-    const int inst = __ldg(s.chunk_inst + (blockIdx.x * (BLOCK / LPP)) / CHUNK);
+    __shared__ Grid gsh;
+    __shared__ Params psh;
+    const int inst = ONE ? 0 : __ldg(s.chunk_inst + (blockIdx.x * (BLOCK / LPP)) / CHUNK);
     const Ctrl* const cu = use + inst;
     Ctrl* const ctrl = s.ctrls + inst;
     const Domain& dom = s.doms[inst];
-    block_copy(&g, s.grids + inst);
-    block_copy(&p, s.params + inst);
-    __syncthreads();
+    if (!ONE) {
+        block_copy(&gsh, s.grids + inst);
+        block_copy(&psh, s.params + inst);
+        __syncthreads();
+    }
+    const Grid& g = ONE ? one.g : gsh;
+    const Params& p = ONE ? one.p : psh;
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) / LPP;
     const bool lead = (threadIdx.x % LPP) == 0;
     if (k < s.n && !live(s, inst, k)) {   // padding: keep the slot as it is
         if (lead) {
+            const Vec4<T> vh = s.VH[k];
+            const T vv[3] = {vh.x, vh.y, vh.z};
             for (int a = 0; a < D; ++a) {
                 o.C[a][k] = s.Cs[a][k];
                 o.O[a][k] = s.Os[a][k];
-                o.V[a][k] = s.Vs[a][k];
+                o.V[a][k] = vv[a];
                 if (o.av[a]) o.av[a][k] = T(0);
             }
-            o.H[k] = s.Hs[k];
+            o.H[k] = vh.w;
             o.G[k] = 0u;
             o.ID[k] = s.IDs[k];
         }
@@ -291,10 +299,12 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 2
     T v[3] = {T(0), T(0), T(0)};
     if (inrange) {
         Rec<T, D>::load(s.P, s.Ms, k, offi, hi, mi);
+        const Vec4<T> vh = s.VH[k];
+        const T vv[3] = {vh.x, vh.y, vh.z};
         for (int a = 0; a < D; ++a) {
             c[a] = s.Cs[a][k];
             o3[a] = s.Os[a][k];
-            v[a] = s.Vs[a][k];
+            v[a] = vv[a];
         }
     }
     const int gi = inrange ? meta_group(mi) : -1, di = inrange ? meta_dim(mi) : 0;
@@ -328,14 +338,15 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 2
         T hid, hi2d;
         hpow(hi, di > 0 ? di : 1, hid, hi2d);
         const T eta_i = visc * kappa * hi * t_sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]) * fast_rcp(hid);
-        // one same-group pair (j at distance r): the viscous term of Eq. 7
-        auto pair = [&](int j, T r, T hj) {
+        // one same-group pair (j at distance r, its a_p and (v, h) loaded): the viscous term of Eq. 7
+        auto pair = [&](const Vec4<T>& aj, const Vec4<T>& vhj, T r) {
             const T invr = fast_rcp(r);
-            const Vec4<T> aj = s.A[j];
+            const T hj = vhj.w;
             const T apj[3] = {aj.x, aj.y, aj.z};
+            const T vj3[3] = {vhj.x, vhj.y, vhj.z};
             T vtj[3] = {T(0), T(0), T(0)};
             for (int a = 0; a < D; ++a) {
-                const T vp = rs ? T(0) : f * s.Vs[a][j];
+                const T vp = rs ? T(0) : f * vj3[a];
                 vtj[a] = vp + dt * (apj[a] - eps * vp);
             }
             T hjd, hj2d;
@@ -358,9 +369,27 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 2
         const int vc = moving ? s.vcnt[lg] : 0;
         const bool ov = sub_sum<LPP>(vc > VCAP ? 1 : 0) != 0;   // overflow in any lane of the particle
         if (moving && !ov)
-            for (int e = 0; e < vc; ++e) {
-                const int j = s.vj[(size_t)e * NL + lg];
-                pair(j, s.vr[(size_t)e * NL + lg], s.Hs[j]);
+            // SPH_VISC_BATCH entries at a time: their loads are all issued before the first use
+            for (int e0 = 0; e0 < vc; e0 += SPH_VISC_BATCH) {
+                constexpr int U = SPH_VISC_BATCH;
+                int jj[U];
+                T rr[U];
+                Vec4<T> aj[U], vhj[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (e0 + u < vc) {
+                        jj[u] = s.vj[(size_t)(e0 + u) * NL + lg];
+                        rr[u] = s.vr[(size_t)(e0 + u) * NL + lg];
+                    }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (e0 + u < vc) {
+                        aj[u] = s.A[jj[u]];
+                        vhj[u] = s.VH[jj[u]];
+                    }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (e0 + u < vc) pair(aj[u], vhj[u], rr[u]);
             }
         int li = 0, ci[3] = {0, 0, 0};
         if (moving && ov) own_cell<T, D>(g, s, k, hi, li, ci);
@@ -369,8 +398,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 2
             [&](int j, const T*, T r2, T hj, unsigned mj) -> bool {
                 return meta_group(mj) == gi && j != k && r2 < pair_rc2(hi, hj, hk) && r2 > T(0);
             },
-            [&](int j, const T*, T r2, T hj, unsigned, const T*, int, int, int, int) {
-                pair(j, r2 * fast_rsqrt(r2), hj);
+            [&](int j, const T*, T r2, T, unsigned, const T*, int, int, int, int) {
+                pair(s.A[j], s.VH[j], r2 * fast_rsqrt(r2));
             });
         for (int a = 0; a < D; ++a) av[a] = sub_sum<LPP>(av[a]);
         if (moving) tangent_map<T>(di, D, tg, av);
@@ -448,16 +477,20 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 2
     o.ID[k] = s.IDs[k];
 }
 
-template <typename T, int D> void launch_control(const State<T>& s, cudaStream_t st) {
-    k_control<T, D><<<s.NI, 256, 0, st>>>(s);
+template <typename T, int D> void launch_control(const State<T>& s, const One* one, cudaStream_t st) {
+    if (one) k_control<T, D, true><<<s.NI, 256, 0, st>>>(s, *one);
+    else k_control<T, D, false><<<s.NI, 256, 0, st>>>(s, One());
 }
-template <typename T, int D> void launch_integrate(const State<T>& s, const Ctrl* use, const Out<T>& o, cudaStream_t st) {
-    k_integrate<T, D><<<div_up((long long)s.n * Lpp<D>::v, BLOCK), BLOCK, 0, st>>>(s, use, o);
+template <typename T, int D>
+void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const Out<T>& o, cudaStream_t st) {
+    const int nb = div_up((long long)s.n * Lpp<D>::v, BLOCK);
+    if (one) k_integrate<T, D, true><<<nb, BLOCK, 0, st>>>(s, *one, use, o);
+    else k_integrate<T, D, false><<<nb, BLOCK, 0, st>>>(s, One(), use, o);
 }
 
 #define SPH_INST(T, D)                                                      \
-    template void launch_control<T, D>(const State<T>&, cudaStream_t);      \
-    template void launch_integrate<T, D>(const State<T>&, const Ctrl*, const Out<T>&, cudaStream_t);
+    template void launch_control<T, D>(const State<T>&, const One*, cudaStream_t);      \
+    template void launch_integrate<T, D>(const State<T>&, const One*, const Ctrl*, const Out<T>&, cudaStream_t);
 SPH_INST(float, 2)
 SPH_INST(float, 3)
 SPH_INST(double, 2)

@@ -13,24 +13,30 @@
 // On sampling steps each block also writes its per-group sums of V~ (Eq. 22) in a fixed order.
 //
 // A block serves BLOCK/LPP consecutive slots, which lie in one chunk and so in one instance:
-// the instance's grid and parameters are copied into shared memory once per block.
+// the instance's grid and parameters are copied into shared memory once per block (a batch of
+// one passes them as kernel parameters instead).
 #include "sph_internal.cuh"
 
 namespace sph {
 
-template <typename T, int D>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTERACT_MINB : 2) k_interact(State<T> s, T* dbg_sigma, T* dbg_gamma) {
+template <typename T, int D, bool ONE>
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTERACT_MINB : 2)
+    k_interact(State<T> s, One one, T* dbg_sigma, T* dbg_gamma) {
     constexpr int LPP = Lpp<D>::v;
     __shared__ unsigned long long sh_dta[MAXF], sh_dtv[MAXF];
     __shared__ double sh_part[BLOCK / 32][MAXF];
     __shared__ int2 sbuf[BUF_CAP * BLOCK];
-    __shared__ Grid g;
-    __shared__ Params p;
-    const int inst = __ldg(s.chunk_inst + (blockIdx.x * (BLOCK / LPP)) / CHUNK);
+    __shared__ Grid gsh;
+    __shared__ Params psh;
+    const int inst = ONE ? 0 : __ldg(s.chunk_inst + (blockIdx.x * (BLOCK / LPP)) / CHUNK);
     Ctrl* const ctrl = s.ctrls + inst;
     const Domain& dom = s.doms[inst];
-    block_copy(&g, s.grids + inst);
-    block_copy(&p, s.params + inst);
+    if (!ONE) {
+        block_copy(&gsh, s.grids + inst);
+        block_copy(&psh, s.params + inst);
+    }
+    const Grid& g = ONE ? one.g : gsh;
+    const Params& p = ONE ? one.p : psh;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int t = threadIdx.x; t < MAXF; t += blockDim.x) {
         sh_dta[t] = inf_bits<T>();
@@ -146,7 +152,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTERACT_MINB : 2)
         vtil = T(1) / sig;
         const T rc = kappa * hi;
         const T an = t_sqrt(ap[0] * ap[0] + ap[1] * ap[1] + ap[2] * ap[2]);
-        const T v0 = s.Vs[0][k], v1 = s.Vs[1][k], v2 = D == 3 ? s.Vs[2][k] : T(0);
+        const Vec4<T> vh = s.VH[k];
+        const T v0 = vh.x, v1 = vh.y, v2 = vh.z;
         const T vn = t_sqrt(v0 * v0 + v1 * v1 + v2 * v2);
         const T dta = an > T(0) ? wp<T>(p.cfl_a, p.cfl_a_f) * t_sqrt(rc / an) : T(CUDART_INF_F);
         const T dtv = vn > T(0) ? wp<T>(p.cfl_v, p.cfl_v_f) * rc / vn : T(CUDART_INF_F);
@@ -265,8 +272,10 @@ __global__ void __launch_bounds__(BLOCK) k_pair_counts(State<T> s, unsigned long
     }
 }
 
-template <typename T, int D> void launch_interact(const State<T>& s, T* dbg_sigma, T* dbg_gamma, cudaStream_t st) {
-    k_interact<T, D><<<s.nblk, BLOCK, 0, st>>>(s, dbg_sigma, dbg_gamma);
+template <typename T, int D>
+void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, cudaStream_t st) {
+    if (one) k_interact<T, D, true><<<s.nblk, BLOCK, 0, st>>>(s, *one, dbg_sigma, dbg_gamma);
+    else k_interact<T, D, false><<<s.nblk, BLOCK, 0, st>>>(s, One(), dbg_sigma, dbg_gamma);
 }
 template <typename T, int D>
 void launch_neighbors(const State<T>& s, int mode, int* counts, const long long* offsets, int* lists, cudaStream_t st) {
@@ -277,7 +286,7 @@ template <typename T, int D> void launch_pair_counts(const State<T>& s, unsigned
 }
 
 #define SPH_INST(T, D)                                                                                        \
-    template void launch_interact<T, D>(const State<T>&, T*, T*, cudaStream_t);                               \
+    template void launch_interact<T, D>(const State<T>&, const One*, T*, T*, cudaStream_t);                   \
     template void launch_neighbors<T, D>(const State<T>&, int, int*, const long long*, int*, cudaStream_t);   \
     template void launch_pair_counts<T, D>(const State<T>&, unsigned long long*, cudaStream_t);
 SPH_INST(float, 2)

@@ -8,11 +8,11 @@
 namespace sph {
 
 // ---- key + histogram ----
-template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_hash(State<T> s) {
+template <typename T, int D, bool ONE> __global__ void __launch_bounds__(BLOCK) k_hash(State<T> s, One one) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
-    const int inst = inst_of(s, i);
-    const Grid& g = s.grids[inst];
+    const int inst = ONE ? 0 : inst_of(s, i);
+    const Grid& g = ONE ? one.g : s.grids[inst];
     int key;
     if (!live(s, inst, i)) {
         key = g.base[MAXL];                      // padding: the instance's dummy cell
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(BLOCK) k_cellsort(int ncell, int n, const int*
 // whose stored index has rank (k - start_c) among the cell's particles, which makes the
 // counting sort stable.  Usually a cell's particles were consecutive in the stored order (it
 // is the previous step's sorted order), and the rank is found from the cell's minimum.
-template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_gather(State<T> s) {
+template <typename T, int D, bool ONE> __global__ void __launch_bounds__(BLOCK) k_gather(State<T> s, One one) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= s.n) return;
     int i = s.perm[k];
@@ -189,20 +189,24 @@ template <typename T, int D> __global__ void __launch_bounds__(BLOCK) k_gather(S
     T o[3] = {T(0), T(0), T(0)};
     const T h = s.H[i];
     const unsigned meta = s.G[i];
+    Vec4<T> vh;
+    vh.x = s.V[0][i];
+    vh.y = s.V[1][i];
+    vh.z = D == 3 ? s.V[2][i] : T(0);
+    vh.w = h;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
         c[a] = s.C[a][i];
         o[a] = s.O[a][i];
         s.Cs[a][k] = c[a];
         s.Os[a][k] = o[a];
-        s.Vs[a][k] = s.V[a][i];
     }
-    s.Hs[k] = h;
+    s.VH[k] = vh;
     s.IDs[k] = s.ID[i];
     s.Ks[k] = s.K[i];
-    const int inst = inst_of(s, k);
+    const int inst = ONE ? 0 : inst_of(s, k);
     if (!live(s, inst, k)) return;               // padding slot (sorted last in its instance)
-    const Grid& g = s.grids[inst];
+    const Grid& g = ONE ? one.g : s.grids[inst];
     const int l = level_of(g, h);
     int cell[3];
     T off[3];
@@ -242,21 +246,27 @@ __global__ void __launch_bounds__(BLOCK) k_repack(State<T> s, const int* __restr
     if (r >= __ldg(move_n + i)) return;
     if (pass == 0) {
         const int src = __ldg(old_off + i) + r;
+        Vec4<T> vh;
+        vh.x = s.V[0][src];
+        vh.y = s.V[1][src];
+        vh.z = D == 3 ? s.V[2][src] : T(0);
+        vh.w = s.H[src];
         for (int a = 0; a < D; ++a) {
             s.Cs[a][k] = s.C[a][src];
             s.Os[a][k] = s.O[a][src];
-            s.Vs[a][k] = s.V[a][src];
         }
-        s.Hs[k] = s.H[src];
+        s.VH[k] = vh;
         s.Ms[k] = s.G[src];
         s.IDs[k] = s.ID[src];
     } else {
+        const Vec4<T> vh = s.VH[k];
+        const T vv[3] = {vh.x, vh.y, vh.z};
         for (int a = 0; a < D; ++a) {
             s.C[a][k] = s.Cs[a][k];
             s.O[a][k] = s.Os[a][k];
-            s.V[a][k] = s.Vs[a][k];
+            s.V[a][k] = vv[a];
         }
-        s.H[k] = s.Hs[k];
+        s.H[k] = vh.w;
         s.G[k] = s.Ms[k];
         s.ID[k] = s.IDs[k];
     }
@@ -268,8 +278,9 @@ template <typename T, int D> void launch_repack(const State<T>& s, const int* ol
     k_repack<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s, old_off, move_n, 1);
 }
 
-template <typename T, int D> void launch_hash(const State<T>& s, cudaStream_t st) {
-    k_hash<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s);
+template <typename T, int D> void launch_hash(const State<T>& s, const One* one, cudaStream_t st) {
+    if (one) k_hash<T, D, true><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s, *one);
+    else k_hash<T, D, false><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s, One());
 }
 void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t st, unsigned* occ, int nocc,
                  bool relative) {
@@ -284,16 +295,17 @@ template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st) {
 void launch_cellsort(int ncell, int n, const int* cell_start, int* perm, int* count, cudaStream_t st) {
     k_cellsort<<<div_up(ncell, BLOCK), BLOCK, 0, st>>>(ncell, n, cell_start, perm, count);
 }
-template <typename T, int D> void launch_gather(const State<T>& s, cudaStream_t st) {
-    k_gather<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s);
+template <typename T, int D> void launch_gather(const State<T>& s, const One* one, cudaStream_t st) {
+    if (one) k_gather<T, D, true><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s, *one);
+    else k_gather<T, D, false><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s, One());
 }
 template <typename T, int D> void launch_init_h(const State<T>& s, int inst, cudaStream_t st) {
     k_init_h<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s, inst);   // threads past the instance exit
 }
 
 #define SPH_INST(T, D)                                                    \
-    template void launch_hash<T, D>(const State<T>&, cudaStream_t);        \
-    template void launch_gather<T, D>(const State<T>&, cudaStream_t);      \
+    template void launch_hash<T, D>(const State<T>&, const One*, cudaStream_t);        \
+    template void launch_gather<T, D>(const State<T>&, const One*, cudaStream_t);      \
     template void launch_init_h<T, D>(const State<T>&, int, cudaStream_t);  \
     template void launch_repack<T, D>(const State<T>&, const int*, const int*, cudaStream_t);
 SPH_INST(float, 2)

@@ -1,13 +1,14 @@
 // sph_device.cuh -- device-side data layout and inline helpers of the relaxation kernels.
 //
-// Layout in HBM (one instance, n particles, all arrays sized for the handle's capacity):
-//   stored state ("cur", in the order of the previous step's sort):
-//     X[a][n] double  positions (FP64 master copy, used by the update and the projection)
+// Layout in HBM (a batch of instances packed into n slots; per-instance slot ranges):
+//   stored state (in the order of the previous step's sort):
+//     C[a][n] int32   finest-level cell of the position;  O[a][n] T  offset inside that cell
+//                     (position = origin + C*c0 + O, reconstructed in FP64 where needed)
 //     V[a][n] T       velocities;  H[n] T smoothing length;  G[n] uint32 meta;  ID[n] int32
-//   sorted state ("srt", written by the gather of the rebuild, read by the pair passes):
-//     Xs, Vs, Hs, IDs as above, Ks[n] cell key, Ms[n] meta with the particle's x-cell,
-//     P[n] T4 = cell-relative offsets + h (FP32 build, 2D: (ox, oy, h, meta bits)),
-//     A[n] T4 = (a_p.x, a_p.y, a_p.z, V~) from the pressure pass.
+//   sorted state (written by the gather of the rebuild, read by the pair passes):
+//     Cs, Os, Vs, Hs, IDs as above, Ks[n] cell key, Ms[n] meta with the particle's x-cell,
+//     P[n] T4 = offsets inside the particle's own level cell + h (FP32 build, 2D:
+//     (ox, oy, h, meta bits)), A[n] T4 = (a_p.x, a_p.y, a_p.z, V~) from the pressure pass.
 //   meta bits: 0-5 group (feature index), 6-7 intrinsic dimension, 8-31 x index of the cell
 //   (sorted arrays only).
 // T is float (FP32 pair sums) or double (FP64 build); D is 2 or 3.
@@ -388,69 +389,6 @@ template <typename T> __device__ __forceinline__ void boundary_normal(const Feat
     }
 }
 
-// ---- the multi-level stencil walk ----
-// For query particle i at level li with cell coordinates ci (at li) and offsets offi, visits every
-// particle j stored in the cells that can hold a j with |x_i-x_j| < max(kappa*(h_i+h_j)/2, kappa*h_i):
-// at level l all particles have kappa*h_j <= c_l, so the radius R_l = max((kappa h_i + c_l)/2,
-// kappa h_i) (widened by 2^-10) bounds every candidate.  For each candidate the functor receives
-// j, dx = x_i - x_j computed as (off_i - off_j) + m*c0 with m = ci*2^li - cj*2^l (exact
-// integers), r2 = |dx|^2, h_j, meta_j and j's cell coordinates at level l.
-template <typename T, int D, typename F>
-__device__ __forceinline__ void walk(const Grid& g, const int* __restrict__ cell_start, int n,
-                                     const Vec4<T>* __restrict__ P, const unsigned* __restrict__ M, int li,
-                                     const int ci[3], const T offi[3], T hi, T kappa, F&& fn) {
-    const T c0 = (T)g.c0;
-    const T inv_c0 = T(1) / c0;
-    int Pi[3];
-    T fi[3];
-    for (int a = 0; a < 3; ++a) {
-        Pi[a] = ci[a] << li;
-        fi[a] = offi[a] * inv_c0;
-    }
-    const T rhi = kappa * hi;
-    for (int l = 0; l < g.L; ++l) {
-        T cl = wp<T>(g.c[l], g.cf[l]);
-        T R = T(0.5) * (rhi + cl);
-        R = (R > rhi ? R : rhi) * T(1.0 + 1.0 / 1024.0);
-        T Rc = R * inv_c0;
-        int lo[3] = {0, 0, 0}, hiC[3] = {0, 0, 0};
-        for (int a = 0; a < D; ++a) {
-            int a0 = Pi[a] + (int)t_floor(fi[a] - Rc);
-            int a1 = Pi[a] + (int)t_floor(fi[a] + Rc);
-            a0 >>= l;
-            a1 >>= l;
-            lo[a] = a0 < 0 ? 0 : a0;
-            hiC[a] = a1 > g.dims[l][a] - 1 ? g.dims[l][a] - 1 : a1;
-        }
-        if (lo[0] > hiC[0] || lo[1] > hiC[1] || (D == 3 && lo[2] > hiC[2])) continue;
-        for (int cz = lo[2]; cz <= hiC[2]; ++cz) {
-            T mcz = T(0);
-            if (D == 3) mcz = rn_mul((T)(Pi[2] - (cz << l)), c0);
-            for (int cy = lo[1]; cy <= hiC[1]; ++cy) {
-                const int row = g.base[l] + (cz * g.dims[l][1] + cy) * g.dims[l][0];
-                const int s = max(__ldg(cell_start + row + lo[0]), 0);
-                const int e = min(__ldg(cell_start + row + hiC[0] + 1), n);
-                if (s >= e) continue;
-                const T mcy = rn_mul((T)(Pi[1] - (cy << l)), c0);
-                for (int j = s; j < e; ++j) {
-                    T offj[3], hj;
-                    unsigned mj;
-                    Rec<T, D>::load(P, M, j, offj, hj, mj);
-                    const int cxj = meta_cx(mj);
-                    const T mcx = rn_mul((T)(Pi[0] - (cxj << l)), c0);
-                    T dx[3];
-                    dx[0] = rn_add(rn_sub(offi[0], offj[0]), mcx);
-                    dx[1] = rn_add(rn_sub(offi[1], offj[1]), mcy);
-                    dx[2] = D == 3 ? rn_add(rn_sub(offi[2], offj[2]), mcz) : T(0);
-                    T r2 = rn_add(rn_mul(dx[0], dx[0]), rn_mul(dx[1], dx[1]));
-                    if (D == 3) r2 = rn_add(r2, rn_mul(dx[2], dx[2]));
-                    fn(j, dx, r2, hj, mj, offj, l, cxj, cy, cz);
-                }
-            }
-        }
-    }
-}
-
 // the two predicates of the pair sums, evaluated op by op:
 //   pair: r2 < ((h_i + h_j) * kappa/2)^2   (j != i);   self: r2 < (kappa h_i)^2
 template <typename T> __device__ __forceinline__ T pair_rc2(T hi, T hj, T half_kappa) {
@@ -469,15 +407,23 @@ __device__ __forceinline__ float fast_rsqrt(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double fast_rsqrt(double v) { return 1.0 / sqrt(v); }
 
 // ---- sub-warp stencil walk ----
-// LPP consecutive lanes handle one particle.  They share the particle's stencil (the same as in
-// `walk`) and split the candidates of every stencil row between them (lane r takes s+r,
-// s+r+LPP, ...).  A candidate j for which accept(j, dx, r2, h_j, meta_j) holds is kept in the
+// For query particle i at level li with cell coordinates ci (at li) and offsets offi, the walk
+// visits every particle j stored in the cells that can hold a j with
+// |x_i - x_j| < max(kappa (h_i + h_j)/2, kappa h_i): at level l all particles have
+// kappa h_j <= c_l, so the radius R_l = max((kappa h_i + c_l)/2, kappa h_i) (widened by 2^-10)
+// bounds every candidate.  dx = x_i - x_j is computed as (off_i - off_j) + m c0 with
+// m = ci 2^li - cj 2^l (exact integers), r2 = |dx|^2, both op by op.
+// LPP consecutive lanes handle one particle.  They share the particle's stencil and split the
+// candidates of every stencil row between them (lane r takes s+r, s+r+LPP, ...).  A candidate j for which accept(j, dx, r2, h_j, meta_j) holds is kept in the
 // lane's slice of `buf` (CAP entries of (j, level | row), stride BLOCK, in shared memory); the
 // kept candidates are handed to fn(j, dx, r2, h_j, meta_j, off_j, l, cx_j, cy, cz) when the
 // buffer is full and at the end, so the per-pair work runs with the lanes mostly converged.
 // Levels with no particle in the 3^D top-level cells around i (bit l of `occ`, built by the
-// gather) are skipped.  dx and r2 are computed exactly as in `walk`, so a candidate is
-// accepted or rejected identically by both.  No warp-synchronous operation is used inside.
+// gather) are skipped.  Every lane count computes dx and r2 identically, so a candidate is
+// accepted or rejected the same way whatever LPP.  No warp-synchronous operation is used
+// inside.  (Measured and not kept: trimming rows to the chord of the search disc, and sharing
+// the level-mask loads among the lanes -- both cost more than they saved, since every lane
+// repeats the row bookkeeping.)
 template <typename T, int D>
 __device__ __forceinline__ int candidate_dx(const Vec4<T>* __restrict__ P, const unsigned* __restrict__ M, int j,
                                             const int Pi[3], const T offi[3], T c0, int l, int cy, int cz, T offj[3],

@@ -37,8 +37,7 @@ template <typename T> struct State {
     // sorted state
     int* Cs[3];
     T* Os[3];
-    T* Vs[3];
-    T* Hs;
+    Vec4<T>* VH;       // (v.x, v.y, v.z, h): one 16-byte (FP64: 32-byte) load per neighbour
     unsigned* Ms;
     int* IDs;
     int* Ks;
@@ -64,6 +63,13 @@ template <typename T> struct State {
     // per-block, per-group partial sums of V~ (sample steps); nblk = blocks of the pair passes
     double* partials;
     int nblk;
+};
+
+// The grid and parameters of a batch of one, passed to the kernels by value so that they are
+// read as constant-bank operands; with more instances the kernels read the per-instance tables.
+struct One {
+    Grid g;
+    Params p;
 };
 
 // output set of the update kernel (the stored state, or scratch for inspection calls)
@@ -95,7 +101,11 @@ constexpr int VCAP_MAX = 12;
 #define SPH_INTERACT_MINB 4
 #endif
 #ifndef SPH_INTEGRATE_MINB
-#define SPH_INTEGRATE_MINB 3
+#define SPH_INTEGRATE_MINB 4
+#endif
+// entries of the pressure-to-viscous hand-over list fetched together by the viscous pass
+#ifndef SPH_VISC_BATCH
+#define SPH_VISC_BATCH 2
 #endif
 
 // instance of slot k, and whether the slot holds a particle
@@ -128,24 +138,27 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // rebuild.cu
-template <typename T, int D> void launch_hash(const State<T>& s, cudaStream_t st);
+// `one`: the descriptors of a batch of one (nullptr: read the per-instance tables)
+template <typename T, int D> void launch_hash(const State<T>& s, const One* one, cudaStream_t st);
 void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t st, unsigned* occ = nullptr,
                  int nocc = 0, bool relative = false);
 template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st);
 void launch_cellsort(int ncell, int n, const int* cell_start, int* perm, int* count, cudaStream_t st);
-template <typename T, int D> void launch_gather(const State<T>& s, cudaStream_t st);
+template <typename T, int D> void launch_gather(const State<T>& s, const One* one, cudaStream_t st);
 template <typename T, int D> void launch_init_h(const State<T>& s, int inst, cudaStream_t st);
 template <typename T, int D> void launch_repack(const State<T>& s, const int* old_off, const int* move_n, cudaStream_t st);
 
 // interact.cu
-template <typename T, int D> void launch_interact(const State<T>& s, T* dbg_sigma, T* dbg_gamma, cudaStream_t st);
+template <typename T, int D>
+void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, cudaStream_t st);
 template <typename T, int D>
 void launch_neighbors(const State<T>& s, int mode, int* counts, const long long* offsets, int* lists, cudaStream_t st);
 template <typename T, int D> void launch_pair_counts(const State<T>& s, unsigned long long* out2, cudaStream_t st);
 
 // integrate.cu
-template <typename T, int D> void launch_control(const State<T>& s, cudaStream_t st);
-template <typename T, int D> void launch_integrate(const State<T>& s, const Ctrl* use, const Out<T>& o, cudaStream_t st);
+template <typename T, int D> void launch_control(const State<T>& s, const One* one, cudaStream_t st);
+template <typename T, int D>
+void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const Out<T>& o, cudaStream_t st);
 
 // sets the message returned by sph_last_error() on the calling thread (capi.cu)
 void set_last_error(const char* msg);
