@@ -43,8 +43,8 @@ METRIC = "particle-steps/s"
 WORKLOAD = "disk_holes_2d_120k"
 FLOP_PER_PAIR = 50.0       # FP32 operations per interacting pair of the pressure pass (see design notes)
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-# one step: hash, three scan passes, scatter, gather, pressure pass, controller, update
-KERNELS_PER_STEP = 9
+# one step: one-pass scan, scatter, gather, pressure pass, controller, update (+ next keys)
+KERNELS_PER_STEP = 6
 
 
 def parse():

@@ -118,6 +118,9 @@ typedef struct {
                               0: the sum exactly as printed                              [1]  */
     int32_t precision;     /* 32: FP32 pair sums (FP64 projection and reductions);
                               64: FP64 everywhere                                         [32] */
+    int32_t cells_per_support;  /* cell grid refinement m (see sph_grid_spec): 1, 2 or 4;
+                              0: the library's choice for the dimension (not a paper
+                              parameter; it changes no result beyond rounding)          [0]  */
 } sph_params;
 
 /* Controller phases (Sec. 3.4) */
@@ -130,7 +133,8 @@ typedef struct {
     int64_t ramp_start;                /* step at which Phase One ended (RAMP began)           */
     int64_t escapes;                   /* volume particles moved back inside the domain        */
     uint32_t status;                   /* bit 0: non-finite value seen; bit 1: particle outside
-                                          the cell grid; bit 2: h outside [lo, hi]             */
+                                          the cell grid; bit 2: h outside [lo, hi]; bit 3: the
+                                          cell scan gave up waiting (internal error)           */
     uint32_t pad;
     double E_t, E_avg, E_sys;          /* convergence errors of the last evaluated sample       */
     double vbar[SPH_MAX_FEATURES];     /* last sampled V-bar per group (Eq. 22, V_ref = 1)     */
@@ -196,15 +200,18 @@ const char* sph_last_error(void);
  * Cell grid (Algorithm 1, "update the multi-level data structure").  Pure host function.
  * Level l has cubic cells of edge c0 * 2^l; a particle goes to the first level whose
  * threshold thr[l] is >= its h.  Keys number the cells of all levels consecutively
- * (row-major within a level, x fastest).  Specification:
- *   c0 = kappa*h_lo*(1+2^-10) rounded up to float; L = the least count with
- *   c0*2^(L-1) >= kappa*h_hi*(1+2^-10) (at most SPH_MAX_LEVELS); thr[l] = c0*2^l /
+ * (row-major within a level, x fastest).  With m = cells_per_support (1, 2 or 4: a level's
+ * cell edge is 1/m of the largest support it holds; smaller cells visit fewer candidates and
+ * more cell rows), the specification is:
+ *   c0 = kappa*h_lo*(1+2^-10)/m rounded up to float; L = the least count with
+ *   m*c0*2^(L-1) >= kappa*h_hi*(1+2^-10) (at most SPH_MAX_LEVELS); thr[l] = m*c0*2^l /
  *   (kappa*(1+2^-10)) rounded down to float for l < L-1, +inf for the top level;
- *   origin = bbox_lo - c0*2^(L-1) rounded down to float; dims[l] = ceil((bbox_hi +
- *   c0*2^(L-1) - origin) / (c0*2^l)) + 1 per axis (1 for unused axes).
+ *   with M = m*c0*2^(L-1): origin = bbox_lo - M rounded down to float; dims[l] =
+ *   ceil((bbox_hi + M - origin) / (c0*2^l)) + 1 per axis (1 for unused axes).
  * ------------------------------------------------------------------------------------------ */
 typedef struct {
     int32_t dim, levels;
+    int32_t cells_per_support;
     float c0;
     float origin[3];
     float thr[SPH_MAX_LEVELS];
@@ -214,7 +221,7 @@ typedef struct {
 } sph_grid_info;
 
 sph_status sph_grid_spec(int32_t dim, const double* bbox_lo, const double* bbox_hi, double h_lo,
-                         double h_hi, double kappa, sph_grid_info* out);
+                         double h_hi, double kappa, int32_t cells_per_support, sph_grid_info* out);
 sph_status sph_mesh_grid(const sph_mesh* m, sph_grid_info* out);
 
 /* ------------------------------------------------------------------------------------------
@@ -278,9 +285,9 @@ sph_status sph_debug_pair_counts(sph_mesh* m, int64_t* candidates, int64_t* acce
  * how small problems fill the GPU (the paper relaxes one problem at a time).
  *
  * All instances of a batch share the ambient dimension and the precision.  The batch allocates
- * particle slots for the sum of the max_particles given at creation (each rounded up to 64);
- * any instance may hold any count as long as the loaded instances' counts, each rounded up to
- * 64, fit that total.  Loaded instances occupy consecutive slot ranges; loading or emptying
+ * particle slots for the sum of the max_particles given at creation (each rounded up to
+ * SPH_SLOT_CHUNK); any instance may hold any count as long as the loaded instances' counts, each
+ * rounded up to SPH_SLOT_CHUNK, fit that total.  Loaded instances occupy consecutive slot ranges; loading or emptying
  * one moves the others on the device and makes the next step re-capture its graph.  A freshly
  * created instance is empty and idle (controller DONE).  An empty instance costs nothing per
  * step; a converged (DONE) one costs a pass over its slots and no pair work.  Instance results
@@ -289,6 +296,7 @@ sph_status sph_debug_pair_counts(sph_mesh* m, int64_t* candidates, int64_t* acce
  * Indices `inst` run from 0 to n_inst-1; out-of-range indices give SPH_E_INVALID.
  * ------------------------------------------------------------------------------------------ */
 #define SPH_MAX_INSTANCES 4096
+#define SPH_SLOT_CHUNK 128   /* an instance's slots are its particle count rounded up to this */
 typedef struct sph_batch sph_batch;
 
 /* Creates a batch of n_inst instances; domains, sizings, params and max_particles are arrays of
@@ -357,7 +365,7 @@ sph_status sph_batch_slot_bytes(int32_t dim, int32_t precision, int64_t* bytes_p
  *      value or a particle outside the grid (SPH_JOB_FAILED): its particles are copied to host
  *      memory and its instance and slots are freed;
  *   2. admit queued jobs in arrival order while an instance is free and the job's particles
- *      (rounded up to 64) fit the free slots -- a job that does not fit waits, later smaller
+ *      (rounded up to SPH_SLOT_CHUNK) fit the free slots -- a job that does not fit waits, later smaller
  *      jobs may pass it;
  *   3. advance every resident job by steps_per_poll steps and wait for them.
  * A job's result does not depend on the other jobs resident with it: it equals the result of

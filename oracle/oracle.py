@@ -57,7 +57,7 @@ class Ctrl(C.Structure):
 
 
 class Grid(C.Structure):
-    _fields_ = [("D", C.c_int32), ("L", C.c_int32), ("c0", C.c_float), ("origin", C.c_float * 3),
+    _fields_ = [("D", C.c_int32), ("L", C.c_int32), ("cps", C.c_int32), ("c0", C.c_float), ("origin", C.c_float * 3),
                 ("thr", C.c_float * MAX_LEVELS), ("dims", (C.c_int64 * 3) * MAX_LEVELS),
                 ("base", C.c_int64 * MAX_LEVELS), ("ncell", C.c_int64)]
 
@@ -94,7 +94,7 @@ def lib():
         L.orc_feature_measure_density.argtypes = [vp, vp, C.c_int, C.c_int]
         L.orc_neighbors_brute.restype = i64
         L.orc_neighbors_brute.argtypes = [i64, C.c_int, vp, vp, d, i64, vp, i64]
-        L.orc_grid_spec.argtypes = [C.c_int, vp, vp, d, d, d, vp]
+        L.orc_grid_spec.argtypes = [C.c_int, vp, vp, d, d, d, C.c_int, vp]
         L.orc_grid_repr.argtypes = [vp, i64, vp, vp, i32, vp, vp, vp, vp, vp]
         L.orc_neighbors_repr.restype = i64
         L.orc_neighbors_repr.argtypes = [vp, i64, vp, vp, i32, d, i32, i64, vp, i64]
@@ -233,11 +233,11 @@ def neighbors_brute(x, h, i, D, kappa=2.0):
     return out[:c].copy()
 
 
-def grid_spec(D, lo, hi, h_lo, h_hi, kappa=2.0) -> Grid:
+def grid_spec(D, lo, hi, h_lo, h_hi, kappa=2.0, cells_per_support=1) -> Grid:
     g = Grid()
     lo = np.ascontiguousarray(lo, dtype=np.float64)
     hi = np.ascontiguousarray(hi, dtype=np.float64)
-    lib().orc_grid_spec(D, _p(lo), _p(hi), h_lo, h_hi, kappa, _ref(g))
+    lib().orc_grid_spec(D, _p(lo), _p(hi), h_lo, h_hi, kappa, int(cells_per_support), _ref(g))
     return g
 
 

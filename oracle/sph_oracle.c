@@ -286,12 +286,14 @@ int64_t orc_neighbors_brute(int64_t n, int D, const double* x, const double* h, 
 }
 
 /* Representation used by the data-parallel cell lists (Algorithm 1 "update the multi-level
- * data structure" and "construct Verlet neighbour list").  Specification:
- *   c0  = kappa*h_lo*(1+2^-10) rounded up to a float;  level l has cell edge c_l = c0*2^l;
- *   L   = the smallest count with c0*2^(L-1) >= kappa*h_hi*(1+2^-10);
- *   thr[l] = c_l/(kappa*(1+2^-10)) rounded down to a float (l < L-1), thr[L-1] = +inf;
+ * data structure" and "construct Verlet neighbour list").  Specification, with m the number of
+ * cells per support (1, 2 or 4: a level's cells are 1/m of the largest support it holds):
+ *   c0  = kappa*h_lo*(1+2^-10)/m rounded up to a float;  level l has cell edge c_l = c0*2^l;
+ *   L   = the smallest count with m*c0*2^(L-1) >= kappa*h_hi*(1+2^-10);
+ *   thr[l] = m*c_l/(kappa*(1+2^-10)) rounded down to a float (l < L-1), thr[L-1] = +inf;
  *   a particle's level is the first l with h <= thr[l];
- *   origin = (lo - c_{L-1}) rounded down to floats;  dims_l = ceil((hi + c_{L-1} - origin)/c_l)+1;
+ *   with M = m*c_{L-1}: origin = (lo - M) rounded down to floats;
+ *   dims_l = ceil((hi + M - origin)/c_l)+1;
  *   finest cell c = floor((x - origin) * (1/c0)) with 1/c0 rounded once in FP64 (clamped into
  *          the finest grid) and finest offset o = (x - origin) - c*c0 rounded to the working
  *          precision (it may fall an ulp outside [0, c0) where the rounded inverse puts x on
@@ -311,17 +313,19 @@ static float f_round_down(double v) {
 }
 
 void orc_grid_spec(int D, const double* lo, const double* hi, double h_lo, double h_hi,
-                   double kappa, orc_grid* g) {
+                   double kappa, int cells_per_support, orc_grid* g) {
     const double m = 1.0 + ldexp(1.0, -10);
+    const double cps = (double)cells_per_support;
     memset(g, 0, sizeof(*g));
     g->D = D;
-    g->c0 = f_round_up(kappa * h_lo * m);
+    g->cps = cells_per_support;
+    g->c0 = f_round_up(kappa * h_lo * m / cps);
     int L = 1;
-    while (L < ORC_MAX_LEVELS && ldexp((double)g->c0, L - 1) < kappa * h_hi * m) ++L;
+    while (L < ORC_MAX_LEVELS && cps * ldexp((double)g->c0, L - 1) < kappa * h_hi * m) ++L;
     g->L = L;
     for (int l = 0; l < ORC_MAX_LEVELS; ++l)
-        g->thr[l] = (l < L - 1) ? f_round_down(ldexp((double)g->c0, l) / (kappa * m)) : INFINITY;
-    double top = ldexp((double)g->c0, L - 1);
+        g->thr[l] = (l < L - 1) ? f_round_down(cps * ldexp((double)g->c0, l) / (kappa * m)) : INFINITY;
+    double top = cps * ldexp((double)g->c0, L - 1);
     for (int a = 0; a < 3; ++a) g->origin[a] = (a < D) ? f_round_down(lo[a] - top) : 0.0f;
     int64_t base = 0;
     for (int l = 0; l < L; ++l) {

@@ -115,6 +115,7 @@ typedef struct {
 /* cell-list representation used by the data-parallel neighbour search (multi-level grid) */
 typedef struct {
     int32_t D, L;
+    int32_t cps;                    /* cells per support: 1, 2 or 4                          */
     float c0;                       /* finest cell edge (exactly representable in float)     */
     float origin[3];
     float thr[ORC_MAX_LEVELS];      /* level l holds particles with thr[l-1] < h <= thr[l]  */
@@ -143,7 +144,7 @@ double orc_feature_measure_density(const orc_domain* dom, const orc_sizing* s, i
 int64_t orc_neighbors_brute(int64_t n, int D, const double* x, const double* h, double kappa,
                             int64_t i, int32_t* out, int64_t cap);
 void orc_grid_spec(int D, const double* lo, const double* hi, double h_lo, double h_hi,
-                   double kappa, orc_grid* g);
+                   double kappa, int cells_per_support, orc_grid* g);
 void orc_grid_repr(const orc_grid* g, int64_t n, const double* x, const double* h, int32_t prec,
                    int32_t* level, int64_t* cell, double* off, int64_t* key, int32_t* clamped);
 int64_t orc_neighbors_repr(const orc_grid* g, int64_t n, const double* x, const double* h,

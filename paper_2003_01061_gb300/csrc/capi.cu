@@ -56,26 +56,29 @@ float round_down_f(double v) {
 }
 
 // Cell-grid specification (documented with sph_grid_spec in the header).
-sph_status grid_spec(int D, const double* lo, const double* hi, double h_lo, double h_hi, double kappa,
+sph_status grid_spec(int D, const double* lo, const double* hi, double h_lo, double h_hi, double kappa, int cps,
                      sph_grid_info* out) {
     if (D != 2 && D != 3) return fail(SPH_E_INVALID, "grid: dim must be 2 or 3");
     if (!(h_lo > 0) || !(h_hi >= h_lo) || !(kappa > 0)) return fail(SPH_E_INVALID, "grid: need 0 < h_lo <= h_hi, kappa > 0");
+    if (cps != 1 && cps != 2 && cps != 4) return fail(SPH_E_INVALID, "grid: cells_per_support must be 1, 2 or 4");
     for (int a = 0; a < D; ++a)
         if (!(hi[a] > lo[a])) return fail(SPH_E_INVALID, "grid: empty bounding box on axis %d", a);
     const double m = 1.0 + std::ldexp(1.0, -10);
+    const double cm = (double)cps;
     sph_grid_info g;
     std::memset(&g, 0, sizeof g);
     g.dim = D;
-    g.c0 = round_up_f(kappa * h_lo * m);
+    g.cells_per_support = cps;
+    g.c0 = round_up_f(kappa * h_lo * m / cm);
     int L = 1;
-    while (std::ldexp((double)g.c0, L - 1) < kappa * h_hi * m) {
+    while (cm * std::ldexp((double)g.c0, L - 1) < kappa * h_hi * m) {
         if (L == SPH_MAX_LEVELS) return fail(SPH_E_INVALID, "grid: h_hi/h_lo too large for %d levels", SPH_MAX_LEVELS);
         ++L;
     }
     g.levels = L;
     for (int l = 0; l < SPH_MAX_LEVELS; ++l)
-        g.thr[l] = l < L - 1 ? round_down_f(std::ldexp((double)g.c0, l) / (kappa * m)) : INFINITY;
-    const double top = std::ldexp((double)g.c0, L - 1);
+        g.thr[l] = l < L - 1 ? round_down_f(cm * std::ldexp((double)g.c0, l) / (kappa * m)) : INFINITY;
+    const double top = cm * std::ldexp((double)g.c0, L - 1);
     for (int a = 0; a < 3; ++a) g.origin[a] = a < D ? round_down_f(lo[a] - top) : 0.0f;
     int64_t base = 0;
     for (int l = 0; l < L; ++l) {
@@ -103,7 +106,9 @@ struct KTime {
     const char* name;
     int kernels;   // kernel launches per step in this stage
 };
-const KTime kStages[4] = {{"rebuild", 6}, {"interact", 1}, {"control", 1}, {"integrate", 1}};
+// the step graph: rebuild = one-pass scan, scatter, gather (the keys and histogram come from
+// the previous step's update); the update also computes the next keys
+const KTime kStages[4] = {{"rebuild", 3}, {"interact", 1}, {"control", 1}, {"integrate", 1}};
 
 // host copy of one instance
 struct Inst {
@@ -148,6 +153,7 @@ struct sph_batch {
     int* d_old_off = nullptr;         // re-packing: previous offsets and slots to move, per instance
     int* d_move_n = nullptr;
     One one;                          // descriptors passed by value when NI == 1
+    bool hashed = false;              // keys and histogram of the stored state are in place
     bool mesh = false;                // created by sph_mesh_create
     // CUDA graph of one step; rebuilt when the layout or the timing mode changes
     cudaGraphExec_t gexec = nullptr;
@@ -173,7 +179,12 @@ template <typename T> State<T>& st(sph_batch* b);
 template <> State<float>& st<float>(sph_batch* b) { return b->sf; }
 template <> State<double>& st<double>(sph_batch* b) { return b->sd; }
 
+// cell keys of a batch (int32 keys and cell starts; the one-pass scan has no other bound)
+constexpr long long MAX_KEYS = 1ll << 30;
+
 int lpp_of(int D) { return D == 2 ? Lpp<2>::v : Lpp<3>::v; }
+// cells per support when the parameters leave it to the library (measured per dimension)
+int default_cps(int D) { return D == 2 ? SPH_DEFAULT_CPS_2D : SPH_DEFAULT_CPS_3D; }
 int vcap_of(int D) { return D == 2 ? Vcap<2>::v : Vcap<3>::v; }
 
 // Validates one instance's descriptors and fills its host copy (grid bases instance-relative).
@@ -212,12 +223,14 @@ sph_status make_instance(const sph_domain_desc* dd, const sph_sizing_desc* sz, c
             if (!(d0 * d0 + d1 * d1 + d2 * d2 > 0)) return fail(SPH_E_INVALID, "feature %d: zero-length segment", k);
         }
     }
+    int cps = pp->cells_per_support;
+    if (cps == 0) cps = default_cps(D);
     sph_grid_info gi;
-    sph_status r = grid_spec(D, dd->bbox_lo, dd->bbox_hi, sz->lo, sz->hi, pp->kappa, &gi);
+    sph_status r = grid_spec(D, dd->bbox_lo, dd->bbox_hi, sz->lo, sz->hi, pp->kappa, cps, &gi);
     if (r != SPH_OK) return r;
-    if (gi.n_cells > (int64_t)SCAN_TILE * SCAN_TILE)
-        return fail(SPH_E_INVALID, "grid: %lld cells is more than the %lld the cell scan supports", (long long)gi.n_cells,
-                    (long long)SCAN_TILE * SCAN_TILE);
+    if (gi.n_cells > MAX_KEYS)
+        return fail(SPH_E_INVALID, "grid: %lld cells is more than the %lld cell keys supported", (long long)gi.n_cells,
+                    (long long)MAX_KEYS);
     for (int l = 0; l < gi.levels; ++l)
         if (gi.dims[l][0] >= ((int64_t)1 << 23) || gi.dims[l][1] >= ((int64_t)1 << 14) || gi.dims[l][2] >= ((int64_t)1 << 14))
             return fail(SPH_E_INVALID, "grid: too many cells (x < 2^23, y and z < 2^14 per level)");
@@ -242,8 +255,16 @@ sph_status make_instance(const sph_domain_desc* dd, const sph_sizing_desc* sz, c
     }
     I.ncell = (int)gi.n_cells;
     g.ncell = I.ncell;
+    g.sm = cps == 1 ? 0 : (cps == 2 ? 1 : 2);
+    // occupancy cells: cps top-level cells per axis, so that a search window (at most one
+    // support of the largest particle) spans at most one of them on each side
     const int t = gi.levels - 1;
-    I.nocc = (int)(gi.dims[t][0] * gi.dims[t][1] * gi.dims[t][2]);
+    int64_t nocc = 1;
+    for (int a = 0; a < 3; ++a) {
+        g.od[a] = a < D ? (int)((gi.dims[t][a] + cps - 1) / cps) : 1;
+        nocc *= g.od[a];
+    }
+    I.nocc = (int)nocc;
     Params& p = I.params;
     std::memset(&p, 0, sizeof p);
     p.kappa = pp->kappa;
@@ -430,6 +451,9 @@ template <typename T> void set_cell_arrays(sph_batch* b) {
     s.count = (int*)take(b->cell_cap * 4);
     s.cell_start = (int*)take((b->cell_cap + 1) * 4);
     s.bsum = (int*)take((size_t)SCAN_TILE * 4);
+    s.tstate = (unsigned long long*)take((size_t)div_up((long long)b->cell_cap, SCAN_TILE) * 8);
+    s.ticket = (int*)take(4);
+    s.ntile = div_up(b->ncell, SCAN_TILE);
     s.occ = (unsigned*)take(b->occ_cap * 4);
     s.ncell = b->ncell;
     s.nocc = b->nocc;
@@ -471,13 +495,13 @@ sph_status relayout(sph_batch* b, int changed, int new_n, int desc) {
             keys += b->in[i].ncell + 1;
             occ += b->in[i].nocc;
         }
-    if (keys > (long long)SCAN_TILE * SCAN_TILE)
-        return fail(SPH_E_INVALID, "batch: %lld cell keys is more than the %lld the cell scan supports", keys,
-                    (long long)SCAN_TILE * SCAN_TILE);
+    if (keys > MAX_KEYS)
+        return fail(SPH_E_INVALID, "batch: %lld cell keys is more than the %lld supported", keys, (long long)MAX_KEYS);
     if (!b->cpool || (size_t)keys > b->cell_cap || (size_t)occ > b->occ_cap) {
         const size_t kc = std::max({(size_t)keys, b->cell_cap, (size_t)1});
         const size_t oc = std::max({(size_t)occ, b->occ_cap, (size_t)1});
-        const size_t bytes = kc * 4 + (kc + 1) * 4 + (size_t)SCAN_TILE * 4 + oc * 4 + 4 * 256;
+        const size_t bytes = kc * 4 + (kc + 1) * 4 + (size_t)SCAN_TILE * 4 + oc * 4 +
+                             (size_t)div_up((long long)kc, SCAN_TILE) * 8 + 4 + 6 * 256;
         void* p = nullptr;
         if (cudaMalloc(&p, bytes) != cudaSuccess)
             return fail(SPH_E_NOMEM, "device allocation of %zu bytes of cell arrays failed", bytes);
@@ -536,6 +560,9 @@ sph_status relayout(sph_batch* b, int changed, int new_n, int desc) {
     CK(cudaMemsetAsync(b->prec == 32 ? sf.count : sd.count, 0, (size_t)std::max<long long>(keys, 1) * 4, b->stream));
     CK(cudaMemsetAsync(b->prec == 32 ? sf.cell_start : sd.cell_start, 0, (size_t)(keys + 1) * 4, b->stream));
     CK(cudaMemsetAsync(b->prec == 32 ? sf.occ : sd.occ, 0, (size_t)std::max<long long>(occ, 1) * 4, b->stream));
+    CK(cudaMemsetAsync(b->prec == 32 ? sf.tstate : sd.tstate, 0, (size_t)div_up(std::max<long long>(keys, 1), SCAN_TILE) * 8,
+                       b->stream));
+    CK(cudaMemsetAsync(b->prec == 32 ? sf.ticket : sd.ticket, 0, 4, b->stream));
     std::vector<Grid> g(NI);
     for (int i = 0; i < NI; ++i) g[i] = b->in[i].grid;
     CK(cudaMemcpyAsync(b->d_grids, g.data(), sizeof(Grid) * NI, cudaMemcpyHostToDevice, b->stream));
@@ -554,6 +581,7 @@ sph_status relayout(sph_batch* b, int changed, int new_n, int desc) {
     CK(cudaMemcpyAsync(b->d_sizs + d0, z.data(), sizeof(Sizing) * nd, cudaMemcpyHostToDevice, b->stream));
     CK(cudaStreamSynchronize(b->stream));   // the host vectors above go out of scope
     b->layout_version += 1;
+    b->hashed = false;
     return SPH_OK;
 }
 
@@ -635,9 +663,16 @@ sph_status batch_init(sph_batch* b, void* stream) {
 
 const One* one_of(const sph_batch* b) { return b->NI == 1 ? &b->one : nullptr; }
 
-template <typename T, int D> void enqueue_rebuild(const sph_batch* b, const State<T>& s, cudaStream_t stream) {
+// keys + histogram of the stored state, unless the last update already computed them
+template <typename T, int D> void ensure_hashed(sph_batch* b, const State<T>& s, cudaStream_t stream) {
+    if (b->hashed) return;
     launch_hash<T, D>(s, one_of(b), stream);
-    launch_scan(s.ncell, s.count, s.cell_start, s.bsum, stream, s.occ, s.nocc, true);
+    b->hashed = true;
+}
+
+// the rebuild after the keys and histogram are in place (they are consumed by the scatter)
+template <typename T, int D> void enqueue_rebuild(const sph_batch* b, const State<T>& s, cudaStream_t stream) {
+    launch_scan_onepass<T>(s, stream);
     launch_scatter<T>(s, stream);
     launch_gather<T, D>(s, one_of(b), stream);
 }
@@ -653,6 +688,8 @@ template <typename T> Out<T> out_stored(const State<T>& s) {
     o.H = s.H;
     o.G = s.G;
     o.ID = s.ID;
+    o.K = s.K;
+    o.count = s.count;
     return o;
 }
 
@@ -708,6 +745,7 @@ template <typename T, int D> sph_status step_impl(sph_batch* b, int32_t n_steps)
         sph_status r = build_graph<T, D>(b);
         if (r != SPH_OK) return r;
     }
+    if (n_steps > 0) ensure_hashed<T, D>(b, st<T>(b), b->stream);
     for (int i = 0; i < n_steps; ++i) {
         if (b->timing) {
             sph_status r = collect_timing(b);
@@ -876,7 +914,9 @@ template <typename T> sph_status dbg_state(sph_batch* b, State<T>& out, const Ct
 template <typename T, int D> sph_status dbg_prepare(sph_batch* b, State<T>& s, const Ctrl* init) {
     sph_status r = dbg_state<T>(b, s, init);
     if (r != SPH_OK) return r;
+    ensure_hashed<T, D>(b, s, b->stream);
     enqueue_rebuild<T, D>(b, s, b->stream);
+    b->hashed = false;   // the scatter consumed the histogram; the stored state is unchanged
     CK(cudaGetLastError());
     return SPH_OK;
 }
@@ -1048,6 +1088,8 @@ sph_status dbg_update_impl(sph_batch* b, const double* dt, const int32_t* reset,
     o.H = (T*)take(nn * sizeof(T));
     o.G = (unsigned*)take(nn * 4);
     o.ID = (int*)take(nn * 4);
+    o.K = nullptr;       // scratch output: no keys for a next step
+    o.count = nullptr;
     launch_integrate<T, D>(s, one_of(b), b->d_ctrl_dbg, o, b->stream);
     CK(cudaGetLastError());
     r = download<T>(b, 0, o.C, o.O, o.V, o.H, o.G, o.ID, x_out, nullptr, v_out, h_out);
@@ -1225,9 +1267,9 @@ sph_status sph_params_default(sph_params* p) {
 }
 
 sph_status sph_grid_spec(int32_t dim, const double* lo, const double* hi, double h_lo, double h_hi, double kappa,
-                         sph_grid_info* out) {
+                         int32_t cells_per_support, sph_grid_info* out) {
     if (!lo || !hi || !out) return fail(SPH_E_INVALID, "grid: NULL argument");
-    return grid_spec(dim, lo, hi, h_lo, h_hi, kappa, out);
+    return grid_spec(dim, lo, hi, h_lo, h_hi, kappa, cells_per_support, out);
 }
 
 // ---- single instance ----
@@ -1309,7 +1351,7 @@ void sph_mesh_destroy(sph_mesh* m) {
 sph_status sph_mesh_grid(const sph_mesh* m, sph_grid_info* out) {
     if (!m || !out) return fail(SPH_E_INVALID, "grid: NULL argument");
     const Inst& I = m->in[0];
-    return grid_spec(m->D, I.dom.lo, I.dom.hi, I.h_lo, I.h_hi, I.params.kappa, out);
+    return grid_spec(m->D, I.dom.lo, I.dom.hi, I.h_lo, I.h_hi, I.params.kappa, 1 << I.grid.sm, out);
 }
 
 sph_status sph_debug_rebuild(sph_mesh* m, int64_t* key_out, int64_t* cs_out, int64_t* perm_out) {

@@ -274,6 +274,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 2
     }
     const Grid& g = ONE ? one.g : gsh;
     const Params& p = ONE ? one.p : psh;
+    if (o.K) reset_scan_state(s);   // this kernel produces the next scan's histogram
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) / LPP;
     const bool lead = (threadIdx.x % LPP) == 0;
     if (k < s.n && !live(s, inst, k)) {   // padding: keep the slot as it is
@@ -289,6 +290,10 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 2
             o.H[k] = vh.w;
             o.G[k] = 0u;
             o.ID[k] = s.IDs[k];
+            if (o.K) {   // the next rebuild's key: the instance's dummy cell
+                o.K[k] = g.base[MAXL];
+                atomicAdd(o.count + g.base[MAXL], 1);
+            }
         }
     }
     const bool inrange = k < s.n && live(s, inst, k);
@@ -475,6 +480,13 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 2
     o.H[k] = hnew;
     o.G[k] = mi & 255u;
     o.ID[k] = s.IDs[k];
+    if (o.K) {   // the next rebuild's key and histogram (what the hash pass would compute)
+        const int l = level_of(g, hnew);
+        int cell[3] = {c[0] >> l, c[1] >> l, D == 3 ? c[2] >> l : 0};
+        const int key = key_of(g, l, cell);
+        o.K[k] = key;
+        atomicAdd(o.count + key, 1);
+    }
 }
 
 template <typename T, int D> void launch_control(const State<T>& s, const One* one, cudaStream_t st) {

@@ -85,6 +85,8 @@ extern "C" sph_status sph_cell_sort_noalloc(const sph_grid_info* grid, int64_t n
     if (grid->dim != 2 && grid->dim != 3) return na_fail(SPH_E_INVALID, "cell_sort_noalloc: dim must be 2 or 3");
     if (grid->levels < 1 || grid->levels > SPH_MAX_LEVELS)
         return na_fail(SPH_E_INVALID, "cell_sort_noalloc: levels out of range");
+    const int cps = grid->cells_per_support;
+    if (cps != 1 && cps != 2 && cps != 4) return na_fail(SPH_E_INVALID, "cell_sort_noalloc: cells_per_support must be 1, 2 or 4");
     if (grid->n_cells < 1 || grid->n_cells > SPH_NOALLOC_MAX_CELLS)
         return na_fail(SPH_E_INVALID, "cell_sort_noalloc: the grid has %lld cells; this entry point supports at most %d",
                        (long long)grid->n_cells, SPH_NOALLOC_MAX_CELLS);
@@ -124,6 +126,7 @@ extern "C" sph_status sph_cell_sort_noalloc(const sph_grid_info* grid, int64_t n
     }
     g.base[MAXL] = (int)grid->n_cells;
     g.ncell = (int)grid->n_cells;
+    g.sm = cps == 1 ? 0 : (cps == 2 ? 1 : 2);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

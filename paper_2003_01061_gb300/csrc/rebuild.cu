@@ -9,6 +9,7 @@ namespace sph {
 
 // ---- key + histogram ----
 template <typename T, int D, bool ONE> __global__ void __launch_bounds__(BLOCK) k_hash(State<T> s, One one) {
+    reset_scan_state(s);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
     const int inst = ONE ? 0 : inst_of(s, i);
@@ -122,12 +123,103 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(int ncell, int* __re
     }
 }
 
+// ---- the step's scan in one pass: decoupled look-back ----
+// Every block takes the next tile by ticket (so all tiles before it are running or done),
+// computes its counts (relative: count[c] - cell_start[c+1], the previous scatter having left
+// count[c] = cell_start[c+1]) and their sum, publishes the sum, then walks back over the
+// preceding tiles' words (32 at a time, one per lane of its first warp) until it meets a
+// published inclusive prefix, publishes its own
+// inclusive prefix and writes cell_start and the scatter cursors of its cells.  A tile reads
+// the old cell_start[c+1] of its last cell (the next tile's first) before it publishes its
+// sum, and the next tile writes it only after it has seen that sum, so the read comes first.
+// Spins are bounded: a tile that waits too long records ST_SCAN and goes on (the walks and the
+// gather clamp every cell range, so the step stays in bounds; the host reports the error).
+constexpr unsigned long long TS_AGG = 1ull << 62, TS_PRE = 2ull << 62, TS_VAL = 0xffffffffull;
+constexpr int SCAN_SPIN_LIMIT = 1 << 20;
+
+template <typename T> __global__ void __launch_bounds__(SCAN_THREADS) k_scan_onepass(State<T> s) {
+    __shared__ int ws[32];
+    __shared__ int sh_tile, sh_prefix;
+    if (threadIdx.x == 0) sh_tile = atomicAdd(s.ticket, 1);
+    __syncthreads();
+    const int tile = sh_tile;
+    const int ncell = s.ncell;
+    // occupancy bits are rebuilt by the gather
+    for (int t = tile * SCAN_THREADS + threadIdx.x; t < s.nocc; t += gridDim.x * SCAN_THREADS) s.occ[t] = 0u;
+    const int base = tile * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int loc[SCAN_ITEMS];
+    int v = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        loc[k] = 0;
+        if (base + k < ncell) loc[k] = s.count[base + k] - s.cell_start[base + k + 1];
+        v += loc[k];
+    }
+    int agg;
+    int ex = block_exclusive_scan(v, ws, agg);
+    if (threadIdx.x < 32) {   // warp 0: publish, then look back 32 tiles at a time
+        const int lane = threadIdx.x;
+        if (tile == 0) {
+            if (lane == 0) {
+                atomicExch(s.tstate, TS_PRE | (unsigned)agg);
+                sh_prefix = 0;
+            }
+        } else {
+            if (lane == 0) atomicExch(s.tstate + tile, TS_AGG | (unsigned)agg);
+            int prefix = 0, top = tile - 1, spins = 0;
+            while (true) {
+                const int p = top - lane;
+                // before tile 0: an inclusive prefix of 0
+                unsigned long long w = 2ull << 62;
+                if (p >= 0) w = *reinterpret_cast<volatile unsigned long long*>(s.tstate + p);
+                const unsigned flag = (unsigned)(w >> 62);
+                const unsigned pre = __ballot_sync(0xffffffffu, flag == 2u);
+                const unsigned none = __ballot_sync(0xffffffffu, flag == 0u);
+                const int first = pre ? __ffs(pre) - 1 : 32;            // nearest inclusive prefix
+                const unsigned need = first >= 31 ? 0xffffffffu : ((2u << first) - 1u);
+                if (none & need) {                                      // a word it needs is not out yet
+                    if (++spins >= SCAN_SPIN_LIMIT) {
+                        if (lane == 0) atomicOr(&s.ctrls[0].status, ST_SCAN);
+                        break;
+                    }
+                    continue;
+                }
+                int val = lane <= first ? (int)(w & TS_VAL) : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+                prefix += val;
+                if (first < 32) break;
+                top -= 32;
+            }
+            if (lane == 0) {
+                atomicExch(s.tstate + tile, TS_PRE | (unsigned)(prefix + agg));
+                sh_prefix = prefix;
+            }
+        }
+    }
+    __syncthreads();
+    ex += sh_prefix;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < ncell) {
+            s.cell_start[base + k] = ex;
+            s.count[base + k] = ex;    // scatter cursor
+        }
+        ex += loc[k];
+    }
+    if (base + SCAN_ITEMS >= ncell && base < ncell) s.cell_start[ncell] = ex;   // the thread holding the last cell
+}
+
 // ---- scatter into cells (order inside a cell fixed afterwards) ----
 template <typename T> __global__ void __launch_bounds__(BLOCK) k_scatter(State<T> s) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
-    int pos = atomicAdd(s.count + s.K[i], 1);
-    if ((unsigned)pos < (unsigned)s.n) s.perm[pos] = i;
+    const int key = s.K[i];
+    int pos = atomicAdd(s.count + key, 1);
+    if ((unsigned)pos < (unsigned)s.n) {
+        s.perm[pos] = i;
+        s.Ks[pos] = key;   // every slot of a cell has the cell's key, whichever particle lands there
+    }
 }
 
 // ---- per cell: order by stored index (stable sort), reset the count for the next rebuild ----
@@ -157,12 +249,13 @@ template <typename T, int D, bool ONE> __global__ void __launch_bounds__(BLOCK) 
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= s.n) return;
     int i = s.perm[k];
-    if ((unsigned)i >= (unsigned)s.n) {   // defensive: a broken permutation is reported, not followed
+    const int key = s.Ks[k];
+    if ((unsigned)i >= (unsigned)s.n || (unsigned)key >= (unsigned)s.ncell) {
+        // defensive: a broken permutation is reported, not followed
         atomicOr(&s.ctrls[0].status, ST_NONFINITE);
-        i = 0;
+        return;
     }
     {
-        const int key = s.K[i];
         const int c0s = max(s.cell_start[key], 0), c0e = min(s.cell_start[key + 1], s.n);
         const int m = c0e - c0s, r = k - c0s;
         if (m > 1 && r >= 0 && r < m) {
@@ -203,7 +296,6 @@ template <typename T, int D, bool ONE> __global__ void __launch_bounds__(BLOCK) 
     }
     s.VH[k] = vh;
     s.IDs[k] = s.ID[i];
-    s.Ks[k] = s.K[i];
     const int inst = ONE ? 0 : inst_of(s, k);
     if (!live(s, inst, k)) return;               // padding slot (sorted last in its instance)
     const Grid& g = ONE ? one.g : s.grids[inst];
@@ -212,11 +304,11 @@ template <typename T, int D, bool ONE> __global__ void __launch_bounds__(BLOCK) 
     T off[3];
     level_repr<T, D>(g, l, c, o, cell, off);
     Rec<T, D>::store(s.P, s.Ms, k, off, h, (meta & 255u) | ((unsigned)cell[0] << 8));
-    if (s.occ) {   // level occupancy of the top-level cell holding the particle
-        const int t = g.L - 1;
+    if (s.occ) {   // level occupancy of the occupancy cell holding the particle
+        const int sh = g.L - 1 + g.sm;
         int ct[3] = {0, 0, 0};
-        for (int a = 0; a < D; ++a) ct[a] = min((cell[a] << l) >> t, g.dims[t][a] - 1);
-        atomicOr(s.occ + g.occ_base + (ct[2] * g.dims[t][1] + ct[1]) * g.dims[t][0] + ct[0], 1u << l);
+        for (int a = 0; a < D; ++a) ct[a] = min((cell[a] << l) >> sh, g.od[a] - 1);
+        atomicOr(s.occ + g.occ_base + (ct[2] * g.od[1] + ct[1]) * g.od[0] + ct[0], 1u << l);
     }
 }
 
@@ -289,6 +381,9 @@ void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t
     k_scan_top<<<1, SCAN_THREADS, 0, st>>>(nb, ncell, bsum, cell_start, occ, nocc);
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(ncell, count, bsum, cell_start);
 }
+template <typename T> void launch_scan_onepass(const State<T>& s, cudaStream_t st) {
+    k_scan_onepass<T><<<div_up(s.ncell, SCAN_TILE), SCAN_THREADS, 0, st>>>(s);
+}
 template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st) {
     k_scatter<T><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s);
 }
@@ -312,6 +407,8 @@ SPH_INST(float, 2)
 SPH_INST(float, 3)
 SPH_INST(double, 2)
 SPH_INST(double, 3)
+template void launch_scan_onepass<float>(const State<float>&, cudaStream_t);
+template void launch_scan_onepass<double>(const State<double>&, cudaStream_t);
 template void launch_scatter<float>(const State<float>&, cudaStream_t);
 template void launch_scatter<double>(const State<double>&, cudaStream_t);
 

@@ -27,7 +27,7 @@ constexpr int BLOCK = 256;
 
 enum { K_VOLUME = 0, K_POINT = 1, K_SEGMENT = 2, K_CIRCLE = 3, K_RECT = 4, K_SPHERE = 5 };
 enum { PH1 = 1, PH_RAMP = 2, PH2 = 3, PH_DONE = 4 };
-enum { ST_NONFINITE = 1u, ST_OUTSIDE_GRID = 2u, ST_H_RANGE = 4u };
+enum { ST_NONFINITE = 1u, ST_OUTSIDE_GRID = 2u, ST_H_RANGE = 4u, ST_SCAN = 8u };
 
 struct Feat {
     int kind, dim;
@@ -74,7 +74,9 @@ struct Grid {
     int dims[MAXL][3];
     int base[MAXL + 1];  // first key of each level; base[MAXL]: the instance's dummy key
     int ncell;           // cells of the instance (its keys are base[0] .. base[0]+ncell-1)
-    int occ_base;        // first entry of the instance's top-level cells in the occupancy array
+    int sm;              // log2 of the cells per support m: level l holds kappa h <= m c_l
+    int od[3];           // occupancy grid: cells of m top-level cells per axis
+    int occ_base;        // first entry of the instance's occupancy cells in the occupancy array
 };
 
 struct Params {
@@ -439,22 +441,22 @@ __device__ __forceinline__ int candidate_dx(const Vec4<T>* __restrict__ P, const
     return cxj;
 }
 
-// bit l set: some particle of level l lies in the 3^D top-level cells around the particle
+// bit l set: some particle of level l lies in the 3^D occupancy cells (m top-level cells per
+// axis each) around the particle
 template <int D>
 __device__ __forceinline__ unsigned level_mask(const Grid& g, const unsigned* __restrict__ occ, const int Pi[3],
                                                const int fl[3]) {
     if (!occ) return (1u << g.L) - 1u;
-    const int T_ = g.L - 1;
+    const int sh = g.L - 1 + g.sm;
     int ct[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) ct[a] = (Pi[a] + fl[a]) >> T_;
+    for (int a = 0; a < D; ++a) ct[a] = (Pi[a] + fl[a]) >> sh;
     unsigned m = 0;
-    const int z0 = D == 3 ? max(ct[2] - 1, 0) : 0, z1 = D == 3 ? min(ct[2] + 1, g.dims[T_][2] - 1) : 0;
-    const int y0 = max(ct[1] - 1, 0), y1 = min(ct[1] + 1, g.dims[T_][1] - 1);
-    const int x0 = max(ct[0] - 1, 0), x1 = min(ct[0] + 1, g.dims[T_][0] - 1);
+    const int z0 = D == 3 ? max(ct[2] - 1, 0) : 0, z1 = D == 3 ? min(ct[2] + 1, g.od[2] - 1) : 0;
+    const int y0 = max(ct[1] - 1, 0), y1 = min(ct[1] + 1, g.od[1] - 1);
+    const int x0 = max(ct[0] - 1, 0), x1 = min(ct[0] + 1, g.od[0] - 1);
     for (int z = z0; z <= z1; ++z)
         for (int y = y0; y <= y1; ++y)
-            for (int x = x0; x <= x1; ++x)
-                m |= __ldg(occ + g.occ_base + (z * g.dims[T_][1] + y) * g.dims[T_][0] + x);
+            for (int x = x0; x <= x1; ++x) m |= __ldg(occ + g.occ_base + (z * g.od[1] + y) * g.od[0] + x);
     return m;
 }
 
@@ -490,7 +492,8 @@ __device__ __forceinline__ void walk_sub(const Grid& g, const int* __restrict__ 
     };
     for (int l = 0; l < g.L; ++l) {
         if (!((lmask >> l) & 1u)) continue;
-        const T cl = wp<T>(g.c[l], g.cf[l]);
+        // every particle of level l has kappa h_j <= m c_l
+        const T cl = wp<T>(g.c[l], g.cf[l]) * (T)(1 << g.sm);
         T R = T(0.5) * (rhi + cl);
         R = (R > rhi ? R : rhi) * T(1.0 + 1.0 / 1024.0);
         const T Rc = R * inv_c0;

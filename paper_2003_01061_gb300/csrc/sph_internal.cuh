@@ -9,11 +9,12 @@
 // grids[i].base[MAXL]-1, followed by its dummy key grids[i].base[MAXL].  Every kernel serves all
 // instances in one launch over the n slots in use.
 #pragma once
+#include "../../include/sphmesh.h"
 #include "sph_device.cuh"
 
 namespace sph {
 
-constexpr int CHUNK = 64;      // slot alignment of instances (a multiple of every pair-pass block)
+constexpr int CHUNK = SPH_SLOT_CHUNK;   // slot alignment of instances (a multiple of every pair-pass block)
 
 template <typename T> struct State {
     int n;             // total slots of the batch
@@ -48,6 +49,11 @@ template <typename T> struct State {
     int* count;
     int* cell_start;
     int* bsum;
+    // one-pass scan: per-tile status words (flag << 62 | value) and the tile ticket, cleared by
+    // whichever kernel produces the histogram
+    unsigned long long* tstate;
+    int* ticket;
+    int ntile;
     int* perm;         // slot -> stored index as left by the scatter (unordered inside a cell)
     int* sperm;        // slot -> stored index, stable (ordered inside a cell; written by the gather)
     int ncell;         // total keys (all instances' cells and dummy cells)
@@ -81,19 +87,22 @@ template <typename T> struct Out {
     unsigned* G;
     int* ID;
     T* av[3];          // optional: viscous acceleration (inspection only)
+    int* K;            // optional (stored state): the next rebuild's cell keys ...
+    int* count;        // ... and per-cell histogram, so that the next step needs no hash pass
 };
 
 constexpr int BUF_CAP = 16;   // kept candidates per lane between flushes of the walk (shared memory)
-// lanes per particle in the pair passes
+// lanes per particle in the pair passes (measured: 1, 2, 4, 8 in 2D and 2, 4, 8, 16 in 3D;
+// fewer lanes repeat less of the per-particle stencil work, more lanes balance the candidates)
 template <int D> struct Lpp {
-    static constexpr int v = D == 2 ? 4 : 8;
+    static constexpr int v = D == 2 ? 2 : 4;
 };
-constexpr int LPP_MAX = 8;
 // same-group pair slots per lane in the pressure-to-viscous hand-over list
 template <int D> struct Vcap {
-    static constexpr int v = D == 2 ? 8 : 12;
+    static constexpr int v = D == 2 ? 12 : 16;
 };
-constexpr int VCAP_MAX = 12;
+static_assert(CHUNK % (BLOCK / Lpp<2>::v) == 0 && CHUNK % (BLOCK / Lpp<3>::v) == 0,
+              "a pair-pass block must lie in one chunk");
 
 // minimum resident blocks per SM asked of the compiler for the two pair passes (FP32 build;
 // the FP64 build asks for 2): it bounds the registers per thread, trading spills for occupancy
@@ -102,6 +111,13 @@ constexpr int VCAP_MAX = 12;
 #endif
 #ifndef SPH_INTEGRATE_MINB
 #define SPH_INTEGRATE_MINB 4
+#endif
+// cells per support of the cell grid when the parameters leave the choice to the library
+#ifndef SPH_DEFAULT_CPS_2D
+#define SPH_DEFAULT_CPS_2D 1
+#endif
+#ifndef SPH_DEFAULT_CPS_3D
+#define SPH_DEFAULT_CPS_3D 2
 #endif
 // entries of the pressure-to-viscous hand-over list fetched together by the viscous pass
 #ifndef SPH_VISC_BATCH
@@ -114,6 +130,13 @@ template <typename T> __device__ __forceinline__ int inst_of(const State<T>& s, 
 }
 template <typename T> __device__ __forceinline__ bool live(const State<T>& s, int i, int k) {
     return k - __ldg(s.inst_off + i) < __ldg(s.inst_n + i);
+}
+
+// the one-pass scan's tile states back to "nothing published" (grid-stride over any grid)
+template <typename T> __device__ __forceinline__ void reset_scan_state(const State<T>& s) {
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (int t = t0; t < s.ntile; t += stride) s.tstate[t] = 0ull;
+    if (t0 == 0) *s.ticket = 0;
 }
 
 // copy a struct into shared memory with the whole block (one round trip)
@@ -142,6 +165,8 @@ inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 template <typename T, int D> void launch_hash(const State<T>& s, const One* one, cudaStream_t st);
 void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t st, unsigned* occ = nullptr,
                  int nocc = 0, bool relative = false);
+// relative one-pass scan of the step (decoupled look-back over tiles taken in ticket order)
+template <typename T> void launch_scan_onepass(const State<T>& s, cudaStream_t st);
 template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st);
 void launch_cellsort(int ncell, int n, const int* cell_start, int* perm, int* count, cudaStream_t st);
 template <typename T, int D> void launch_gather(const State<T>& s, const One* one, cudaStream_t st);

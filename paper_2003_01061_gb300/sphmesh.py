@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libsphmesh.so")
 
 MAX_FEATURES, MAX_HOLES, MAX_LEVELS = 64, 8, 8
+SLOT_CHUNK = 128   # SPH_SLOT_CHUNK: an instance's slots are its particle count rounded up to this
 FEATURE_KIND = {"volume": 0, "point": 1, "segment": 2, "circle": 3, "rect": 4, "sphere": 5}
 SIZING_KIND = {"const": 0, "hole_dist": 1, "radial": 2}
 SPH_OK, SPH_E_INVALID, SPH_E_NOMEM, SPH_E_CUDA, SPH_E_DIVERGED, SPH_E_NOT_CONVERGED, SPH_E_OVERFLOW = range(7)
@@ -50,7 +51,7 @@ class sph_params(C.Structure):
                 ("cfl_v", C.c_double), ("eps1", C.c_double), ("dt_cap", C.c_double), ("dt_collapse", C.c_double),
                 ("threshold", C.c_double), ("reset_period", C.c_int32), ("sample_every", C.c_int32),
                 ("window", C.c_int32), ("ramp_len", C.c_int32), ("boundary_rho", C.c_int32),
-                ("precision", C.c_int32)]
+                ("precision", C.c_int32), ("cells_per_support", C.c_int32)]
 
 
 class sph_report(C.Structure):
@@ -61,7 +62,8 @@ class sph_report(C.Structure):
 
 
 class sph_grid_info(C.Structure):
-    _fields_ = [("dim", C.c_int32), ("levels", C.c_int32), ("c0", C.c_float), ("origin", C.c_float * 3),
+    _fields_ = [("dim", C.c_int32), ("levels", C.c_int32), ("cells_per_support", C.c_int32), ("c0", C.c_float),
+                ("origin", C.c_float * 3),
                 ("thr", C.c_float * MAX_LEVELS), ("dims", (C.c_int64 * 3) * MAX_LEVELS),
                 ("base", C.c_int64 * MAX_LEVELS), ("n_cells", C.c_int64)]
 
@@ -120,7 +122,7 @@ def lib():
             "sph_mesh_run_until_converged": [vp, i64, vp],
             "sph_mesh_positions": [vp, vp, vp, vp, vp, i64, vp],
             "sph_mesh_report": [vp, vp],
-            "sph_grid_spec": [i32, vp, vp, d, d, d, vp],
+            "sph_grid_spec": [i32, vp, vp, d, d, d, i32, vp],
             "sph_mesh_grid": [vp, vp],
             "sph_debug_rebuild": [vp, vp, vp, vp],
             "sph_debug_neighbors": [vp, i32, vp, vp, i64, vp],
@@ -240,11 +242,11 @@ def params_struct(p: dict, precision: int = 32) -> sph_params:
 # ----------------------------------------------------------------------------------------
 # entry points (same names as the C ABI)
 # ----------------------------------------------------------------------------------------
-def sph_grid_spec(dim, lo, hi, h_lo, h_hi, kappa=2.0) -> sph_grid_info:
+def sph_grid_spec(dim, lo, hi, h_lo, h_hi, kappa=2.0, cells_per_support=1) -> sph_grid_info:
     g = sph_grid_info()
     lo = np.ascontiguousarray(lo, dtype=np.float64)
     hi = np.ascontiguousarray(hi, dtype=np.float64)
-    _check(lib().sph_grid_spec(dim, _p(lo), _p(hi), h_lo, h_hi, kappa, C.addressof(g)))
+    _check(lib().sph_grid_spec(dim, _p(lo), _p(hi), h_lo, h_hi, kappa, int(cells_per_support), C.addressof(g)))
     return g
 
 

@@ -35,15 +35,26 @@ def test_library_exports_every_declared_function():
     assert set(names) == set(S.EXPORTS)
 
 
+def test_binding_constants_match_header():
+    src = open(os.path.join(ROOT, "include", "sphmesh.h")).read()
+    defs = dict(re.findall(r"^#define\s+(SPH_\w+)\s+(\d+)", src, re.M))
+    assert int(defs["SPH_SLOT_CHUNK"]) == S.SLOT_CHUNK
+    assert int(defs["SPH_MAX_FEATURES"]) == S.MAX_FEATURES
+    assert int(defs["SPH_MAX_HOLES"]) == S.MAX_HOLES
+    assert int(defs["SPH_MAX_LEVELS"]) == S.MAX_LEVELS
+
+
+@pytest.mark.parametrize("cps", [1, 2, 4])
 @pytest.mark.parametrize("D,lo,hi,hlo,hhi", [
     (2, [0, 0, 0], [1, 1, 0], 0.02, 0.02),
     (2, [-1, -1, 0], [1, 1, 0], 0.0018, 0.018),
     (3, [0, 0, 0], [1, 1, 1], 0.0053, 0.033),
     (3, [-0.3, 0.1, 2.0], [0.7, 0.4, 2.5], 0.001, 0.05),
 ])
-def test_grid_spec_matches_oracle(D, lo, hi, hlo, hhi):
-    a = S.sph_grid_spec(D, lo, hi, hlo, hhi, 2.0)
-    b = O.grid_spec(D, lo, hi, hlo, hhi, 2.0)
+def test_grid_spec_matches_oracle(D, lo, hi, hlo, hhi, cps):
+    a = S.sph_grid_spec(D, lo, hi, hlo, hhi, 2.0, cps)
+    b = O.grid_spec(D, lo, hi, hlo, hhi, 2.0, cps)
+    assert a.cells_per_support == b.cps == cps
     assert a.levels == b.L and a.c0 == b.c0 and a.n_cells == b.ncell
     for l in range(8):
         assert a.thr[l] == b.thr[l]
@@ -83,6 +94,13 @@ def test_invalid_descriptors_are_rejected():
     assert e.value.status == S.SPH_E_INVALID
     with pytest.raises(S.SphError):
         S.sph_grid_spec(2, [0, 0, 0], [1, 1, 0], 1e-6, 1.0)     # needs more than 8 levels
+    for bad in (3, -1, 8):
+        with pytest.raises(S.SphError):
+            S.sph_grid_spec(2, [0, 0, 0], [1, 1, 0], 0.01, 0.02, 2.0, bad)
+        d, z, p = _descs(w)
+        p.cells_per_support = bad
+        with pytest.raises(S.SphError):
+            S.sph_mesh_create(d, z, p, 10)
 
 
 def test_params_default_are_the_papers():

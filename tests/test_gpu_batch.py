@@ -133,7 +133,8 @@ def test_batch_rejects_bad_arguments():
     b = S.Batch([w2], precision=32)
     with pytest.raises(S.SphError):
         S.sph_batch_set_state(b.h, 1, w2["x"], w2["group"])   # no such instance
-    cap = (len(w2["x"]) + 63) // 64 * 64
+    C = S.SLOT_CHUNK
+    cap = (len(w2["x"]) + C - 1) // C * C
     with pytest.raises(S.SphError):             # more particles than the batch holds
         S.sph_batch_set_state(b.h, 0, np.tile(w2["x"], (2, 1)), np.tile(w2["group"], 2))
     with pytest.raises(S.SphError):
@@ -152,7 +153,8 @@ def test_batch_capacity_is_shared_between_instances():
     b = S.Batch([w, w], precision=32, max_particles=[n, n])
     _, _, cap = S.sph_batch_size(b.h)
     big = WL.square2d(h=0.037, seed=32)
-    assert (n + 63) // 64 * 64 < (len(big["x"]) + 63) // 64 * 64 <= cap
+    C = S.SLOT_CHUNK
+    assert (n + C - 1) // C * C < (len(big["x"]) + C - 1) // C * C <= cap
     b.set_problem(0, big)
     b.set_state(0)
     with pytest.raises(S.SphError) as e:

@@ -52,23 +52,34 @@ def oracle_h(w):
     return o.h
 
 
-def make(w, prec, h=None, v=None):
-    m = S.Mesh(w, precision=prec)
+def make(w, prec, h=None, v=None, cps=0):
+    m = S.Mesh(w, precision=prec, params=dict(w["params"], cells_per_support=cps))
     m.set_state(v=v, h=h)
     return m
+
+
+def oracle_grid(w, m):
+    """The oracle's grid for the mesh's problem, with the mesh's cells per support."""
+    g = S.sph_mesh_grid(m.h)
+    return O.grid_spec(w["domain"]["D"], w["domain"]["lo"], w["domain"]["hi"], w["h_lo"], w["h_hi"],
+                       cells_per_support=g.cells_per_support)
 
 
 CASES = [("square", 32), ("square", 64), ("disk", 32), ("disk", 64), ("cube", 32), ("cube", 64)]
 
 
-@pytest.mark.parametrize("name,prec", CASES)
-def test_rebuild_bit_exact(name, prec):
+CPS_CASES = [("disk", 1), ("disk", 2), ("disk", 4), ("cube", 1), ("cube", 2), ("cube", 4)]
+
+
+@pytest.mark.parametrize("name,prec,cps", [(n, p, 0) for n, p in CASES] + [(n, 32, c) for n, c in CPS_CASES])
+def test_rebuild_bit_exact(name, prec, cps):
     w = workload(name)
     h = oracle_h(w)
-    m = make(w, prec, h=h)
+    m = make(w, prec, h=h, cps=cps)
     g = S.sph_mesh_grid(m.h)
+    assert cps == 0 or g.cells_per_support == cps
     key, cs, perm = S.sph_debug_rebuild(m.h, m.n, g.n_cells)
-    og = O.grid_spec(w["domain"]["D"], w["domain"]["lo"], w["domain"]["hi"], w["h_lo"], w["h_hi"])
+    og = oracle_grid(w, m)
     rep = O.grid_repr(og, w["x"], h, prec=prec)
     assert not rep["clamped"].any()
     ocs, operm = O.counting_sort(rep["key"], og.ncell)
@@ -85,15 +96,15 @@ def _split(counts, lists):
     return [lists[off[i]:off[i + 1]] for i in range(len(counts))]
 
 
-@pytest.mark.parametrize("name,prec", CASES)
+@pytest.mark.parametrize("name,prec,cps", [(n, p, 0) for n, p in CASES] + [(n, 32, c) for n, c in CPS_CASES])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_neighbor_sets_bit_exact(name, prec, mode):
+def test_neighbor_sets_bit_exact(name, prec, cps, mode):
     w = workload(name)
     h = oracle_h(w)
-    m = make(w, prec, h=h)
+    m = make(w, prec, h=h, cps=cps)
     counts, lists = S.sph_debug_neighbors(m.h, m.n, mode)
     got = _split(counts, lists)
-    og = O.grid_spec(w["domain"]["D"], w["domain"]["lo"], w["domain"]["hi"], w["h_lo"], w["h_hi"])
+    og = oracle_grid(w, m)
     n = m.n
     rng = np.random.default_rng(1)
     idx = np.arange(n) if n <= 3000 else np.sort(rng.choice(n, 1500, replace=False))
@@ -216,7 +227,7 @@ def test_lattice_on_cell_faces_bit_exact():
     w2 = dict(w)
     w2["x"] = x
     h = oracle_h(w2)
-    m = make(w2, 32, h=h)
+    m = make(w2, 32, h=h, cps=1)
     key, cs, perm = S.sph_debug_rebuild(m.h, m.n, g.ncell)
     rep = O.grid_repr(g, x, h, prec=32)
     assert np.array_equal(key, rep["key"])

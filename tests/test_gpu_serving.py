@@ -49,7 +49,8 @@ def test_served_jobs_match_alone(cap2d):
     n2 = [len(w["x"]) for w, _, _ in js if w["domain"]["D"] == 2]
     n3 = [len(w["x"]) for w, _, _ in js if w["domain"]["D"] == 3]
     # cap2d: room for one or two 2D jobs at a time, so that later ones wait for retirements
-    caps = (cap2d or sum(n2) + 64 * len(n2), sum(n3) + 64 * len(n3))
+    C = S.SLOT_CHUNK
+    caps = (cap2d or sum(n2) + C * len(n2), sum(n3) + C * len(n3))
     srv = S.Server(precision=32, max_jobs=3, slot_capacity=caps, steps_per_poll=20)
     ids = []
     # arrivals spread over the first rounds

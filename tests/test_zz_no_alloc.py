@@ -24,7 +24,7 @@ def test_noalloc_rebuild_matches_handle_rebuild(name):
     w = WL.disk_holes(n_target=6000, seed=2) if name == "disk" else WL.cube_sphere(n_target=12000, seed=3)
     D = w["domain"]["D"]
     h = WL.sizing_eval(w["sizing"], w["x"]).astype(np.float32)
-    m = S.Mesh(w, precision=32)
+    m = S.Mesh(w, precision=32, params=dict(w["params"], cells_per_support=1))
     m.set_state(h=h.astype(np.float64))
     grid = S.sph_mesh_grid(m.h)
     key_ref, cs_ref, perm_ref = S.sph_debug_rebuild(m.h, m.n, grid.n_cells)
