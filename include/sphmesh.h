@@ -287,8 +287,9 @@ sph_status sph_debug_pair_counts(sph_mesh* m, int64_t* candidates, int64_t* acce
  * All instances of a batch share the ambient dimension and the precision.  The batch allocates
  * particle slots for the sum of the max_particles given at creation (each rounded up to
  * SPH_SLOT_CHUNK); any instance may hold any count as long as the loaded instances' counts, each
- * rounded up to SPH_SLOT_CHUNK, fit that total.  Loaded instances occupy consecutive slot ranges; loading or emptying
- * one moves the others on the device and makes the next step re-capture its graph.  A freshly
+ * rounded up to SPH_SLOT_CHUNK, fit that total.  Loaded instances occupy consecutive slot
+ * ranges; loading or emptying one moves the others on the device and makes the next step
+ * re-capture its graph.  A freshly
  * created instance is empty and idle (controller DONE).  An empty instance costs nothing per
  * step; a converged (DONE) one costs a pass over its slots and no pair work.  Instance results
  * do not depend on the other instances of the batch: a particle only interacts with particles
@@ -296,7 +297,9 @@ sph_status sph_debug_pair_counts(sph_mesh* m, int64_t* candidates, int64_t* acce
  * Indices `inst` run from 0 to n_inst-1; out-of-range indices give SPH_E_INVALID.
  * ------------------------------------------------------------------------------------------ */
 #define SPH_MAX_INSTANCES 4096
+#ifndef SPH_SLOT_CHUNK
 #define SPH_SLOT_CHUNK 128   /* an instance's slots are its particle count rounded up to this */
+#endif
 typedef struct sph_batch sph_batch;
 
 /* Creates a batch of n_inst instances; domains, sizings, params and max_particles are arrays of

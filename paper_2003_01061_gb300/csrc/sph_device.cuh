@@ -423,9 +423,11 @@ __device__ __forceinline__ double fast_rsqrt(double v) { return 1.0 / sqrt(v); }
 // Levels with no particle in the 3^D top-level cells around i (bit l of `occ`, built by the
 // gather) are skipped.  Every lane count computes dx and r2 identically, so a candidate is
 // accepted or rejected the same way whatever LPP.  No warp-synchronous operation is used
-// inside.  (Measured and not kept: trimming rows to the chord of the search disc, and sharing
-// the level-mask loads among the lanes -- both cost more than they saved, since every lane
-// repeats the row bookkeeping.)
+// inside.  (Measured and not kept: trimming rows to the chord of the search disc, sharing the
+// level-mask loads among the lanes, loading the next row's range ahead of the current row's
+// scan, and a warp-cooperative walk over the union of the warp's stencils with candidates
+// staged in shared memory -- the first three cost more registers or instructions than they saved,
+// the last tests about twice the candidates, since a warp's particles span several cells.)
 template <typename T, int D>
 __device__ __forceinline__ int candidate_dx(const Vec4<T>* __restrict__ P, const unsigned* __restrict__ M, int j,
                                             const int Pi[3], const T offi[3], T c0, int l, int cy, int cz, T offj[3],

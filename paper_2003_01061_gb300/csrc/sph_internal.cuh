@@ -94,12 +94,18 @@ template <typename T> struct Out {
 constexpr int BUF_CAP = 16;   // kept candidates per lane between flushes of the walk (shared memory)
 // lanes per particle in the pair passes (measured: 1, 2, 4, 8 in 2D and 2, 4, 8, 16 in 3D;
 // fewer lanes repeat less of the per-particle stencil work, more lanes balance the candidates)
+#ifndef SPH_LPP_2D
+#define SPH_LPP_2D 2
+#endif
+#ifndef SPH_LPP_3D
+#define SPH_LPP_3D 4
+#endif
 template <int D> struct Lpp {
-    static constexpr int v = D == 2 ? 2 : 4;
+    static constexpr int v = D == 2 ? SPH_LPP_2D : SPH_LPP_3D;
 };
 // same-group pair slots per lane in the pressure-to-viscous hand-over list
 template <int D> struct Vcap {
-    static constexpr int v = D == 2 ? 12 : 16;
+    static constexpr int v = D == 2 ? 24 / Lpp<2>::v : 64 / Lpp<3>::v;
 };
 static_assert(CHUNK % (BLOCK / Lpp<2>::v) == 0 && CHUNK % (BLOCK / Lpp<3>::v) == 0,
               "a pair-pass block must lie in one chunk");
