@@ -42,9 +42,12 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s"
 WORKLOAD = "disk_holes_2d_120k"
 FLOP_PER_PAIR = 50.0       # FP32 operations per interacting pair of the pressure pass (see design notes)
+# DRAM bytes (read + write) of one pressure-pass launch on this workload, from an ncu capture
+# (cold L2); None once the kernel changes until it is captured again
+INTERACT_DRAM_BYTES = 6.339072e6 + 1.087744e6
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-# one step: one-pass scan, scatter, gather, pressure pass, controller, update (+ next keys)
-KERNELS_PER_STEP = 6
+# one step: one-pass scan, scatter, gather, pressure pass (+ controller), update (+ next keys)
+KERNELS_PER_STEP = 5
 
 
 def parse():
@@ -333,7 +336,8 @@ def run_ours(args):
                           "control": 0}
     hbm_gbs = n * bytes_per_particle[dom] / t_dom / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None, "kernel": dom,
+                "frac": achieved / fp32_peak, "traffic": INTERACT_DRAM_BYTES if dom == "interact" else None,
+                "kernel": dom,
                 "peak_source": f"FP32: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {SM_MAX_MHZ:.0f} MHz",
                 "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak(peaks), "hbm_frac": hbm_gbs / hbm_peak(peaks),
                 "hbm_peak_source": peak_src}
@@ -433,6 +437,8 @@ def batched_run(S, torch, dev, ws, steps):
         b = S.Batch(g, precision=32, stream=st.cuda_stream)
         for i in range(len(g)):
             b.set_state(i)
+        # cell size chosen by the library's autotuner on the loaded state (untimed)
+        b.tuned = S.sph_batch_autotune(b.h, 5)
         batches.append((b, st, sum(len(w["x"]) for w in g)))
     for b, _, _ in batches:
         b.step(3)
@@ -464,6 +470,8 @@ def batched_run(S, torch, dev, ws, steps):
         t = S.sph_batch_kernel_times(b.h)
         _, slots, _ = S.sph_batch_size(b.h)
         out["per_dim"][f"{d}d"] = {"instances": b.n_inst, "particles": n, "slots": slots,
+                                   "cells_per_support": b.tuned[0],
+                                   "autotune_trial_ms": {"1": b.tuned[1][0], "2": b.tuned[1][1], "4": b.tuned[1][2]},
                                    "stages_ms": {k: (v[1] / max(steps, 1)) for k, v in t.items()}}
         S.sph_batch_set_timing(b.h, 0)
         b.sync()

@@ -190,6 +190,17 @@ sph_status sph_mesh_positions(sph_mesh* m, double* x_out, int32_t* group_out, do
 /* Copies the controller state (Sec. 3.4) and the device status word. */
 sph_status sph_mesh_report(sph_mesh* m, sph_report* out);
 
+/* Checkpoint and resume.  sph_mesh_snapshot writes the state into buf: the particles exactly
+ * as stored on the device (cell, offset, velocity, h, feature tag, input index, in the order
+ * of the last sort), the controller (Sec. 3.4) and a fingerprint of the problem and its grid.
+ * With buf NULL (or cap too small: SPH_E_OVERFLOW) it only stores the size needed in *used.
+ * sph_mesh_restore loads such a snapshot into a handle of the same problem (same descriptors,
+ * same cells per support, same precision; SPH_E_INVALID otherwise) with room for its
+ * particles; the run then continues bit for bit as if it had not been interrupted.  The
+ * format is the host's native byte order.  Both wait for the handle's stream. */
+sph_status sph_mesh_snapshot(sph_mesh* m, void* buf, size_t cap, size_t* used);
+sph_status sph_mesh_restore(sph_mesh* m, const void* buf, size_t len);
+
 /* Releases the handle and its device memory.  NULL is ignored. */
 void sph_mesh_destroy(sph_mesh* m);
 
@@ -349,6 +360,19 @@ sph_status sph_batch_reports(sph_batch* b, sph_report* out, int32_t cap);
 /* Per-stage timing over the whole batch, as sph_mesh_set_timing / sph_mesh_kernel_times. */
 sph_status sph_batch_set_timing(sph_batch* b, int32_t enable);
 sph_status sph_batch_kernel_times(sph_batch* b, sph_kernel_time* out, int32_t cap, int32_t* n_out);
+
+/* sph_mesh_snapshot / sph_mesh_restore for instance inst. */
+sph_status sph_batch_snapshot(sph_batch* b, int32_t inst, void* buf, size_t cap, size_t* used);
+sph_status sph_batch_restore(sph_batch* b, int32_t inst, const void* buf, size_t len);
+
+/* Cell-size autotuning: runs trial_steps steps (after two untimed ones) of the loaded state
+ * with 1, 2 and 4 cells per support (see sph_grid_spec), keeps the fastest for every instance,
+ * and leaves the batch holding the state it had before the call -- re-represented on the
+ * chosen grid, so later results change only by rounding -- with the controllers as they were.
+ * cells_per_support receives the choice; trial_ms (3 entries, may be NULL) the trial times in
+ * milliseconds (-1: that grid was not possible, e.g. too many cells).  Waits for the stream.
+ * Errors: SPH_E_INVALID (nothing loaded), SPH_E_NOMEM, SPH_E_CUDA. */
+sph_status sph_batch_autotune(sph_batch* b, int32_t trial_steps, int32_t* cells_per_support, float* trial_ms);
 
 /* Releases the batch and its device memory.  NULL is ignored. */
 void sph_batch_destroy(sph_batch* b);

@@ -108,7 +108,8 @@ struct KTime {
 };
 // the step graph: rebuild = one-pass scan, scatter, gather (the keys and histogram come from
 // the previous step's update); the update also computes the next keys
-const KTime kStages[4] = {{"rebuild", 3}, {"interact", 1}, {"control", 1}, {"integrate", 1}};
+constexpr int NSTAGE = 3;
+const KTime kStages[NSTAGE] = {{"rebuild", 3}, {"interact", 1}, {"integrate", 1}};
 
 // host copy of one instance
 struct Inst {
@@ -123,6 +124,10 @@ struct Inst {
     int64_t cap = 0;      // max_particles given at creation
     int off = 0, slots = 0;   // current slot range [off, off + slots) (slots = 0 while empty)
     int n = 0;            // particles loaded
+    // the descriptors as given (to derive the grid again with other cells per support)
+    sph_domain_desc dd;
+    sph_sizing_desc sz;
+    sph_params pp;
 };
 
 }  // namespace
@@ -163,7 +168,7 @@ struct sph_batch {
     bool timing = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     bool ev_pending = false;
-    double stage_ms[4] = {0, 0, 0, 0};
+    double stage_ms[4] = {0, 0, 0, 0};   // NSTAGE entries used
     int64_t stage_steps = 0;
 };
 
@@ -236,6 +241,9 @@ sph_status make_instance(const sph_domain_desc* dd, const sph_sizing_desc* sz, c
             return fail(SPH_E_INVALID, "grid: too many cells (x < 2^23, y and z < 2^14 per level)");
 
     I = Inst();
+    I.dd = *dd;
+    I.sz = *sz;
+    I.pp = *pp;
     I.cap = max_particles;
     I.h_lo = sz->lo;
     I.h_hi = sz->hi;
@@ -699,18 +707,16 @@ template <typename T, int D> void enqueue_step(sph_batch* b, bool timed) {
     if (timed) cudaEventRecordWithFlags(b->ev[0], stream, cudaEventRecordExternal);
     enqueue_rebuild<T, D>(b, s, stream);
     if (timed) cudaEventRecordWithFlags(b->ev[1], stream, cudaEventRecordExternal);
-    launch_interact<T, D>(s, one_of(b), nullptr, nullptr, stream);
+    launch_interact<T, D>(s, one_of(b), nullptr, nullptr, true, stream);   // + the controllers
     if (timed) cudaEventRecordWithFlags(b->ev[2], stream, cudaEventRecordExternal);
-    launch_control<T, D>(s, one_of(b), stream);
-    if (timed) cudaEventRecordWithFlags(b->ev[3], stream, cudaEventRecordExternal);
     launch_integrate<T, D>(s, one_of(b), s.ctrls, out_stored<T>(s), stream);
-    if (timed) cudaEventRecordWithFlags(b->ev[4], stream, cudaEventRecordExternal);
+    if (timed) cudaEventRecordWithFlags(b->ev[3], stream, cudaEventRecordExternal);
 }
 
 sph_status collect_timing(sph_batch* b) {
     if (!b->ev_pending) return SPH_OK;
-    CK(cudaEventSynchronize(b->ev[4]));
-    for (int k = 0; k < 4; ++k) {
+    CK(cudaEventSynchronize(b->ev[NSTAGE]));
+    for (int k = 0; k < NSTAGE; ++k) {
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, b->ev[k], b->ev[k + 1]));
         b->stage_ms[k] += ms;
@@ -833,7 +839,7 @@ sph_status check_args(const sph_batch* b, int inst, int64_t n, const double* x, 
 // controller: Phase One at step 0, or, for an empty batch instance, the idle state DONE.
 template <typename T, int D> sph_status set_state_impl(sph_batch* b, int inst, int64_t n, const double* x,
                                                        const int32_t* group, const double* v, const double* h,
-                                                       bool idle_when_empty) {
+                                                       bool idle_when_empty, const Ctrl* keep = nullptr) {
     State<T>& s = st<T>(b);
     Inst& I = b->in[inst];
     const int nn = (int)n;
@@ -881,6 +887,7 @@ template <typename T, int D> sph_status set_state_impl(sph_batch* b, int inst, i
         c.f = 0.0;
         c.f_f = 0.0f;
     }
+    if (keep) c = *keep;   // re-representation of the same state: the controller carries on
     CK(cudaMemcpyAsync(b->d_ctrl + inst, &c, sizeof c, cudaMemcpyHostToDevice, b->stream));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(b->stream));
@@ -1003,7 +1010,7 @@ sph_status dbg_interact_impl(sph_batch* b, double* a_p, double* sigma, double* g
     T *d_sig = nullptr, *d_gam = nullptr;
     CK(cudaMalloc(&d_sig, sizeof(T) * (size_t)std::max(ns, 1)));
     CK(cudaMalloc(&d_gam, sizeof(T) * (size_t)std::max(ns, 1)));
-    launch_interact<T, D>(s, one_of(b), d_sig, d_gam, b->stream);
+    launch_interact<T, D>(s, one_of(b), d_sig, d_gam, false, b->stream);
     CK(cudaGetLastError());
     std::vector<Vec4<T>> A(ns);
     std::vector<T> sg(ns), gm(ns);
@@ -1068,7 +1075,7 @@ sph_status dbg_update_impl(sph_batch* b, const double* dt, const int32_t* reset,
     State<T> s;
     sph_status r = dbg_prepare<T, D>(b, s, &c);
     if (r != SPH_OK) return r;
-    launch_interact<T, D>(s, one_of(b), nullptr, nullptr, b->stream);
+    launch_interact<T, D>(s, one_of(b), nullptr, nullptr, false, b->stream);
     // scratch output arrays
     Out<T> o;
     void* buf = nullptr;
@@ -1128,6 +1135,249 @@ sph_status read_ctrls(sph_batch* b, std::vector<Ctrl>& c) {
     c.resize(b->NI);
     CK(cudaMemcpyAsync(c.data(), b->d_ctrl, sizeof(Ctrl) * b->NI, cudaMemcpyDeviceToHost, b->stream));
     CK(cudaStreamSynchronize(b->stream));
+    return SPH_OK;
+}
+
+// ---- checkpoint / resume ----
+// A snapshot holds one instance's particles exactly as stored (finest cell, offset, velocity,
+// h, meta, input index, in stored order, padding included), its controller, and a fingerprint
+// of its problem and grid, so that a restored instance continues bit for bit.
+struct SnapHeader {
+    char magic[8];
+    int32_t version, dim, precision, n, slots, pad;
+    uint64_t fingerprint;
+    uint64_t payload;
+};
+constexpr char kSnapMagic[8] = {'S', 'P', 'H', 'S', 'N', 'A', 'P', '1'};
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= c[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// the instance's problem and grid, independent of where the batch put it
+uint64_t fingerprint(const Inst& I, int prec) {
+    Grid g = I.grid;
+    for (int l = 0; l <= MAXL; ++l) g.base[l] = 0;
+    g.occ_base = 0;
+    g.ncell = I.ncell;
+    uint64_t h = 14695981039346656037ull;
+    h = fnv(h, &prec, sizeof prec);
+    h = fnv(h, &g, sizeof g);
+    h = fnv(h, I.lbase, sizeof I.lbase);
+    h = fnv(h, &I.params, sizeof I.params);
+    h = fnv(h, &I.dom, sizeof I.dom);
+    h = fnv(h, &I.siz, sizeof I.siz);
+    return h;
+}
+
+template <typename T> size_t slot_bytes_of(int D) { return (size_t)D * (4 + 2 * sizeof(T)) + sizeof(T) + 8; }
+
+template <typename T, int D>
+sph_status snapshot_impl(sph_batch* b, int inst, void* buf, size_t cap, size_t* used) {
+    const Inst& I = b->in[inst];
+    const size_t payload = sizeof(Ctrl) + (size_t)I.slots * slot_bytes_of<T>(D);
+    const size_t need = sizeof(SnapHeader) + payload;
+    if (used) *used = need;
+    if (!buf) return SPH_OK;
+    if (cap < need) return fail(SPH_E_OVERFLOW, "snapshot: %zu bytes needed, %zu given", need, cap);
+    SnapHeader hd;
+    std::memset(&hd, 0, sizeof hd);
+    std::memcpy(hd.magic, kSnapMagic, 8);
+    hd.version = 1;
+    hd.dim = D;
+    hd.precision = b->prec;
+    hd.n = I.n;
+    hd.slots = I.slots;
+    hd.fingerprint = fingerprint(I, b->prec);
+    hd.payload = payload;
+    char* p = static_cast<char*>(buf);
+    std::memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    State<T>& s = st<T>(b);
+    const int o0 = I.off, ns = I.slots;
+    CK(cudaMemcpyAsync(p, b->d_ctrl + inst, sizeof(Ctrl), cudaMemcpyDeviceToHost, b->stream));
+    p += sizeof(Ctrl);
+    for (int a = 0; a < D; ++a) {
+        CK(cudaMemcpyAsync(p, s.C[a] + o0, 4 * (size_t)ns, cudaMemcpyDeviceToHost, b->stream));
+        p += 4 * (size_t)ns;
+        CK(cudaMemcpyAsync(p, s.O[a] + o0, sizeof(T) * ns, cudaMemcpyDeviceToHost, b->stream));
+        p += sizeof(T) * ns;
+        CK(cudaMemcpyAsync(p, s.V[a] + o0, sizeof(T) * ns, cudaMemcpyDeviceToHost, b->stream));
+        p += sizeof(T) * ns;
+    }
+    CK(cudaMemcpyAsync(p, s.H + o0, sizeof(T) * ns, cudaMemcpyDeviceToHost, b->stream));
+    p += sizeof(T) * ns;
+    CK(cudaMemcpyAsync(p, s.G + o0, 4 * (size_t)ns, cudaMemcpyDeviceToHost, b->stream));
+    p += 4 * (size_t)ns;
+    CK(cudaMemcpyAsync(p, s.ID + o0, 4 * (size_t)ns, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return SPH_OK;
+}
+
+template <typename T, int D> sph_status restore_impl(sph_batch* b, int inst, const void* buf, size_t len) {
+    SnapHeader hd;
+    if (len < sizeof hd) return fail(SPH_E_INVALID, "restore: buffer shorter than a snapshot header");
+    std::memcpy(&hd, buf, sizeof hd);
+    if (std::memcmp(hd.magic, kSnapMagic, 8) != 0 || hd.version != 1)
+        return fail(SPH_E_INVALID, "restore: not a snapshot of this library");
+    if (hd.dim != D || hd.precision != b->prec)
+        return fail(SPH_E_INVALID, "restore: snapshot of a %dD, precision %d instance", hd.dim, hd.precision);
+    Inst& I = b->in[inst];
+    if (hd.fingerprint != fingerprint(I, b->prec))
+        return fail(SPH_E_INVALID, "restore: the snapshot is of another problem or grid");
+    const int64_t cap = b->mesh ? I.cap : (int64_t)b->slot_cap;
+    if (hd.n < 0 || hd.n > cap || hd.slots != (hd.n + CHUNK - 1) / CHUNK * CHUNK)
+        return fail(SPH_E_INVALID, "restore: particle count out of range");
+    const size_t payload = sizeof(Ctrl) + (size_t)hd.slots * slot_bytes_of<T>(D);
+    if (hd.payload != payload || len < sizeof hd + payload) return fail(SPH_E_INVALID, "restore: truncated snapshot");
+    const char* p = static_cast<const char*>(buf) + sizeof hd;
+    Ctrl c;
+    std::memcpy(&c, p, sizeof c);
+    p += sizeof c;
+    // host copies: the device reads them after this function returns the stream synchronised
+    const int ns = hd.slots;
+    std::vector<char> data(p, p + (payload - sizeof(Ctrl)));
+    CK(cudaSetDevice(b->device));
+    sph_status r = relayout(b, inst, hd.n, inst);
+    if (r != SPH_OK) return r;
+    State<T>& s = st<T>(b);
+    const int o0 = I.off;
+    const char* q = data.data();
+    for (int a = 0; a < D; ++a) {
+        CK(cudaMemcpyAsync(s.C[a] + o0, q, 4 * (size_t)ns, cudaMemcpyHostToDevice, b->stream));
+        q += 4 * (size_t)ns;
+        CK(cudaMemcpyAsync(s.O[a] + o0, q, sizeof(T) * ns, cudaMemcpyHostToDevice, b->stream));
+        q += sizeof(T) * ns;
+        CK(cudaMemcpyAsync(s.V[a] + o0, q, sizeof(T) * ns, cudaMemcpyHostToDevice, b->stream));
+        q += sizeof(T) * ns;
+    }
+    CK(cudaMemcpyAsync(s.H + o0, q, sizeof(T) * ns, cudaMemcpyHostToDevice, b->stream));
+    q += sizeof(T) * ns;
+    CK(cudaMemcpyAsync(s.G + o0, q, 4 * (size_t)ns, cudaMemcpyHostToDevice, b->stream));
+    q += 4 * (size_t)ns;
+    CK(cudaMemcpyAsync(s.ID + o0, q, 4 * (size_t)ns, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->d_ctrl + inst, &c, sizeof c, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    b->stage_steps = 0;
+    for (double& t : b->stage_ms) t = 0;
+    b->ev_pending = false;
+    return SPH_OK;
+}
+
+// ---- cell-size autotuning ----
+// The state of every loaded instance in host memory (positions, velocities, h, groups in
+// original order) and every controller, to re-represent it on another grid.
+struct Snapshot {
+    std::vector<std::vector<double>> x, v, h;
+    std::vector<std::vector<int32_t>> g;
+    std::vector<Ctrl> ctrl;
+};
+
+template <typename T, int D> sph_status snapshot(sph_batch* b, Snapshot& sn) {
+    sph_status r = read_ctrls(b, sn.ctrl);
+    if (r != SPH_OK) return r;
+    State<T>& s = st<T>(b);
+    const int NI = b->NI;
+    sn.x.assign(NI, {});
+    sn.v.assign(NI, {});
+    sn.h.assign(NI, {});
+    sn.g.assign(NI, {});
+    for (int i = 0; i < NI; ++i) {
+        const int n = b->in[i].n;
+        if (n == 0) continue;
+        sn.x[i].resize((size_t)n * 3);
+        sn.v[i].resize((size_t)n * 3);
+        sn.h[i].resize(n);
+        sn.g[i].resize(n);
+        r = download<T>(b, i, s.C, s.O, s.V, s.H, s.G, s.ID, sn.x[i].data(), sn.g[i].data(), sn.v[i].data(),
+                        sn.h[i].data());
+        if (r != SPH_OK) return r;
+    }
+    return SPH_OK;
+}
+
+// Every instance's grid with `cps` cells per support, and the snapshot loaded onto it (the
+// controllers carry on).  Fails, leaving the batch on the snapshot's grids, when a grid is
+// invalid or does not fit.
+template <typename T, int D> sph_status regrid(sph_batch* b, int cps, const Snapshot& sn) {
+    std::vector<Inst> next(b->in);
+    for (int i = 0; i < b->NI; ++i) {
+        sph_params pp = b->in[i].pp;
+        pp.cells_per_support = cps;
+        Inst J;
+        sph_status r = make_instance(&b->in[i].dd, &b->in[i].sz, &pp, b->in[i].cap, J);
+        if (r != SPH_OK) return r;
+        J.off = b->in[i].off;
+        J.slots = b->in[i].slots;
+        J.n = b->in[i].n;
+        next[i] = J;
+    }
+    b->in = next;
+    sph_status r = relayout(b, -1, 0, -1);
+    if (r != SPH_OK) return r;
+    for (int i = 0; i < b->NI; ++i) {
+        const int n = b->in[i].n;
+        if (n == 0) continue;
+        r = set_state_impl<T, D>(b, i, n, sn.x[i].data(), sn.g[i].data(), sn.v[i].data(), sn.h[i].data(), true,
+                                 &sn.ctrl[i]);
+        if (r != SPH_OK) return r;
+    }
+    return SPH_OK;
+}
+
+// Times `steps` steps (after two untimed ones that also capture the graph) on the batch's
+// stream; the state is reloaded from the snapshot afterwards by the caller.
+template <typename T, int D> sph_status time_steps(sph_batch* b, int steps, float* ms) {
+    sph_status r = step_impl<T, D>(b, 2);
+    if (r != SPH_OK) return r;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, b->stream));
+    r = step_impl<T, D>(b, steps);
+    CK(cudaEventRecord(e1, b->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return r;
+}
+
+// Tries 1, 2 and 4 cells per support on the loaded state, keeps the fastest, and leaves the
+// batch holding the state it had (re-represented on the chosen grid).
+template <typename T, int D> sph_status autotune_impl(sph_batch* b, int steps, int32_t* chosen, float* ms_out) {
+    Snapshot sn;
+    sph_status r = snapshot<T, D>(b, sn);
+    if (r != SPH_OK) return r;
+    const int start = 1 << b->in[0].grid.sm;
+    int best = start;
+    float best_ms = INFINITY;
+    for (int cps : {1, 2, 4}) {
+        float ms = INFINITY;
+        if (regrid<T, D>(b, cps, sn) == SPH_OK && time_steps<T, D>(b, steps, &ms) == SPH_OK) {
+            if (ms_out) ms_out[cps == 1 ? 0 : (cps == 2 ? 1 : 2)] = ms;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cps;
+            }
+        } else if (ms_out) {
+            ms_out[cps == 1 ? 0 : (cps == 2 ? 1 : 2)] = -1.0f;
+        }
+    }
+    r = regrid<T, D>(b, best, sn);
+    if (r != SPH_OK) {
+        // the best grid worked a moment ago; fall back to the starting one
+        r = regrid<T, D>(b, start, sn);
+        if (r != SPH_OK) return r;
+        best = start;
+    }
+    for (Inst& I : b->in) I.pp.cells_per_support = best;
+    if (chosen) *chosen = best;
     return SPH_OK;
 }
 
@@ -1215,7 +1465,7 @@ sph_status kernel_times_impl(sph_batch* b, sph_kernel_time* out, int32_t cap, in
     sph_status r = collect_timing(b);
     if (r != SPH_OK) return r;
     int k = 0;
-    for (; k < 4 && k < cap; ++k) {
+    for (; k < NSTAGE && k < cap; ++k) {
         std::memset(out[k].name, 0, sizeof out[k].name);
         std::snprintf(out[k].name, sizeof out[k].name, "%s", kStages[k].name);
         out[k].launches = b->stage_steps * kStages[k].kernels;
@@ -1331,6 +1581,17 @@ sph_status sph_mesh_positions(sph_mesh* m, double* x_out, int32_t* group_out, do
     if (capacity < n) return fail(SPH_E_INVALID, "positions: capacity %lld < n %d", (long long)capacity, n);
     if (n == 0) return SPH_OK;
     return DISPATCH(m, positions_impl, m, 0, x_out, group_out, v_out, h_out);
+}
+
+sph_status sph_mesh_snapshot(sph_mesh* m, void* buf, size_t cap, size_t* used) {
+    if (!m) return fail(SPH_E_INVALID, "snapshot: NULL handle");
+    if (!buf && !used) return fail(SPH_E_INVALID, "snapshot: NULL buffer and size");
+    return DISPATCH(m, snapshot_impl, m, 0, buf, cap, used);
+}
+
+sph_status sph_mesh_restore(sph_mesh* m, const void* buf, size_t len) {
+    if (!m || !buf) return fail(SPH_E_INVALID, "restore: NULL argument");
+    return DISPATCH(m, restore_impl, m, 0, buf, len);
 }
 
 sph_status sph_mesh_report(sph_mesh* m, sph_report* out) {
@@ -1550,6 +1811,27 @@ sph_status sph_batch_slot_bytes(int32_t dim, int32_t precision, int64_t* bytes_p
     // plus the chunk table
     *bytes_per_slot = (int64_t)((bytes + (size_t)b.slot_cap - 1) / (size_t)b.slot_cap) + 1;
     return SPH_OK;
+}
+
+sph_status sph_batch_autotune(sph_batch* b, int32_t trial_steps, int32_t* cells_per_support, float* trial_ms) {
+    if (!b) return fail(SPH_E_INVALID, "autotune: NULL handle");
+    if (trial_steps < 1) return fail(SPH_E_INVALID, "autotune: trial_steps must be positive");
+    if (b->nslots == 0) return fail(SPH_E_INVALID, "autotune: no instance is loaded");
+    CK(cudaSetDevice(b->device));
+    return DISPATCH(b, autotune_impl, b, trial_steps, cells_per_support, trial_ms);
+}
+
+sph_status sph_batch_snapshot(sph_batch* b, int32_t inst, void* buf, size_t cap, size_t* used) {
+    if (!b) return fail(SPH_E_INVALID, "snapshot: NULL handle");
+    if (inst < 0 || inst >= b->NI) return fail(SPH_E_INVALID, "snapshot: instance %d out of range", inst);
+    if (!buf && !used) return fail(SPH_E_INVALID, "snapshot: NULL buffer and size");
+    return DISPATCH(b, snapshot_impl, b, inst, buf, cap, used);
+}
+
+sph_status sph_batch_restore(sph_batch* b, int32_t inst, const void* buf, size_t len) {
+    if (!b || !buf) return fail(SPH_E_INVALID, "restore: NULL argument");
+    if (inst < 0 || inst >= b->NI) return fail(SPH_E_INVALID, "restore: instance %d out of range", inst);
+    return DISPATCH(b, restore_impl, b, inst, buf, len);
 }
 
 void sph_batch_destroy(sph_batch* b) {

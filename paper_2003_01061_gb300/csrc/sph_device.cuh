@@ -23,7 +23,10 @@ namespace sph {
 constexpr int MAXF = 64;
 constexpr int MAXH = 8;
 constexpr int MAXL = 8;
-constexpr int BLOCK = 256;
+#ifndef SPH_BLOCK
+#define SPH_BLOCK 128
+#endif
+constexpr int BLOCK = SPH_BLOCK;   // threads per block of the per-slot and pair-pass kernels
 
 enum { K_VOLUME = 0, K_POINT = 1, K_SEGMENT = 2, K_CIRCLE = 3, K_RECT = 4, K_SPHERE = 5 };
 enum { PH1 = 1, PH_RAMP = 2, PH2 = 3, PH_DONE = 4 };
@@ -93,7 +96,7 @@ struct Ctrl {
     long long n, ramp_start;
     unsigned long long escapes;
     unsigned int status;
-    int pad;
+    int blocks_done;   // pressure-pass blocks of this step that have finished (the last runs the controller)
     double wsum[MAXF], A_last[MAXF], A_prev[MAXF], Vbar[MAXF], dt_prev[MAXF], dt[MAXF];
     int reset[MAXF];
     double E_t, E_avg, E_sys, eps, f;

@@ -91,7 +91,10 @@ template <typename T> struct Out {
     int* count;        // ... and per-cell histogram, so that the next step needs no hash pass
 };
 
-constexpr int BUF_CAP = 16;   // kept candidates per lane between flushes of the walk (shared memory)
+#ifndef SPH_BUF_CAP
+#define SPH_BUF_CAP 16
+#endif
+constexpr int BUF_CAP = SPH_BUF_CAP;   // kept candidates per lane between flushes of the walk (shared memory)
 // lanes per particle in the pair passes (measured: 1, 2, 4, 8 in 2D and 2, 4, 8, 16 in 3D;
 // fewer lanes repeat less of the per-particle stencil work, more lanes balance the candidates)
 #ifndef SPH_LPP_2D
@@ -111,12 +114,12 @@ static_assert(CHUNK % (BLOCK / Lpp<2>::v) == 0 && CHUNK % (BLOCK / Lpp<3>::v) ==
               "a pair-pass block must lie in one chunk");
 
 // minimum resident blocks per SM asked of the compiler for the two pair passes (FP32 build;
-// the FP64 build asks for 2): it bounds the registers per thread, trading spills for occupancy
+// the FP64 build asks for 4): it bounds the registers per thread, trading spills for occupancy
 #ifndef SPH_INTERACT_MINB
-#define SPH_INTERACT_MINB 4
+#define SPH_INTERACT_MINB 8
 #endif
 #ifndef SPH_INTEGRATE_MINB
-#define SPH_INTEGRATE_MINB 4
+#define SPH_INTEGRATE_MINB 8
 #endif
 // cells per support of the cell grid when the parameters leave the choice to the library
 #ifndef SPH_DEFAULT_CPS_2D
@@ -180,14 +183,15 @@ template <typename T, int D> void launch_init_h(const State<T>& s, int inst, cud
 template <typename T, int D> void launch_repack(const State<T>& s, const int* old_off, const int* move_n, cudaStream_t st);
 
 // interact.cu
+// run_control: the last block of every instance then runs the instance's controller (a step);
+// inspection calls pass false
 template <typename T, int D>
-void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, cudaStream_t st);
+void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, bool run_control, cudaStream_t st);
 template <typename T, int D>
 void launch_neighbors(const State<T>& s, int mode, int* counts, const long long* offsets, int* lists, cudaStream_t st);
 template <typename T, int D> void launch_pair_counts(const State<T>& s, unsigned long long* out2, cudaStream_t st);
 
 // integrate.cu
-template <typename T, int D> void launch_control(const State<T>& s, const One* one, cudaStream_t st);
 template <typename T, int D>
 void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const Out<T>& o, cudaStream_t st);
 

@@ -98,7 +98,8 @@ EXPORTS = ["sph_params_default", "sph_mesh_create", "sph_mesh_set_state", "sph_m
            "sph_debug_pair_counts", "sph_cell_sort_noalloc", "sph_batch_create", "sph_batch_size",
            "sph_batch_set_problem", "sph_batch_set_state", "sph_batch_step", "sph_batch_sync",
            "sph_batch_run_until_converged", "sph_batch_positions", "sph_batch_reports", "sph_batch_set_timing",
-           "sph_batch_kernel_times", "sph_batch_destroy", "sph_batch_slot_bytes", "sph_server_create",
+           "sph_batch_kernel_times", "sph_batch_destroy", "sph_batch_slot_bytes", "sph_batch_autotune",
+           "sph_mesh_snapshot", "sph_mesh_restore", "sph_batch_snapshot", "sph_batch_restore", "sph_server_create",
            "sph_server_submit", "sph_server_poll", "sph_server_drain", "sph_server_job", "sph_server_release",
            "sph_server_destroy"]
 
@@ -144,6 +145,11 @@ def lib():
             "sph_batch_set_timing": [vp, i32],
             "sph_batch_kernel_times": [vp, vp, i32, vp],
             "sph_batch_slot_bytes": [i32, i32, vp],
+            "sph_batch_autotune": [vp, i32, vp, vp],
+            "sph_mesh_snapshot": [vp, vp, C.c_size_t, vp],
+            "sph_mesh_restore": [vp, vp, C.c_size_t],
+            "sph_batch_snapshot": [vp, i32, vp, C.c_size_t, vp],
+            "sph_batch_restore": [vp, i32, vp, C.c_size_t],
             "sph_server_create": [vp, vp],
             "sph_server_submit": [vp, vp, vp, vp, i64, vp, vp, vp, i64, vp],
             "sph_server_poll": [vp, vp],
@@ -442,6 +448,38 @@ def sph_batch_kernel_times(b):
 def sph_batch_destroy(b):
     if b:
         lib().sph_batch_destroy(b)
+
+
+def sph_mesh_snapshot(m) -> bytes:
+    need = C.c_size_t(0)
+    _check(lib().sph_mesh_snapshot(m, None, 0, C.addressof(need)))
+    buf = (C.c_char * need.value)()
+    _check(lib().sph_mesh_snapshot(m, buf, need.value, C.addressof(need)))
+    return bytes(buf)
+
+
+def sph_mesh_restore(m, snap: bytes):
+    _check(lib().sph_mesh_restore(m, snap, len(snap)))
+
+
+def sph_batch_snapshot(b, inst) -> bytes:
+    need = C.c_size_t(0)
+    _check(lib().sph_batch_snapshot(b, int(inst), None, 0, C.addressof(need)))
+    buf = (C.c_char * need.value)()
+    _check(lib().sph_batch_snapshot(b, int(inst), buf, need.value, C.addressof(need)))
+    return bytes(buf)
+
+
+def sph_batch_restore(b, inst, snap: bytes):
+    _check(lib().sph_batch_restore(b, int(inst), snap, len(snap)))
+
+
+def sph_batch_autotune(b, trial_steps=10):
+    """Returns (chosen cells per support, trial times in ms for 1, 2, 4; -1 = not possible)."""
+    c = C.c_int32(0)
+    t = (C.c_float * 3)()
+    _check(lib().sph_batch_autotune(b, int(trial_steps), C.addressof(c), t))
+    return c.value, list(t)
 
 
 def sph_batch_slot_bytes(dim, precision=32):

@@ -168,3 +168,29 @@ def test_batch_capacity_is_shared_between_instances():
     pa, ra = alone(w, 30, 32)
     same(pa, b.positions(1))
     b.close()
+
+
+def test_autotune_keeps_the_state():
+    ws = [WL.disk_holes(n_target=5000, seed=61), WL.square2d(h=0.04, seed=62)]
+    b = S.Batch(ws, precision=32)
+    for i in range(len(ws)):
+        b.set_state(i)
+    b.step(30)
+    b.sync()
+    before = [b.positions(i) for i in range(len(ws))]
+    rep0 = b.reports()
+    cps, ms = S.sph_batch_autotune(b.h, 5)
+    assert cps in (1, 2, 4) and ms[[1, 2, 4].index(cps)] > 0
+    after = [b.positions(i) for i in range(len(ws))]
+    rep1 = b.reports()
+    for i, w in enumerate(ws):
+        assert rep1[i].iteration == rep0[i].iteration == 30 and rep1[i].phase == rep0[i].phase
+        # re-represented on the chosen grid: equal up to the rounding of the stored offsets
+        tol = 1e-6 * w["sizing"]["lo"]
+        assert np.abs(after[i]["x"] - before[i]["x"]).max() <= tol
+        assert np.array_equal(after[i]["group"], before[i]["group"])
+        assert np.allclose(after[i]["v"], before[i]["v"], rtol=0, atol=0)
+    b.step(20)
+    b.sync()
+    assert all(r.iteration == 50 for r in b.reports())
+    b.close()
