@@ -46,8 +46,8 @@ FLOP_PER_PAIR = 50.0       # FP32 operations per interacting pair of the pressur
 # (cold L2); None once the kernel changes until it is captured again
 INTERACT_DRAM_BYTES = 6.339072e6 + 1.087744e6
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-# one step: one-pass scan, scatter, gather, pressure pass (+ controller), update (+ next keys)
-KERNELS_PER_STEP = 5
+# one step: one-pass scan, scatter, gather, pressure pass, controller, update (+ next keys)
+KERNELS_PER_STEP = 6
 
 
 def parse():
@@ -136,6 +136,25 @@ class Clocks:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def replica_throughput(local_ms, particles, steps, device=None):
+    """Replicas (one independent instance per rank, no collective on the data path): the job
+    time is the slowest rank's, the throughput counts every rank's particles.  Returns
+    (max ms over ranks, particle-steps/s of the whole job)."""
+    import torch
+
+    ws = 1
+    if torch.distributed.is_available() and torch.distributed.is_initialized():
+        ws = torch.distributed.get_world_size()
+        t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        n = torch.tensor([float(particles)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(n, op=torch.distributed.ReduceOp.SUM)
+        local_ms, total = float(t.item()), float(n.item())
+    else:
+        total = float(particles)
+    return local_ms, total * steps / (local_ms / 1e3)
 
 
 def dist_env():
@@ -313,11 +332,7 @@ def run_ours(args):
     m.sync()
     rep = m.report()
 
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = n * ws * args.steps / (total_ms / 1e3)
+    total_ms, value = replica_throughput(total_ms, n, args.steps, dev)
 
     # per-stage averages and the dominant kernel's roofline
     cand, accd = S.sph_debug_pair_counts(m.h)

@@ -108,8 +108,8 @@ struct KTime {
 };
 // the step graph: rebuild = one-pass scan, scatter, gather (the keys and histogram come from
 // the previous step's update); the update also computes the next keys
-constexpr int NSTAGE = 3;
-const KTime kStages[NSTAGE] = {{"rebuild", 3}, {"interact", 1}, {"integrate", 1}};
+constexpr int NSTAGE = 4;
+const KTime kStages[NSTAGE] = {{"rebuild", 3}, {"interact", 1}, {"control", 1}, {"integrate", 1}};
 
 // host copy of one instance
 struct Inst {
@@ -707,10 +707,12 @@ template <typename T, int D> void enqueue_step(sph_batch* b, bool timed) {
     if (timed) cudaEventRecordWithFlags(b->ev[0], stream, cudaEventRecordExternal);
     enqueue_rebuild<T, D>(b, s, stream);
     if (timed) cudaEventRecordWithFlags(b->ev[1], stream, cudaEventRecordExternal);
-    launch_interact<T, D>(s, one_of(b), nullptr, nullptr, true, stream);   // + the controllers
+    launch_interact<T, D>(s, one_of(b), nullptr, nullptr, stream);
     if (timed) cudaEventRecordWithFlags(b->ev[2], stream, cudaEventRecordExternal);
-    launch_integrate<T, D>(s, one_of(b), s.ctrls, out_stored<T>(s), stream);
+    launch_control<T, D>(s, one_of(b), stream);
     if (timed) cudaEventRecordWithFlags(b->ev[3], stream, cudaEventRecordExternal);
+    launch_integrate<T, D>(s, one_of(b), s.ctrls, out_stored<T>(s), stream);
+    if (timed) cudaEventRecordWithFlags(b->ev[4], stream, cudaEventRecordExternal);
 }
 
 sph_status collect_timing(sph_batch* b) {
@@ -1010,7 +1012,7 @@ sph_status dbg_interact_impl(sph_batch* b, double* a_p, double* sigma, double* g
     T *d_sig = nullptr, *d_gam = nullptr;
     CK(cudaMalloc(&d_sig, sizeof(T) * (size_t)std::max(ns, 1)));
     CK(cudaMalloc(&d_gam, sizeof(T) * (size_t)std::max(ns, 1)));
-    launch_interact<T, D>(s, one_of(b), d_sig, d_gam, false, b->stream);
+    launch_interact<T, D>(s, one_of(b), d_sig, d_gam, b->stream);
     CK(cudaGetLastError());
     std::vector<Vec4<T>> A(ns);
     std::vector<T> sg(ns), gm(ns);
@@ -1075,7 +1077,7 @@ sph_status dbg_update_impl(sph_batch* b, const double* dt, const int32_t* reset,
     State<T> s;
     sph_status r = dbg_prepare<T, D>(b, s, &c);
     if (r != SPH_OK) return r;
-    launch_interact<T, D>(s, one_of(b), nullptr, nullptr, false, b->stream);
+    launch_interact<T, D>(s, one_of(b), nullptr, nullptr, b->stream);
     // scratch output arrays
     Out<T> o;
     void* buf = nullptr;

@@ -1,8 +1,201 @@
-// integrate.cu -- the viscous pass + update + projection of one relaxation step (Algorithm 1:
-// mid-point velocity, viscous force, map, predicted velocity, position, map).
+// integrate.cu -- per-step controller (Sec. 3.4, Eq. 24) and the viscous pass + update +
+// projection of one relaxation step (Algorithm 1: mid-point velocity, viscous force, map,
+// predicted velocity, position, map).
 #include "sph_internal.cuh"
 
 namespace sph {
+
+__device__ __forceinline__ double rel_err(double a, double b) {
+    if (b != 0.0) return fabs(a - b) / fabs(b);
+    return a == 0.0 ? 0.0 : CUDART_INF;
+}
+
+__device__ inline void window_reset(Ctrl* c) {
+    c->wcount = 0;
+    c->nwin = 0;
+    for (int g = 0; g < MAXF; ++g) {
+        c->wsum[g] = 0.0;
+        c->A_last[g] = 0.0;
+        c->A_prev[g] = 0.0;
+    }
+}
+
+// One block of 256 threads per instance.  The controller state is copied into shared memory at once, the
+// per-block V~ sums of a sampling step are reduced in a fixed order, and the controller for
+// step n runs with one thread per group (thread 0 keeps the scalar state):
+//  1. RAMP -> PHASE2 after ramp_len steps (windows restart);
+//  2. in PHASE1 / PHASE2 on steps n % sample_every == 0: V-bar_g enters the open window; a full
+//     window closes with its mean; with two closed windows E_t = max_g |V-bar - A_last|/|A_last|,
+//     E_avg = max_g |A_last - A_prev|/|A_prev|, E_sys = max; E_sys < threshold moves
+//     PHASE1 -> RAMP or PHASE2 -> DONE (Sec. 3.4.2);
+//  3. step parameters: PHASE1 eps = eps1, f = 1, nullify when n % reset_period == 0; RAMP
+//     s = (n - ramp_start)/ramp_len, eps = eps1 (1 - s), f = (1 + cos(pi s))/2; PHASE2 eps = 0,
+//     nullify every step (Sec. 3.4.3, 3.4.4);
+//  4. per group dt = min(dta, dtv/f), nullified (dt = dta) on the schedule or when dt falls
+//     below dt_collapse times the group's previous step; dt <= dt_cap (Eq. 24).
+// DONE freezes the state (dt = 0, the step counter stops).
+template <typename T, int D, bool ONE> __global__ void __launch_bounds__(256) k_control(State<T> s, One one) {
+    __shared__ double vs[MAXF], et[MAXF], ea[MAXF];
+    __shared__ Ctrl sc;
+    __shared__ Params psh;
+    __shared__ int fl[4];          // 0: done, 1: sampling step, 2: window closes, 3: reset windows
+    __shared__ double par[3];      // eps, f, periodic
+    const int inst = blockIdx.x;
+    constexpr int NW = (int)(sizeof(Ctrl) / sizeof(unsigned));
+    unsigned* scw = reinterpret_cast<unsigned*>(&sc);
+    unsigned* gw = reinterpret_cast<unsigned*>(s.ctrls + inst);
+    const int t = threadIdx.x;
+    for (int k = t; k < NW; k += blockDim.x) scw[k] = gw[k];
+    if (!ONE) block_copy(&psh, s.params + inst);
+    const Params& p = ONE ? one.p : psh;
+    __syncthreads();
+    const int G = p.G;
+    if (sc.sample_now != 0) {
+        // the pair-pass blocks of this instance (BLOCK/LPP slots each)
+        constexpr int PB = BLOCK / Lpp<D>::v;
+        const int b0 = __ldg(s.inst_off + inst) / PB, b1 = __ldg(s.inst_off + inst + 1) / PB;
+        const int lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+        for (int g = wid; g < G; g += nw) {
+            double acc = 0.0;
+            for (int b = b0 + lane; b < b1; b += 32) acc += s.partials[(size_t)b * MAXF + g];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (lane == 0) vs[g] = acc;
+        }
+    }
+    if (t == 0) {
+        const bool done = sc.phase == PH_DONE;
+        bool reset = false;
+        if (!done && sc.phase == PH_RAMP && sc.n - sc.ramp_start >= p.ramp_len) {
+            sc.phase = PH2;
+            sc.wcount = 0;
+            sc.nwin = 0;
+            reset = true;
+        }
+        const bool smp = !done && (sc.phase == PH1 || sc.phase == PH2) && sc.n % p.sample_every == 0;
+        fl[0] = done;
+        fl[1] = smp;
+        fl[2] = smp && sc.wcount + 1 == p.window;
+        fl[3] = reset;
+    }
+    __syncthreads();
+    if (fl[3] && t < MAXF) {
+        sc.wsum[t] = 0.0;
+        sc.A_last[t] = 0.0;
+        sc.A_prev[t] = 0.0;
+    }
+    __syncthreads();
+    if (fl[1] && t < G) {
+        sc.Vbar[t] = p.gdim[t] > 0 ? vs[t] : 0.0;
+        sc.wsum[t] += sc.Vbar[t];
+        if (fl[2]) {
+            sc.A_prev[t] = sc.A_last[t];
+            sc.A_last[t] = sc.wsum[t] / p.window;
+            sc.wsum[t] = 0.0;
+        }
+    }
+    if (t == 0 && fl[1]) {
+        sc.wcount += 1;
+        if (fl[2]) {
+            sc.wcount = 0;
+            sc.nwin += 1;
+        }
+    }
+    __syncthreads();
+    const bool evaluate = fl[1] && sc.nwin >= 2;
+    if (evaluate && t < MAXF) {
+        const bool use = t < G && p.gdim[t] >= 1;
+        et[t] = use ? rel_err(sc.Vbar[t], sc.A_last[t]) : 0.0;
+        ea[t] = use ? rel_err(sc.A_last[t], sc.A_prev[t]) : 0.0;
+    }
+    __syncthreads();
+    if (t == 0) {
+        bool reset = false;
+        if (evaluate) {
+            double e1 = 0.0, e2 = 0.0;
+            for (int g = 0; g < G; ++g) {
+                e1 = fmax(e1, et[g]);
+                e2 = fmax(e2, ea[g]);
+            }
+            sc.E_t = e1;
+            sc.E_avg = e2;
+            sc.E_sys = fmax(e1, e2);
+            if (sc.E_sys < p.threshold) {
+                if (sc.phase == PH1) {
+                    sc.phase = PH_RAMP;
+                    sc.ramp_start = sc.n;
+                    sc.wcount = 0;
+                    sc.nwin = 0;
+                    reset = true;
+                } else {
+                    sc.phase = PH_DONE;
+                    fl[0] = 1;
+                }
+            }
+        }
+        fl[3] = reset;
+        double eps = p.eps1, f = 1.0;
+        bool periodic = (sc.n % p.reset_period) == 0;
+        if (sc.phase == PH_RAMP) {
+            const double sr = (double)(sc.n - sc.ramp_start) / (double)p.ramp_len;
+            eps = p.eps1 * (1.0 - sr);
+            f = 0.5 * (1.0 + cos(CUDART_PI * sr));
+        } else if (sc.phase == PH2) {
+            eps = 0.0;
+            periodic = true;
+        }
+        par[0] = eps;
+        par[1] = f;
+        par[2] = periodic ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (fl[3] && t < MAXF) {
+        sc.wsum[t] = 0.0;
+        sc.A_last[t] = 0.0;
+        sc.A_prev[t] = 0.0;
+    }
+    if (t < G) {
+        const double dta = (double)from_bits<T>(sc.dta_bits[t]);
+        const double dtv = (double)from_bits<T>(sc.dtv_bits[t]);
+        if (fl[0] || p.gdim[t] < 1) {
+            sc.dt[t] = 0.0;
+            sc.dt_f[t] = 0.0f;
+            sc.reset[t] = 1;
+        } else {
+            const double f = par[1];
+            const double dv = f > 0.0 ? dtv / f : CUDART_INF;
+            const double cand = fmin(dta, dv);
+            const bool rs = par[2] != 0.0 || (sc.dt_prev[t] > 0.0 && cand < p.dt_collapse * sc.dt_prev[t]);
+            double dt = rs ? dta : cand;
+            dt = fmin(dt, p.dt_cap);
+            sc.dt_prev[t] = dt;
+            sc.dt[t] = dt;
+            sc.dt_f[t] = (float)dt;
+            sc.reset[t] = rs ? 1 : 0;
+        }
+    }
+    if (t < MAXF) {
+        sc.dta_bits[t] = inf_bits<T>();
+        sc.dtv_bits[t] = inf_bits<T>();
+    }
+    if (t == 0) {
+        if (fl[0]) {
+            sc.phase = PH_DONE;
+            sc.eps = 0.0;
+            sc.f = 0.0;
+            sc.sample_now = 0;
+        } else {
+            sc.eps = par[0];
+            sc.f = par[1];
+            sc.n += 1;
+            sc.sample_now = (sc.n % p.sample_every) == 0 ? 1 : 0;
+        }
+        sc.eps_f = (float)sc.eps;
+        sc.f_f = (float)sc.f;
+    }
+    __syncthreads();
+    for (int k = t; k < NW; k += blockDim.x) gw[k] = scw[k];
+}
 
 // h_t(x) and the level set in the working precision, from the position in that precision and
 // constants stored in it (no FP64 instruction in the FP32 build): the FP32 build stores h as a
@@ -296,6 +489,10 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 4
     }
 }
 
+template <typename T, int D> void launch_control(const State<T>& s, const One* one, cudaStream_t st) {
+    if (one) k_control<T, D, true><<<s.NI, 256, 0, st>>>(s, *one);
+    else k_control<T, D, false><<<s.NI, 256, 0, st>>>(s, One());
+}
 template <typename T, int D>
 void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const Out<T>& o, cudaStream_t st) {
     const int nb = div_up((long long)s.n * Lpp<D>::v, BLOCK);
@@ -304,6 +501,7 @@ void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const 
 }
 
 #define SPH_INST(T, D)                                                      \
+    template void launch_control<T, D>(const State<T>&, const One*, cudaStream_t);      \
     template void launch_integrate<T, D>(const State<T>&, const One*, const Ctrl*, const Out<T>&, cudaStream_t);
 SPH_INST(float, 2)
 SPH_INST(float, 3)

@@ -15,13 +15,13 @@
 // A block serves BLOCK/LPP consecutive slots, which lie in one chunk and so in one instance:
 // the instance's grid and parameters are copied into shared memory once per block (a batch of
 // one passes them as kernel parameters instead).
-#include "control.cuh"
+#include "sph_internal.cuh"
 
 namespace sph {
 
 template <typename T, int D, bool ONE>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTERACT_MINB : 4)
-    k_interact(State<T> s, One one, T* dbg_sigma, T* dbg_gamma, bool run_control) {
+    k_interact(State<T> s, One one, T* dbg_sigma, T* dbg_gamma) {
     constexpr int LPP = Lpp<D>::v;
     __shared__ unsigned long long sh_dta[MAXF], sh_dtv[MAXF];
     __shared__ double sh_part[BLOCK / 32][MAXF];
@@ -196,21 +196,6 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTERACT_MINB : 4)
             s.partials[(size_t)blockIdx.x * MAXF + t] = acc;
         }
     }
-    if (!run_control) return;
-    // the last of the instance's blocks to finish runs its controller (a3, a5): every block's
-    // minima and partial sums are visible to it once it has seen the count
-    __shared__ int sh_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        constexpr int PB = BLOCK / LPP;
-        const int nb = ONE ? (int)gridDim.x : (__ldg(s.inst_off + inst + 1) - __ldg(s.inst_off + inst)) / PB;
-        sh_last = atomicAdd(&ctrl->blocks_done, 1) == nb - 1;
-    }
-    __syncthreads();
-    if (!sh_last) return;
-    __threadfence();
-    controller_step<T, D>(s, inst, p, *reinterpret_cast<CtrlShared*>(sbuf));   // the buffer is free now
 }
 
 // neighbour sets for inspection, through the same walk as the pair passes (one lane per
@@ -288,9 +273,9 @@ __global__ void __launch_bounds__(BLOCK) k_pair_counts(State<T> s, unsigned long
 }
 
 template <typename T, int D>
-void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, bool run_control, cudaStream_t st) {
-    if (one) k_interact<T, D, true><<<s.nblk, BLOCK, 0, st>>>(s, *one, dbg_sigma, dbg_gamma, run_control);
-    else k_interact<T, D, false><<<s.nblk, BLOCK, 0, st>>>(s, One(), dbg_sigma, dbg_gamma, run_control);
+void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, cudaStream_t st) {
+    if (one) k_interact<T, D, true><<<s.nblk, BLOCK, 0, st>>>(s, *one, dbg_sigma, dbg_gamma);
+    else k_interact<T, D, false><<<s.nblk, BLOCK, 0, st>>>(s, One(), dbg_sigma, dbg_gamma);
 }
 template <typename T, int D>
 void launch_neighbors(const State<T>& s, int mode, int* counts, const long long* offsets, int* lists, cudaStream_t st) {
@@ -301,7 +286,7 @@ template <typename T, int D> void launch_pair_counts(const State<T>& s, unsigned
 }
 
 #define SPH_INST(T, D)                                                                                        \
-    template void launch_interact<T, D>(const State<T>&, const One*, T*, T*, bool, cudaStream_t);             \
+    template void launch_interact<T, D>(const State<T>&, const One*, T*, T*, cudaStream_t);                   \
     template void launch_neighbors<T, D>(const State<T>&, int, int*, const long long*, int*, cudaStream_t);   \
     template void launch_pair_counts<T, D>(const State<T>&, unsigned long long*, cudaStream_t);
 SPH_INST(float, 2)

@@ -96,7 +96,7 @@ struct Ctrl {
     long long n, ramp_start;
     unsigned long long escapes;
     unsigned int status;
-    int blocks_done;   // pressure-pass blocks of this step that have finished (the last runs the controller)
+    int pad;
     double wsum[MAXF], A_last[MAXF], A_prev[MAXF], Vbar[MAXF], dt_prev[MAXF], dt[MAXF];
     int reset[MAXF];
     double E_t, E_avg, E_sys, eps, f;

@@ -183,15 +183,14 @@ template <typename T, int D> void launch_init_h(const State<T>& s, int inst, cud
 template <typename T, int D> void launch_repack(const State<T>& s, const int* old_off, const int* move_n, cudaStream_t st);
 
 // interact.cu
-// run_control: the last block of every instance then runs the instance's controller (a step);
-// inspection calls pass false
 template <typename T, int D>
-void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, bool run_control, cudaStream_t st);
+void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, cudaStream_t st);
 template <typename T, int D>
 void launch_neighbors(const State<T>& s, int mode, int* counts, const long long* offsets, int* lists, cudaStream_t st);
 template <typename T, int D> void launch_pair_counts(const State<T>& s, unsigned long long* out2, cudaStream_t st);
 
 // integrate.cu
+template <typename T, int D> void launch_control(const State<T>& s, const One* one, cudaStream_t st);
 template <typename T, int D>
 void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const Out<T>& o, cudaStream_t st);
 
