@@ -411,12 +411,6 @@ __device__ __forceinline__ double fast_rcp(double v) { return 1.0 / v; }
 __device__ __forceinline__ float fast_rsqrt(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double fast_rsqrt(double v) { return 1.0 / sqrt(v); }
 
-// 1: for records without the meta word in the vector (3D, FP64), the walk derives a
-// candidate's x cell from the row's cell starts instead of loading its meta word
-#ifndef SPH_CELL_TRACK
-#define SPH_CELL_TRACK 1
-#endif
-
 // ---- sub-warp stencil walk ----
 // For query particle i at level li with cell coordinates ci (at li) and offsets offi, the walk
 // visits every particle j stored in the cells that can hold a j with
@@ -434,8 +428,9 @@ __device__ __forceinline__ double fast_rsqrt(double v) { return 1.0 / sqrt(v); }
 // accepted or rejected the same way whatever LPP.  No warp-synchronous operation is used
 // inside.  (Measured and not kept: trimming rows to the chord of the search disc, sharing the
 // level-mask loads among the lanes, loading the next row's range ahead of the current row's
-// scan, and a warp-cooperative walk over the union of the warp's stencils with candidates
-// staged in shared memory -- the first three cost more registers or instructions than they saved,
+// scan, deriving a 3D candidate's x cell from the row's cell starts instead of its meta word,
+// and a warp-cooperative walk over the union of the warp's stencils with candidates
+// staged in shared memory -- the first four cost more registers or instructions than they saved,
 // the last tests about twice the candidates, since a warp's particles span several cells.)
 template <typename T, int D>
 __device__ __forceinline__ int candidate_dx(const Vec4<T>* __restrict__ P, const unsigned* __restrict__ M, int j,
@@ -530,40 +525,18 @@ __device__ __forceinline__ void walk_sub(const Grid& g, const int* __restrict__ 
                 const int row = g.base[l] + rid * dxl;
                 const int s = max(__ldg(cell_start + row + lo[0]), 0);
                 const int e = min(__ldg(cell_start + row + hb[0] + 1), n);
-                if (Rec<T, D>::packed || !SPH_CELL_TRACK) {
-                    for (int j = s + sub; j < e; j += LPP) {
-                        T offj[3], hj, dx[3];
-                        unsigned mj;
-                        Rec<T, D>::load(P, M, j, offj, hj, mj);
-                        dx[0] = rn_add(rn_sub(offi[0], offj[0]), rn_mul((T)(Pi[0] - (meta_cx(mj) << l)), c0));
-                        dx[1] = rn_add(rn_sub(offi[1], offj[1]), mcy);
-                        dx[2] = D == 3 ? rn_add(rn_sub(offi[2], offj[2]), mcz) : T(0);
-                        T r2 = rn_add(rn_mul(dx[0], dx[0]), rn_mul(dx[1], dx[1]));
-                        if (D == 3) r2 = rn_add(r2, rn_mul(dx[2], dx[2]));
-                        if (r2 < R2 && accept(j, dx, r2, hj, mj)) {
-                            buf[cnt * BLOCK] = make_int2(j, (l << 28) | (cz << 14) | cy);
-                            if (++cnt == CAP) flush();
-                        }
-                    }
-                } else {
-                    // records without the meta word: the candidate's x cell follows from the row's
-                    // cell starts as the scan passes them, and the meta word is read only for
-                    // candidates within R
-                    int cx = lo[0], nextb = __ldg(cell_start + row + cx + 1);
-                    for (int j = s + sub; j < e; j += LPP) {
-                        while (j >= nextb && cx < hb[0]) nextb = __ldg(cell_start + row + (++cx) + 1);
-                        const Vec4<T> pj = P[j];
-                        const T offj[3] = {pj.x, pj.y, pj.z};
-                        T dx[3];
-                        dx[0] = rn_add(rn_sub(offi[0], offj[0]), rn_mul((T)(Pi[0] - (cx << l)), c0));
-                        dx[1] = rn_add(rn_sub(offi[1], offj[1]), mcy);
-                        dx[2] = D == 3 ? rn_add(rn_sub(offi[2], offj[2]), mcz) : T(0);
-                        T r2 = rn_add(rn_mul(dx[0], dx[0]), rn_mul(dx[1], dx[1]));
-                        if (D == 3) r2 = rn_add(r2, rn_mul(dx[2], dx[2]));
-                        if (r2 < R2 && accept(j, dx, r2, pj.w, __ldg(M + j))) {
-                            buf[cnt * BLOCK] = make_int2(j, (l << 28) | (cz << 14) | cy);
-                            if (++cnt == CAP) flush();
-                        }
+                for (int j = s + sub; j < e; j += LPP) {
+                    T offj[3], hj, dx[3];
+                    unsigned mj;
+                    Rec<T, D>::load(P, M, j, offj, hj, mj);
+                    dx[0] = rn_add(rn_sub(offi[0], offj[0]), rn_mul((T)(Pi[0] - (meta_cx(mj) << l)), c0));
+                    dx[1] = rn_add(rn_sub(offi[1], offj[1]), mcy);
+                    dx[2] = D == 3 ? rn_add(rn_sub(offi[2], offj[2]), mcz) : T(0);
+                    T r2 = rn_add(rn_mul(dx[0], dx[0]), rn_mul(dx[1], dx[1]));
+                    if (D == 3) r2 = rn_add(r2, rn_mul(dx[2], dx[2]));
+                    if (r2 < R2 && accept(j, dx, r2, hj, mj)) {
+                        buf[cnt * BLOCK] = make_int2(j, (l << 28) | (cz << 14) | cy);
+                        if (++cnt == CAP) flush();
                     }
                 }
             }
