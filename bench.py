@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--serve-iters", type=int, default=600)
     ap.add_argument("--serve-max-n", type=int, default=200_000)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cube", action="store_true")
+    ap.add_argument("--cube-steps", type=int, default=100)
     return ap.parse_args()
 
 
@@ -176,6 +178,8 @@ def _gen_one(spec):
     kind, n, seed, r = spec
     if kind == 2:
         return WL.disk_holes(n_target=n, seed=seed, mc_samples=100_000)
+    if kind == 4:   # the single-instance 3D workload, with the generator's default integration
+        return WL.cube_sphere(n_target=n, seed=seed, sphere_r=r)
     return WL.cube_sphere(n_target=n, seed=seed, sphere_r=r, mc_samples=100_000)
 
 
@@ -277,7 +281,9 @@ def run_ours(args):
 
     ws, rank, local = dist_env()
     # batch and serving inputs, generated before the first GPU call
-    batch_ws, serve_ws, serve_t = None, None, None
+    batch_ws, serve_ws, serve_t, cube_w = None, None, None, None
+    if rank == 0 and not args.no_cube:
+        cube_w = generate([(4, 1_200_000, 3, 0.3)])[0]
     if rank == 0 and not args.no_batch:
         specs, _ = _specs(64, 4, 1_000, 200_000, alternate=True)
         batch_ws = generate(specs)
@@ -361,6 +367,10 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = e2e_run(S, w, stream, args.steps)
 
+    cube = None
+    if cube_w is not None:
+        cube = cube_run(S, torch, dev, cube_w, args.cube_steps)
+
     batched = None
     if batch_ws is not None:
         batched = batched_run(S, torch, dev, batch_ws, args.batch_steps)
@@ -400,6 +410,7 @@ def run_ours(args):
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "cube_3d": cube,
         "batched": batched,
         "serving": serving,
     }
@@ -439,6 +450,39 @@ def e2e_run(S, w, stream, steps):
     return {"value": n * steps / (t1 - t0), "unit": METRIC, "h2d_bytes_per_step": h2d / steps,
             "d2h_bytes_per_step": d2h, "wall_s": t1 - t0,
             "job": f"upload of {n} particles, {steps} steps each with a controller-report read, final download"}
+
+
+def cube_run(S, torch, dev, w, steps):
+    """The 3D cube minus a sphere at ~1.2M particles, one instance, device-timed steps."""
+    stream = torch.cuda.Stream(device=dev)
+    m = S.Mesh(w, precision=32, stream=stream.cuda_stream)
+    m.set_state()
+    m.step(3)
+    m.sync()
+    S.sph_mesh_set_timing(m.h, 1)
+    m.step(1)
+    m.sync()
+    S.sph_mesh_set_timing(m.h, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    m.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    t = S.sph_mesh_kernel_times(m.h)
+    g = S.sph_mesh_grid(m.h)
+    n = len(w["x"])
+    out = {"value": n * steps / (ms / 1e3), "unit": METRIC, "steps": steps, "ms_per_step": ms / steps,
+           "particles": n, "cells_per_support": g.cells_per_support,
+           "stages_ms": {k: v[1] / max(steps, 1) for k, v in t.items()},
+           "config": {"workload": "cube_sphere_3d_1.2M: unit cube minus a centred sphere r=0.3, "
+                                  "h = min(0.008 + 0.04|d|, 0.05) scaled to 1.2M particles (seed 3)",
+                      "l2": "working set larger than L2 (no flush)"}}
+    S.sph_mesh_set_timing(m.h, 0)
+    m.sync()
+    m.close()
+    return out
 
 
 def batched_run(S, torch, dev, ws, steps):

@@ -41,9 +41,10 @@ template <typename T, int D, bool ONE> __global__ void __launch_bounds__(256) k_
     __shared__ int fl[4];          // 0: done, 1: sampling step, 2: window closes, 3: reset windows
     __shared__ double par[3];      // eps, f, periodic
     const int inst = blockIdx.x;
-    constexpr int NW = (int)(sizeof(Ctrl) / sizeof(unsigned));
-    unsigned* scw = reinterpret_cast<unsigned*>(&sc);
-    unsigned* gw = reinterpret_cast<unsigned*>(s.ctrls + inst);
+    static_assert(sizeof(Ctrl) % sizeof(int4) == 0, "the controller is copied in 16-byte vectors");
+    constexpr int NW = (int)(sizeof(Ctrl) / sizeof(int4));
+    int4* scw = reinterpret_cast<int4*>(&sc);
+    int4* gw = reinterpret_cast<int4*>(s.ctrls + inst);
     const int t = threadIdx.x;
     for (int k = t; k < NW; k += blockDim.x) scw[k] = gw[k];
     if (!ONE) block_copy(&psh, s.params + inst);

@@ -6,7 +6,7 @@
 //                     (position = origin + C*c0 + O, reconstructed in FP64 where needed)
 //     V[a][n] T       velocities;  H[n] T smoothing length;  G[n] uint32 meta;  ID[n] int32
 //   sorted state (written by the gather of the rebuild, read by the pair passes):
-//     Cs, Os, Vs, Hs, IDs as above, Ks[n] cell key, Ms[n] meta with the particle's x-cell,
+//     Cs, Os, IDs as above, VH[n] T4 = (v, h), Ks[n] cell key, Ms[n] meta with the x-cell,
 //     P[n] T4 = offsets inside the particle's own level cell + h (FP32 build, 2D:
 //     (ox, oy, h, meta bits)), A[n] T4 = (a_p.x, a_p.y, a_p.z, V~) from the pressure pass.
 //   meta bits: 0-5 group (feature index), 6-7 intrinsic dimension, 8-31 x index of the cell
@@ -90,8 +90,9 @@ struct Params {
     float kappa_f, p0_f, visc_f, cfl_a_f, cfl_v_f;   // float copies for the FP32 kernels
 };
 
-// controller state + per-step accumulators (one per instance, in device memory)
-struct Ctrl {
+// controller state + per-step accumulators (one per instance, in device memory; 16-byte
+// aligned so that it is copied in vectors)
+struct alignas(16) Ctrl {
     int phase, wcount, nwin, sample_now;
     long long n, ramp_start;
     unsigned long long escapes;
@@ -406,7 +407,7 @@ template <typename T> __device__ __forceinline__ T self_rc2(T hi, T kappa) {
 }
 
 // ---- reciprocal / reciprocal square root for the pair arithmetic (not the predicate) ----
-__device__ __forceinline__ float fast_rcp(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ float fast_rcp(float v) { return __fdividef(1.0f, v); }   // 2-ulp intrinsic division
 __device__ __forceinline__ double fast_rcp(double v) { return 1.0 / v; }
 __device__ __forceinline__ float fast_rsqrt(float v) { return rsqrtf(v); }
 __device__ __forceinline__ double fast_rsqrt(double v) { return 1.0 / sqrt(v); }
