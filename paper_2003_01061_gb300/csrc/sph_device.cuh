@@ -430,8 +430,9 @@ __device__ __forceinline__ double fast_rsqrt(double v) { return 1.0 / sqrt(v); }
 // inside.  (Measured and not kept: trimming rows to the chord of the search disc, sharing the
 // level-mask loads among the lanes, loading the next row's range ahead of the current row's
 // scan, deriving a 3D candidate's x cell from the row's cell starts instead of its meta word,
+// letting a particle's lanes set up LPP rows at once and pass the ranges round by shuffles,
 // and a warp-cooperative walk over the union of the warp's stencils with candidates
-// staged in shared memory -- the first four cost more registers or instructions than they saved,
+// staged in shared memory -- the first five cost more registers or instructions than they saved,
 // the last tests about twice the candidates, since a warp's particles span several cells.)
 template <typename T, int D>
 __device__ __forceinline__ int candidate_dx(const Vec4<T>* __restrict__ P, const unsigned* __restrict__ M, int j,
