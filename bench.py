@@ -12,7 +12,10 @@ hole (0.004-0.04 scaled to ~120k particles), FP32 pair sums with FP64 projection
 * e2e:    the same metric through the public C ABI from pinned host buffers: upload of the
           initial state, K steps each followed by the read-back of the controller report,
           read-back of the final positions -- all inside the host-timed region.
-* roofline: the dominant kernel's achieved rate from its live CUDA-event times.
+* roofline: the dominant kernel's achieved rate from its live CUDA-event times, taken in a
+          second timed region (up to 1000 more steps, same L2 flush) whose step graph holds an
+          event between the stages; the headline region runs the graph without them, so that
+          its kernel-to-kernel edges keep their programmatic (early) launch.
 * cpu_baseline / --impl reference: the FP64 CPU oracle on the host cores (bounded sample).
 * batched: 64 independent instances (half 2D disks with holes, half 3D cubes minus a sphere,
           particle counts log-uniform over 1k-200k, seeded), one batch per dimension on its own
@@ -43,8 +46,9 @@ METRIC = "particle-steps/s"
 WORKLOAD = "disk_holes_2d_120k"
 FLOP_PER_PAIR = 50.0       # FP32 operations per interacting pair of the pressure pass (see design notes)
 # DRAM bytes (read + write) of one pressure-pass launch on this workload, from an ncu capture
-# (cold L2); None once the kernel changes until it is captured again
-INTERACT_DRAM_BYTES = None
+# (cold L2; profiles/k_interact_disk_holes_2d_120k.md); None once the kernel changes until it
+# is captured again
+INTERACT_DRAM_BYTES = 6_381_312 + 1_131_520
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # one step: one-pass scan, scatter, gather, pressure pass, controller, update (+ next keys)
 KERNELS_PER_STEP = 6
@@ -311,30 +315,37 @@ def run_ours(args):
     # warm-up (also captures the step graph)
     m.step(max(args.warmup, 1))
     m.sync()
-    S.sph_mesh_set_timing(m.h, 1)
-    m.step(1)                       # re-capture with the stage events
-    m.sync()
-    S.sph_mesh_set_timing(m.h, 1)   # zero the accumulators
 
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with Clocks(local) as clk:
-        time.sleep(0.3)             # let the sampler start before the timed region
+    def timed_steps(n_steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
         with torch.cuda.stream(stream):
-            for k in range(args.steps):
+            for k in range(n_steps):
                 evs[k][0].record(stream)
                 m.step(1)
                 evs[k][1].record(stream)
                 flush.zero_()       # 256 MiB write between timed steps evicts the 129 MB L2
         torch.cuda.synchronize()
+        return float(sum(a.elapsed_time(b) for a, b in evs))
+
     if ws > 1:
         torch.distributed.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = float(sum(step_ms))
-    stage = S.sph_mesh_kernel_times(m.h)
-    S.sph_mesh_set_timing(m.h, 0)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        time.sleep(0.3)             # let the sampler start before the timed region
+        # the whole step, as a user runs it (graph without stage events)
+        total_ms = timed_steps(args.steps)
+        if ws > 1:
+            torch.distributed.barrier()
+        # the per-kernel split: the same steps with an event between the stages (the events
+        # turn the kernel-to-kernel edges they sit on into ordinary ones)
+        S.sph_mesh_set_timing(m.h, 1)
+        m.step(1)                   # re-capture with the stage events
+        m.sync()
+        S.sph_mesh_set_timing(m.h, 1)   # zero the accumulators
+        stage_steps = min(args.steps, 1000)
+        staged_ms = timed_steps(stage_steps)
+        stage = S.sph_mesh_kernel_times(m.h)
+        S.sph_mesh_set_timing(m.h, 0)
     m.sync()
     rep = m.report()
 
@@ -342,7 +353,7 @@ def run_ours(args):
 
     # per-stage averages and the dominant kernel's roofline
     cand, accd = S.sph_debug_pair_counts(m.h)
-    stages = {k: {"launches": int(v[0]), "avg_ms": (v[1] / max(v[0], 1)) if k != "rebuild" else v[1] / max(args.steps, 1)}
+    stages = {k: {"launches": int(v[0]), "avg_ms": (v[1] / max(v[0], 1)) if k != "rebuild" else v[1] / max(stage_steps, 1)}
               for k, v in stage.items()}
     peaks, peak_src = measured_peaks()
     clocks = clk.summary()
@@ -405,6 +416,7 @@ def run_ours(args):
                    "iteration_at_end": int(rep.iteration)},
         "roofline": roofline,
         "stages_ms": {k: v["avg_ms"] for k, v in stages.items()},
+        "stages_timing": {"steps": stage_steps, "ms_per_step_with_stage_events": staged_ms / stage_steps},
         "pairs_per_particle": {"candidates": cand / n, "interacting": accd / n},
         "clocks": clocks,
         "gpu_launches": KERNELS_PER_STEP * args.steps,

@@ -681,8 +681,8 @@ template <typename T, int D> void ensure_hashed(sph_batch* b, const State<T>& s,
 // the rebuild after the keys and histogram are in place (they are consumed by the scatter)
 template <typename T, int D> void enqueue_rebuild(const sph_batch* b, const State<T>& s, cudaStream_t stream) {
     launch_scan_onepass<T>(s, stream);
-    launch_scatter<T>(s, stream);
-    launch_gather<T, D>(s, one_of(b), stream);
+    launch_scatter<T>(s, stream, true);
+    launch_gather<T, D>(s, one_of(b), stream, true);
 }
 
 template <typename T> Out<T> out_stored(const State<T>& s) {
@@ -707,11 +707,13 @@ template <typename T, int D> void enqueue_step(sph_batch* b, bool timed) {
     if (timed) cudaEventRecordWithFlags(b->ev[0], stream, cudaEventRecordExternal);
     enqueue_rebuild<T, D>(b, s, stream);
     if (timed) cudaEventRecordWithFlags(b->ev[1], stream, cudaEventRecordExternal);
-    launch_interact<T, D>(s, one_of(b), nullptr, nullptr, stream);
+    // kernel-to-kernel edges start the successor early (programmatic dependent launch); an
+    // event between two kernels makes the edge an ordinary one
+    launch_interact<T, D>(s, one_of(b), nullptr, nullptr, stream, !timed);
     if (timed) cudaEventRecordWithFlags(b->ev[2], stream, cudaEventRecordExternal);
-    launch_control<T, D>(s, one_of(b), stream);
+    launch_control<T, D>(s, one_of(b), stream, !timed);
     if (timed) cudaEventRecordWithFlags(b->ev[3], stream, cudaEventRecordExternal);
-    launch_integrate<T, D>(s, one_of(b), s.ctrls, out_stored<T>(s), stream);
+    launch_integrate<T, D>(s, one_of(b), s.ctrls, out_stored<T>(s), stream, !timed);
     if (timed) cudaEventRecordWithFlags(b->ev[4], stream, cudaEventRecordExternal);
 }
 

@@ -35,6 +35,8 @@ __device__ inline void window_reset(Ctrl* c) {
 //     below dt_collapse times the group's previous step; dt <= dt_cap (Eq. 24).
 // DONE freezes the state (dt = 0, the step counter stops).
 template <typename T, int D, bool ONE> __global__ void __launch_bounds__(256) k_control(State<T> s, One one) {
+    dep_launch();
+    dep_wait();
     __shared__ double vs[MAXF], et[MAXF], ea[MAXF];
     __shared__ Ctrl sc;
     __shared__ Params psh;
@@ -254,13 +256,17 @@ template <typename T> __device__ __forceinline__ T domain_phi_t(const Domain& do
 //   v+ = v~ + dt a_v;  x+ = x + dt v+  (FP64);  curves/surfaces: x+ onto the feature in FP64,
 //   v+ <- Pi(x+) v+;  volume: phi(x+) < 0 -> back to phi = 0.01 h along grad phi (FP64),
 //   v+ = 0, escape counted;  h+ = h_t(x+).
-// The neighbour sum uses the walk of the pressure pass (same pairs, same predicate), with LPP
-// lanes per particle; the lead lane does the update.  As in the pressure pass, a block lies in
-// one instance.  Padding slots are copied through unchanged.
+// The neighbour sum runs over the same-group pairs the pressure pass handed over (its LPI
+// list columns per particle, LPI/LPP of them per lane of this pass), or, where a column
+// overflowed, over the walk of the pressure pass (same pairs, same predicate) with LPP lanes;
+// the lead lane does the update.  As in the pressure pass, a block lies in one instance.
+// Padding slots are copied through unchanged.
 template <typename T, int D, bool ONE>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 4)
     k_integrate(State<T> s, One one, const Ctrl* use, Out<T> o) {
-    constexpr int LPP = Lpp<D>::v;
+    dep_launch();
+    dep_wait();
+    constexpr int LPP = ILpp<D>::v, LPI = Lpp<D>::v, NCOL = LPI / LPP;
     __shared__ int2 sbuf[BUF_CAP * BLOCK];
     __shared__ Grid gsh;
     __shared__ Params psh;
@@ -371,31 +377,42 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 4
         };
         // the pairs the pressure pass found (list), or the cell walk where the list overflowed
         constexpr int VCAP = Vcap<D>::v;
-        const int NL = s.n * LPP, lg = blockIdx.x * blockDim.x + threadIdx.x;
-        const int vc = moving ? s.vcnt[lg] : 0;
-        const bool ov = sub_sum<LPP>(vc > VCAP ? 1 : 0) != 0;   // overflow in any lane of the particle
+        // this lane's columns of the hand-over list: pressure-pass lanes sub + t LPP, t < NCOL
+        const int NL = s.n * LPI, lg0 = k * LPI + (int)(threadIdx.x % LPP);
+        int vc[NCOL];
+        int over = 0;
+#pragma unroll
+        for (int t = 0; t < NCOL; ++t) {
+            vc[t] = moving ? s.vcnt[lg0 + t * LPP] : 0;
+            over |= vc[t] > VCAP ? 1 : 0;
+        }
+        const bool ov = sub_sum<LPP>(over) != 0;   // overflow in any column of the particle
         if (moving && !ov)
-            // SPH_VISC_BATCH entries at a time: their loads are all issued before the first use
-            for (int e0 = 0; e0 < vc; e0 += SPH_VISC_BATCH) {
-                constexpr int U = SPH_VISC_BATCH;
-                int jj[U];
-                T rr[U];
-                Vec4<T> aj[U], vhj[U];
 #pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (e0 + u < vc) {
-                        jj[u] = s.vj[(size_t)(e0 + u) * NL + lg];
-                        rr[u] = s.vr[(size_t)(e0 + u) * NL + lg];
-                    }
+            for (int t = 0; t < NCOL; ++t) {
+                const int lg = lg0 + t * LPP;
+                // SPH_VISC_BATCH entries at a time: their loads are all issued before the first use
+                for (int e0 = 0; e0 < vc[t]; e0 += SPH_VISC_BATCH) {
+                    constexpr int U = SPH_VISC_BATCH;
+                    int jj[U];
+                    T rr[U];
+                    Vec4<T> aj[U], vhj[U];
 #pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (e0 + u < vc) {
-                        aj[u] = s.A[jj[u]];
-                        vhj[u] = s.VH[jj[u]];
-                    }
+                    for (int u = 0; u < U; ++u)
+                        if (e0 + u < vc[t]) {
+                            jj[u] = s.vj[(size_t)(e0 + u) * NL + lg];
+                            rr[u] = s.vr[(size_t)(e0 + u) * NL + lg];
+                        }
 #pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (e0 + u < vc) pair(aj[u], vhj[u], rr[u]);
+                    for (int u = 0; u < U; ++u)
+                        if (e0 + u < vc[t]) {
+                            aj[u] = s.A[jj[u]];
+                            vhj[u] = s.VH[jj[u]];
+                        }
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (e0 + u < vc[t]) pair(aj[u], vhj[u], rr[u]);
+                }
             }
         int li = 0, ci[3] = {0, 0, 0};
         if (moving && ov) own_cell<T, D>(g, s, k, hi, li, ci);
@@ -490,20 +507,21 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 4
     }
 }
 
-template <typename T, int D> void launch_control(const State<T>& s, const One* one, cudaStream_t st) {
-    if (one) k_control<T, D, true><<<s.NI, 256, 0, st>>>(s, *one);
-    else k_control<T, D, false><<<s.NI, 256, 0, st>>>(s, One());
+template <typename T, int D> void launch_control(const State<T>& s, const One* one, cudaStream_t st, bool pdl) {
+    if (one) launch_k(k_control<T, D, true>, s.NI, 256, st, pdl, s, *one);
+    else launch_k(k_control<T, D, false>, s.NI, 256, st, pdl, s, One());
 }
 template <typename T, int D>
-void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const Out<T>& o, cudaStream_t st) {
-    const int nb = div_up((long long)s.n * Lpp<D>::v, BLOCK);
-    if (one) k_integrate<T, D, true><<<nb, BLOCK, 0, st>>>(s, *one, use, o);
-    else k_integrate<T, D, false><<<nb, BLOCK, 0, st>>>(s, One(), use, o);
+void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const Out<T>& o, cudaStream_t st,
+                      bool pdl) {
+    const int nb = div_up((long long)s.n * ILpp<D>::v, BLOCK);
+    if (one) launch_k(k_integrate<T, D, true>, nb, BLOCK, st, pdl, s, *one, use, o);
+    else launch_k(k_integrate<T, D, false>, nb, BLOCK, st, pdl, s, One(), use, o);
 }
 
 #define SPH_INST(T, D)                                                      \
-    template void launch_control<T, D>(const State<T>&, const One*, cudaStream_t);      \
-    template void launch_integrate<T, D>(const State<T>&, const One*, const Ctrl*, const Out<T>&, cudaStream_t);
+    template void launch_control<T, D>(const State<T>&, const One*, cudaStream_t, bool);      \
+    template void launch_integrate<T, D>(const State<T>&, const One*, const Ctrl*, const Out<T>&, cudaStream_t, bool);
 SPH_INST(float, 2)
 SPH_INST(float, 3)
 SPH_INST(double, 2)

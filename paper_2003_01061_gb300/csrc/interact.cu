@@ -22,6 +22,8 @@ namespace sph {
 template <typename T, int D, bool ONE>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTERACT_MINB : 4)
     k_interact(State<T> s, One one, T* dbg_sigma, T* dbg_gamma) {
+    dep_launch();
+    dep_wait();
     constexpr int LPP = Lpp<D>::v;
     __shared__ unsigned long long sh_dta[MAXF], sh_dtv[MAXF];
     __shared__ double sh_part[BLOCK / 32][MAXF];
@@ -273,9 +275,9 @@ __global__ void __launch_bounds__(BLOCK) k_pair_counts(State<T> s, unsigned long
 }
 
 template <typename T, int D>
-void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, cudaStream_t st) {
-    if (one) k_interact<T, D, true><<<s.nblk, BLOCK, 0, st>>>(s, *one, dbg_sigma, dbg_gamma);
-    else k_interact<T, D, false><<<s.nblk, BLOCK, 0, st>>>(s, One(), dbg_sigma, dbg_gamma);
+void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, cudaStream_t st, bool pdl) {
+    if (one) launch_k(k_interact<T, D, true>, s.nblk, BLOCK, st, pdl, s, *one, dbg_sigma, dbg_gamma);
+    else launch_k(k_interact<T, D, false>, s.nblk, BLOCK, st, pdl, s, One(), dbg_sigma, dbg_gamma);
 }
 template <typename T, int D>
 void launch_neighbors(const State<T>& s, int mode, int* counts, const long long* offsets, int* lists, cudaStream_t st) {
@@ -286,7 +288,7 @@ template <typename T, int D> void launch_pair_counts(const State<T>& s, unsigned
 }
 
 #define SPH_INST(T, D)                                                                                        \
-    template void launch_interact<T, D>(const State<T>&, const One*, T*, T*, cudaStream_t);                   \
+    template void launch_interact<T, D>(const State<T>&, const One*, T*, T*, cudaStream_t, bool);             \
     template void launch_neighbors<T, D>(const State<T>&, int, int*, const long long*, int*, cudaStream_t);   \
     template void launch_pair_counts<T, D>(const State<T>&, unsigned long long*, cudaStream_t);
 SPH_INST(float, 2)

@@ -212,6 +212,8 @@ template <typename T> __global__ void __launch_bounds__(SCAN_THREADS) k_scan_one
 
 // ---- scatter into cells (order inside a cell fixed afterwards) ----
 template <typename T> __global__ void __launch_bounds__(BLOCK) k_scatter(State<T> s) {
+    dep_launch();
+    dep_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
     const int key = s.K[i];
@@ -246,6 +248,8 @@ __global__ void __launch_bounds__(BLOCK) k_cellsort(int ncell, int n, const int*
 // counting sort stable.  Usually a cell's particles were consecutive in the stored order (it
 // is the previous step's sorted order), and the rank is found from the cell's minimum.
 template <typename T, int D, bool ONE> __global__ void __launch_bounds__(BLOCK) k_gather(State<T> s, One one) {
+    dep_launch();
+    dep_wait();
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= s.n) return;
     int i = s.perm[k];
@@ -384,15 +388,15 @@ void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t
 template <typename T> void launch_scan_onepass(const State<T>& s, cudaStream_t st) {
     k_scan_onepass<T><<<div_up(s.ncell, SCAN_TILE), SCAN_THREADS, 0, st>>>(s);
 }
-template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st) {
-    k_scatter<T><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s);
+template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st, bool pdl) {
+    launch_k(k_scatter<T>, div_up(s.n, BLOCK), BLOCK, st, pdl, s);
 }
 void launch_cellsort(int ncell, int n, const int* cell_start, int* perm, int* count, cudaStream_t st) {
     k_cellsort<<<div_up(ncell, BLOCK), BLOCK, 0, st>>>(ncell, n, cell_start, perm, count);
 }
-template <typename T, int D> void launch_gather(const State<T>& s, const One* one, cudaStream_t st) {
-    if (one) k_gather<T, D, true><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s, *one);
-    else k_gather<T, D, false><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s, One());
+template <typename T, int D> void launch_gather(const State<T>& s, const One* one, cudaStream_t st, bool pdl) {
+    if (one) launch_k(k_gather<T, D, true>, div_up(s.n, BLOCK), BLOCK, st, pdl, s, *one);
+    else launch_k(k_gather<T, D, false>, div_up(s.n, BLOCK), BLOCK, st, pdl, s, One());
 }
 template <typename T, int D> void launch_init_h(const State<T>& s, int inst, cudaStream_t st) {
     k_init_h<T, D><<<div_up(s.n, BLOCK), BLOCK, 0, st>>>(s, inst);   // threads past the instance exit
@@ -400,7 +404,7 @@ template <typename T, int D> void launch_init_h(const State<T>& s, int inst, cud
 
 #define SPH_INST(T, D)                                                    \
     template void launch_hash<T, D>(const State<T>&, const One*, cudaStream_t);        \
-    template void launch_gather<T, D>(const State<T>&, const One*, cudaStream_t);      \
+    template void launch_gather<T, D>(const State<T>&, const One*, cudaStream_t, bool);      \
     template void launch_init_h<T, D>(const State<T>&, int, cudaStream_t);  \
     template void launch_repack<T, D>(const State<T>&, const int*, const int*, cudaStream_t);
 SPH_INST(float, 2)
@@ -409,7 +413,7 @@ SPH_INST(double, 2)
 SPH_INST(double, 3)
 template void launch_scan_onepass<float>(const State<float>&, cudaStream_t);
 template void launch_scan_onepass<double>(const State<double>&, cudaStream_t);
-template void launch_scatter<float>(const State<float>&, cudaStream_t);
-template void launch_scatter<double>(const State<double>&, cudaStream_t);
+template void launch_scatter<float>(const State<float>&, cudaStream_t, bool);
+template void launch_scatter<double>(const State<double>&, cudaStream_t, bool);
 
 }  // namespace sph

@@ -110,16 +110,33 @@ template <int D> struct Lpp {
 template <int D> struct Vcap {
     static constexpr int v = D == 2 ? 24 / Lpp<2>::v : 64 / Lpp<3>::v;
 };
-static_assert(CHUNK % (BLOCK / Lpp<2>::v) == 0 && CHUNK % (BLOCK / Lpp<3>::v) == 0,
+// lanes per particle in the viscous pass; each lane reads Lpp/ILpp of the pressure pass's
+// hand-over columns, and the list-overflow fallback walks with ILpp lanes (measured: one lane
+// in 2D, 2 % faster than 2; in 3D 4 lanes, 1 and 2 were 13 % and 2 % slower)
+#ifndef SPH_ILPP_2D
+#define SPH_ILPP_2D 1
+#endif
+#ifndef SPH_ILPP_3D
+#define SPH_ILPP_3D SPH_LPP_3D
+#endif
+template <int D> struct ILpp {
+    static constexpr int v = D == 2 ? SPH_ILPP_2D : SPH_ILPP_3D;
+};
+static_assert(CHUNK % (BLOCK / Lpp<2>::v) == 0 && CHUNK % (BLOCK / Lpp<3>::v) == 0 &&
+                  CHUNK % (BLOCK / ILpp<2>::v) == 0 && CHUNK % (BLOCK / ILpp<3>::v) == 0,
               "a pair-pass block must lie in one chunk");
+static_assert(Lpp<2>::v % ILpp<2>::v == 0 && Lpp<3>::v % ILpp<3>::v == 0,
+              "the viscous lanes split the pressure pass's columns evenly");
 
 // minimum resident blocks per SM asked of the compiler for the two pair passes (FP32 build;
 // the FP64 build asks for 4): it bounds the registers per thread, trading spills for occupancy
+// (measured on the pressure pass: 10 and 12 spill and are 17 % and 40 % slower than 8; on the
+// viscous pass 7 is 3 % faster than 8 in 2D and the same in 3D)
 #ifndef SPH_INTERACT_MINB
 #define SPH_INTERACT_MINB 8
 #endif
 #ifndef SPH_INTEGRATE_MINB
-#define SPH_INTEGRATE_MINB 8
+#define SPH_INTEGRATE_MINB 7
 #endif
 // cells per support of the cell grid when the parameters leave the choice to the library
 #ifndef SPH_DEFAULT_CPS_2D
@@ -169,6 +186,34 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// Programmatic dependent launch between the kernels of a step.  A kernel launched with
+// pdl = true may be scheduled while its predecessor in the stream is still running (once every
+// block of the predecessor has started); its blocks then wait in dep_wait() until the
+// predecessor has completed and its writes are visible.  Every step kernel calls dep_wait()
+// before its first access to device memory other than its kernel parameters, so the order of
+// the stream is kept; without the attribute dep_wait() returns at once.  dep_launch() lets
+// the successor be scheduled as soon as every block of this kernel is running.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+#ifndef SPH_PDL
+#define SPH_PDL 1
+#endif
+template <typename... K, typename... A>
+inline void launch_k(void (*kern)(K...), int grid, int block, cudaStream_t st, bool pdl, A&&... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = (pdl && SPH_PDL) ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<A&&>(args)...);
+}
+
 // rebuild.cu
 // `one`: the descriptors of a batch of one (nullptr: read the per-instance tables)
 template <typename T, int D> void launch_hash(const State<T>& s, const One* one, cudaStream_t st);
@@ -176,23 +221,25 @@ void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t
                  int nocc = 0, bool relative = false);
 // relative one-pass scan of the step (decoupled look-back over tiles taken in ticket order)
 template <typename T> void launch_scan_onepass(const State<T>& s, cudaStream_t st);
-template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st);
+template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st, bool pdl = false);
 void launch_cellsort(int ncell, int n, const int* cell_start, int* perm, int* count, cudaStream_t st);
-template <typename T, int D> void launch_gather(const State<T>& s, const One* one, cudaStream_t st);
+template <typename T, int D> void launch_gather(const State<T>& s, const One* one, cudaStream_t st, bool pdl = false);
 template <typename T, int D> void launch_init_h(const State<T>& s, int inst, cudaStream_t st);
 template <typename T, int D> void launch_repack(const State<T>& s, const int* old_off, const int* move_n, cudaStream_t st);
 
 // interact.cu
 template <typename T, int D>
-void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, cudaStream_t st);
+void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, cudaStream_t st,
+                     bool pdl = false);
 template <typename T, int D>
 void launch_neighbors(const State<T>& s, int mode, int* counts, const long long* offsets, int* lists, cudaStream_t st);
 template <typename T, int D> void launch_pair_counts(const State<T>& s, unsigned long long* out2, cudaStream_t st);
 
 // integrate.cu
-template <typename T, int D> void launch_control(const State<T>& s, const One* one, cudaStream_t st);
+template <typename T, int D> void launch_control(const State<T>& s, const One* one, cudaStream_t st, bool pdl = false);
 template <typename T, int D>
-void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const Out<T>& o, cudaStream_t st);
+void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const Out<T>& o, cudaStream_t st,
+                      bool pdl = false);
 
 // sets the message returned by sph_last_error() on the calling thread (capi.cu)
 void set_last_error(const char* msg);

@@ -43,8 +43,22 @@ def workload(name):
             w = WL.disk_holes(n_target=6000, seed=2)
         elif name == "cube":
             w = WL.cube_sphere(n_target=12000, seed=3)
+        elif name == "square_dense":
+            w = denser(WL.square2d(h=0.05, seed=7, jitter=0.3), WL.square2d(h=0.025, seed=8, jitter=0.3))
+        elif name == "cube_dense":
+            w = denser(WL.cube_sphere(n_target=4000, seed=3, mc_samples=200_000),
+                       WL.cube_sphere(n_target=15000, seed=3, mc_samples=200_000))
         _cache[name] = w
     return _cache[name]
+
+
+def denser(w, fine):
+    """w's problem (domain, features, sizing, grid) with the particles of a finer instance of it:
+    several times the neighbours per particle, so that most particles have more same-group
+    pairs than the pressure pass hands over to the viscous pass, and the viscous pass takes
+    its cell walk instead."""
+    assert fine["domain"]["features"] == w["domain"]["features"]
+    return dict(w, x=fine["x"], group=fine["group"])
 
 
 def oracle_h(w):
@@ -66,6 +80,9 @@ def oracle_grid(w, m):
 
 
 CASES = [("square", 32), ("square", 64), ("disk", 32), ("disk", 64), ("cube", 32), ("cube", 64)]
+DENSE_CASES = [("square_dense", 32), ("square_dense", 64), ("cube_dense", 32)]
+# hand-over list capacity per particle (same-group pairs) of the pressure pass
+LIST_CAP = {2: 24, 3: 64}
 
 
 CPS_CASES = [("disk", 1), ("disk", 2), ("disk", 4), ("cube", 1), ("cube", 2), ("cube", 4)]
@@ -119,7 +136,7 @@ def _oracle_pressure(w, h, prec, sub=None):
     return o, o.interact(sub=sub, use_grid=True)
 
 
-@pytest.mark.parametrize("name,prec", CASES)
+@pytest.mark.parametrize("name,prec", CASES + DENSE_CASES)
 def test_pressure_pass_parity(name, prec):
     w = workload(name)
     h = oracle_h(w)
@@ -150,7 +167,7 @@ def test_pressure_pass_parity(name, prec):
     m.close()
 
 
-@pytest.mark.parametrize("name,prec", CASES)
+@pytest.mark.parametrize("name,prec", CASES + DENSE_CASES)
 @pytest.mark.parametrize("reset", [1, 0])
 def test_update_parity(name, prec, reset):
     w = workload(name)
@@ -187,6 +204,22 @@ def test_update_parity(name, prec, reset):
     assert np.all(ev[moving] <= 50 * tol * vs[moving]), (ev / vs).max()
     assert np.allclose(got["h"], ref["h"], rtol=4 * tol if prec == 32 else 1e-14, atol=0)
     m.close()
+
+
+@pytest.mark.parametrize("name", ["square_dense", "cube_dense"])
+def test_dense_cases_overflow_the_hand_over_list(name):
+    # the dense cases reach the viscous pass's cell walk: most moving particles have more
+    # same-group neighbours within the support than the hand-over list holds (counted by
+    # brute force on a sample)
+    w = workload(name)
+    h = oracle_h(w)
+    D = w["domain"]["D"]
+    o = O.Oracle(w, h=h)
+    rng = np.random.default_rng(4)
+    vol = np.flatnonzero(w["group"] == 0)
+    idx = rng.choice(vol, 100, replace=False)
+    same = [np.sum(w["group"][O.neighbors_brute(w["x"], h, int(i), D)] == 0) - 1 for i in idx]
+    assert o.gdim[0] == D and np.median(same) > LIST_CAP[D], np.median(same)
 
 
 def test_empty_and_lone_particle_states():
