@@ -503,7 +503,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 4
         int cell[3] = {c[0] >> l, c[1] >> l, D == 3 ? c[2] >> l : 0};
         const int key = key_of(g, l, cell);
         o.K[k] = key;
-        atomicAdd(o.count + key, 1);
+        const unsigned peers = __match_any_sync(__activemask(), key);   // one atomic per cell in the warp
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(o.count + key, __popc(peers));
     }
 }
 

@@ -217,7 +217,13 @@ template <typename T> __global__ void __launch_bounds__(BLOCK) k_scatter(State<T
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
     const int key = s.K[i];
-    int pos = atomicAdd(s.count + key, 1);
+    // one atomic per cell present in the warp (sorted neighbours mostly share cells); each
+    // lane takes the cursor plus its rank among the lanes of its cell
+    const unsigned peers = __match_any_sync(__activemask(), key);
+    const int lane = threadIdx.x & 31, lead = __ffs(peers) - 1;
+    int pos = 0;
+    if (lane == lead) pos = atomicAdd(s.count + key, __popc(peers));
+    pos = __shfl_sync(peers, pos, lead) + __popc(peers & ((1u << lane) - 1u));
     if ((unsigned)pos < (unsigned)s.n) {
         s.perm[pos] = i;
         s.Ks[pos] = key;   // every slot of a cell has the cell's key, whichever particle lands there
@@ -312,7 +318,10 @@ template <typename T, int D, bool ONE> __global__ void __launch_bounds__(BLOCK) 
         const int sh = g.L - 1 + g.sm;
         int ct[3] = {0, 0, 0};
         for (int a = 0; a < D; ++a) ct[a] = min((cell[a] << l) >> sh, g.od[a] - 1);
-        atomicOr(s.occ + g.occ_base + (ct[2] * g.od[1] + ct[1]) * g.od[0] + ct[0], 1u << l);
+        const int w = g.occ_base + (ct[2] * g.od[1] + ct[1]) * g.od[0] + ct[0];
+        // sorted neighbours share the word and the level: one atomic per distinct pair in the warp
+        const unsigned peers = __match_any_sync(__activemask(), ((unsigned long long)w << 4) | (unsigned)l);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicOr(s.occ + w, 1u << l);
     }
 }
 
