@@ -264,12 +264,15 @@ sph_status make_instance(const sph_domain_desc* dd, const sph_sizing_desc* sz, c
     I.ncell = (int)gi.n_cells;
     g.ncell = I.ncell;
     g.sm = cps == 1 ? 0 : (cps == 2 ? 1 : 2);
-    // occupancy cells: cps top-level cells per axis, so that a search window (at most one
-    // support of the largest particle) spans at most one of them on each side
+    // occupancy cells: cps top-level cells per axis (a search window spans at most one of them
+    // on each side), in 3D divided SPH_OCC_FINER times in two (there a level's search is
+    // skipped when the occupancy cells covering its own cell box hold none of its particles)
     const int t = gi.levels - 1;
+    const int fin = D == 3 ? std::min(SPH_OCC_FINER, t + g.sm) : 0;
+    g.osh = t + g.sm - fin;
     int64_t nocc = 1;
     for (int a = 0; a < 3; ++a) {
-        g.od[a] = a < D ? (int)((gi.dims[t][a] + cps - 1) / cps) : 1;
+        g.od[a] = a < D ? (int)((((int64_t)gi.dims[t][a] << fin) + cps - 1) / cps) : 1;
         nocc *= g.od[a];
     }
     I.nocc = (int)nocc;

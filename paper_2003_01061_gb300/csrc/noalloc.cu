@@ -127,6 +127,7 @@ extern "C" sph_status sph_cell_sort_noalloc(const sph_grid_info* grid, int64_t n
     g.base[MAXL] = (int)grid->n_cells;
     g.ncell = (int)grid->n_cells;
     g.sm = cps == 1 ? 0 : (cps == 2 ? 1 : 2);
+    g.osh = grid->levels - 1 + g.sm;   // no occupancy grid here
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -315,7 +315,7 @@ template <typename T, int D, bool ONE> __global__ void __launch_bounds__(BLOCK) 
     level_repr<T, D>(g, l, c, o, cell, off);
     Rec<T, D>::store(s.P, s.Ms, k, off, h, (meta & 255u) | ((unsigned)cell[0] << 8));
     if (s.occ) {   // level occupancy of the occupancy cell holding the particle
-        const int sh = g.L - 1 + g.sm;
+        const int sh = g.osh;
         int ct[3] = {0, 0, 0};
         for (int a = 0; a < D; ++a) ct[a] = min((cell[a] << l) >> sh, g.od[a] - 1);
         const int w = g.occ_base + (ct[2] * g.od[1] + ct[1]) * g.od[0] + ct[0];

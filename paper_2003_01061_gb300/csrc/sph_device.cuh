@@ -78,7 +78,8 @@ struct Grid {
     int base[MAXL + 1];  // first key of each level; base[MAXL]: the instance's dummy key
     int ncell;           // cells of the instance (its keys are base[0] .. base[0]+ncell-1)
     int sm;              // log2 of the cells per support m: level l holds kappa h <= m c_l
-    int od[3];           // occupancy grid: cells of m top-level cells per axis
+    int osh;             // occupancy cells of 2^osh finest cells per axis
+    int od[3];           // occupancy grid dimensions
     int occ_base;        // first entry of the instance's occupancy cells in the occupancy array
 };
 
@@ -424,8 +425,8 @@ __device__ __forceinline__ double fast_rsqrt(double v) { return 1.0 / sqrt(v); }
 // lane's slice of `buf` (CAP entries of (j, level | row), stride BLOCK, in shared memory); the
 // kept candidates are handed to fn(j, dx, r2, h_j, meta_j, off_j, l, cx_j, cy, cz) when the
 // buffer is full and at the end, so the per-pair work runs with the lanes mostly converged.
-// Levels with no particle in the 3^D top-level cells around i (bit l of `occ`, built by the
-// gather) are skipped.  Every lane count computes dx and r2 identically, so a candidate is
+// A level is skipped when no particle of it lies in the occupancy cells around the particle
+// (2D) or covering the level's cell box (3D) (bit l of `occ`, built by the gather).  Every lane count computes dx and r2 identically, so a candidate is
 // accepted or rejected the same way whatever LPP.  No warp-synchronous operation is used
 // inside.  (Measured and not kept: trimming rows to the chord of the search disc, sharing the
 // level-mask loads among the lanes, loading the next row's range ahead of the current row's
@@ -449,15 +450,14 @@ __device__ __forceinline__ int candidate_dx(const Vec4<T>* __restrict__ P, const
     return cxj;
 }
 
-// bit l set: some particle of level l lies in the 3^D occupancy cells (m top-level cells per
-// axis each) around the particle
+// bit l set: some particle of level l lies in the 3^D occupancy cells around the particle
+// (an occupancy cell spans at least one support of the largest particle: 2D grids)
 template <int D>
 __device__ __forceinline__ unsigned level_mask(const Grid& g, const unsigned* __restrict__ occ, const int Pi[3],
                                                const int fl[3]) {
     if (!occ) return (1u << g.L) - 1u;
-    const int sh = g.L - 1 + g.sm;
     int ct[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) ct[a] = (Pi[a] + fl[a]) >> sh;
+    for (int a = 0; a < D; ++a) ct[a] = (Pi[a] + fl[a]) >> g.osh;
     unsigned m = 0;
     const int z0 = D == 3 ? max(ct[2] - 1, 0) : 0, z1 = D == 3 ? min(ct[2] + 1, g.od[2] - 1) : 0;
     const int y0 = max(ct[1] - 1, 0), y1 = min(ct[1] + 1, g.od[1] - 1);
@@ -466,6 +466,31 @@ __device__ __forceinline__ unsigned level_mask(const Grid& g, const unsigned* __
         for (int y = y0; y <= y1; ++y)
             for (int x = x0; x <= x1; ++x) m |= __ldg(occ + g.occ_base + (z * g.od[1] + y) * g.od[0] + x);
     return m;
+}
+
+// whether some particle of level l lies in the occupancy cells (bit l of a word, set by the
+// gather) that cover the level-l cell box lo..hb (3D grids)
+template <int D>
+__device__ __forceinline__ bool level_present(const Grid& g, const unsigned* __restrict__ occ, int l, const int lo[3],
+                                              const int hb[3]) {
+    if (!occ) return true;
+    const int sh = g.osh;
+    int o0[3] = {0, 0, 0}, o1[3] = {0, 0, 0};
+    for (int a = 0; a < D; ++a) {   // a particle past the last occupancy cell is counted in it
+        o0[a] = min((lo[a] << l) >> sh, g.od[a] - 1);
+        o1[a] = min((hb[a] << l) >> sh, g.od[a] - 1);
+    }
+    // a box of many occupancy cells is searched without the test (it would cost more loads
+    // than it can save)
+    if ((o1[0] - o0[0] + 1) * (o1[1] - o0[1] + 1) * (o1[2] - o0[2] + 1) > 64) return true;
+    const unsigned bit = 1u << l;
+    for (int z = o0[2]; z <= o1[2]; ++z)
+        for (int y = o0[1]; y <= o1[1]; ++y) {
+            unsigned m = 0;
+            for (int x = o0[0]; x <= o1[0]; ++x) m |= __ldg(occ + g.occ_base + (z * g.od[1] + y) * g.od[0] + x);
+            if (m & bit) return true;
+        }
+    return false;
 }
 
 template <typename T, int D, int LPP, int CAP, typename A, typename F>
@@ -484,7 +509,10 @@ __device__ __forceinline__ void walk_sub(const Grid& g, const int* __restrict__ 
         fi[a] = offi[a] * inv_c0;
         fl[a] = (int)t_floor(fi[a]);
     }
-    const unsigned lmask = level_mask<D>(g, occ, Pi, fl);
+    // 2D: the levels present around the particle, tested once; 3D: each level's own box
+    // (measured: the box test is 9 % faster in 3D and 3 % slower in 2D, where a particle
+    // visits ~7 stencil rows against ~85 in 3D)
+    const unsigned lmask = D == 2 ? level_mask<D>(g, occ, Pi, fl) : ~0u;
     const T rhi = kappa * hi;
     int cnt = 0;
     auto flush = [&]() {
@@ -514,7 +542,7 @@ __device__ __forceinline__ void walk_sub(const Grid& g, const int* __restrict__ 
             hb[a] = a1 > g.dims[l][a] - 1 ? g.dims[l][a] - 1 : a1;
             empty = empty || lo[a] > hb[a];
         }
-        if (empty) continue;
+        if (empty || (D == 3 && !level_present<D>(g, occ, l, lo, hb))) continue;
         // every radius the callers test at this level is below R: candidates beyond it are
         // rejected on the distance alone
         const T R2 = R * R;

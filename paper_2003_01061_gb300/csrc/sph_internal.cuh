@@ -106,9 +106,16 @@ constexpr int BUF_CAP = SPH_BUF_CAP;   // kept candidates per lane between flush
 template <int D> struct Lpp {
     static constexpr int v = D == 2 ? SPH_LPP_2D : SPH_LPP_3D;
 };
-// same-group pair slots per lane in the pressure-to-viscous hand-over list
+// same-group pair slots per particle (SPH_VCAP_2D/3D) and per lane (Vcap) in the
+// pressure-to-viscous hand-over list
+#ifndef SPH_VCAP_2D
+#define SPH_VCAP_2D 24
+#endif
+#ifndef SPH_VCAP_3D
+#define SPH_VCAP_3D 64
+#endif
 template <int D> struct Vcap {
-    static constexpr int v = D == 2 ? 24 / Lpp<2>::v : 64 / Lpp<3>::v;
+    static constexpr int v = D == 2 ? SPH_VCAP_2D / Lpp<2>::v : SPH_VCAP_3D / Lpp<3>::v;
 };
 // lanes per particle in the viscous pass; each lane reads Lpp/ILpp of the pressure pass's
 // hand-over columns, and the list-overflow fallback walks with ILpp lanes (measured: one lane
@@ -127,6 +134,12 @@ static_assert(CHUNK % (BLOCK / Lpp<2>::v) == 0 && CHUNK % (BLOCK / Lpp<3>::v) ==
               "a pair-pass block must lie in one chunk");
 static_assert(Lpp<2>::v % ILpp<2>::v == 0 && Lpp<3>::v % ILpp<3>::v == 0,
               "the viscous lanes split the pressure pass's columns evenly");
+
+// 3D occupancy cells finer than the cells-per-support top-level cells by 2^SPH_OCC_FINER per axis
+// (measured on the 3D cube: 1 and 2 make the pressure pass 5 % and 21 % slower than 0)
+#ifndef SPH_OCC_FINER
+#define SPH_OCC_FINER 0
+#endif
 
 // minimum resident blocks per SM asked of the compiler for the two pair passes (FP32 build;
 // the FP64 build asks for 4): it bounds the registers per thread, trading spills for occupancy
