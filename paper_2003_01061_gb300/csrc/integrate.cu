@@ -262,7 +262,7 @@ template <typename T> __device__ __forceinline__ T domain_phi_t(const Domain& do
 // the lead lane does the update.  As in the pressure pass, a block lies in one instance.
 // Padding slots are copied through unchanged.
 template <typename T, int D, bool ONE>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTEGRATE_MINB : 4)
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRATE_MINB_2D : SPH_INTEGRATE_MINB_3D) : 4)
     k_integrate(State<T> s, One one, const Ctrl* use, Out<T> o) {
     dep_launch();
     dep_wait();

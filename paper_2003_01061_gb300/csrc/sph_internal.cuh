@@ -107,24 +107,27 @@ template <int D> struct Lpp {
     static constexpr int v = D == 2 ? SPH_LPP_2D : SPH_LPP_3D;
 };
 // same-group pair slots per particle (SPH_VCAP_2D/3D) and per lane (Vcap) in the
-// pressure-to-viscous hand-over list
+// pressure-to-viscous hand-over list (measured on the viscous pass, whose overflowing
+// particles walk the cells again: in 3D 96 slots are 29 % faster than 64, 128 no faster than
+// 96, 48 81 % slower than 64; in 2D 32 is 7 % faster than 24)
 #ifndef SPH_VCAP_2D
-#define SPH_VCAP_2D 24
+#define SPH_VCAP_2D 32
 #endif
 #ifndef SPH_VCAP_3D
-#define SPH_VCAP_3D 64
+#define SPH_VCAP_3D 96
 #endif
 template <int D> struct Vcap {
     static constexpr int v = D == 2 ? SPH_VCAP_2D / Lpp<2>::v : SPH_VCAP_3D / Lpp<3>::v;
 };
 // lanes per particle in the viscous pass; each lane reads Lpp/ILpp of the pressure pass's
 // hand-over columns, and the list-overflow fallback walks with ILpp lanes (measured: one lane
-// in 2D, 2 % faster than 2; in 3D 4 lanes, 1 and 2 were 13 % and 2 % slower)
+// in 2D, 2 % faster than 2; in 3D, with 96 list slots per particle, 2 lanes are 19 % faster
+// than 4 and 1 lane 2 % faster than 2)
 #ifndef SPH_ILPP_2D
 #define SPH_ILPP_2D 1
 #endif
 #ifndef SPH_ILPP_3D
-#define SPH_ILPP_3D SPH_LPP_3D
+#define SPH_ILPP_3D 1
 #endif
 template <int D> struct ILpp {
     static constexpr int v = D == 2 ? SPH_ILPP_2D : SPH_ILPP_3D;
@@ -144,12 +147,16 @@ static_assert(Lpp<2>::v % ILpp<2>::v == 0 && Lpp<3>::v % ILpp<3>::v == 0,
 // minimum resident blocks per SM asked of the compiler for the two pair passes (FP32 build;
 // the FP64 build asks for 4): it bounds the registers per thread, trading spills for occupancy
 // (measured on the pressure pass: 10 and 12 spill and are 17 % and 40 % slower than 8; on the
-// viscous pass 7 is 3 % faster than 8 in 2D and the same in 3D)
+// viscous pass with one lane per particle 7 is 3 % faster than 8 in 2D, and 6 is 5 % faster
+// than 7 in 3D but 26 % slower in 2D)
 #ifndef SPH_INTERACT_MINB
 #define SPH_INTERACT_MINB 8
 #endif
-#ifndef SPH_INTEGRATE_MINB
-#define SPH_INTEGRATE_MINB 7
+#ifndef SPH_INTEGRATE_MINB_2D
+#define SPH_INTEGRATE_MINB_2D 7
+#endif
+#ifndef SPH_INTEGRATE_MINB_3D
+#define SPH_INTEGRATE_MINB_3D 6
 #endif
 // cells per support of the cell grid when the parameters leave the choice to the library
 #ifndef SPH_DEFAULT_CPS_2D
