@@ -24,6 +24,9 @@ hole (0.004-0.04 scaled to ~120k particles), FP32 pair sums with FP64 projection
           by memory, retired on convergence or at the iteration limit), p50/p99 job latency and
           aggregate particle-steps/s, beside the same jobs served one at a time by the plain
           FP64 single-instance path (FIFO on the measured service times).
+* method_presets: the comparison of Sec. 4.1 on its Square (Eq. 25 sizing): iterations to the
+          Phase-One target and to the end for the improved method and the earlier method's two
+          presets (velocities zeroed every step / every 100 steps, no feature-boundary sum).
 Multi-GPU (torchrun): every rank runs an independent replica (weak scaling, no collective on
 the data path); value = particles of all ranks x K / max rank time.
 """
@@ -48,7 +51,7 @@ FLOP_PER_PAIR = 50.0       # FP32 operations per interacting pair of the pressur
 # DRAM bytes (read + write) of one pressure-pass launch on this workload, from an ncu capture
 # (cold L2; profiles/k_interact_disk_holes_2d_120k.md); None once the kernel changes until it
 # is captured again
-INTERACT_DRAM_BYTES = None
+INTERACT_DRAM_BYTES = 6_384_640 + 1_134_080
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # one step: one-pass scan, scatter, gather, pressure pass, controller, update (+ next keys)
 KERNELS_PER_STEP = 6
@@ -72,6 +75,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cube", action="store_true")
     ap.add_argument("--cube-steps", type=int, default=100)
+    ap.add_argument("--no-presets", action="store_true")
+    ap.add_argument("--preset-iters", type=int, default=40_000)
     return ap.parse_args()
 
 
@@ -288,6 +293,11 @@ def run_ours(args):
     batch_ws, serve_ws, serve_t, cube_w = None, None, None, None
     if rank == 0 and not args.no_cube:
         cube_w = generate([(4, 1_200_000, 3, 0.3)])[0]
+    preset_w = None
+    if rank == 0 and not args.no_presets:
+        from paper_2003_01061_gb300 import workloads as WL
+
+        preset_w = WL.square_radial(seed=6)
     if rank == 0 and not args.no_batch:
         specs, _ = _specs(64, 4, 1_000, 200_000, alternate=True)
         batch_ws = generate(specs)
@@ -382,6 +392,10 @@ def run_ours(args):
     if cube_w is not None:
         cube = cube_run(S, torch, dev, cube_w, args.cube_steps)
 
+    presets = None
+    if preset_w is not None:
+        presets = presets_run(S, preset_w, args.preset_iters)
+
     batched = None
     if batch_ws is not None:
         batched = batched_run(S, torch, dev, batch_ws, args.batch_steps)
@@ -423,6 +437,7 @@ def run_ours(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "cube_3d": cube,
+        "method_presets": presets,
         "batched": batched,
         "serving": serving,
     }
@@ -465,16 +480,13 @@ def e2e_run(S, w, stream, steps):
 
 
 def cube_run(S, torch, dev, w, steps):
-    """The 3D cube minus a sphere at ~1.2M particles, one instance, device-timed steps."""
+    """The 3D cube minus a sphere at ~1.2M particles, one instance, device-timed steps (graph
+    without stage events), then up to 20 more steps with stage events for the split."""
     stream = torch.cuda.Stream(device=dev)
     m = S.Mesh(w, precision=32, stream=stream.cuda_stream)
     m.set_state()
     m.step(3)
     m.sync()
-    S.sph_mesh_set_timing(m.h, 1)
-    m.step(1)
-    m.sync()
-    S.sph_mesh_set_timing(m.h, 1)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -482,18 +494,54 @@ def cube_run(S, torch, dev, w, steps):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    S.sph_mesh_set_timing(m.h, 1)
+    m.step(1)
+    m.sync()
+    S.sph_mesh_set_timing(m.h, 1)
+    staged = min(steps, 20)
+    m.step(staged)
+    m.sync()
     t = S.sph_mesh_kernel_times(m.h)
     g = S.sph_mesh_grid(m.h)
     n = len(w["x"])
     out = {"value": n * steps / (ms / 1e3), "unit": METRIC, "steps": steps, "ms_per_step": ms / steps,
            "particles": n, "cells_per_support": g.cells_per_support,
-           "stages_ms": {k: v[1] / max(steps, 1) for k, v in t.items()},
+           "stages_ms": {k: v[1] / max(staged, 1) for k, v in t.items()}, "stage_steps": staged,
            "config": {"workload": "cube_sphere_3d_1.2M: unit cube minus a centred sphere r=0.3, "
                                   "h = min(0.008 + 0.04|d|, 0.05) scaled to 1.2M particles (seed 3)",
                       "l2": "working set larger than L2 (no flush)"}}
     S.sph_mesh_set_timing(m.h, 0)
     m.sync()
     m.close()
+    return out
+
+
+def presets_run(S, w, max_iters):
+    """The comparison of Sec. 4.1 (Square, Eq. 25): the same initial particles relaxed by the
+    improved method and by the two presets of the earlier method, each until the end of
+    Phase Two or max_iters steps.  Iterations to the Phase-One target (the start of the
+    transition) and to the end, host wall time of the whole run."""
+    from paper_2003_01061_gb300 import workloads as WL
+
+    out = {}
+    # the improved method also with Phase-One damping eps1 = 0.1 and 0.2 (Sec. 3.4.3 suggests
+    # [0, 0.2] for ill-posed initial samplings; the earlier method has no damping)
+    runs = [("improved", "improved", 0.0), ("improved_eps0.1", "improved", 0.1), ("improved_eps0.2", "improved", 0.2),
+            ("fu2019_v2", "fu2019_v2", 0.0), ("fu2019", "fu2019", 0.0)]
+    for label, name, eps in runs:
+        m = S.Mesh(w, precision=32, params=dict(WL.method_preset(w["params"], name), eps1=eps))
+        m.set_state()
+        m.sync()
+        t0 = time.perf_counter()
+        ok, iters = S.sph_mesh_run_until_converged(m.h, max_iters)
+        wall = time.perf_counter() - t0
+        r = m.report()
+        phase_one = int(r.ramp_start) if r.phase in (S.RAMP, S.PHASE2, S.DONE) else None
+        out[label] = {"phase_one_iters": phase_one, "iters": int(iters), "done": bool(ok), "wall_s": wall,
+                      "escapes": int(r.escapes), "E_sys": float(r.E_sys)}
+        m.close()
+    out["config"] = {"workload": f"square_radial_2d: [0,100]^2, Eq. 25 sizing (h 0.244-4.88), {len(w['x'])} "
+                                 f"particles (seed 6), FP32, paper controller, max {max_iters} iterations"}
     return out
 
 
@@ -515,10 +563,6 @@ def batched_run(S, torch, dev, ws, steps):
         b.step(3)
     for b, _, _ in batches:
         b.sync()
-        S.sph_batch_set_timing(b.h, 1)
-        b.step(1)
-        b.sync()
-        S.sph_batch_set_timing(b.h, 1)
     torch.cuda.synchronize()
     start = torch.cuda.Event(enable_timing=True)
     start.record(torch.cuda.current_stream(dev))
@@ -537,13 +581,22 @@ def batched_run(S, torch, dev, ws, steps):
     out = {"value": parts * steps / (ms / 1e3), "unit": METRIC, "steps": steps, "ms_per_step": ms / steps,
            "instances": len(ws), "particles": parts,
            "per_dim": {}}
+    # the per-stage split: a few more steps per batch with stage events (alone on the GPU)
+    staged = min(steps, 20)
     for (b, _, n), d in zip(batches, (2, 3)):
+        S.sph_batch_set_timing(b.h, 1)
+        b.step(1)
+        b.sync()
+        S.sph_batch_set_timing(b.h, 1)
+        b.step(staged)
+        b.sync()
         t = S.sph_batch_kernel_times(b.h)
         _, slots, _ = S.sph_batch_size(b.h)
         out["per_dim"][f"{d}d"] = {"instances": b.n_inst, "particles": n, "slots": slots,
                                    "cells_per_support": b.tuned[0],
                                    "autotune_trial_ms": {"1": b.tuned[1][0], "2": b.tuned[1][1], "4": b.tuned[1][2]},
-                                   "stages_ms": {k: (v[1] / max(steps, 1)) for k, v in t.items()}}
+                                   "stages_ms": {k: (v[1] / max(staged, 1)) for k, v in t.items()},
+                                   "stage_steps": staged}
         S.sph_batch_set_timing(b.h, 0)
         b.sync()
         b.close()

@@ -121,7 +121,16 @@ typedef struct {
     int32_t cells_per_support;  /* cell grid refinement m (see sph_grid_spec): 1, 2 or 4;
                               0: the library's choice for the dimension (not a paper
                               parameter; it changes no result beyond rounding)          [0]  */
+    int32_t boundary_correction;  /* 1: the feature-boundary sum of Eq. 19 (this paper's
+                              correction, Sec. 3.2) acts on every particle; 0: it is left out,
+                              as in the earlier method compared in Sec. 4.1              [1]  */
 } sph_params;
+
+/* Method presets of the comparison in Sec. 4.1 (Square, its table of N_iter): the improved
+ * method of this paper, the earlier SPH mesh generator it is compared with (velocities set to
+ * zero every step, no feature-boundary correction) and that method's variant "v2" (velocities
+ * set to zero every 100 steps, as in the improved method). */
+typedef enum { SPH_METHOD_IMPROVED = 0, SPH_METHOD_FU2019 = 1, SPH_METHOD_FU2019_V2 = 2 } sph_method;
 
 /* Controller phases (Sec. 3.4) */
 typedef enum { SPH_PHASE1 = 1, SPH_RAMP = 2, SPH_PHASE2 = 3, SPH_DONE = 4 } sph_phase;
@@ -155,6 +164,12 @@ sph_status sph_mesh_create(const sph_domain_desc* domain, const sph_sizing_desc*
 
 /* Fills params with the paper's defaults (bracketed values above). */
 sph_status sph_params_default(sph_params* params);
+
+/* Sets the fields that distinguish the methods of Sec. 4.1 (reset_period and
+ * boundary_correction) for method (a sph_method) and leaves every other field as it is:
+ * IMPROVED 100 / 1, FU2019 1 / 0, FU2019_V2 100 / 0.  The controller and the step size
+ * rules are the same for all three.  Errors: SPH_E_INVALID (NULL params, unknown method). */
+sph_status sph_params_preset(sph_params* params, int32_t method);
 
 /* Loads a particle set (Algorithm 1, "allocate particles ... initial particle sampling") and
  * resets the controller to Phase One, step 0.  x: [n][3] positions; group: feature index of

@@ -44,7 +44,7 @@ class Params(C.Structure):
                 ("cfl_v", C.c_double), ("eps1", C.c_double), ("dt_cap", C.c_double), ("dt_collapse", C.c_double),
                 ("threshold", C.c_double), ("reset_period", C.c_int32), ("sample_every", C.c_int32),
                 ("window", C.c_int32), ("ramp_len", C.c_int32), ("boundary_rho", C.c_int32),
-                ("max_newton", C.c_int32)]
+                ("max_newton", C.c_int32), ("boundary_correction", C.c_int32)]
 
 
 class Ctrl(C.Structure):

@@ -581,7 +581,7 @@ void orc_interact(int64_t n, const orc_domain* dom, const orc_params* prm,
                             for (int a = 0; a < 3; ++a) f[a] += c1 * rij[a] / r;
                             mag += fabs(c1);
                         }
-                    } else if (dj < d && r < kappa * hij) {
+                    } else if (prm->boundary_correction && dj < d && r < kappa * hij) {
                         double nb[3], tg[3];
                         orc_frame(dom, gj, x + 3 * j, nb, tg);
                         orc_tangent(dom, gi, x + 3 * i, nb);

@@ -90,6 +90,8 @@ typedef struct {
     int32_t boundary_rho;  /* 1: boundary term carries rho_b (units-consistent reading of
                               Eq. 19); 0: Eq. 19 as printed                                    */
     int32_t max_newton;    /* projection iterations onto the domain for escaped particles       */
+    int32_t boundary_correction;  /* 1: the feature-boundary sum of Eq. 19 (Sec. 3.2) is applied;
+                              0: it is left out (the earlier method compared in Sec. 4.1)       */
 } orc_params;
 
 /* two-phase controller state (Sec. 3.4) */

@@ -203,7 +203,8 @@ sph_status make_instance(const sph_domain_desc* dd, const sph_sizing_desc* sz, c
     if (pp->precision != 32 && pp->precision != 64) return fail(SPH_E_INVALID, "params: precision must be 32 or 64");
     if (!(pp->kappa > 0) || !(pp->p0 > 0) || pp->visc < 0 || !(pp->cfl_a > 0) || !(pp->cfl_v > 0) || pp->eps1 < 0 ||
         !(pp->dt_cap > 0) || pp->dt_collapse < 0 || !(pp->threshold > 0) || pp->reset_period < 1 ||
-        pp->sample_every < 1 || pp->window < 1 || pp->ramp_len < 1)
+        pp->sample_every < 1 || pp->window < 1 || pp->ramp_len < 1 || (pp->boundary_rho != 0 && pp->boundary_rho != 1) ||
+        (pp->boundary_correction != 0 && pp->boundary_correction != 1))
         return fail(SPH_E_INVALID, "params: value out of range");
     if (max_particles < 0 || max_particles > (int64_t)1 << 30) return fail(SPH_E_INVALID, "max_particles out of range");
     if (sz->kind < 0 || sz->kind > 2 || !(sz->lo > 0) || !(sz->hi >= sz->lo) || sz->n_ref < 0 || sz->n_ref > SPH_MAX_HOLES)
@@ -292,6 +293,7 @@ sph_status make_instance(const sph_domain_desc* dd, const sph_sizing_desc* sz, c
     p.window = pp->window;
     p.ramp_len = pp->ramp_len;
     p.boundary_rho = pp->boundary_rho;
+    p.boundary_corr = pp->boundary_correction;
     p.kappa_f = (float)p.kappa;
     p.p0_f = (float)p.p0;
     p.visc_f = (float)p.visc;
@@ -1520,7 +1522,18 @@ sph_status sph_params_default(sph_params* p) {
     p->ramp_len = 200;
     p->boundary_rho = 1;
     p->precision = 32;
+    p->boundary_correction = 1;
     return SPH_OK;
+}
+
+sph_status sph_params_preset(sph_params* p, int32_t method) {
+    if (!p) return fail(SPH_E_INVALID, "params: NULL");
+    switch (method) {
+        case SPH_METHOD_IMPROVED: p->reset_period = 100; p->boundary_correction = 1; return SPH_OK;
+        case SPH_METHOD_FU2019: p->reset_period = 1; p->boundary_correction = 0; return SPH_OK;
+        case SPH_METHOD_FU2019_V2: p->reset_period = 100; p->boundary_correction = 0; return SPH_OK;
+        default: return fail(SPH_E_INVALID, "params: unknown method preset %d", (int)method);
+    }
 }
 
 sph_status sph_grid_spec(int32_t dim, const double* lo, const double* hi, double h_lo, double h_hi, double kappa,

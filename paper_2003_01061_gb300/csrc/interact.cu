@@ -7,7 +7,8 @@
 //   sigma_i = sum_{j in g, r < kappa h_i} W_d(r_ij, h_i)             (Eq. 20 denominator, j = i included)
 //   gamma_i = sum_{j in g, r < kappa h_i} W_d(r_ij, h_i) h_j^d         (Eq. 18)
 //   F_i     = sum_{j in g, j != i, r < kappa h_ij} (P_i + P_j) W_d'(r_ij, h_ij) e_ij          (Eq. 19, 1st sum)
-//           + sum_{b: d_b < d, r < kappa h_ib} rho_b (P_i + P_b) W_d(r_ib, h_ib) n_b|i A_b  (Eq. 19, 2nd sum)
+//           + sum_{b: d_b < d, r < kappa h_ib} rho_b (P_i + P_b) W_d(r_ib, h_ib) n_b|i A_b  (Eq. 19, 2nd sum;
+//             left out with boundary_correction = 0, the earlier method compared in Sec. 4.1)
 //   a_p,i   = Pi_i(-F_i / gamma_i),  V~_i = 1 / sigma_i
 // and the Eq. 24 candidates 0.25 sqrt(r_c/|a_p|), r_c/(40 |v|), reduced to per-group minima.
 // On sampling steps each block also writes its per-group sums of V~ (Eq. 22) in a fixed order.
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTERACT_MINB : 4)
         g, s.cell_start, s.occ, s.n, s.P, s.Ms, sbuf + threadIdx.x, active, li, ci, offi, hi, kappa,
         [&](int j, const T*, T r2, T hj, unsigned mj) -> bool {
             if (meta_group(mj) == gi) return r2 < rci2 || (j != k && r2 < pair_rc2(hi, hj, hk));
-            return meta_dim(mj) < di && r2 < pair_rc2(hi, hj, hk);
+            return p.boundary_corr != 0 && meta_dim(mj) < di && r2 < pair_rc2(hi, hj, hk);
         },
         [&](int j, const T dx[3], T r2, T hj, unsigned mj, const T offj[3], int l, int cxj, int cy, int cz) {
             const T invr = r2 > T(0) ? fast_rsqrt(r2) : T(0);

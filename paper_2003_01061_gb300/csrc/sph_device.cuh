@@ -86,6 +86,7 @@ struct Grid {
 struct Params {
     double kappa, p0, visc, cfl_a, cfl_v, eps1, dt_cap, dt_collapse, threshold;
     int reset_period, sample_every, window, ramp_len, boundary_rho;
+    int boundary_corr;   // 0: the boundary sum of Eq. 19 is left out (earlier method, Sec. 4.1)
     int G;
     int gdim[MAXF];      // intrinsic dimension of every group (feature)
     float kappa_f, p0_f, visc_f, cfl_a_f, cfl_v_f;   // float copies for the FP32 kernels

@@ -51,7 +51,7 @@ class sph_params(C.Structure):
                 ("cfl_v", C.c_double), ("eps1", C.c_double), ("dt_cap", C.c_double), ("dt_collapse", C.c_double),
                 ("threshold", C.c_double), ("reset_period", C.c_int32), ("sample_every", C.c_int32),
                 ("window", C.c_int32), ("ramp_len", C.c_int32), ("boundary_rho", C.c_int32),
-                ("precision", C.c_int32), ("cells_per_support", C.c_int32)]
+                ("precision", C.c_int32), ("cells_per_support", C.c_int32), ("boundary_correction", C.c_int32)]
 
 
 class sph_report(C.Structure):
@@ -89,9 +89,10 @@ class sph_server_stats(C.Structure):
 
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_NOT_CONVERGED, JOB_FAILED = 1, 2, 3, 4, 5
+METHOD_IMPROVED, METHOD_FU2019, METHOD_FU2019_V2 = 0, 1, 2
 
 
-EXPORTS = ["sph_params_default", "sph_mesh_create", "sph_mesh_set_state", "sph_mesh_step", "sph_mesh_sync",
+EXPORTS = ["sph_params_default", "sph_params_preset", "sph_mesh_create", "sph_mesh_set_state", "sph_mesh_step", "sph_mesh_sync",
            "sph_mesh_run_until_converged", "sph_mesh_positions", "sph_mesh_report", "sph_mesh_destroy",
            "sph_last_error", "sph_grid_spec", "sph_mesh_grid", "sph_debug_rebuild", "sph_debug_neighbors",
            "sph_debug_interact", "sph_debug_update", "sph_mesh_set_timing", "sph_mesh_kernel_times",
@@ -116,6 +117,7 @@ def lib():
         vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
         sig = {
             "sph_params_default": [vp],
+            "sph_params_preset": [vp, i32],
             "sph_mesh_create": [vp, vp, vp, i64, vp, vp],
             "sph_mesh_set_state": [vp, i64, vp, vp, vp, vp],
             "sph_mesh_step": [vp, i32],
@@ -243,6 +245,11 @@ def params_struct(p: dict, precision: int = 32) -> sph_params:
             setattr(q, name, p[name])
     q.precision = precision
     return q
+
+
+def sph_params_preset(params: sph_params, method: int) -> sph_params:
+    _check(lib().sph_params_preset(C.addressof(params), method))
+    return params
 
 
 # ----------------------------------------------------------------------------------------

@@ -32,8 +32,21 @@ import numpy as np
 PAPER_PARAMS = dict(
     kappa=2.0, p0=1.0, visc=0.1, cfl_a=0.25, cfl_v=1.0 / 40.0, eps1=0.0, dt_cap=1e30,
     dt_collapse=0.1, threshold=5e-6, reset_period=100, sample_every=20, window=10,
-    ramp_len=200, boundary_rho=1, max_newton=3,
+    ramp_len=200, boundary_rho=1, max_newton=3, boundary_correction=1,
 )
+
+# The methods compared in Sec. 4.1 (Square): velocities set to zero every reset_period steps
+# in Phase One, with or without the feature-boundary sum of Eq. 19.
+METHOD_PRESETS = {
+    "improved": dict(reset_period=100, boundary_correction=1),
+    "fu2019": dict(reset_period=1, boundary_correction=0),
+    "fu2019_v2": dict(reset_period=100, boundary_correction=0),
+}
+
+
+def method_preset(params: dict, method: str) -> dict:
+    """params with the two fields that distinguish the methods of Sec. 4.1 set for `method`."""
+    return dict(params, **METHOD_PRESETS[method])
 
 
 # ----------------------------------------------------------------------------------------
@@ -190,6 +203,39 @@ def square2d(h: float = 0.02, seed: int = 1, jitter: float = 0.1, params: dict |
         xs.append(np.array([[p[0], p[1], 0.0]]))
         gs.append(np.full(1, 5 + k))
     return _finish("square2d", dom, siz, feats, xs, gs, params or PAPER_PARAMS, h_lo=h, h_hi=h)
+
+
+def square_radial(seed: int = 6, params: dict | None = None, mc_samples: int = 400_000):
+    """The Square of Sec. 4.1: [0,100]^2 with h_t = (h_max - h_min)/(100 sqrt 2) |x - (100,100)|
+    + h_min (Eq. 25), h_min = 0.244, h_max = 4.88.  Volume particles by rejection sampling
+    proportional to h_t^-2, edge particles by inverting the cumulative 1/h_t density, 4 fixed
+    corners; per-feature counts from the integrals of rho_t = h_t^-d (Eqs. 10, 11).  The paper's
+    own initial distribution is not given; this is a seeded stand-in with its density."""
+    rng = np.random.default_rng(seed)
+    L, hmin, hmax = 100.0, 0.244, 4.88
+    dom = dict(D=2, base="box", lo=[0.0, 0.0, 0.0], hi=[L, L, 0.0], ball_c=[0, 0, 0], ball_r=0.0, holes=[])
+    siz = dict(kind="radial", a=hmin, b=(hmax - hmin) / (L * math.sqrt(2.0)), lo=hmin, hi=hmax,
+               q=[L, L, 0.0], refs=[])
+    s2 = 1.0 / math.sqrt(2.0)
+    feats = [dict(kind="volume", dim=2)]
+    edges = [((0, 0), (L, 0), (0, -1)), ((L, 0), (L, L), (1, 0)), ((L, L), (0, L), (0, 1)), ((0, L), (0, 0), (-1, 0))]
+    for a, b, nb in edges:
+        feats.append(dict(kind="segment", dim=1, a=[a[0], a[1], 0.0], b=[b[0], b[1], 0.0], nb=[nb[0], nb[1], 0.0]))
+    corners = [((0, 0), (-s2, -s2)), ((L, 0), (s2, -s2)), ((L, L), (s2, s2)), ((0, L), (-s2, s2))]
+    for c, nb in corners:
+        feats.append(dict(kind="point", dim=0, p=[c[0], c[1], 0.0], nb=[nb[0], nb[1], 0.0]))
+    nv = int(round(_mc_volume_count(np.random.default_rng(seed + 100), dom, siz, mc_samples)))
+    xs, gs = [_sample_volume(rng, dom, siz, nv, hmin)], [np.zeros(nv)]
+    for k, (a, b, _) in enumerate(edges):
+        a_, b_ = np.array([a[0], a[1], 0.0]), np.array([b[0], b[1], 0.0])
+        at = lambda t, a_=a_, b_=b_: a_ + (t / L)[:, None] * (b_ - a_)
+        m = int(round(_count_curve(L, at, siz)))
+        xs.append(_line_positions(rng, m, L, at, siz))
+        gs.append(np.full(m, 1 + k))
+    for k, (c, _) in enumerate(corners):
+        xs.append(np.array([[c[0], c[1], 0.0]]))
+        gs.append(np.full(1, 5 + k))
+    return _finish("square_radial", dom, siz, feats, xs, gs, params or PAPER_PARAMS, h_lo=hmin, h_hi=hmax)
 
 
 def _disk_holes_geometry(rng, n_holes=3):

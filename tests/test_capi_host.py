@@ -105,5 +105,23 @@ def test_invalid_descriptors_are_rejected():
 
 def test_params_default_are_the_papers():
     q = S.params_struct({})
-    for k in ("kappa", "p0", "visc", "cfl_a", "cfl_v", "threshold", "reset_period", "sample_every", "window"):
+    for k in ("kappa", "p0", "visc", "cfl_a", "cfl_v", "threshold", "reset_period", "sample_every", "window",
+              "boundary_correction"):
         assert getattr(q, k) == WL.PAPER_PARAMS[k], k
+
+
+def test_method_presets_match_the_workload_table():
+    names = {S.METHOD_IMPROVED: "improved", S.METHOD_FU2019: "fu2019", S.METHOD_FU2019_V2: "fu2019_v2"}
+    for method, name in names.items():
+        q = S.params_struct({"visc": 0.3, "reset_period": 7, "boundary_correction": 1})
+        S.sph_params_preset(q, method)
+        want = WL.method_preset({"visc": 0.3}, name)
+        assert q.reset_period == want["reset_period"] and q.boundary_correction == want["boundary_correction"]
+        assert q.visc == 0.3                       # other fields untouched
+    with pytest.raises(S.SphError):
+        S.sph_params_preset(S.params_struct({}), 3)
+    w = WL.square2d(h=0.05)
+    d, z, p = _descs(w)
+    p.boundary_correction = 2
+    with pytest.raises(S.SphError):
+        S.sph_mesh_create(d, z, p, 10)

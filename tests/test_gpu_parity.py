@@ -66,8 +66,8 @@ def oracle_h(w):
     return o.h
 
 
-def make(w, prec, h=None, v=None, cps=0):
-    m = S.Mesh(w, precision=prec, params=dict(w["params"], cells_per_support=cps))
+def make(w, prec, h=None, v=None, cps=0, params=None):
+    m = S.Mesh(w, precision=prec, params=dict(params or w["params"], cells_per_support=cps))
     m.set_state(v=v, h=h)
     return m
 
@@ -136,9 +136,12 @@ def _oracle_pressure(w, h, prec, sub=None):
     return o, o.interact(sub=sub, use_grid=True)
 
 
-@pytest.mark.parametrize("name,prec", CASES + DENSE_CASES)
-def test_pressure_pass_parity(name, prec):
+@pytest.mark.parametrize("name,prec,method", [(n, p, "improved") for n, p in CASES + DENSE_CASES] +
+                         [("square", 32, "fu2019"), ("disk", 64, "fu2019"), ("cube", 32, "fu2019_v2")])
+def test_pressure_pass_parity(name, prec, method):
+    # method: the presets of Sec. 4.1; the earlier method has no feature-boundary sum
     w = workload(name)
+    prm = WL.method_preset(w["params"], method)
     h = oracle_h(w)
     if prec == 32:
         h = h.astype(np.float32).astype(np.float64)    # both sides see the same stored h
@@ -147,9 +150,9 @@ def test_pressure_pass_parity(name, prec):
     v[:, : w["domain"]["D"]] = rng.normal(0, 1e-3, (len(w["x"]), w["domain"]["D"]))
     if prec == 32:
         v = v.astype(np.float32).astype(np.float64)
-    m = make(w, prec, h=h, v=v)
+    m = make(w, prec, h=h, v=v, params=prm)
     got = S.sph_debug_interact(m.h, m.n, m.n_groups)
-    o = O.Oracle(w, h=h, v=v)
+    o = O.Oracle(w, h=h, v=v, params=prm)
     ref = o.interact(use_grid=True)
     tol = TOL[prec]
     err = np.linalg.norm(got["a_p"] - ref["a_p"], axis=1)

@@ -87,7 +87,7 @@ def test_uniform_lattice_interior_has_no_force():
     assert abs(r["gamma"][0] - r["sigma"][0] * h * h) < 1e-14
 
 
-def _wall_setup(h, rows=12, half_width=20, boundary=True, boundary_rho=1):
+def _wall_setup(h, rows=12, half_width=20, boundary=True, boundary_rho=1, correction=1):
     # volume particles at cell centres ((i h, (j+1/2) h)); boundary (curve) particles on y = 0
     xs, gs = [], []
     for j in range(rows):
@@ -101,6 +101,7 @@ def _wall_setup(h, rows=12, half_width=20, boundary=True, boundary_rho=1):
              dict(kind="segment", dim=1 if boundary else 2, a=[-100, 0, 0], b=[100, 0, 0], nb=[0, -1, 0])]
     p = dict(WL.PAPER_PARAMS)
     p["boundary_rho"] = boundary_rho
+    p["boundary_correction"] = correction
     w = box_workload(xs, gs, feats, h, lo=(-100, 0, 0), hi=(100, 100, 0), params=p)
     o = O.Oracle(w)
     col = [j * (2 * half_width + 1) + half_width for j in range(3)]
@@ -131,6 +132,25 @@ def test_boundary_term_as_printed_is_not_scale_free():
     ref = np.linalg.norm(_wall_setup(h, boundary=False)["a_p"][0])
     lit = np.linalg.norm(_wall_setup(h, boundary_rho=0)["a_p"][0])
     assert lit > 0.5 * ref
+
+
+@pytest.mark.parametrize("h", [1.0, 0.02])
+def test_method_without_correction_ignores_the_boundary(h):
+    # Sec. 4.1's earlier method has no feature-boundary sum: with the correction off, the
+    # volume rows feel exactly what they feel when the wall particles belong to no lower
+    # dimension (they then take no part in the volume's sums at all), i.e. the full push of
+    # the truncated support; with it on, the push cancels.
+    off = _wall_setup(h, boundary=True, correction=0)
+    ref = _wall_setup(h, boundary=False)
+    on = _wall_setup(h, boundary=True, correction=1)
+    for k in ("a_p", "sigma", "gamma"):
+        assert np.array_equal(off[k], ref[k]), k
+    assert np.linalg.norm(on["a_p"][0]) <= 2e-3 * np.linalg.norm(off["a_p"][0])
+    # the presets of the three methods differ only in these two fields
+    for name, d in WL.METHOD_PRESETS.items():
+        q = WL.method_preset(WL.PAPER_PARAMS, name)
+        assert {k for k in q if q[k] != WL.PAPER_PARAMS[k]} <= {"reset_period", "boundary_correction"}
+    assert WL.method_preset(WL.PAPER_PARAMS, "improved") == WL.PAPER_PARAMS
 
 
 def test_p0_invariance_is_exact():
