@@ -516,6 +516,35 @@ def cube_run(S, torch, dev, w, steps):
     return out
 
 
+def mesh_quality_2d(w, x):
+    """Quality of the Delaunay triangulation of final 2D positions with the measures of Sec. 4
+    (G = 2 sqrt(3) S / (P H), angles); triangles whose centroid lies outside the domain are
+    dropped.  Measurement only: the method never triangulates."""
+    import math
+
+    from scipy.spatial import Delaunay
+
+    from paper_2003_01061_gb300 import workloads as WL
+
+    tri = Delaunay(x[:, :2])
+    P = x[tri.simplices][:, :, :2]
+    cen = np.concatenate([P.mean(axis=1), np.zeros((len(P), 1))], axis=1)
+    P = P[WL.domain_phi(w["domain"], cen) > 0]
+    e = np.stack([np.linalg.norm(P[:, 1] - P[:, 2], axis=1), np.linalg.norm(P[:, 0] - P[:, 2], axis=1),
+                  np.linalg.norm(P[:, 0] - P[:, 1], axis=1)], axis=1)
+    u, v = P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]
+    area = 0.5 * np.abs(u[:, 0] * v[:, 1] - u[:, 1] * v[:, 0])
+    G = 2 * math.sqrt(3) * area / (0.5 * e.sum(axis=1) * e.max(axis=1))
+    ang = []
+    for k in range(3):
+        a, b, c = e[:, k], e[:, (k + 1) % 3], e[:, (k + 2) % 3]
+        ang.append(np.degrees(np.arccos(np.clip((b * b + c * c - a * a) / (2 * b * c), -1, 1))))
+    ang = np.stack(ang, 1)
+    return {"G_avg": float(G.mean()), "G_min": float(G.min()), "theta_max": float(ang.max()),
+            "theta_min": float(ang.min()), "theta_min_avg": float(ang.min(axis=1).mean()),
+            "theta_lt30": int((ang.min(axis=1) < 30).sum()), "N_tri": int(len(P))}
+
+
 def presets_run(S, w, max_iters):
     """The comparison of Sec. 4.1 (Square, Eq. 25): the same initial particles relaxed by the
     improved method and by the two presets of the earlier method, each until the end of
@@ -538,8 +567,12 @@ def presets_run(S, w, max_iters):
         r = m.report()
         phase_one = int(r.ramp_start) if r.phase in (S.RAMP, S.PHASE2, S.DONE) else None
         out[label] = {"phase_one_iters": phase_one, "iters": int(iters), "done": bool(ok), "wall_s": wall,
-                      "escapes": int(r.escapes), "E_sys": float(r.E_sys)}
+                      "escapes": int(r.escapes), "E_sys": float(r.E_sys),
+                      "quality": mesh_quality_2d(w, m.positions()["x"])}
         m.close()
+    out["initial_quality"] = mesh_quality_2d(w, w["x"])
+    with open(os.path.join(ROOT, "tests", "golden", "paper_cases.json")) as f:
+        out["paper_table"] = json.load(f)["square_table"]
     out["config"] = {"workload": f"square_radial_2d: [0,100]^2, Eq. 25 sizing (h 0.244-4.88), {len(w['x'])} "
                                  f"particles (seed 6), FP32, paper controller, max {max_iters} iterations"}
     return out
