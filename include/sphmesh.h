@@ -124,6 +124,11 @@ typedef struct {
     int32_t boundary_correction;  /* 1: the feature-boundary sum of Eq. 19 (this paper's
                               correction, Sec. 3.2) acts on every particle; 0: it is left out,
                               as in the earlier method compared in Sec. 4.1              [1]  */
+    int32_t group_convergence;  /* 0: the instance changes phase when E_sys (the largest
+                              group error) passes the threshold (Sec. 3.4.2); 1: every group
+                              runs its own phases on its own error and stops moving once it
+                              has converged (Algorithm 1 skips a converged feature); the
+                              instance is then in the phase of its least advanced group   [0]  */
 } sph_params;
 
 /* Method presets of the comparison in Sec. 4.1 (Square, its table of N_iter): the improved
@@ -149,6 +154,9 @@ typedef struct {
     double vbar[SPH_MAX_FEATURES];     /* last sampled V-bar per group (Eq. 22, V_ref = 1)     */
     double dt[SPH_MAX_FEATURES];       /* step size of each group in the last step (Eq. 24)    */
     int32_t reset[SPH_MAX_FEATURES];   /* 1 if the group's velocities were nullified            */
+    int32_t group_phase[SPH_MAX_FEATURES];  /* each group's phase (the instance's unless
+                                          group_convergence = 1)                               */
+    double group_E[SPH_MAX_FEATURES];  /* each group's last error E_g (group_convergence = 1)  */
 } sph_report;
 
 typedef struct sph_mesh sph_mesh;

@@ -44,7 +44,7 @@ class Params(C.Structure):
                 ("cfl_v", C.c_double), ("eps1", C.c_double), ("dt_cap", C.c_double), ("dt_collapse", C.c_double),
                 ("threshold", C.c_double), ("reset_period", C.c_int32), ("sample_every", C.c_int32),
                 ("window", C.c_int32), ("ramp_len", C.c_int32), ("boundary_rho", C.c_int32),
-                ("max_newton", C.c_int32), ("boundary_correction", C.c_int32)]
+                ("max_newton", C.c_int32), ("boundary_correction", C.c_int32), ("group_convergence", C.c_int32)]
 
 
 class Ctrl(C.Structure):
@@ -53,7 +53,10 @@ class Ctrl(C.Structure):
                 ("wsum", C.c_double * MAX_FEAT), ("A_last", C.c_double * MAX_FEAT), ("A_prev", C.c_double * MAX_FEAT),
                 ("Vbar", C.c_double * MAX_FEAT), ("dt_prev", C.c_double * MAX_FEAT), ("dt", C.c_double * MAX_FEAT),
                 ("reset", C.c_int32 * MAX_FEAT), ("E_t", C.c_double), ("E_avg", C.c_double), ("E_sys", C.c_double),
-                ("eps", C.c_double), ("ramp_f", C.c_double)]
+                ("eps", C.c_double), ("ramp_f", C.c_double),
+                ("gphase", C.c_int32 * MAX_FEAT), ("gwcount", C.c_int32 * MAX_FEAT), ("gnwin", C.c_int32 * MAX_FEAT),
+                ("gramp_start", C.c_int64 * MAX_FEAT), ("gE", C.c_double * MAX_FEAT), ("geps", C.c_double * MAX_FEAT),
+                ("gf", C.c_double * MAX_FEAT)]
 
 
 class Grid(C.Structure):
@@ -302,6 +305,15 @@ class Oracle:
                        m, _p(sub_a), int(use_grid), _p(out["sigma"]), _p(out["gamma"]), _p(out["F"]),
                        _p(out["a_p"]), _p(out["S"]), _p(out["dta"]), _p(out["dtv"]))
         return out
+
+    def set_step_params(self, dt, reset, eps, f):
+        """The per-group step parameters the controller would hand to the update (Eq. 23)."""
+        for g in range(self.G):
+            self.ctrl.dt[g] = dt[g]
+            self.ctrl.reset[g] = int(reset[g])
+            self.ctrl.geps[g] = eps
+            self.ctrl.gf[g] = f
+        self.ctrl.eps, self.ctrl.ramp_f = eps, f
 
     def control(self, Vsum, dta, dtv):
         Vsum = np.ascontiguousarray(Vsum, dtype=np.float64)

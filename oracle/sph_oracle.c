@@ -633,6 +633,10 @@ void orc_ctrl_init(orc_ctrl* c) {
     memset(c, 0, sizeof(*c));
     c->phase = ORC_PHASE1;
     c->ramp_f = 1.0;
+    for (int g = 0; g < ORC_MAX_FEAT; ++g) {
+        c->gphase[g] = ORC_PHASE1;
+        c->gf[g] = 1.0;
+    }
 }
 
 static double rel_err(double a, double b) {
@@ -644,6 +648,108 @@ static void window_reset(orc_ctrl* c) {
     c->wcount = 0;
     c->nwin = 0;
     for (int g = 0; g < ORC_MAX_FEAT; ++g) { c->wsum[g] = 0; c->A_last[g] = 0; c->A_prev[g] = 0; }
+}
+
+static void group_window_reset(orc_ctrl* c, int g) {
+    c->gwcount[g] = 0;
+    c->gnwin[g] = 0;
+    c->wsum[g] = 0;
+    c->A_last[g] = 0;
+    c->A_prev[g] = 0;
+}
+
+/* the step size of one moving group from its Eq. 24 terms, its attenuation f and whether it is
+ * nullified on the schedule (step 4 below) */
+static void group_step(const orc_params* prm, int g, const double* dta, const double* dtv, double f,
+                       int periodic, orc_ctrl* c) {
+    double dv = (f > 0) ? dtv[g] / f : INFINITY;
+    double cand = dta[g] < dv ? dta[g] : dv;
+    int rs = periodic || (c->dt_prev[g] > 0 && cand < prm->dt_collapse * c->dt_prev[g]);
+    double dt = rs ? dta[g] : cand;
+    if (dt > prm->dt_cap) dt = prm->dt_cap;
+    c->dt_prev[g] = dt;
+    c->dt[g] = dt;
+    c->reset[g] = rs;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * The same controller run by every group on its own (group_convergence = 1; Algorithm 1
+ * skips a feature whose V-bar_k has converged).  For each moving group g at step n:
+ *  1. RAMP -> PHASE2 once ramp_len steps have passed since the group's switch;
+ *  2. in PHASE1 / PHASE2 on sampling steps: V-bar_g enters the group's window; with two
+ *     closed windows E_g = max(|V-bar_g - A_last,g|/|A_last,g|, |A_last,g - A_prev,g|/|A_prev,g|);
+ *     E_g < threshold moves the group PHASE1 -> RAMP or PHASE2 -> DONE;
+ *  3. eps, f and the nullification schedule of the group's phase (as for the instance);
+ *  4. the group's step size; a DONE group does not move (dt = 0).
+ * The instance's phase is that of its least advanced moving group (DONE when all are);
+ * E_sys is the largest E_g; ramp_start is the step at which the last group left PHASE1.
+ * ------------------------------------------------------------------------------------------ */
+static void control_per_group(const orc_params* prm, int G, const int32_t* gdim, const double* Vsum,
+                              const double* dta, const double* dtv, orc_ctrl* c) {
+    const int sampling = c->n % prm->sample_every == 0;
+    int lowest = ORC_DONE, evaluated = 0;
+    double et = 0, ea = 0, es = 0;
+    for (int g = 0; g < G; ++g) {
+        if (gdim[g] < 1) { c->dt[g] = 0; c->reset[g] = 1; c->geps[g] = 0; c->gf[g] = 0; continue; }
+        int ph = c->gphase[g];
+        if (ph == ORC_RAMP && c->n - c->gramp_start[g] >= prm->ramp_len) {
+            ph = ORC_PHASE2;
+            group_window_reset(c, g);
+        }
+        if ((ph == ORC_PHASE1 || ph == ORC_PHASE2) && sampling) {
+            c->Vbar[g] = Vsum[g];
+            c->wsum[g] += c->Vbar[g];
+            c->gwcount[g] += 1;
+            if (c->gwcount[g] == prm->window) {
+                c->A_prev[g] = c->A_last[g];
+                c->A_last[g] = c->wsum[g] / prm->window;
+                c->wsum[g] = 0;
+                c->gwcount[g] = 0;
+                c->gnwin[g] += 1;
+            }
+            if (c->gnwin[g] >= 2) {
+                double e1 = rel_err(c->Vbar[g], c->A_last[g]);
+                double e2 = rel_err(c->A_last[g], c->A_prev[g]);
+                c->gE[g] = e1 > e2 ? e1 : e2;
+                if (e1 > et) et = e1;
+                if (e2 > ea) ea = e2;
+                evaluated = 1;
+                if (c->gE[g] < prm->threshold) {
+                    if (ph == ORC_PHASE1) {
+                        ph = ORC_RAMP;
+                        c->gramp_start[g] = c->n;
+                        group_window_reset(c, g);
+                    } else {
+                        ph = ORC_DONE;
+                    }
+                }
+            }
+        }
+        c->gphase[g] = ph;
+        if (c->gE[g] > es) es = c->gE[g];
+        if (ph < lowest) lowest = ph;
+        if (ph == ORC_DONE) { c->dt[g] = 0; c->reset[g] = 1; c->geps[g] = 0; c->gf[g] = 0; continue; }
+        double eps = prm->eps1, f = 1.0;
+        int periodic = (c->n % prm->reset_period) == 0;
+        if (ph == ORC_RAMP) {
+            double sr = (double)(c->n - c->gramp_start[g]) / (double)prm->ramp_len;
+            eps = prm->eps1 * (1.0 - sr);
+            f = 0.5 * (1.0 + cos(M_PI * sr));
+        } else if (ph == ORC_PHASE2) {
+            eps = 0.0;
+            periodic = 1;
+        }
+        group_step(prm, g, dta, dtv, f, periodic, c);
+        c->geps[g] = eps;
+        c->gf[g] = f;
+    }
+    if (evaluated) {
+        c->E_t = et;
+        c->E_avg = ea;
+    }
+    c->E_sys = es;
+    if (c->phase == ORC_PHASE1 && lowest > ORC_PHASE1) c->ramp_start = c->n;
+    c->phase = lowest;
 }
 
 /* ------------------------------------------------------------------------------------------
@@ -666,8 +772,12 @@ static void window_reset(orc_ctrl* c) {
 void orc_control(const orc_params* prm, int G, const int32_t* gdim, const double* Vsum,
                  const double* dta, const double* dtv, orc_ctrl* c) {
     if (c->phase == ORC_DONE) {
-        for (int g = 0; g < G; ++g) { c->dt[g] = 0; c->reset[g] = 1; }
+        for (int g = 0; g < G; ++g) { c->dt[g] = 0; c->reset[g] = 1; c->gphase[g] = ORC_DONE; c->geps[g] = 0; c->gf[g] = 0; }
         c->eps = 0; c->ramp_f = 0;
+        return;
+    }
+    if (prm->group_convergence) {
+        control_per_group(prm, G, gdim, Vsum, dta, dtv, c);
         return;
     }
     if (c->phase == ORC_RAMP && c->n - c->ramp_start >= prm->ramp_len) {
@@ -708,7 +818,7 @@ void orc_control(const orc_params* prm, int G, const int32_t* gdim, const double
                     window_reset(c);
                 } else {
                     c->phase = ORC_DONE;
-                    for (int g = 0; g < G; ++g) { c->dt[g] = 0; c->reset[g] = 1; }
+                    for (int g = 0; g < G; ++g) { c->dt[g] = 0; c->reset[g] = 1; c->gphase[g] = ORC_DONE; c->geps[g] = 0; c->gf[g] = 0; }
                     c->eps = 0; c->ramp_f = 0;
                     return;
                 }
@@ -726,15 +836,11 @@ void orc_control(const orc_params* prm, int G, const int32_t* gdim, const double
         periodic = 1;
     }
     for (int g = 0; g < G; ++g) {
+        c->gphase[g] = c->phase;
+        c->geps[g] = eps;
+        c->gf[g] = f;
         if (gdim[g] < 1) { c->dt[g] = 0; c->reset[g] = 1; continue; }
-        double dv = (f > 0) ? dtv[g] / f : INFINITY;
-        double cand = dta[g] < dv ? dta[g] : dv;
-        int rs = periodic || (c->dt_prev[g] > 0 && cand < prm->dt_collapse * c->dt_prev[g]);
-        double dt = rs ? dta[g] : cand;
-        if (dt > prm->dt_cap) dt = prm->dt_cap;
-        c->dt_prev[g] = dt;
-        c->dt[g] = dt;
-        c->reset[g] = rs;
+        group_step(prm, g, dta, dtv, f, periodic, c);
     }
     c->eps = eps;
     c->ramp_f = f;
@@ -752,7 +858,8 @@ void orc_control(const orc_params* prm, int G, const int32_t* gdim, const double
  *   curves / surfaces: x+ projected onto the feature, v+ <- Pi(x+) v+;
  *   volume: if phi(x+) < 0 the particle is moved back to phi = 0.01 h_i along grad phi,
  *   its velocity is zeroed and the escape is counted;  h+ = h_t(x+).
- * Singular particles keep their position and zero velocity.
+ * Singular particles keep their position and zero velocity; the particles of a group that has
+ * converged on its own (group_convergence = 1, Algorithm 1) keep position, velocity and h.
  * ------------------------------------------------------------------------------------------ */
 void orc_integrate(int64_t n, const orc_domain* dom, const orc_sizing* siz, const orc_params* prm,
                    const orc_ctrl* c, const double* x, const double* h, const int32_t* grp,
@@ -767,8 +874,8 @@ void orc_integrate(int64_t n, const orc_domain* dom, const orc_sizing* siz, cons
         int g = grp[j];
         double dt = c->dt[g];
         for (int a = 0; a < 3; ++a) {
-            double vp = c->reset[g] ? 0.0 : c->ramp_f * v[3 * j + a];
-            vt[3 * j + a] = vp + dt * (a_p[3 * j + a] - c->eps * vp);
+            double vp = c->reset[g] ? 0.0 : c->gf[g] * v[3 * j + a];
+            vt[3 * j + a] = vp + dt * (a_p[3 * j + a] - c->geps[g] * vp);
         }
     }
     ugrid u;
@@ -783,8 +890,10 @@ void orc_integrate(int64_t n, const orc_domain* dom, const orc_sizing* siz, cons
             int64_t i = sub ? sub[s] : s;
             int gi = grp[i], d = feat_dim(dom, gi);
             double xo[3], vo[3], av[3] = {0, 0, 0};
-            for (int a = 0; a < 3; ++a) { xo[a] = x[3 * i + a]; vo[a] = 0; }
-            if (d > 0 && c->phase != ORC_DONE) {
+            /* a converged group (group_convergence = 1) keeps its state as it is */
+            const int frozen = d > 0 && c->gphase[gi] == ORC_DONE;
+            for (int a = 0; a < 3; ++a) { xo[a] = x[3 * i + a]; vo[a] = frozen ? v[3 * i + a] : 0; }
+            if (d > 0 && !frozen) {
                 double dt = c->dt[gi];
                 double rci = kappa * h[i];
                 double eta_i = pow(h[i], -(double)d) * prm->visc * rci * norm3(vt + 3 * i);
@@ -832,7 +941,7 @@ void orc_integrate(int64_t n, const orc_domain* dom, const orc_sizing* siz, cons
                 v_out[3 * s + a] = vo[a];
                 if (a_v) a_v[3 * s + a] = av[a];
             }
-            h_out[s] = (d > 0) ? orc_h(siz, xo) : h[i];
+            h_out[s] = (d > 0 && !frozen) ? orc_h(siz, xo) : h[i];
         }
         free(buf);
     }

@@ -92,6 +92,9 @@ typedef struct {
     int32_t max_newton;    /* projection iterations onto the domain for escaped particles       */
     int32_t boundary_correction;  /* 1: the feature-boundary sum of Eq. 19 (Sec. 3.2) is applied;
                               0: it is left out (the earlier method compared in Sec. 4.1)       */
+    int32_t group_convergence;    /* 0: the instance changes phase on E_sys (Sec. 3.4.2);
+                              1: every group runs its own phases on its own E_g and stops when
+                              it has converged (Algorithm 1: "if V-bar_k is not converged")     */
 } orc_params;
 
 /* two-phase controller state (Sec. 3.4) */
@@ -112,6 +115,11 @@ typedef struct {
     int32_t reset[ORC_MAX_FEAT];  /* velocity reset applied to each group in the last step    */
     double E_t, E_avg, E_sys;
     double eps, ramp_f;           /* damping and velocity attenuation used in the last step   */
+    /* per group: phase, window counters, switch step, last error, and the damping and
+       attenuation used in the last step (the instance's values when group_convergence = 0) */
+    int32_t gphase[ORC_MAX_FEAT], gwcount[ORC_MAX_FEAT], gnwin[ORC_MAX_FEAT];
+    int64_t gramp_start[ORC_MAX_FEAT];
+    double gE[ORC_MAX_FEAT], geps[ORC_MAX_FEAT], gf[ORC_MAX_FEAT];
 } orc_ctrl;
 
 /* cell-list representation used by the data-parallel neighbour search (multi-level grid) */

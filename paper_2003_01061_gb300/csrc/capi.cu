@@ -204,7 +204,8 @@ sph_status make_instance(const sph_domain_desc* dd, const sph_sizing_desc* sz, c
     if (!(pp->kappa > 0) || !(pp->p0 > 0) || pp->visc < 0 || !(pp->cfl_a > 0) || !(pp->cfl_v > 0) || pp->eps1 < 0 ||
         !(pp->dt_cap > 0) || pp->dt_collapse < 0 || !(pp->threshold > 0) || pp->reset_period < 1 ||
         pp->sample_every < 1 || pp->window < 1 || pp->ramp_len < 1 || (pp->boundary_rho != 0 && pp->boundary_rho != 1) ||
-        (pp->boundary_correction != 0 && pp->boundary_correction != 1))
+        (pp->boundary_correction != 0 && pp->boundary_correction != 1) ||
+        (pp->group_convergence != 0 && pp->group_convergence != 1))
         return fail(SPH_E_INVALID, "params: value out of range");
     if (max_particles < 0 || max_particles > (int64_t)1 << 30) return fail(SPH_E_INVALID, "max_particles out of range");
     if (sz->kind < 0 || sz->kind > 2 || !(sz->lo > 0) || !(sz->hi >= sz->lo) || sz->n_ref < 0 || sz->n_ref > SPH_MAX_HOLES)
@@ -294,6 +295,7 @@ sph_status make_instance(const sph_domain_desc* dd, const sph_sizing_desc* sz, c
     p.ramp_len = pp->ramp_len;
     p.boundary_rho = pp->boundary_rho;
     p.boundary_corr = pp->boundary_correction;
+    p.group_conv = pp->group_convergence;
     p.kappa_f = (float)p.kappa;
     p.p0_f = (float)p.p0;
     p.visc_f = (float)p.visc;
@@ -376,12 +378,26 @@ sph_status make_instance(const sph_domain_desc* dd, const sph_sizing_desc* sz, c
     return SPH_OK;
 }
 
+// the instance's phase, damping and attenuation, copied to every group
+void host_ctrl_phase(Ctrl* c, int phase, double eps, double f) {
+    c->phase = phase;
+    c->eps = eps;
+    c->f = f;
+    c->eps_f = (float)eps;
+    c->f_f = (float)f;
+    for (int g = 0; g < MAXF; ++g) {
+        c->gphase[g] = phase;
+        c->geps[g] = eps;
+        c->gf[g] = f;
+        c->geps_f[g] = (float)eps;
+        c->gf_f[g] = (float)f;
+    }
+}
+
 void host_ctrl_init(Ctrl* c) {
     std::memset(c, 0, sizeof *c);
-    c->phase = PH1;
     c->sample_now = 1;
-    c->f = 1.0;
-    c->f_f = 1.0f;
+    host_ctrl_phase(c, PH1, 0.0, 1.0);
 }
 
 template <typename T> void ctrl_inf_bits(Ctrl* c) {
@@ -891,10 +907,8 @@ template <typename T, int D> sph_status set_state_impl(sph_batch* b, int inst, i
     host_ctrl_init(&c);
     ctrl_inf_bits<T>(&c);
     if (nn == 0 && idle_when_empty) {
-        c.phase = PH_DONE;
+        host_ctrl_phase(&c, PH_DONE, 0.0, 0.0);
         c.sample_now = 0;
-        c.f = 0.0;
-        c.f_f = 0.0f;
     }
     if (keep) c = *keep;   // re-representation of the same state: the controller carries on
     CK(cudaMemcpyAsync(b->d_ctrl + inst, &c, sizeof c, cudaMemcpyHostToDevice, b->stream));
@@ -920,6 +934,8 @@ template <typename T> sph_status dbg_state(sph_batch* b, State<T>& out, const Ct
         ctrl_inf_bits<T>(&x);
         x.sample_now = 0;
         if (!init && x.phase == PH_DONE) x.phase = PH2;   // inspect a converged state as well
+        for (int g = 0; g < MAXF; ++g)
+            if (!init && x.gphase[g] == PH_DONE) x.gphase[g] = PH2;
     }
     CK(cudaMemcpyAsync(b->d_ctrl_dbg, c.data(), sizeof(Ctrl) * b->NI, cudaMemcpyHostToDevice, b->stream));
     CK(cudaStreamSynchronize(b->stream));
@@ -1077,10 +1093,7 @@ sph_status dbg_update_impl(sph_batch* b, const double* dt, const int32_t* reset,
         c.dt_f[g] = (float)dt[g];
         c.reset[g] = reset[g];
     }
-    c.eps = eps;
-    c.f = f;
-    c.eps_f = (float)eps;
-    c.f_f = (float)f;
+    host_ctrl_phase(&c, PH1, eps, f);
     State<T> s;
     sph_status r = dbg_prepare<T, D>(b, s, &c);
     if (r != SPH_OK) return r;
@@ -1428,6 +1441,8 @@ void fill_report(const sph_batch* b, int inst, const Ctrl& c, sph_report* out) {
         out->vbar[g] = c.Vbar[g];
         out->dt[g] = c.dt[g];
         out->reset[g] = c.reset[g];
+        out->group_phase[g] = c.gphase[g];
+        out->group_E[g] = c.gE[g];
     }
 }
 
@@ -1716,10 +1731,8 @@ sph_status sph_batch_create(int32_t n_inst, const sph_domain_desc* domains, cons
     for (Ctrl& x : c) {
         host_ctrl_init(&x);
         ctrl_inf_bits(b->prec, &x);
-        x.phase = PH_DONE;
+        host_ctrl_phase(&x, PH_DONE, 0.0, 0.0);
         x.sample_now = 0;
-        x.f = 0.0;
-        x.f_f = 0.0f;
     }
     if (cudaMemcpyAsync(b->d_ctrl, c.data(), sizeof(Ctrl) * b->NI, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess) {

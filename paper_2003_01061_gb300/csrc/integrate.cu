@@ -20,6 +20,143 @@ __device__ inline void window_reset(Ctrl* c) {
     }
 }
 
+__device__ inline void group_window_reset(Ctrl& c, int g) {
+    c.gwcount[g] = 0;
+    c.gnwin[g] = 0;
+    c.wsum[g] = 0.0;
+    c.A_last[g] = 0.0;
+    c.A_prev[g] = 0.0;
+}
+
+// The controller run by every group on its own (group_convergence = 1; Algorithm 1 skips a
+// feature whose V-bar_k has converged), one thread per group, on the block's copy of the
+// controller: RAMP -> PHASE2 after ramp_len steps since the group's switch; on sampling steps
+// V-bar_g enters the group's window and, with two closed windows, E_g = max(E_t,g, E_avg,g)
+// below the threshold moves the group PHASE1 -> RAMP or PHASE2 -> DONE; the group's eps, f,
+// nullification schedule and step size follow its phase; a DONE group does not move.  Thread
+// 0 then sets the instance's phase to that of its least advanced moving group (DONE when all
+// are), E_sys to the largest E_g and ramp_start to the step the last group left PHASE1.
+template <typename T>
+__device__ void control_groups(Ctrl& sc, const Params& p, const double* vs, int t) {
+    __shared__ int gl[MAXF], gev[MAXF];
+    __shared__ double ge1[MAXF], ge2[MAXF];
+    const int G = p.G;
+    const bool inst_done = sc.phase == PH_DONE;
+    const bool sampling = sc.n % p.sample_every == 0;
+    if (t < MAXF) {
+        gl[t] = PH_DONE;
+        gev[t] = 0;
+        ge1[t] = 0.0;
+        ge2[t] = 0.0;
+    }
+    if (t < G) {
+        const int g = t;
+        int ph = inst_done ? PH_DONE : sc.gphase[g];
+        if (p.gdim[g] >= 1 && ph != PH_DONE) {
+            if (ph == PH_RAMP && sc.n - sc.gramp_start[g] >= p.ramp_len) {
+                ph = PH2;
+                group_window_reset(sc, g);
+            }
+            if ((ph == PH1 || ph == PH2) && sampling) {
+                sc.Vbar[g] = vs[g];
+                sc.wsum[g] += sc.Vbar[g];
+                sc.gwcount[g] += 1;
+                if (sc.gwcount[g] == p.window) {
+                    sc.A_prev[g] = sc.A_last[g];
+                    sc.A_last[g] = sc.wsum[g] / p.window;
+                    sc.wsum[g] = 0.0;
+                    sc.gwcount[g] = 0;
+                    sc.gnwin[g] += 1;
+                }
+                if (sc.gnwin[g] >= 2) {
+                    const double e1 = rel_err(sc.Vbar[g], sc.A_last[g]);
+                    const double e2 = rel_err(sc.A_last[g], sc.A_prev[g]);
+                    sc.gE[g] = fmax(e1, e2);
+                    ge1[g] = e1;
+                    ge2[g] = e2;
+                    gev[g] = 1;
+                    if (sc.gE[g] < p.threshold) {
+                        if (ph == PH1) {
+                            ph = PH_RAMP;
+                            sc.gramp_start[g] = sc.n;
+                            group_window_reset(sc, g);
+                        } else {
+                            ph = PH_DONE;
+                        }
+                    }
+                }
+            }
+            gl[g] = ph;
+        }
+        if (p.gdim[g] >= 1) sc.gphase[g] = ph;
+        double eps = 0.0, f = 0.0;
+        if (p.gdim[g] < 1 || ph == PH_DONE) {
+            sc.dt[g] = 0.0;
+            sc.dt_f[g] = 0.0f;
+            sc.reset[g] = 1;
+        } else {
+            eps = p.eps1;
+            f = 1.0;
+            bool periodic = (sc.n % p.reset_period) == 0;
+            if (ph == PH_RAMP) {
+                const double sr = (double)(sc.n - sc.gramp_start[g]) / (double)p.ramp_len;
+                eps = p.eps1 * (1.0 - sr);
+                f = 0.5 * (1.0 + cos(CUDART_PI * sr));
+            } else if (ph == PH2) {
+                eps = 0.0;
+                periodic = true;
+            }
+            const double dta = (double)from_bits<T>(sc.dta_bits[g]);
+            const double dtv = (double)from_bits<T>(sc.dtv_bits[g]);
+            const double dv = f > 0.0 ? dtv / f : CUDART_INF;
+            const double cand = fmin(dta, dv);
+            const bool rs = periodic || (sc.dt_prev[g] > 0.0 && cand < p.dt_collapse * sc.dt_prev[g]);
+            double dt = rs ? dta : cand;
+            dt = fmin(dt, p.dt_cap);
+            sc.dt_prev[g] = dt;
+            sc.dt[g] = dt;
+            sc.dt_f[g] = (float)dt;
+            sc.reset[g] = rs ? 1 : 0;
+        }
+        sc.geps[g] = eps;
+        sc.gf[g] = f;
+        sc.geps_f[g] = (float)eps;
+        sc.gf_f[g] = (float)f;
+    }
+    if (t < MAXF) {
+        sc.dta_bits[t] = inf_bits<T>();
+        sc.dtv_bits[t] = inf_bits<T>();
+    }
+    __syncthreads();
+    if (t == 0 && !inst_done) {
+        int lowest = PH_DONE, any = 0;
+        double es = 0.0, et = 0.0, ea = 0.0;
+        for (int g = 0; g < G; ++g) {
+            if (p.gdim[g] < 1) continue;
+            lowest = min(lowest, gl[g]);
+            es = fmax(es, sc.gE[g]);
+            if (gev[g]) {
+                any = 1;
+                et = fmax(et, ge1[g]);
+                ea = fmax(ea, ge2[g]);
+            }
+        }
+        if (any) {
+            sc.E_t = et;
+            sc.E_avg = ea;
+        }
+        sc.E_sys = es;
+        if (sc.phase == PH1 && lowest > PH1) sc.ramp_start = sc.n;
+        sc.phase = lowest;
+        if (lowest == PH_DONE) {
+            sc.sample_now = 0;
+        } else {
+            sc.n += 1;
+            sc.sample_now = (sc.n % p.sample_every) == 0 ? 1 : 0;
+        }
+    }
+}
+
 // One block of 256 threads per instance.  The controller state is copied into shared memory at once, the
 // per-block V~ sums of a sampling step are reduced in a fixed order, and the controller for
 // step n runs with one thread per group (thread 0 keeps the scalar state):
@@ -65,6 +202,13 @@ template <typename T, int D, bool ONE> __global__ void __launch_bounds__(256) k_
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
             if (lane == 0) vs[g] = acc;
         }
+    }
+    if (p.group_conv) {
+        __syncthreads();
+        control_groups<T>(sc, p, vs, t);
+        __syncthreads();
+        for (int k = t; k < NW; k += blockDim.x) gw[k] = scw[k];
+        return;
     }
     if (t == 0) {
         const bool done = sc.phase == PH_DONE;
@@ -197,6 +341,14 @@ template <typename T, int D, bool ONE> __global__ void __launch_bounds__(256) k_
         sc.f_f = (float)sc.f;
     }
     __syncthreads();
+    if (t < MAXF) {   // the update reads the per-group copies
+        sc.gphase[t] = sc.phase;
+        sc.geps[t] = sc.eps;
+        sc.gf[t] = sc.f;
+        sc.geps_f[t] = sc.eps_f;
+        sc.gf_f[t] = sc.f_f;
+    }
+    __syncthreads();
     for (int k = t; k < NW; k += blockDim.x) gw[k] = scw[k];
 }
 
@@ -320,7 +472,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRAT
         }
     }
     const int gi = inrange ? meta_group(mi) : -1, di = inrange ? meta_dim(mi) : 0;
-    const bool done = cu->phase == PH_DONE;          // the same for every thread
+    const bool done = inrange && di > 0 && cu->gphase[gi] == PH_DONE;   // a converged group stays put
     const bool moving = inrange && di > 0 && !done;
     T av[3] = {T(0), T(0), T(0)};
     T hnew = hi;
@@ -331,8 +483,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRAT
     if (moving) {
         dt = wp<T>(cu->dt[gi], cu->dt_f[gi]);
         rs = cu->reset[gi] != 0;
-        f = wp<T>(cu->f, cu->f_f);
-        eps = wp<T>(cu->eps, cu->eps_f);
+        f = wp<T>(cu->gf[gi], cu->gf_f[gi]);
+        eps = wp<T>(cu->geps[gi], cu->geps_f[gi]);
         const Vec4<T> ai = s.A[k];
         const T api[3] = {ai.x, ai.y, ai.z};
         for (int a = 0; a < 3; ++a) {

@@ -87,6 +87,7 @@ struct Params {
     double kappa, p0, visc, cfl_a, cfl_v, eps1, dt_cap, dt_collapse, threshold;
     int reset_period, sample_every, window, ramp_len, boundary_rho;
     int boundary_corr;   // 0: the boundary sum of Eq. 19 is left out (earlier method, Sec. 4.1)
+    int group_conv;      // 1: every group runs its own phases (Algorithm 1's per-feature check)
     int G;
     int gdim[MAXF];      // intrinsic dimension of every group (feature)
     float kappa_f, p0_f, visc_f, cfl_a_f, cfl_v_f;   // float copies for the FP32 kernels
@@ -105,6 +106,12 @@ struct alignas(16) Ctrl {
     double E_t, E_avg, E_sys, eps, f;
     float dt_f[MAXF], eps_f, f_f;      // float copies of dt, eps, f for the FP32 update
     unsigned long long dta_bits[MAXF], dtv_bits[MAXF];   // per-group minima of Eq. 24 terms
+    // per group: phase, window counters, switch step, last error (group_convergence = 1), and
+    // the phase, damping and attenuation the update uses (the instance's when it is 0)
+    int gphase[MAXF], gwcount[MAXF], gnwin[MAXF], gpad[MAXF];
+    long long gramp_start[MAXF];
+    double gE[MAXF], geps[MAXF], gf[MAXF];
+    float geps_f[MAXF], gf_f[MAXF];
 };
 
 template <typename T> struct alignas(4 * sizeof(T)) Vec4 { T x, y, z, w; };

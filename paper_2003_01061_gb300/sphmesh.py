@@ -51,14 +51,16 @@ class sph_params(C.Structure):
                 ("cfl_v", C.c_double), ("eps1", C.c_double), ("dt_cap", C.c_double), ("dt_collapse", C.c_double),
                 ("threshold", C.c_double), ("reset_period", C.c_int32), ("sample_every", C.c_int32),
                 ("window", C.c_int32), ("ramp_len", C.c_int32), ("boundary_rho", C.c_int32),
-                ("precision", C.c_int32), ("cells_per_support", C.c_int32), ("boundary_correction", C.c_int32)]
+                ("precision", C.c_int32), ("cells_per_support", C.c_int32), ("boundary_correction", C.c_int32),
+                ("group_convergence", C.c_int32)]
 
 
 class sph_report(C.Structure):
     _fields_ = [("phase", C.c_int32), ("n_groups", C.c_int32), ("iteration", C.c_int64), ("ramp_start", C.c_int64),
                 ("escapes", C.c_int64), ("status", C.c_uint32), ("pad", C.c_uint32), ("E_t", C.c_double),
                 ("E_avg", C.c_double), ("E_sys", C.c_double), ("vbar", C.c_double * MAX_FEATURES),
-                ("dt", C.c_double * MAX_FEATURES), ("reset", C.c_int32 * MAX_FEATURES)]
+                ("dt", C.c_double * MAX_FEATURES), ("reset", C.c_int32 * MAX_FEATURES),
+                ("group_phase", C.c_int32 * MAX_FEATURES), ("group_E", C.c_double * MAX_FEATURES)]
 
 
 class sph_grid_info(C.Structure):

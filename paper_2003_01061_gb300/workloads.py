@@ -32,7 +32,7 @@ import numpy as np
 PAPER_PARAMS = dict(
     kappa=2.0, p0=1.0, visc=0.1, cfl_a=0.25, cfl_v=1.0 / 40.0, eps1=0.0, dt_cap=1e30,
     dt_collapse=0.1, threshold=5e-6, reset_period=100, sample_every=20, window=10,
-    ramp_len=200, boundary_rho=1, max_newton=3, boundary_correction=1,
+    ramp_len=200, boundary_rho=1, max_newton=3, boundary_correction=1, group_convergence=0,
 )
 
 # The methods compared in Sec. 4.1 (Square): velocities set to zero every reset_period steps

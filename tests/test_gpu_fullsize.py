@@ -55,10 +55,7 @@ def test_disk_full_update_sampled(disk):
     o = O.Oracle(w, h=h)
     r = o.interact(use_grid=True)
     dt = np.where(o.gdim > 0, r["dta"], 0.0)
-    for g in range(o.G):
-        o.ctrl.dt[g] = dt[g]
-        o.ctrl.reset[g] = 1
-    o.ctrl.eps, o.ctrl.ramp_f = 0.0, 1.0
+    o.set_step_params(dt, [1] * o.G, 0.0, 1.0)
     sub = np.sort(np.random.default_rng(1).choice(o.n, 2000, replace=False))
     ref = o.integrate(r["a_p"], sub=sub, use_grid=True)
     m = S.Mesh(w, precision=32)

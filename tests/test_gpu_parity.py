@@ -187,10 +187,7 @@ def test_update_parity(name, prec, reset):
     G = o.G
     dt = np.where(o.gdim > 0, np.minimum(r["dta"], 1e3), 0.0)
     eps, f = 0.1, 0.75
-    o.ctrl.eps, o.ctrl.ramp_f = eps, f
-    for g in range(G):
-        o.ctrl.dt[g] = dt[g]
-        o.ctrl.reset[g] = reset
+    o.set_step_params(dt, [reset] * G, eps, f)
     ref = o.integrate(r["a_p"], use_grid=True)
     m = make(w, prec, h=h, v=v)
     got = S.sph_debug_update(m.h, m.n, dt, np.full(G, reset, np.int32), eps, f)
