@@ -24,6 +24,8 @@ hole (0.004-0.04 scaled to ~120k particles), FP32 pair sums with FP64 projection
           by memory, retired on convergence or at the iteration limit), p50/p99 job latency and
           aggregate particle-steps/s, beside the same jobs served one at a time by the plain
           FP64 single-instance path (FIFO on the measured service times).
+* init_sampling: the 1.2M cube's initial particles drawn on the device (target counts of
+          Eqs. 10, 11 and rho_t-proportional sampling, Sec. 3.6), beside the host generator.
 * method_presets: the comparison of Sec. 4.1 on its Square (Eq. 25 sizing): iterations to the
           Phase-One target and to the end for the improved method and the earlier method's two
           presets (velocities zeroed every step / every 100 steps, no feature-boundary sum).
@@ -291,8 +293,11 @@ def run_ours(args):
     ws, rank, local = dist_env()
     # batch and serving inputs, generated before the first GPU call
     batch_ws, serve_ws, serve_t, cube_w = None, None, None, None
+    gen_s = None
     if rank == 0 and not args.no_cube:
+        t0 = time.perf_counter()
         cube_w = generate([(4, 1_200_000, 3, 0.3)])[0]
+        gen_s = time.perf_counter() - t0
     preset_w = None
     if rank == 0 and not args.no_presets:
         from paper_2003_01061_gb300 import workloads as WL
@@ -396,6 +401,10 @@ def run_ours(args):
     if preset_w is not None:
         presets = presets_run(S, preset_w, args.preset_iters)
 
+    sampling = None
+    if cube_w is not None:
+        sampling = sampling_run(S, cube_w, gen_s, with_oracle=not args.no_cpu_baseline)
+
     batched = None
     if batch_ws is not None:
         batched = batched_run(S, torch, dev, batch_ws, args.batch_steps)
@@ -438,6 +447,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "cube_3d": cube,
         "method_presets": presets,
+        "init_sampling": sampling,
         "batched": batched,
         "serving": serving,
     }
@@ -543,6 +553,38 @@ def mesh_quality_2d(w, x):
     return {"G_avg": float(G.mean()), "G_min": float(G.min()), "theta_max": float(ang.max()),
             "theta_min": float(ang.min()), "theta_min_avg": float(ang.min(axis=1).mean()),
             "theta_lt30": int((ang.min(axis=1) < 30).sum()), "N_tri": int(len(P))}
+
+
+def sampling_run(S, w, gen_s, with_oracle=True):
+    """The initial particles of the 1.2M cube drawn on the device (Sec. 3.6: target counts of
+    Eqs. 10, 11 + rho_t-proportional rejection sampling), host wall time including the copy of
+    the positions to the host; beside it the host-side numpy generator of the benchmark inputs
+    (Monte-Carlo counts + rejection sampling, in a worker process) and the oracle's sampler on
+    a bounded sample of the volume particles (one core)."""
+    d, z = S.domain_desc(w["domain"]), S.sizing_desc(w["sizing"])
+    S.sph_feature_counts(d, z)                       # first use of the kernels (untimed)
+    t0 = time.perf_counter()
+    M, N = S.sph_feature_counts(d, z)
+    t1 = time.perf_counter()
+    x, g = S.sph_sample_particles(d, z, 1, N)
+    t2 = time.perf_counter()
+    n = int(N.sum())
+    out = {"particles": n, "counts_s": t1 - t0, "sample_s": t2 - t1, "value": n / (t2 - t0),
+           "unit": "particles/s", "numpy_generator_s": gen_s,
+           "numpy_generator_particles": len(w["x"])}
+    if with_oracle:
+        from oracle import oracle as O
+
+        O.build()
+        m = 20_000
+        t3 = time.perf_counter()
+        O.sample_feature(w, 0, 1, m)
+        dt = time.perf_counter() - t3
+        out["oracle"] = {"value": m / dt, "unit": "particles/s", "cores": 1,
+                         "sample": f"first {m} volume particles of the same problem and seed"}
+    out["config"] = {"workload": "cube_sphere_3d_1.2M descriptors (seed 3): counts by the midpoint rule "
+                                 "(256^3 volume cells), Philox4x32-10 seed 1"}
+    return out
 
 
 def presets_run(S, w, max_iters):

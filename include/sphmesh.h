@@ -187,6 +187,49 @@ sph_status sph_params_preset(sph_params* params, int32_t method);
 sph_status sph_mesh_set_state(sph_mesh* m, int64_t n, const double* x, const int32_t* group,
                               const double* v, const double* h);
 
+/* ---- initial particles on the device (Sec. 3.6; Algorithm 1: "calculate the target
+ * information (Eqs. 10, 11)", "allocate particles ... initial particle sampling") ---- */
+
+/* Quadrature points of the target counts: the midpoint rule on a grid of SPH_QUAD_AREA^2 (2D) or
+ * SPH_QUAD_VOLUME^3 (3D) cells of the bounding box (cells whose centre has phi > 0 count),
+ * SPH_QUAD_CURVE points per curve, SPH_QUAD_FACE^2 per face, SPH_QUAD_SPHERE x 2 SPH_QUAD_SPHERE
+ * (polar x azimuthal) per sphere. */
+#define SPH_QUAD_AREA 2048
+#define SPH_QUAD_VOLUME 256
+#define SPH_QUAD_CURVE 65536
+#define SPH_QUAD_FACE 1024
+#define SPH_QUAD_SPHERE 512
+
+/* Target particle count of every feature: N_k = the integral of rho_t = h_t^-d over feature k
+ * (Eqs. 10, 11) with the quadrature above, computed on the device of `stream` (a point feature:
+ * 1).  integral_out[k] (may be NULL) receives the integral, count_out[k] (may be NULL) its
+ * nearest integer; both hold domain->n_features entries.  Errors: SPH_E_INVALID (descriptors,
+ * as for sph_mesh_create; no output), SPH_E_CUDA. */
+sph_status sph_feature_counts(const sph_domain_desc* domain, const sph_sizing_desc* sizing, void* stream,
+                              double* integral_out, int64_t* count_out);
+
+/* Draws counts[k] particles on every feature k with probability proportional to rho_t (Sec.
+ * 3.6), on the device of `stream`, by rejection: candidate c of feature k takes the four words of
+ * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011) for counter (c, c >> 32, k, 0) and key
+ * (seed, seed >> 32) as uniforms u = (w + 1/2) 2^-32 and is accepted with probability
+ * (h_min / h_t(x))^d, h_min = sizing->lo; a volume candidate is uniform in the bounding box and
+ * also needs phi(x) > h_t(x)/4, a curve candidate is uniform along the segment or (circle) in
+ * angle, a face candidate uniform on the face at least h_t(x)/4 inside its edges, a sphere
+ * candidate uniform in direction; a point feature gives its point (counts[k] <= 1).  Feature k
+ * keeps its first counts[k] accepted candidates in candidate order, so the result is a
+ * function of (problem, seed, counts) alone.  Caller-owned host outputs: x_out
+ * [sum counts][3] and group_out [sum counts] in feature order.  Errors: SPH_E_INVALID
+ * (descriptors; negative counts; a feature whose acceptance is too small to reach its count
+ * within 2^36 candidates), SPH_E_CUDA. */
+sph_status sph_sample_particles(const sph_domain_desc* domain, const sph_sizing_desc* sizing, uint64_t seed,
+                                const int64_t* counts, void* stream, double* x_out, int32_t* group_out);
+
+/* sph_feature_counts + sph_sample_particles for the mesh's problem on its stream, then the
+ * particles are loaded as by sph_mesh_set_state (v = 0, h = h_t(x)).  n_out (may be NULL)
+ * receives the particle count.  Errors: SPH_E_NOMEM (more particles than max_particles), and
+ * those of the two calls. */
+sph_status sph_mesh_sample(sph_mesh* m, uint64_t seed, int64_t* n_out);
+
 /* Enqueues n_steps relaxation steps (Algorithm 1, one pass of the while loop each: cell-list
  * rebuild, pressure pass with the feature-boundary correction of Eq. 19, per-group step size
  * of Eq. 24 and the two-phase controller of Sec. 3.4, viscous pass, update and projection).

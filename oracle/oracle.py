@@ -107,6 +107,9 @@ def lib():
         L.orc_integrate.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, i64, vp, i32, vp, vp, vp, vp, vp]
         L.orc_ctrl_init.argtypes = [vp]
         L.orc_step.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32]
+        L.orc_philox4x32_10.argtypes = [vp, vp, vp]
+        L.orc_sample_feature.restype = i64
+        L.orc_sample_feature.argtypes = [vp, vp, C.c_int, C.c_uint64, i64, vp]
         _lib = L
     return _lib
 
@@ -226,6 +229,33 @@ def tangent(dom: Domain, k: int, x, v):
 
 def feature_mass(dom: Domain, siz: Sizing, k: int, nq: int = 400) -> float:
     return lib().orc_feature_measure_density(_ref(dom), _ref(siz), k, nq)
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of the 4-word counter under the 2-word key (Sec. 3.6 sampling)."""
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    lib().orc_philox4x32_10(C.addressof(c), C.addressof(k), C.addressof(o))
+    return [int(v) for v in o]
+
+
+def sample_feature(w: dict, k: int, seed: int, n: int):
+    """The first n accepted candidates of feature k (Sec. 3.6); returns (positions, candidates)."""
+    dom, siz = make_domain(w["domain"]), make_sizing(w["sizing"])
+    out = np.zeros((max(n, 1), 3))
+    used = lib().orc_sample_feature(_ref(dom), _ref(siz), k, seed, n, _p(out))
+    return out[:n], int(used)
+
+
+def sample(w: dict, seed: int, counts):
+    """All features' samples in feature order (positions, groups)."""
+    xs, gs = [], []
+    for k, n in enumerate(counts):
+        x, _ = sample_feature(w, k, seed, int(n))
+        xs.append(x)
+        gs.append(np.full(int(n), k, np.int32))
+    return np.concatenate(xs), np.concatenate(gs)
 
 
 def neighbors_brute(x, h, i, D, kappa=2.0):

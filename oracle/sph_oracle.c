@@ -981,3 +981,115 @@ void orc_step(int64_t n, const orc_domain* dom, const orc_sizing* siz, const orc
     }
     free(sigma); free(ap); free(x2); free(v2); free(h2);
 }
+
+/* ------------------------------------------------------------------------------------------
+ * Initial particle sampling (Sec. 3.6): particles of feature k are drawn at random with
+ * probability proportional to the target density rho_t = h_t^-d, by rejection.  The random
+ * numbers come from a counter-based generator, so that any candidate's numbers can be drawn
+ * on their own: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+ * as 1, 2, 3", SC 2011) -- ten rounds of its S-box on a 128-bit counter under a 64-bit key,
+ * the key advanced by the two Weyl constants between rounds.
+ * ------------------------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0, hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Candidate c of feature k: counter (c low word, c high word, k, 0), key = the seed's two words;
+ * its four numbers as uniforms in (0, 1): u = (x + 1/2) 2^-32 (exact in FP64). */
+static void candidate_uniforms(uint64_t seed, int k, int64_t c, double u[4]) {
+    uint32_t ctr[4] = {(uint32_t)c, (uint32_t)((uint64_t)c >> 32), (uint32_t)k, 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    for (int a = 0; a < 4; ++a) u[a] = ((double)o[a] + 0.5) * (1.0 / 4294967296.0);
+}
+
+/* Whether candidate u of feature k is accepted, and its position.  Acceptance probability
+ * (h_min/h_t(x))^d, h_min the sizing's lower bound:
+ *   VOLUME  x uniform in the bounding box; also phi(x) > h_t(x)/4 (away from the boundary);
+ *   SEGMENT x = a + u0 (b - a);
+ *   CIRCLE / SPHERE  p = 2u - 1 (2 or 3 components) kept when 0 < |p|^2 <= 1, x = c + r p/|p|;
+ *   RECT    (s, t) = (u0 l_u, u1 l_w), kept at least h_t(x)/4 inside the face's edges,
+ *           x = o + s e_u + t e_w;
+ *   POINT   the point itself. */
+static int candidate_accept(const orc_domain* dom, const orc_sizing* s, int k, const double u[4], double x[3]) {
+    const orc_feature* f = &dom->feat[k];
+    const int D = dom->D;
+    x[0] = x[1] = x[2] = 0.0;
+    double h, acc;
+    switch (f->kind) {
+        case ORC_VOLUME: {
+            for (int a = 0; a < D; ++a) x[a] = dom->lo[a] + u[a] * (dom->hi[a] - dom->lo[a]);
+            h = orc_h(s, x);
+            if (!(orc_phi(dom, x, NULL) > 0.25 * h)) return 0;
+            double r = s->lo / h;
+            double rd = r * r;
+            if (D == 3) rd = rd * r;
+            return u[3] < rd;
+        }
+        case ORC_SEGMENT:
+            for (int a = 0; a < 3; ++a) x[a] = f->p[a] + u[0] * (f->p[3 + a] - f->p[a]);
+            h = orc_h(s, x);
+            return u[1] < s->lo / h;
+        case ORC_CIRCLE: {
+            double p0 = 2.0 * u[0] - 1.0, p1 = 2.0 * u[1] - 1.0;
+            double q = p0 * p0 + p1 * p1;
+            if (!(q > 0.0 && q <= 1.0)) return 0;
+            double r = sqrt(q);
+            x[0] = f->p[0] + f->p[2] * (p0 / r);
+            x[1] = f->p[1] + f->p[2] * (p1 / r);
+            h = orc_h(s, x);
+            return u[2] < s->lo / h;
+        }
+        case ORC_SPHERE: {
+            double p0 = 2.0 * u[0] - 1.0, p1 = 2.0 * u[1] - 1.0, p2 = 2.0 * u[2] - 1.0;
+            double q = (p0 * p0 + p1 * p1) + p2 * p2;
+            if (!(q > 0.0 && q <= 1.0)) return 0;
+            double r = sqrt(q);
+            x[0] = f->p[0] + f->p[3] * (p0 / r);
+            x[1] = f->p[1] + f->p[3] * (p1 / r);
+            x[2] = f->p[2] + f->p[3] * (p2 / r);
+            h = orc_h(s, x);
+            acc = s->lo / h;
+            return u[3] < acc * acc;
+        }
+        case ORC_RECT: {
+            double sv = u[0] * f->p[9], tv = u[1] * f->p[10];
+            for (int a = 0; a < 3; ++a) x[a] = (f->p[a] + sv * f->p[3 + a]) + tv * f->p[6 + a];
+            h = orc_h(s, x);
+            double m = 0.25 * h;
+            if (!(sv > m && sv < f->p[9] - m && tv > m && tv < f->p[10] - m)) return 0;
+            acc = s->lo / h;
+            return u[2] < acc * acc;
+        }
+        default: /* ORC_POINT */
+            for (int a = 0; a < D; ++a) x[a] = f->p[a];
+            return 1;
+    }
+}
+
+int64_t orc_sample_feature(const orc_domain* dom, const orc_sizing* s, int k, uint64_t seed, int64_t n,
+                           double* x_out) {
+    int64_t got = 0, c = 0;
+    while (got < n) {
+        double u[4], x[3];
+        candidate_uniforms(seed, k, c, u);
+        if (candidate_accept(dom, s, k, u, x)) {
+            for (int a = 0; a < 3; ++a) x_out[3 * got + a] = x[a];
+            ++got;
+        }
+        ++c;
+    }
+    return c;
+}

@@ -177,6 +177,14 @@ void orc_integrate(int64_t n, const orc_domain* dom, const orc_sizing* siz, cons
                    int32_t use_grid, double* x_out, double* v_out, double* h_out, double* a_v,
                    int64_t* escapes);
 void orc_ctrl_init(orc_ctrl* c);
+
+/* ---- initial particle sampling (Sec. 3.6) ---- */
+/* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC 2011). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* The first n accepted candidates of feature k for seed (positions x_out[n][3]); returns the
+ * number of candidates examined. */
+int64_t orc_sample_feature(const orc_domain* dom, const orc_sizing* s, int k, uint64_t seed, int64_t n,
+                           double* x_out);
 void orc_step(int64_t n, const orc_domain* dom, const orc_sizing* siz, const orc_params* prm,
               orc_ctrl* c, double* x, double* v, double* h, const int32_t* grp,
               int32_t use_grid, int32_t n_steps);

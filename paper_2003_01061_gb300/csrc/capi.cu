@@ -1441,8 +1441,9 @@ void fill_report(const sph_batch* b, int inst, const Ctrl& c, sph_report* out) {
         out->vbar[g] = c.Vbar[g];
         out->dt[g] = c.dt[g];
         out->reset[g] = c.reset[g];
-        out->group_phase[g] = c.gphase[g];
-        out->group_E[g] = c.gE[g];
+        const bool per_group = b->in[inst].params.group_conv != 0;
+        out->group_phase[g] = per_group ? c.gphase[g] : c.phase;
+        out->group_E[g] = per_group ? c.gE[g] : 0.0;
     }
 }
 
@@ -1508,6 +1509,73 @@ sph_status set_timing_impl(sph_batch* b, int32_t enable) {
     b->stage_steps = 0;
     for (double& t : b->stage_ms) t = 0;
     b->ev_pending = false;
+    return SPH_OK;
+}
+
+// ---- initial sampling (sample.cu): validated device copies of a problem's domain and sizing ----
+struct ProblemDev {
+    Inst I;
+    Domain* d_dom = nullptr;
+    Sizing* d_siz = nullptr;
+    cudaStream_t st = nullptr;
+    ~ProblemDev() {
+        if (d_dom) cudaFreeAsync(d_dom, st);
+        if (d_siz) cudaFreeAsync(d_siz, st);
+    }
+};
+
+sph_status problem_dev(const sph_domain_desc* dd, const sph_sizing_desc* sz, cudaStream_t st, ProblemDev& P) {
+    sph_params pp;
+    sph_params_default(&pp);
+    sph_status r = make_instance(dd, sz, &pp, 0, P.I);
+    if (r != SPH_OK) return r;
+    P.st = st;
+    CK(cudaMallocAsync((void**)&P.d_dom, sizeof(Domain), st));
+    CK(cudaMallocAsync((void**)&P.d_siz, sizeof(Sizing), st));
+    CK(cudaMemcpyAsync(P.d_dom, &P.I.dom, sizeof(Domain), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(P.d_siz, &P.I.siz, sizeof(Sizing), cudaMemcpyHostToDevice, st));
+    return SPH_OK;
+}
+
+sph_status feature_counts_impl(const sph_domain_desc* dd, const sph_sizing_desc* sz, cudaStream_t st,
+                               double* integral_out, int64_t* count_out) {
+    ProblemDev P;
+    sph_status r = problem_dev(dd, sz, st, P);
+    if (r != SPH_OK) return r;
+    std::vector<double> M(MAXF, 0.0);
+    cudaError_t e = feature_integrals(P.I.dom, P.d_dom, P.d_siz, st, M.data());
+    if (e != cudaSuccess) return fail(SPH_E_CUDA, "feature_counts: %s", cudaGetErrorString(e));
+    for (int k = 0; k < dd->n_features; ++k) {
+        if (integral_out) integral_out[k] = M[k];
+        if (count_out) count_out[k] = (int64_t)std::llround(M[k]);
+    }
+    return SPH_OK;
+}
+
+sph_status sample_impl(const sph_domain_desc* dd, const sph_sizing_desc* sz, uint64_t seed, const int64_t* counts,
+                       cudaStream_t st, double* x_out, int32_t* group_out) {
+    ProblemDev P;
+    sph_status r = problem_dev(dd, sz, st, P);
+    if (r != SPH_OK) return r;
+    int64_t n = 0;
+    for (int k = 0; k < dd->n_features; ++k) {
+        if (counts[k] < 0) return fail(SPH_E_INVALID, "sample: negative count for feature %d", k);
+        if (dd->features[k].kind == SPH_FEAT_POINT && counts[k] > 1)
+            return fail(SPH_E_INVALID, "sample: a point feature holds one particle");
+        n += counts[k];
+    }
+    if (n > ((int64_t)1 << 30)) return fail(SPH_E_INVALID, "sample: %lld particles is too many", (long long)n);
+    double* d_x = nullptr;
+    CK(cudaMallocAsync((void**)&d_x, sizeof(double) * 3 * (size_t)std::max<int64_t>(n, 1), st));
+    cudaError_t e = sample_features(P.I.dom, P.d_dom, P.d_siz, seed, counts, st, d_x);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x_out, d_x, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d_x, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaErrorInvalidValue) return fail(SPH_E_INVALID, "sample: acceptance too low to reach a feature's count");
+    if (e != cudaSuccess) return fail(SPH_E_CUDA, "sample: %s", cudaGetErrorString(e));
+    int64_t o = 0;
+    for (int k = 0; k < dd->n_features; ++k)
+        for (int64_t i = 0; i < counts[k]; ++i) group_out[o++] = k;
     return SPH_OK;
 }
 
@@ -1871,6 +1939,37 @@ void sph_batch_destroy(sph_batch* b) {
     if (!b) return;
     batch_free(b);
     delete b;
+}
+
+sph_status sph_feature_counts(const sph_domain_desc* domain, const sph_sizing_desc* sizing, void* stream,
+                              double* integral_out, int64_t* count_out) {
+    if (!count_out && !integral_out) return fail(SPH_E_INVALID, "feature_counts: no output");
+    return feature_counts_impl(domain, sizing, (cudaStream_t)stream, integral_out, count_out);
+}
+
+sph_status sph_sample_particles(const sph_domain_desc* domain, const sph_sizing_desc* sizing, uint64_t seed,
+                                const int64_t* counts, void* stream, double* x_out, int32_t* group_out) {
+    if (!counts || !x_out || !group_out) return fail(SPH_E_INVALID, "sample_particles: NULL argument");
+    return sample_impl(domain, sizing, seed, counts, (cudaStream_t)stream, x_out, group_out);
+}
+
+sph_status sph_mesh_sample(sph_mesh* m, uint64_t seed, int64_t* n_out) {
+    if (!m) return fail(SPH_E_INVALID, "mesh_sample: NULL handle");
+    const Inst& I = m->in[0];
+    std::vector<int64_t> cnt(I.dd.n_features);
+    sph_status r = feature_counts_impl(&I.dd, &I.sz, m->stream, nullptr, cnt.data());
+    if (r != SPH_OK) return r;
+    int64_t n = 0;
+    for (int64_t c : cnt) n += c;
+    if (n > I.cap)
+        return fail(SPH_E_NOMEM, "mesh_sample: %lld particles for a mesh created for %lld", (long long)n, (long long)I.cap);
+    std::vector<double> x((size_t)std::max<int64_t>(n, 1) * 3);
+    std::vector<int32_t> g((size_t)std::max<int64_t>(n, 1));
+    r = sample_impl(&I.dd, &I.sz, seed, cnt.data(), m->stream, x.data(), g.data());
+    if (r != SPH_OK) return r;
+    r = sph_mesh_set_state(m, n, x.data(), g.data(), nullptr, nullptr);
+    if (r == SPH_OK && n_out) *n_out = n;
+    return r;
 }
 
 }  // extern "C"

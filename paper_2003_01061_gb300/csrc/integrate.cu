@@ -181,7 +181,9 @@ template <typename T, int D, bool ONE> __global__ void __launch_bounds__(256) k_
     __shared__ double par[3];      // eps, f, periodic
     const int inst = blockIdx.x;
     static_assert(sizeof(Ctrl) % sizeof(int4) == 0, "the controller is copied in 16-byte vectors");
-    constexpr int NW = (int)(sizeof(Ctrl) / sizeof(int4));
+    constexpr int NWALL = (int)(sizeof(Ctrl) / sizeof(int4));
+    static_assert(offsetof(Ctrl, gphase) % sizeof(int4) == 0, "the per-group tail starts on a 16-byte boundary");
+    const int NW = one.p.group_conv || !ONE ? NWALL : (int)(offsetof(Ctrl, gphase) / sizeof(int4));
     int4* scw = reinterpret_cast<int4*>(&sc);
     int4* gw = reinterpret_cast<int4*>(s.ctrls + inst);
     const int t = threadIdx.x;
@@ -341,14 +343,6 @@ template <typename T, int D, bool ONE> __global__ void __launch_bounds__(256) k_
         sc.f_f = (float)sc.f;
     }
     __syncthreads();
-    if (t < MAXF) {   // the update reads the per-group copies
-        sc.gphase[t] = sc.phase;
-        sc.geps[t] = sc.eps;
-        sc.gf[t] = sc.f;
-        sc.geps_f[t] = sc.eps_f;
-        sc.gf_f[t] = sc.f_f;
-    }
-    __syncthreads();
     for (int k = t; k < NW; k += blockDim.x) gw[k] = scw[k];
 }
 
@@ -472,7 +466,9 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRAT
         }
     }
     const int gi = inrange ? meta_group(mi) : -1, di = inrange ? meta_dim(mi) : 0;
-    const bool done = inrange && di > 0 && cu->gphase[gi] == PH_DONE;   // a converged group stays put
+    // a converged instance (or, with group_convergence, group) stays put; the instance's
+    // scalars need no load that waits for the particle's group
+    const bool done = p.group_conv ? (inrange && di > 0 && cu->gphase[gi] == PH_DONE) : cu->phase == PH_DONE;
     const bool moving = inrange && di > 0 && !done;
     T av[3] = {T(0), T(0), T(0)};
     T hnew = hi;
@@ -483,8 +479,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRAT
     if (moving) {
         dt = wp<T>(cu->dt[gi], cu->dt_f[gi]);
         rs = cu->reset[gi] != 0;
-        f = wp<T>(cu->gf[gi], cu->gf_f[gi]);
-        eps = wp<T>(cu->geps[gi], cu->geps_f[gi]);
+        f = p.group_conv ? wp<T>(cu->gf[gi], cu->gf_f[gi]) : wp<T>(cu->f, cu->f_f);
+        eps = p.group_conv ? wp<T>(cu->geps[gi], cu->geps_f[gi]) : wp<T>(cu->eps, cu->eps_f);
         const Vec4<T> ai = s.A[k];
         const T api[3] = {ai.x, ai.y, ai.z};
         for (int a = 0; a < 3; ++a) {

@@ -106,12 +106,15 @@ struct alignas(16) Ctrl {
     double E_t, E_avg, E_sys, eps, f;
     float dt_f[MAXF], eps_f, f_f;      // float copies of dt, eps, f for the FP32 update
     unsigned long long dta_bits[MAXF], dtv_bits[MAXF];   // per-group minima of Eq. 24 terms
-    // per group: phase, window counters, switch step, last error (group_convergence = 1), and
-    // the phase, damping and attenuation the update uses (the instance's when it is 0)
-    int gphase[MAXF], gwcount[MAXF], gnwin[MAXF], gpad[MAXF];
-    long long gramp_start[MAXF];
-    double gE[MAXF], geps[MAXF], gf[MAXF];
+    // per group, used only with group_convergence = 1 (kept last: the instance controller
+    // copies the part before it): phase, damping and attenuation of the last step, window
+    // counters, switch step, last error
+    int gphase[MAXF];
+    double geps[MAXF], gf[MAXF];
     float geps_f[MAXF], gf_f[MAXF];
+    int gwcount[MAXF], gnwin[MAXF];
+    long long gramp_start[MAXF];
+    double gE[MAXF];
 };
 
 template <typename T> struct alignas(4 * sizeof(T)) Vec4 { T x, y, z, w; };

@@ -261,6 +261,15 @@ template <typename T, int D>
 void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const Out<T>& o, cudaStream_t st,
                       bool pdl = false);
 
+// sample.cu: midpoint-rule integrals of rho_t over every feature of dm (Eqs. 10, 11), and the
+// rejection sampling of counts[k] particles per feature into d_out[n][3] in feature order
+// (d_dom / d_siz: device copies of dm and its sizing)
+int quad_points(int kind, int D, long long* npts);
+cudaError_t feature_integrals(const Domain& dm, const Domain* d_dom, const Sizing* d_siz, cudaStream_t st,
+                              double* integral);
+cudaError_t sample_features(const Domain& dm, const Domain* d_dom, const Sizing* d_siz, unsigned long long seed,
+                            const int64_t* counts, cudaStream_t st, double* d_out);
+
 // sets the message returned by sph_last_error() on the calling thread (capi.cu)
 void set_last_error(const char* msg);
 

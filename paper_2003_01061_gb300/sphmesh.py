@@ -94,7 +94,8 @@ JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_NOT_CONVERGED, JOB_FAILED = 1, 2, 3, 4, 5
 METHOD_IMPROVED, METHOD_FU2019, METHOD_FU2019_V2 = 0, 1, 2
 
 
-EXPORTS = ["sph_params_default", "sph_params_preset", "sph_mesh_create", "sph_mesh_set_state", "sph_mesh_step", "sph_mesh_sync",
+EXPORTS = ["sph_params_default", "sph_params_preset", "sph_feature_counts", "sph_sample_particles", "sph_mesh_sample",
+           "sph_mesh_create", "sph_mesh_set_state", "sph_mesh_step", "sph_mesh_sync",
            "sph_mesh_run_until_converged", "sph_mesh_positions", "sph_mesh_report", "sph_mesh_destroy",
            "sph_last_error", "sph_grid_spec", "sph_mesh_grid", "sph_debug_rebuild", "sph_debug_neighbors",
            "sph_debug_interact", "sph_debug_update", "sph_mesh_set_timing", "sph_mesh_kernel_times",
@@ -120,6 +121,9 @@ def lib():
         sig = {
             "sph_params_default": [vp],
             "sph_params_preset": [vp, i32],
+            "sph_feature_counts": [vp, vp, vp, vp, vp],
+            "sph_sample_particles": [vp, vp, C.c_uint64, vp, vp, vp, vp],
+            "sph_mesh_sample": [vp, C.c_uint64, vp],
             "sph_mesh_create": [vp, vp, vp, i64, vp, vp],
             "sph_mesh_set_state": [vp, i64, vp, vp, vp, vp],
             "sph_mesh_step": [vp, i32],
@@ -247,6 +251,31 @@ def params_struct(p: dict, precision: int = 32) -> sph_params:
             setattr(q, name, p[name])
     q.precision = precision
     return q
+
+
+def sph_feature_counts(domain: sph_domain_desc, sizing: sph_sizing_desc, stream: int | None = None):
+    """(integrals, counts) of every feature: N_k of Eqs. 10, 11 on the device."""
+    nf = domain.n_features
+    M = np.zeros(nf)
+    N = np.zeros(nf, np.int64)
+    _check(lib().sph_feature_counts(C.addressof(domain), C.addressof(sizing), stream, _p(M), _p(N)))
+    return M, N
+
+
+def sph_sample_particles(domain: sph_domain_desc, sizing: sph_sizing_desc, seed: int, counts, stream: int | None = None):
+    """(x [n][3], group [n]) drawn on the device (Sec. 3.6)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int64)
+    n = int(counts.sum())
+    x = np.zeros((max(n, 1), 3))
+    g = np.zeros(max(n, 1), np.int32)
+    _check(lib().sph_sample_particles(C.addressof(domain), C.addressof(sizing), seed, _p(counts), stream, _p(x), _p(g)))
+    return x[:n], g[:n]
+
+
+def sph_mesh_sample(m, seed: int) -> int:
+    n = C.c_int64(0)
+    _check(lib().sph_mesh_sample(m, seed, C.addressof(n)))
+    return int(n.value)
 
 
 def sph_params_preset(params: sph_params, method: int) -> sph_params:
@@ -566,6 +595,11 @@ class Mesh:
         group = self.w["group"] if group is None else group
         sph_mesh_set_state(self.h, x, group, v, h)
         self.n = len(x)
+
+    def sample(self, seed: int) -> int:
+        """Initial particles drawn on the device (Sec. 3.6) instead of the workload's own."""
+        self.n = sph_mesh_sample(self.h, seed)
+        return self.n
 
     def step(self, k=1):
         sph_mesh_step(self.h, k)
