@@ -420,6 +420,9 @@ def run_ours(args):
                                          f"max {args.serve_iters} iterations, 20 steps per round"}
         if not args.no_fp64:
             serving["fp64_one_at_a_time"] = fp64_one_at_a_time(S, serve_ws, serve_t, args.serve_iters)
+        # the same arrivals given by their problems alone: particles drawn on the device at
+        # admission, inside each job's latency
+        serving["sampled_on_device"] = serving_run(S, serve_ws, serve_t, args.serve_iters, sampled=True)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -678,8 +681,10 @@ def batched_run(S, torch, dev, ws, steps):
     return out
 
 
-def serving_run(S, jobs, times, max_iters, steps_per_poll=20):
-    """Real-time Poisson arrivals into the server; latency from the scheduled arrival."""
+def serving_run(S, jobs, times, max_iters, steps_per_poll=20, sampled=False):
+    """Real-time Poisson arrivals into the server; latency from the scheduled arrival.  With
+    sampled=True every job is submitted by its problem alone and its particles are drawn on the
+    device at admission (inside its latency)."""
     srv = S.Server(precision=32, max_jobs=64, slot_capacity=(-1, -1), hbm_fraction=0.3,
                    steps_per_poll=steps_per_poll)
     # warm the step graphs with one small job of each dimension
@@ -692,7 +697,7 @@ def serving_run(S, jobs, times, max_iters, steps_per_poll=20):
     while True:
         now = time.perf_counter() - t0
         while k < len(jobs) and times[k] <= now:
-            ids.append(srv.submit(jobs[k], max_iters))
+            ids.append(srv.submit_sampled(jobs[k], max_iters, seed=k + 1) if sampled else srv.submit(jobs[k], max_iters))
             py_sub.append(time.perf_counter() - t0)
             k += 1
         st = srv.poll()

@@ -516,6 +516,15 @@ sph_status sph_server_submit(sph_server* s, const sph_domain_desc* domain, const
                              const sph_params* params, int64_t n, const double* x, const int32_t* group,
                              const double* h, int64_t max_iters, int64_t* job_id);
 
+/* Queues a job given by its problem alone: its target counts are computed at submission
+ * (sph_feature_counts) and its particles are drawn on the device when it is admitted
+ * (sph_sample_particles with this seed), so that its latency includes its initialisation.
+ * Errors: SPH_E_INVALID (descriptors, as for sph_feature_counts; no capacity for its
+ * dimension; other precision; a problem with no particle or more than the server's slots),
+ * SPH_E_CUDA. */
+sph_status sph_server_submit_sampled(sph_server* s, const sph_domain_desc* domain, const sph_sizing_desc* sizing,
+                                     const sph_params* params, uint64_t seed, int64_t max_iters, int64_t* job_id);
+
 /* One scheduling round (see above); stats (may be NULL) receives the counters after it. */
 sph_status sph_server_poll(sph_server* s, sph_server_stats* stats);
 

@@ -468,7 +468,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRAT
     const int gi = inrange ? meta_group(mi) : -1, di = inrange ? meta_dim(mi) : 0;
     // a converged instance (or, with group_convergence, group) stays put; the instance's
     // scalars need no load that waits for the particle's group
-    const bool done = p.group_conv ? (inrange && di > 0 && cu->gphase[gi] == PH_DONE) : cu->phase == PH_DONE;
+    bool done = cu->phase == PH_DONE;
+    if (p.group_conv && !done && inrange && di > 0) done = cu->gphase[gi] == PH_DONE;
     const bool moving = inrange && di > 0 && !done;
     T av[3] = {T(0), T(0), T(0)};
     T hnew = hi;
@@ -479,8 +480,12 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRAT
     if (moving) {
         dt = wp<T>(cu->dt[gi], cu->dt_f[gi]);
         rs = cu->reset[gi] != 0;
-        f = p.group_conv ? wp<T>(cu->gf[gi], cu->gf_f[gi]) : wp<T>(cu->f, cu->f_f);
-        eps = p.group_conv ? wp<T>(cu->geps[gi], cu->geps_f[gi]) : wp<T>(cu->eps, cu->eps_f);
+        f = wp<T>(cu->f, cu->f_f);
+        eps = wp<T>(cu->eps, cu->eps_f);
+        if (p.group_conv) {
+            f = wp<T>(cu->gf[gi], cu->gf_f[gi]);
+            eps = wp<T>(cu->geps[gi], cu->geps_f[gi]);
+        }
         const Vec4<T> ai = s.A[k];
         const T api[3] = {ai.x, ai.y, ai.z};
         for (int a = 0; a < 3; ++a) {

@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTERACT_MINB : 4)
     const int gi = inrange ? meta_group(mi) : -1;
     const int di = inrange ? meta_dim(mi) : 0;
     // a converged (DONE) instance is frozen: no pair work
-    const bool active = inrange && di > 0 && (p.group_conv ? ctrl->gphase[gi] : ctrl->phase) != PH_DONE;
+    bool active = inrange && di > 0 && ctrl->phase != PH_DONE;
+    if (p.group_conv && active) active = ctrl->gphase[gi] != PH_DONE;   // the group itself converged
     T tg[3] = {T(0), T(0), T(0)};
     if (active && di < D) {
         T xi[3] = {T(0), T(0), T(0)};

@@ -49,6 +49,9 @@ struct Job {
     sph_job_info info;
     std::vector<double> xo, ho;       // results
     std::vector<int32_t> go;
+    bool sampled = false;             // particles drawn on the device at admission (Sec. 3.6)
+    uint64_t seed = 0;
+    std::vector<int64_t> counts;      // per feature, fixed at submission
 };
 
 struct Side {
@@ -87,6 +90,7 @@ double now_s(std::chrono::steady_clock::time_point t0) {
 struct sph_server {
     sph_server_config cfg;
     Side side[2];
+    cudaStream_t samp = nullptr;      // the sampling of descriptor-only jobs
     std::map<int64_t, Job> jobs;
     std::deque<int64_t> queue;
     int64_t next_id = 1;
@@ -99,6 +103,7 @@ namespace {
 void server_free(sph_server* s) {
     for (Side& d : s->side)
         if (d.b) sph_batch_destroy(d.b);
+    if (s->samp) cudaStreamDestroy(s->samp);
 }
 
 // copies a finished job's particles to host memory and empties its instance
@@ -136,6 +141,12 @@ sph_status retire(sph_server* s, Job& j, int64_t id, int32_t state, const sph_re
 
 sph_status admit(sph_server* s, Job& j, int lane) {
     Side& d = s->side[j.side];
+    if (j.sampled && j.x.empty()) {
+        j.x.resize((size_t)j.n * 3);
+        j.g.resize((size_t)j.n);
+        sph_status st = sph_sample_particles(&j.dom, &j.siz, j.seed, j.counts.data(), s->samp, j.x.data(), j.g.data());
+        if (st != SPH_OK) return st;
+    }
     sph_status st = sph_batch_set_problem(d.b, lane, &j.dom, &j.siz, &j.prm);
     if (st != SPH_OK) return st;
     st = sph_batch_set_state(d.b, lane, j.n, j.x.data(), j.g.data(), nullptr, j.h.empty() ? nullptr : j.h.data());
@@ -180,6 +191,10 @@ sph_status sph_server_create(const sph_server_config* cfg, sph_server** out) {
     }
     sph_server* s = new sph_server();
     s->cfg = c;
+    if (cudaStreamCreateWithFlags(&s->samp, cudaStreamNonBlocking) != cudaSuccess) {
+        delete s;
+        return sfail(SPH_E_CUDA, "server: cudaStreamCreateWithFlags failed");
+    }
     std::memset(&s->stats, 0, sizeof s->stats);
     s->t0 = std::chrono::steady_clock::now();
     for (int k = 0; k < 2; ++k) {
@@ -232,6 +247,47 @@ sph_status sph_server_submit(sph_server* s, const sph_domain_desc* dom, const sp
     j.x.assign(x, x + n * 3);
     j.g.assign(group, group + n);
     if (h) j.h.assign(h, h + n);
+    std::memset(&j.info, 0, sizeof j.info);
+    j.info.state = SPH_JOB_QUEUED;
+    j.info.n = n;
+    j.info.dim = dom->dim;
+    j.info.t_submit = now_s(s->t0);
+    const int64_t id = s->next_id++;
+    s->jobs.emplace(id, std::move(j));
+    s->queue.push_back(id);
+    s->stats.submitted += 1;
+    *job_id = id;
+    return SPH_OK;
+}
+
+sph_status sph_server_submit_sampled(sph_server* s, const sph_domain_desc* dom, const sph_sizing_desc* siz,
+                                     const sph_params* prm, uint64_t seed, int64_t max_iters, int64_t* job_id) {
+    if (!s || !dom || !siz || !prm || !job_id) return sfail(SPH_E_INVALID, "submit: NULL argument");
+    if (dom->dim != 2 && dom->dim != 3) return sfail(SPH_E_INVALID, "submit: dim must be 2 or 3");
+    if (dom->n_features < 1 || dom->n_features > SPH_MAX_FEATURES) return sfail(SPH_E_INVALID, "submit: n_features out of range");
+    const int k = dom->dim == 2 ? 0 : 1;
+    if (!s->side[k].b) return sfail(SPH_E_INVALID, "submit: the server holds no %dD capacity", dom->dim);
+    if (prm->precision != s->cfg.precision) return sfail(SPH_E_INVALID, "submit: precision differs from the server's");
+    if (max_iters < 0) return sfail(SPH_E_INVALID, "submit: max_iters < 0");
+    std::vector<int64_t> counts(dom->n_features);
+    sph_status st = sph_feature_counts(dom, siz, s->samp, nullptr, counts.data());
+    if (st != SPH_OK) return st;
+    int64_t n = 0;
+    for (int64_t c : counts) n += c;
+    if (n < 1) return sfail(SPH_E_INVALID, "submit: the problem holds no particle");
+    if (slots_of(n) > s->side[k].slot_cap)
+        return sfail(SPH_E_INVALID, "submit: %lld particles never fit the %lld slots of the server", (long long)n,
+                     (long long)s->side[k].slot_cap);
+    Job j;
+    j.dom = *dom;
+    j.siz = *siz;
+    j.prm = *prm;
+    j.n = n;
+    j.max_iters = max_iters;
+    j.side = k;
+    j.sampled = true;
+    j.seed = seed;
+    j.counts = std::move(counts);
     std::memset(&j.info, 0, sizeof j.info);
     j.info.state = SPH_JOB_QUEUED;
     j.info.n = n;

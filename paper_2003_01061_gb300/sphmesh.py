@@ -104,7 +104,7 @@ EXPORTS = ["sph_params_default", "sph_params_preset", "sph_feature_counts", "sph
            "sph_batch_run_until_converged", "sph_batch_positions", "sph_batch_reports", "sph_batch_set_timing",
            "sph_batch_kernel_times", "sph_batch_destroy", "sph_batch_slot_bytes", "sph_batch_autotune",
            "sph_mesh_snapshot", "sph_mesh_restore", "sph_batch_snapshot", "sph_batch_restore", "sph_server_create",
-           "sph_server_submit", "sph_server_poll", "sph_server_drain", "sph_server_job", "sph_server_release",
+           "sph_server_submit", "sph_server_submit_sampled", "sph_server_poll", "sph_server_drain", "sph_server_job", "sph_server_release",
            "sph_server_destroy"]
 
 _lib = None
@@ -160,6 +160,7 @@ def lib():
             "sph_batch_restore": [vp, i32, vp, C.c_size_t],
             "sph_server_create": [vp, vp],
             "sph_server_submit": [vp, vp, vp, vp, i64, vp, vp, vp, i64, vp],
+            "sph_server_submit_sampled": [vp, vp, vp, vp, C.c_uint64, i64, vp],
             "sph_server_poll": [vp, vp],
             "sph_server_drain": [vp, i64, vp],
             "sph_server_job": [vp, i64, vp, vp, vp, vp, i64],
@@ -546,6 +547,14 @@ def sph_server_submit(s, domain: sph_domain_desc, sizing: sph_sizing_desc, param
     return jid.value
 
 
+def sph_server_submit_sampled(s, domain: sph_domain_desc, sizing: sph_sizing_desc, params: sph_params, seed: int,
+                              max_iters=1000):
+    jid = C.c_int64(0)
+    _check(lib().sph_server_submit_sampled(s, C.addressof(domain), C.addressof(sizing), C.addressof(params), seed,
+                                           int(max_iters), C.addressof(jid)))
+    return jid.value
+
+
 def sph_server_poll(s) -> sph_server_stats:
     st = sph_server_stats()
     _check(lib().sph_server_poll(s, C.addressof(st)))
@@ -691,6 +700,14 @@ class Server:
                                 params_struct(params or w["params"], self.precision), w["x"], w["group"], h,
                                 max_iters)
         self.n_of[jid] = len(w["x"])
+        return jid
+
+    def submit_sampled(self, w, max_iters, seed, params: dict | None = None):
+        """A job given by its problem alone; its particles are drawn on the device at admission."""
+        jid = sph_server_submit_sampled(self.h, domain_desc(w["domain"]), sizing_desc(w["sizing"]),
+                                        params_struct(params or w["params"], self.precision), seed, max_iters)
+        _, N = sph_feature_counts(domain_desc(w["domain"]), sizing_desc(w["sizing"]))
+        self.n_of[jid] = int(N.sum())
         return jid
 
     def poll(self):

@@ -94,3 +94,27 @@ def test_server_rejects_and_fails_cleanly():
     p, _, _, _ = run_alone(w2, 50)
     assert np.array_equal(res["x"], p["x"])
     srv.close()
+
+
+def test_sampled_jobs_match_alone():
+    # jobs given by their problem alone: the server draws their particles on the device at
+    # admission; each result equals the same problem sampled with the same seed and run alone
+    js = [(WL.square2d(h=0.05, seed=61), 60, 3), (WL.disk_holes(n_target=3000, seed=62, mc_samples=50_000), 40, 4),
+          (WL.cube_sphere(n_target=4000, seed=63, mc_samples=50_000), 20, 5)]
+    srv = S.Server(precision=32, max_jobs=2, slot_capacity=(8192, 8192), steps_per_poll=20)
+    ids = [srv.submit_sampled(w, it, seed) for w, it, seed in js]
+    st = srv.drain(10000)
+    assert st.finished == len(js)
+    for jid, (w, it, seed) in zip(ids, js):
+        info, res = srv.job(jid)
+        m = S.Mesh(w, precision=32, max_particles=srv.n_of[jid])
+        assert m.sample(seed) == srv.n_of[jid] == info.n
+        ok, it_alone = S.sph_mesh_run_until_converged(m.h, it)
+        p = m.positions()
+        assert info.iterations == it_alone
+        for k in ("x", "h", "group"):
+            assert np.array_equal(res[k], p[k]), (jid, k)
+        assert info.t_submit <= info.t_admit <= info.t_finish
+        m.close()
+        srv.release(jid)
+    srv.close()
