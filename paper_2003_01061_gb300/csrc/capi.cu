@@ -480,9 +480,9 @@ template <typename T> void set_cell_arrays(sph_batch* b) {
     s.count = (int*)take(b->cell_cap * 4);
     s.cell_start = (int*)take((b->cell_cap + 1) * 4);
     s.bsum = (int*)take((size_t)SCAN_TILE * 4);
-    s.tstate = (unsigned long long*)take((size_t)div_up((long long)b->cell_cap, SCAN_TILE) * 8);
+    s.tstate = (unsigned long long*)take((size_t)div_up((long long)b->cell_cap, SCAN1_TILE) * 8);
     s.ticket = (int*)take(4);
-    s.ntile = div_up(b->ncell, SCAN_TILE);
+    s.ntile = div_up(b->ncell, SCAN1_TILE);
     s.occ = (unsigned*)take(b->occ_cap * 4);
     s.ncell = b->ncell;
     s.nocc = b->nocc;
@@ -530,7 +530,7 @@ sph_status relayout(sph_batch* b, int changed, int new_n, int desc) {
         const size_t kc = std::max({(size_t)keys, b->cell_cap, (size_t)1});
         const size_t oc = std::max({(size_t)occ, b->occ_cap, (size_t)1});
         const size_t bytes = kc * 4 + (kc + 1) * 4 + (size_t)SCAN_TILE * 4 + oc * 4 +
-                             (size_t)div_up((long long)kc, SCAN_TILE) * 8 + 4 + 6 * 256;
+                             (size_t)div_up((long long)kc, SCAN1_TILE) * 8 + 4 + 6 * 256;
         void* p = nullptr;
         if (cudaMalloc(&p, bytes) != cudaSuccess)
             return fail(SPH_E_NOMEM, "device allocation of %zu bytes of cell arrays failed", bytes);
@@ -589,7 +589,7 @@ sph_status relayout(sph_batch* b, int changed, int new_n, int desc) {
     CK(cudaMemsetAsync(b->prec == 32 ? sf.count : sd.count, 0, (size_t)std::max<long long>(keys, 1) * 4, b->stream));
     CK(cudaMemsetAsync(b->prec == 32 ? sf.cell_start : sd.cell_start, 0, (size_t)(keys + 1) * 4, b->stream));
     CK(cudaMemsetAsync(b->prec == 32 ? sf.occ : sd.occ, 0, (size_t)std::max<long long>(occ, 1) * 4, b->stream));
-    CK(cudaMemsetAsync(b->prec == 32 ? sf.tstate : sd.tstate, 0, (size_t)div_up(std::max<long long>(keys, 1), SCAN_TILE) * 8,
+    CK(cudaMemsetAsync(b->prec == 32 ? sf.tstate : sd.tstate, 0, (size_t)div_up(std::max<long long>(keys, 1), SCAN1_TILE) * 8,
                        b->stream));
     CK(cudaMemsetAsync(b->prec == 32 ? sf.ticket : sd.ticket, 0, 4, b->stream));
     std::vector<Grid> g(NI);

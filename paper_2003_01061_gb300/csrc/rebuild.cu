@@ -146,11 +146,11 @@ template <typename T> __global__ void __launch_bounds__(SCAN_THREADS) k_scan_one
     const int ncell = s.ncell;
     // occupancy bits are rebuilt by the gather
     for (int t = tile * SCAN_THREADS + threadIdx.x; t < s.nocc; t += gridDim.x * SCAN_THREADS) s.occ[t] = 0u;
-    const int base = tile * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
-    int loc[SCAN_ITEMS];
+    const int base = tile * SCAN1_TILE + threadIdx.x * SCAN1_ITEMS;
+    int loc[SCAN1_ITEMS];
     int v = 0;
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
+    for (int k = 0; k < SCAN1_ITEMS; ++k) {
         loc[k] = 0;
         if (base + k < ncell) loc[k] = s.count[base + k] - s.cell_start[base + k + 1];
         v += loc[k];
@@ -200,14 +200,14 @@ template <typename T> __global__ void __launch_bounds__(SCAN_THREADS) k_scan_one
     __syncthreads();
     ex += sh_prefix;
 #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
+    for (int k = 0; k < SCAN1_ITEMS; ++k) {
         if (base + k < ncell) {
             s.cell_start[base + k] = ex;
             s.count[base + k] = ex;    // scatter cursor
         }
         ex += loc[k];
     }
-    if (base + SCAN_ITEMS >= ncell && base < ncell) s.cell_start[ncell] = ex;   // the thread holding the last cell
+    if (base + SCAN1_ITEMS >= ncell && base < ncell) s.cell_start[ncell] = ex;   // the thread holding the last cell
 }
 
 // ---- scatter into cells (order inside a cell fixed afterwards) ----
@@ -395,7 +395,7 @@ void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(ncell, count, bsum, cell_start);
 }
 template <typename T> void launch_scan_onepass(const State<T>& s, cudaStream_t st) {
-    k_scan_onepass<T><<<div_up(s.ncell, SCAN_TILE), SCAN_THREADS, 0, st>>>(s);
+    k_scan_onepass<T><<<div_up(s.ncell, SCAN1_TILE), SCAN_THREADS, 0, st>>>(s);
 }
 template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st, bool pdl) {
     launch_k(k_scatter<T>, div_up(s.n, BLOCK), BLOCK, st, pdl, s);

@@ -203,6 +203,12 @@ __device__ __forceinline__ void own_cell(const Grid& g, const State<T>& s, int k
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+// cells per thread and per tile of the step's one-pass scan
+#ifndef SPH_SCAN1_ITEMS
+#define SPH_SCAN1_ITEMS 4
+#endif
+constexpr int SCAN1_ITEMS = SPH_SCAN1_ITEMS;
+constexpr int SCAN1_TILE = SCAN_THREADS * SCAN1_ITEMS;
 
 inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 

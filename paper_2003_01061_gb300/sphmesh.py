@@ -706,8 +706,7 @@ class Server:
         """A job given by its problem alone; its particles are drawn on the device at admission."""
         jid = sph_server_submit_sampled(self.h, domain_desc(w["domain"]), sizing_desc(w["sizing"]),
                                         params_struct(params or w["params"], self.precision), seed, max_iters)
-        _, N = sph_feature_counts(domain_desc(w["domain"]), sizing_desc(w["sizing"]))
-        self.n_of[jid] = int(N.sum())
+        self.n_of[jid] = int(sph_server_job(self.h, jid, 0)[0].n)   # the count the server fixed
         return jid
 
     def poll(self):
