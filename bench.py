@@ -28,7 +28,9 @@ hole (0.004-0.04 scaled to ~120k particles), FP32 pair sums with FP64 projection
           Eqs. 10, 11 and rho_t-proportional sampling, Sec. 3.6), beside the host generator.
 * method_presets: the comparison of Sec. 4.1 on its Square (Eq. 25 sizing): iterations to the
           Phase-One target and to the end for the improved method and the earlier method's two
-          presets (velocities zeroed every step / every 100 steps, no feature-boundary sum).
+          presets (velocities zeroed every step / every 100 steps, no feature-boundary sum), and
+          the Cube of Sec. 4 (Eq. 28) for the paper's iteration counts, each final state's mesh
+          quality beside the paper's tables.
 Multi-GPU (torchrun): every rank runs an independent replica (weak scaling, no collective on
 the data path); value = particles of all ranks x K / max rank time.
 """
@@ -298,11 +300,12 @@ def run_ours(args):
         t0 = time.perf_counter()
         cube_w = generate([(4, 1_200_000, 3, 0.3)])[0]
         gen_s = time.perf_counter() - t0
-    preset_w = None
+    preset_w = cube_case_w = None
     if rank == 0 and not args.no_presets:
         from paper_2003_01061_gb300 import workloads as WL
 
         preset_w = WL.square_radial(seed=6)
+        cube_case_w = WL.cube_radial(seed=7)
     if rank == 0 and not args.no_batch:
         specs, _ = _specs(64, 4, 1_000, 200_000, alternate=True)
         batch_ws = generate(specs)
@@ -400,6 +403,7 @@ def run_ours(args):
     presets = None
     if preset_w is not None:
         presets = presets_run(S, preset_w, args.preset_iters)
+        presets["cube_case"] = cube_case_run(S, cube_case_w)
 
     sampling = None
     if cube_w is not None:
@@ -587,6 +591,73 @@ def sampling_run(S, w, gen_s, with_oracle=True):
                          "sample": f"first {m} volume particles of the same problem and seed"}
     out["config"] = {"workload": "cube_sphere_3d_1.2M descriptors (seed 3): counts by the midpoint rule "
                                  "(256^3 volume cells), Philox4x32-10 seed 1"}
+    return out
+
+
+def mesh_quality_3d(w, x):
+    """Quality of the Delaunay tetrahedralisation of final 3D positions with the measures of
+    Sec. 4: dihedral angles and the radius ratio gamma = 3 r_in / r_circ; tetrahedra whose
+    centroid lies outside the domain, and flat ones (volume below 1e-9 of the mean), are
+    dropped.  Measurement only: the method never tetrahedralises."""
+    from scipy.spatial import Delaunay
+
+    from paper_2003_01061_gb300 import workloads as WL
+
+    T = x[Delaunay(x).simplices]
+    T = T[WL.domain_phi(w["domain"], T.mean(axis=1)) > 0]
+    a, b, c = T[:, 1] - T[:, 0], T[:, 2] - T[:, 0], T[:, 3] - T[:, 0]
+    trip = np.einsum("ij,ij->i", a, np.cross(b, c))
+    vol = np.abs(trip) / 6.0
+    keep = vol > 1e-9 * vol.mean()
+    T, a, b, c, trip, vol = T[keep], a[keep], b[keep], c[keep], trip[keep], vol[keep]
+    alpha = (np.einsum("ij,ij->i", a, a)[:, None] * np.cross(b, c) + np.einsum("ij,ij->i", b, b)[:, None] * np.cross(c, a)
+             + np.einsum("ij,ij->i", c, c)[:, None] * np.cross(a, b))
+    r_circ = np.linalg.norm(alpha, axis=1) / (2.0 * np.abs(trip))
+    area = 0.0
+    for f in ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2)):
+        area = area + 0.5 * np.linalg.norm(np.cross(T[:, f[1]] - T[:, f[0]], T[:, f[2]] - T[:, f[0]]), axis=1)
+    gamma = 3.0 * (3.0 * vol / area) / r_circ
+    dih = []
+    for i, j, k, l in ((0, 1, 2, 3), (0, 2, 1, 3), (0, 3, 1, 2), (1, 2, 0, 3), (1, 3, 0, 2), (2, 3, 0, 1)):
+        e = T[:, j] - T[:, i]
+        e = e / np.linalg.norm(e, axis=1, keepdims=True)
+        u, v = T[:, k] - T[:, i], T[:, l] - T[:, i]
+        u = u - np.einsum("ij,ij->i", u, e)[:, None] * e
+        v = v - np.einsum("ij,ij->i", v, e)[:, None] * e
+        cosang = np.einsum("ij,ij->i", u, v) / (np.linalg.norm(u, axis=1) * np.linalg.norm(v, axis=1))
+        dih.append(np.degrees(np.arccos(np.clip(cosang, -1, 1))))
+    dih = np.stack(dih, 1)
+    tmin = dih.min(axis=1)
+    return {"theta_min": float(dih.min()), "theta_max": float(dih.max()), "gamma_min": float(gamma.min()),
+            "gamma_avg": float(gamma.mean()), "theta_min_avg": float(tmin.mean()),
+            "theta_lt10": int((tmin < 10).sum()), "theta_lt20": int((tmin < 20).sum()),
+            "theta_lt30": int((tmin < 30).sum()), "theta_lt40": int((tmin < 40).sum()), "N_tet": int(len(T))}
+
+
+def cube_case_run(S, w):
+    """The Cube of Sec. 4 (Eq. 28): the improved method for the paper's 7,000 iterations and
+    the earlier method (fu2019 preset) for its 28,800, from the same initial particles; the
+    mesh quality of both final states beside the paper's table."""
+    from paper_2003_01061_gb300 import workloads as WL
+
+    out = {}
+    for name, iters in (("improved", 7000), ("fu2019", 28800)):
+        m = S.Mesh(w, precision=32, params=WL.method_preset(w["params"], name))
+        m.set_state()
+        m.sync()
+        t0 = time.perf_counter()
+        ok, it = S.sph_mesh_run_until_converged(m.h, iters)
+        wall = time.perf_counter() - t0
+        r = m.report()
+        out[name] = {"iters": int(it), "done": bool(ok), "wall_s": wall, "escapes": int(r.escapes),
+                     "E_sys": float(r.E_sys), "phase": int(r.phase),
+                     "quality": mesh_quality_3d(w, m.positions()["x"])}
+        m.close()
+    out["initial_quality"] = mesh_quality_3d(w, w["x"])
+    with open(os.path.join(ROOT, "tests", "golden", "paper_cases.json")) as f:
+        out["paper_table"] = json.load(f)["cube_table"]
+    out["config"] = {"workload": f"cube_radial_3d: [0,100]^3, Eq. 28 sizing (h 0.488-4.88), {len(w['x'])} "
+                                 f"particles (seed 7), FP32, paper controller"}
     return out
 
 

@@ -1567,7 +1567,7 @@ sph_status sample_impl(const sph_domain_desc* dd, const sph_sizing_desc* sz, uin
     if (n > ((int64_t)1 << 30)) return fail(SPH_E_INVALID, "sample: %lld particles is too many", (long long)n);
     double* d_x = nullptr;
     CK(cudaMallocAsync((void**)&d_x, sizeof(double) * 3 * (size_t)std::max<int64_t>(n, 1), st));
-    cudaError_t e = sample_features(P.I.dom, P.d_dom, P.d_siz, seed, counts, st, d_x);
+    cudaError_t e = sample_features(P.I.dom, P.I.siz, P.d_dom, P.d_siz, seed, counts, st, d_x);
     if (e == cudaSuccess) e = cudaMemcpyAsync(x_out, d_x, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(d_x, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

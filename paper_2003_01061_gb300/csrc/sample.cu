@@ -308,24 +308,30 @@ int quad_points(int kind, int D, long long* npts) {
 
 cudaError_t feature_integrals(const Domain& dm, const Domain* d_dom, const Sizing* d_siz, cudaStream_t st,
                               double* integral) {
+    // every feature's partial sums in one buffer, one copy back and one wait for all of them
     constexpr int NB = 4 * 152;
     double* d_part = nullptr;
-    cudaError_t e = cudaMallocAsync(&d_part, sizeof(double) * NB, st);
+    const size_t np = (size_t)NB * std::max(dm.nf, 1);
+    cudaError_t e = cudaMallocAsync(&d_part, sizeof(double) * np, st);
     if (e != cudaSuccess) return e;
-    std::vector<double> part(NB);
+    std::vector<double> part(np, 0.0);
+    e = cudaMemsetAsync(d_part, 0, sizeof(double) * np, st);
     for (int k = 0; k < dm.nf && e == cudaSuccess; ++k) {
+        if (dm.f[k].kind == SPH_FEAT_POINT) continue;
+        long long npts = 0;
+        const int nq = quad_points(dm.f[k].kind, dm.D, &npts);
+        k_feature_integral<<<NB, SB, 0, st>>>(d_dom, d_siz, k, npts, nq, d_part + (size_t)k * NB);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(part.data(), d_part, sizeof(double) * np, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (int k = 0; k < dm.nf; ++k) {
         if (dm.f[k].kind == SPH_FEAT_POINT) {
             integral[k] = 1.0;
             continue;
         }
-        long long npts = 0;
-        const int nq = quad_points(dm.f[k].kind, dm.D, &npts);
-        k_feature_integral<<<NB, SB, 0, st>>>(d_dom, d_siz, k, npts, nq, d_part);
-        e = cudaMemcpyAsync(part.data(), d_part, sizeof(double) * NB, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        double s = 0.0;
-        for (int b = 0; b < NB; ++b) s += part[b];
-        integral[k] = s;
+        double sum = 0.0;
+        for (int b = 0; b < NB; ++b) sum += part[(size_t)k * NB + b];
+        integral[k] = sum;
     }
     cudaError_t f = cudaFreeAsync(d_part, st);
     if (e == cudaSuccess) e = f;
@@ -333,36 +339,90 @@ cudaError_t feature_integrals(const Domain& dm, const Domain* d_dom, const Sizin
     return e;
 }
 
-cudaError_t sample_features(const Domain& dm, const Domain* d_dom, const Sizing* d_siz, unsigned long long seed,
-                            const int64_t* counts, cudaStream_t st, double* d_out) {
-    constexpr long long BATCH = 1LL << 22;   // candidates per pass
-    constexpr int NBLK = (int)(BATCH / SB);
+// Expected fraction of accepted candidates of feature k when it holds n particles (n is close to
+// the integral of rho_t, so the acceptance (h_min/h)^d averages to n h_min^d / measure), times
+// the fraction its geometry keeps (the disc in its square, the ball in its cube)
+double acceptance_estimate(const Domain& dm, const Sizing& z, int k, long long n) {
+    const Feat& f = dm.f[k];
+    const int d = f.dim;
+    double meas = 1.0, geo = 1.0;
+    switch (f.kind) {
+        case SPH_FEAT_VOLUME:
+            for (int a = 0; a < dm.D; ++a) meas *= dm.hi[a] - dm.lo[a];
+            break;
+        case SPH_FEAT_SEGMENT: {
+            double L2 = 0.0;
+            for (int a = 0; a < 3; ++a) L2 += (f.g[3 + a] - f.g[a]) * (f.g[3 + a] - f.g[a]);
+            meas = std::sqrt(L2);
+            break;
+        }
+        case SPH_FEAT_CIRCLE:
+            meas = 2.0 * CUDART_PI * f.g[2];
+            geo = CUDART_PI / 4.0;
+            break;
+        case SPH_FEAT_RECT:
+            meas = f.g[9] * f.g[10];
+            break;
+        case SPH_FEAT_SPHERE:
+            meas = 4.0 * CUDART_PI * f.g[3] * f.g[3];
+            geo = CUDART_PI / 6.0;
+            break;
+        default:
+            return 1.0;
+    }
+    const double p = geo * (double)n * std::pow(z.lo, d) / meas;
+    return std::min(1.0, std::max(p, 1e-9));
+}
+
+cudaError_t sample_features(const Domain& dm, const Sizing& z, const Domain* d_dom, const Sizing* d_siz,
+                            unsigned long long seed, const int64_t* counts, cudaStream_t st, double* d_out) {
+    // candidates per pass: enough for the remaining count at the expected acceptance, so that
+    // one pass (one host round trip) usually suffices; a short pass is followed by another one
+    // sized by the acceptance seen so far.  The result does not depend on the pass sizes: it is
+    // always the first accepted candidates in candidate order.
+    constexpr long long MAXB = 1LL << 26;
     int* d_cnt = nullptr;
     long long* d_off = nullptr;
-    cudaError_t e = cudaMallocAsync(&d_cnt, sizeof(int) * NBLK, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&d_off, sizeof(long long) * NBLK, st);
-    std::vector<int> cnt(NBLK);
-    std::vector<long long> off(NBLK);
+    cudaError_t e = cudaMallocAsync(&d_cnt, sizeof(int) * (MAXB / SB), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_off, sizeof(long long) * (MAXB / SB), st);
+    std::vector<int> cnt(MAXB / SB);
+    std::vector<long long> off(MAXB / SB);
     long long base = 0;
     for (int k = 0; k < dm.nf && e == cudaSuccess; ++k) {
         const long long want = counts[k];
-        long long got = 0, c0 = 0;
+        if (want > 0 && dm.f[k].kind == SPH_FEAT_POINT) {   // the point itself
+            double x[3] = {0.0, 0.0, 0.0};
+            for (int a = 0; a < dm.D; ++a) x[a] = dm.f[k].g[a];
+            e = cudaMemcpyAsync(d_out + 3 * base, x, sizeof x, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            base += want;
+            continue;
+        }
+        double p = acceptance_estimate(dm, z, k, want);
+        long long got = 0, c0 = 0, seen = 0, taken = 0;
         while (got < want && e == cudaSuccess) {
-            k_sample_count<<<NBLK, SB, 0, st>>>(d_dom, d_siz, k, seed, c0, BATCH, d_cnt);
-            e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int) * NBLK, cudaMemcpyDeviceToHost, st);
+            const double need = (double)(want - got) / p;
+            long long nc = (long long)(1.05 * need + 6.0 * std::sqrt(need)) + 4096;
+            nc = std::min(MAXB, (nc + SB - 1) / SB * SB);
+            const int nblk = (int)(nc / SB);
+            k_sample_count<<<nblk, SB, 0, st>>>(d_dom, d_siz, k, seed, c0, nc, d_cnt);
+            e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int) * nblk, cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) break;
             long long run = got;
-            for (int b = 0; b < NBLK; ++b) {
+            for (int b = 0; b < nblk; ++b) {
                 off[b] = run;
                 run += cnt[b];
             }
-            e = cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * NBLK, cudaMemcpyHostToDevice, st);
+            e = cudaMemcpyAsync(d_off, off.data(), sizeof(long long) * nblk, cudaMemcpyHostToDevice, st);
             if (e != cudaSuccess) break;
-            k_sample_emit<<<NBLK, SB, 0, st>>>(d_dom, d_siz, k, seed, c0, BATCH, d_off, want, d_out + 3 * base);
+            k_sample_emit<<<nblk, SB, 0, st>>>(d_dom, d_siz, k, seed, c0, nc, d_off, want, d_out + 3 * base);
             e = cudaStreamSynchronize(st);   // off is reused by the next pass
+            seen += nc;
+            taken += run - got;
             got = std::min(run, want);
-            c0 += BATCH;
+            c0 += nc;
+            p = std::max(1e-9, (double)std::max<long long>(taken, 1) / (double)seen);
             if (got < want && c0 >= (1LL << 36)) e = cudaErrorInvalidValue;   // acceptance too small
         }
         base += want;

@@ -238,6 +238,62 @@ def square_radial(seed: int = 6, params: dict | None = None, mc_samples: int = 4
     return _finish("square_radial", dom, siz, feats, xs, gs, params or PAPER_PARAMS, h_lo=hmin, h_hi=hmax)
 
 
+def cube_radial(seed: int = 7, params: dict | None = None, mc_samples: int = 400_000):
+    """The Cube of Sec. 4: [0,100]^3 with h_t = (h_max - h_min)/(100 sqrt 3) |x - (100,100,100)|
+    + h_min (Eq. 28), h_min = 0.488, h_max = 4.88; 6 faces, 12 edges, 8 fixed corners, the volume.
+    Particles by rejection sampling proportional to rho_t = h_t^-d per feature, counts from the
+    integrals of rho_t (Eqs. 10, 11).  The paper's own initial distribution is not given."""
+    rng = np.random.default_rng(seed)
+    L, hmin, hmax = 100.0, 0.488, 4.88
+    dom = dict(D=3, base="box", lo=[0.0, 0.0, 0.0], hi=[L, L, L], ball_c=[0, 0, 0], ball_r=0.0, holes=[])
+    siz = dict(kind="radial", a=hmin, b=(hmax - hmin) / (L * math.sqrt(3.0)), lo=hmin, hi=hmax, q=[L, L, L], refs=[])
+    s2, s3 = 1.0 / math.sqrt(2.0), 1.0 / math.sqrt(3.0)
+    faces, edges, corners = [], [], []
+    for ax in range(3):
+        for side in (0.0, L):
+            o = np.zeros(3); o[ax] = side
+            u = np.zeros(3); u[(ax + 1) % 3] = 1.0
+            w = np.zeros(3); w[(ax + 2) % 3] = 1.0
+            nb = np.zeros(3); nb[ax] = 1.0 if side == L else -1.0
+            faces.append(dict(kind="rect", dim=2, o=o.tolist(), u=u.tolist(), w=w.tolist(), lu=L, lw=L, nb=nb.tolist()))
+    for ax in range(3):
+        for s1 in (0.0, L):
+            for s2_ in (0.0, L):
+                a = np.zeros(3); b = np.zeros(3)
+                a[(ax + 1) % 3] = b[(ax + 1) % 3] = s1
+                a[(ax + 2) % 3] = b[(ax + 2) % 3] = s2_
+                b[ax] = L
+                nb = np.zeros(3)
+                nb[(ax + 1) % 3] = s2 if s1 == L else -s2
+                nb[(ax + 2) % 3] = s2 if s2_ == L else -s2
+                edges.append(dict(kind="segment", dim=1, a=a.tolist(), b=b.tolist(), nb=nb.tolist()))
+    for cx in (0.0, L):
+        for cy in (0.0, L):
+            for cz in (0.0, L):
+                corners.append(dict(kind="point", dim=0, p=[cx, cy, cz], nb=[s3 if c == L else -s3 for c in (cx, cy, cz)]))
+    nv = int(round(_mc_volume_count(np.random.default_rng(seed + 100), dom, siz, mc_samples)))
+    xs, gs = [_sample_volume(rng, dom, siz, nv, hmin)], [np.zeros(nv)]
+    for k, f in enumerate(faces):
+        m = 256
+        st = (np.arange(m) + 0.5) / m * L
+        S, T = np.meshgrid(st, st, indexing="ij")
+        P = np.asarray(f["o"]) + S.ravel()[:, None] * np.asarray(f["u"]) + T.ravel()[:, None] * np.asarray(f["w"])
+        cnt = int(round(float(np.sum(sizing_eval(siz, P) ** -2.0)) * (L / m) ** 2))
+        xs.append(_sample_rect(rng, f, siz, cnt, hmin))
+        gs.append(np.full(cnt, 1 + k))
+    for k, e in enumerate(edges):
+        a_, b_ = np.asarray(e["a"]), np.asarray(e["b"])
+        at = lambda t, a_=a_, b_=b_: a_ + (t / L)[:, None] * (b_ - a_)
+        cnt = int(round(_count_curve(L, at, siz)))
+        xs.append(_line_positions(rng, cnt, L, at, siz))
+        gs.append(np.full(cnt, 7 + k))
+    for k, c in enumerate(corners):
+        xs.append(np.array([c["p"]], float))
+        gs.append(np.full(1, 19 + k))
+    feats = [dict(kind="volume", dim=3)] + faces + edges + corners
+    return _finish("cube_radial", dom, siz, feats, xs, gs, params or PAPER_PARAMS, h_lo=hmin, h_hi=hmax)
+
+
 def _disk_holes_geometry(rng, n_holes=3):
     holes = []
     while len(holes) < n_holes:
