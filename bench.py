@@ -29,8 +29,8 @@ hole (0.004-0.04 scaled to ~120k particles), FP32 pair sums with FP64 projection
 * method_presets: the comparison of Sec. 4.1 on its Square (Eq. 25 sizing): iterations to the
           Phase-One target and to the end for the improved method and the earlier method's two
           presets (velocities zeroed every step / every 100 steps, no feature-boundary sum), and
-          the Cube of Sec. 4 (Eq. 28) for the paper's iteration counts, each final state's mesh
-          quality beside the paper's tables.
+          the Cube (Eq. 28) and Sphere01 cases of Sec. 4 for the paper's iteration counts, each
+          final state's mesh quality beside the paper's tables.
 Multi-GPU (torchrun): every rank runs an independent replica (weak scaling, no collective on
 the data path); value = particles of all ranks x K / max rank time.
 """
@@ -305,7 +305,7 @@ def run_ours(args):
         from paper_2003_01061_gb300 import workloads as WL
 
         preset_w = WL.square_radial(seed=6)
-        cube_case_w = WL.cube_radial(seed=7)
+        cube_case_w = (WL.cube_radial(seed=7), WL.sphere01(seed=8))
     if rank == 0 and not args.no_batch:
         specs, _ = _specs(64, 4, 1_000, 200_000, alternate=True)
         batch_ws = generate(specs)
@@ -403,7 +403,8 @@ def run_ours(args):
     presets = None
     if preset_w is not None:
         presets = presets_run(S, preset_w, args.preset_iters)
-        presets["cube_case"] = cube_case_run(S, cube_case_w)
+        presets["cube_case"] = case_3d_run(S, cube_case_w[0], "cube_table", {"improved": 7000, "fu2019": 28800})
+        presets["sphere01_case"] = case_3d_run(S, cube_case_w[1], "sphere01_table", {"improved": 4600, "fu2019": 17000})
 
     sampling = None
     if cube_w is not None:
@@ -634,19 +635,19 @@ def mesh_quality_3d(w, x):
             "theta_lt30": int((tmin < 30).sum()), "theta_lt40": int((tmin < 40).sum()), "N_tet": int(len(T))}
 
 
-def cube_case_run(S, w):
-    """The Cube of Sec. 4 (Eq. 28): the improved method for the paper's 7,000 iterations and
-    the earlier method (fu2019 preset) for its 28,800, from the same initial particles; the
-    mesh quality of both final states beside the paper's table."""
+def case_3d_run(S, w, table, iters):
+    """A 3D case of Sec. 4 (the Cube of Eq. 28, Sphere01): the improved method and the earlier
+    method (fu2019 preset) for the paper's iteration counts, from the same initial particles;
+    the mesh quality of both final states beside the paper's table."""
     from paper_2003_01061_gb300 import workloads as WL
 
     out = {}
-    for name, iters in (("improved", 7000), ("fu2019", 28800)):
+    for name in ("improved", "fu2019"):
         m = S.Mesh(w, precision=32, params=WL.method_preset(w["params"], name))
         m.set_state()
         m.sync()
         t0 = time.perf_counter()
-        ok, it = S.sph_mesh_run_until_converged(m.h, iters)
+        ok, it = S.sph_mesh_run_until_converged(m.h, iters[name])
         wall = time.perf_counter() - t0
         r = m.report()
         out[name] = {"iters": int(it), "done": bool(ok), "wall_s": wall, "escapes": int(r.escapes),
@@ -655,9 +656,9 @@ def cube_case_run(S, w):
         m.close()
     out["initial_quality"] = mesh_quality_3d(w, w["x"])
     with open(os.path.join(ROOT, "tests", "golden", "paper_cases.json")) as f:
-        out["paper_table"] = json.load(f)["cube_table"]
-    out["config"] = {"workload": f"cube_radial_3d: [0,100]^3, Eq. 28 sizing (h 0.488-4.88), {len(w['x'])} "
-                                 f"particles (seed 7), FP32, paper controller"}
+        out["paper_table"] = json.load(f)[table]
+    out["config"] = {"workload": f"{w['name']}: {len(w['x'])} particles, FP32, paper controller, "
+                                 f"iterations as in the paper's table"}
     return out
 
 

@@ -294,6 +294,30 @@ def cube_radial(seed: int = 7, params: dict | None = None, mc_samples: int = 400
     return _finish("cube_radial", dom, siz, feats, xs, gs, params or PAPER_PARAMS, h_lo=hmin, h_hi=hmax)
 
 
+def sphere01(seed: int = 8, params: dict | None = None, mc_samples: int = 400_000):
+    """The Sphere01 case of Sec. 4: a ball of radius R = 45 with h_t = (h_max - h_min)/(2R)
+    |x - x_1| + h_min, x_1 a point of the sphere (here (R, 0, 0)), h_min = 0.375, h_max = 7.5;
+    the volume and the sphere surface.  Particles by rejection sampling proportional to rho_t
+    per feature, counts from the integrals of rho_t (Eqs. 10, 11).  The paper's own initial
+    distribution is not given."""
+    rng = np.random.default_rng(seed)
+    R, hmin, hmax = 45.0, 0.375, 7.5
+    dom = dict(D=3, base="ball", lo=[-R, -R, -R], hi=[R, R, R], ball_c=[0.0, 0.0, 0.0], ball_r=R, holes=[])
+    siz = dict(kind="radial", a=hmin, b=(hmax - hmin) / (2 * R), lo=hmin, hi=hmax, q=[R, 0.0, 0.0], refs=[])
+    sphere = dict(kind="sphere", dim=2, c=[0.0, 0.0, 0.0], r=R, orient=1.0)
+    nv = int(round(_mc_volume_count(np.random.default_rng(seed + 100), dom, siz, mc_samples)))
+    m = 512
+    th = (np.arange(m) + 0.5) / m * math.pi
+    ph = (np.arange(2 * m) + 0.5) / m * math.pi
+    TH, PH = np.meshgrid(th, ph, indexing="ij")
+    P = R * np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)], -1).reshape(-1, 3)
+    ns = int(round(float(np.sum(np.sin(TH).ravel() * sizing_eval(siz, P) ** -2.0)) * R * R * (math.pi / m) ** 2))
+    xs = [_sample_volume(rng, dom, siz, nv, hmin), _sample_sphere(rng, sphere, siz, ns, hmin)]
+    gs = [np.zeros(nv), np.full(ns, 1)]
+    return _finish("sphere01", dom, siz, [dict(kind="volume", dim=3), sphere], xs, gs, params or PAPER_PARAMS,
+                   h_lo=hmin, h_hi=hmax)
+
+
 def _disk_holes_geometry(rng, n_holes=3):
     holes = []
     while len(holes) < n_holes:
