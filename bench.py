@@ -642,12 +642,12 @@ def case_3d_run(S, w, table, iters):
     from paper_2003_01061_gb300 import workloads as WL
 
     out = {}
-    for name in ("improved", "fu2019"):
-        m = S.Mesh(w, precision=32, params=WL.method_preset(w["params"], name))
+    for name, over in (("improved", {}), ("improved_threshold1e-2", {"threshold": 1e-2}), ("fu2019", {})):
+        m = S.Mesh(w, precision=32, params=dict(WL.method_preset(w["params"], name.split("_")[0]), **over))
         m.set_state()
         m.sync()
         t0 = time.perf_counter()
-        ok, it = S.sph_mesh_run_until_converged(m.h, iters[name])
+        ok, it = S.sph_mesh_run_until_converged(m.h, iters[name.split("_")[0]])
         wall = time.perf_counter() - t0
         r = m.report()
         out[name] = {"iters": int(it), "done": bool(ok), "wall_s": wall, "escapes": int(r.escapes),
@@ -672,10 +672,12 @@ def presets_run(S, w, max_iters):
     out = {}
     # the improved method also with Phase-One damping eps1 = 0.1 and 0.2 (Sec. 3.4.3 suggests
     # [0, 0.2] for ill-posed initial samplings; the earlier method has no damping)
-    runs = [("improved", "improved", 0.0), ("improved_eps0.1", "improved", 0.1), ("improved_eps0.2", "improved", 0.2),
-            ("fu2019_v2", "fu2019_v2", 0.0), ("fu2019", "fu2019", 0.0)]
-    for label, name, eps in runs:
-        m = S.Mesh(w, precision=32, params=dict(WL.method_preset(w["params"], name), eps1=eps))
+    # and with a threshold the Phase-One oscillation reaches (1e-2), so that Phase Two runs
+    runs = [("improved", "improved", {}), ("improved_eps0.1", "improved", {"eps1": 0.1}),
+            ("improved_eps0.2", "improved", {"eps1": 0.2}), ("improved_threshold1e-2", "improved", {"threshold": 1e-2}),
+            ("fu2019_v2", "fu2019_v2", {}), ("fu2019", "fu2019", {})]
+    for label, name, over in runs:
+        m = S.Mesh(w, precision=32, params=dict(WL.method_preset(w["params"], name), **over))
         m.set_state()
         m.sync()
         t0 = time.perf_counter()
