@@ -100,7 +100,9 @@ typedef struct {
 
 /* Method parameters.  Defaults in brackets are the paper's (see each field). */
 typedef struct {
-    double kappa;          /* support radius r_c = kappa*h of the Wendland C2 kernel      [2]  */
+    double kappa;          /* support radius r_c = kappa*h of the Wendland C2 kernel, h the
+                              target size (the paper leaves r_c/h open: 2.6 = twice a
+                              smoothing length of 1.3 h)                                  [2.6]*/
     double p0;             /* EOS constant P0, Eq. 6                                     [1]  */
     double visc;           /* nu = visc * r_c * |v|, Eq. 8; 0 disables viscosity         [0.1]*/
     double cfl_a;          /* Eq. 24 acceleration constant                               [0.25]*/

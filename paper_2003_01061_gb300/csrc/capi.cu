@@ -1590,7 +1590,7 @@ const char* sph_last_error(void) { return g_err.c_str(); }
 sph_status sph_params_default(sph_params* p) {
     if (!p) return fail(SPH_E_INVALID, "params: NULL");
     std::memset(p, 0, sizeof *p);
-    p->kappa = 2.0;
+    p->kappa = 2.6;
     p->p0 = 1.0;
     p->visc = 0.1;
     p->cfl_a = 0.25;

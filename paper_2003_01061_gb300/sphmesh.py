@@ -287,7 +287,7 @@ def sph_params_preset(params: sph_params, method: int) -> sph_params:
 # ----------------------------------------------------------------------------------------
 # entry points (same names as the C ABI)
 # ----------------------------------------------------------------------------------------
-def sph_grid_spec(dim, lo, hi, h_lo, h_hi, kappa=2.0, cells_per_support=1) -> sph_grid_info:
+def sph_grid_spec(dim, lo, hi, h_lo, h_hi, kappa=2.6, cells_per_support=1) -> sph_grid_info:
     g = sph_grid_info()
     lo = np.ascontiguousarray(lo, dtype=np.float64)
     hi = np.ascontiguousarray(hi, dtype=np.float64)

@@ -28,9 +28,12 @@ import math
 import numpy as np
 
 # Paper defaults (Sec. 2.3, Sec. 3.4): Eq. 8 coefficient, Eq. 9/24 constants, reset period
-# 100, sampling every 20 steps, 10 samples per averaging window, threshold 5e-6.
+# 100, sampling every 20 steps, 10 samples per averaging window, threshold 5e-6.  The paper does
+# not relate the kernel's support r_c to the target size h; r_c = 2.6 h (a Wendland C2 kernel of
+# smoothing length 1.3 h, support twice that) is the reading under which the relaxed meshes reach
+# the quality the paper prints for its Square (mean G 0.92 against 0.95; 0.78 with r_c = 2 h).
 PAPER_PARAMS = dict(
-    kappa=2.0, p0=1.0, visc=0.1, cfl_a=0.25, cfl_v=1.0 / 40.0, eps1=0.0, dt_cap=1e30,
+    kappa=2.6, p0=1.0, visc=0.1, cfl_a=0.25, cfl_v=1.0 / 40.0, eps1=0.0, dt_cap=1e30,
     dt_collapse=0.1, threshold=5e-6, reset_period=100, sample_every=20, window=10,
     ramp_len=200, boundary_rho=1, max_newton=3, boundary_correction=1, group_convergence=0,
 )

@@ -76,7 +76,7 @@ def oracle_grid(w, m):
     """The oracle's grid for the mesh's problem, with the mesh's cells per support."""
     g = S.sph_mesh_grid(m.h)
     return O.grid_spec(w["domain"]["D"], w["domain"]["lo"], w["domain"]["hi"], w["h_lo"], w["h_hi"],
-                       cells_per_support=g.cells_per_support)
+                       kappa=w["params"]["kappa"], cells_per_support=g.cells_per_support)
 
 
 CASES = [("square", 32), ("square", 64), ("disk", 32), ("disk", 64), ("cube", 32), ("cube", 64)]
@@ -126,7 +126,7 @@ def test_neighbor_sets_bit_exact(name, prec, cps, mode):
     rng = np.random.default_rng(1)
     idx = np.arange(n) if n <= 3000 else np.sort(rng.choice(n, 1500, replace=False))
     for i in idx:
-        ref = O.neighbors_repr(og, w["x"], h, int(i), prec=prec, self_radius=(mode == 1))
+        ref = O.neighbors_repr(og, w["x"], h, int(i), prec=prec, kappa=w["params"]["kappa"], self_radius=(mode == 1))
         assert np.array_equal(got[i], ref), (i, got[i], ref)
     m.close()
 
@@ -218,7 +218,7 @@ def test_dense_cases_overflow_the_hand_over_list(name):
     rng = np.random.default_rng(4)
     vol = np.flatnonzero(w["group"] == 0)
     idx = rng.choice(vol, 100, replace=False)
-    same = [np.sum(w["group"][O.neighbors_brute(w["x"], h, int(i), D)] == 0) - 1 for i in idx]
+    same = [np.sum(w["group"][O.neighbors_brute(w["x"], h, int(i), D, kappa=w["params"]["kappa"])] == 0) - 1 for i in idx]
     assert o.gdim[0] == D and np.median(same) > LIST_CAP[D], np.median(same)
 
 
@@ -249,7 +249,8 @@ def test_lattice_on_cell_faces_bit_exact():
     # particles placed exactly on cell faces of the finest level: the floor of the rounded
     # product decides the cell on both sides in the same way
     w = WL.square2d(h=0.05, seed=2, jitter=0.0)
-    g = O.grid_spec(2, w["domain"]["lo"], w["domain"]["hi"], 0.05, 0.05)
+    kappa = w["params"]["kappa"]
+    g = O.grid_spec(2, w["domain"]["lo"], w["domain"]["hi"], 0.05, 0.05, kappa=kappa)
     x = w["x"].copy()
     vol = w["group"] == 0
     c0 = float(g.c0)
@@ -267,5 +268,5 @@ def test_lattice_on_cell_faces_bit_exact():
     counts, lists = S.sph_debug_neighbors(m.h, m.n, 0)
     got = _split(counts, lists)
     for i in range(0, m.n, 3):
-        assert np.array_equal(got[i], O.neighbors_repr(g, x, h, i, prec=32))
+        assert np.array_equal(got[i], O.neighbors_repr(g, x, h, i, prec=32, kappa=kappa))
     m.close()

@@ -100,6 +100,7 @@ def _wall_setup(h, rows=12, half_width=20, boundary=True, boundary_rho=1, correc
     feats = [dict(kind="volume", dim=2),
              dict(kind="segment", dim=1 if boundary else 2, a=[-100, 0, 0], b=[100, 0, 0], nb=[0, -1, 0])]
     p = dict(WL.PAPER_PARAMS)
+    p["kappa"] = 2.0        # the figures of these pins (0.2 % / 2 % residual) are for a 2h support
     p["boundary_rho"] = boundary_rho
     p["boundary_correction"] = correction
     w = box_workload(xs, gs, feats, h, lo=(-100, 0, 0), hi=(100, 100, 0), params=p)
@@ -178,7 +179,7 @@ def test_phase_two_step_length():
     r = o.interact(use_grid=False)
     vol = np.where(w["group"] == 0)[0]
     an = np.linalg.norm(r["a_p"], axis=1)
-    rc = 2.0 * o.h
+    rc = p["kappa"] * o.h
     lim = vol[np.argmin(0.25 * np.sqrt(rc[vol] / an[vol]))]
     x0 = o.x.copy()
     o.step(1, use_grid=False)

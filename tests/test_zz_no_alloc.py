@@ -53,7 +53,7 @@ def test_noalloc_rebuild_matches_handle_rebuild(name):
 
 def test_noalloc_rejects_oversized_grid():
     B.build()
-    g = S.sph_grid_spec(2, [0, 0, 0], [1, 1, 0], 0.0004, 0.0004)
+    g = S.sph_grid_spec(2, [0, 0, 0], [1, 1, 0], 0.0004, 0.0004, 2.0)
     assert g.n_cells > (1 << 20)
     with pytest.raises(S.SphError) as e:
         S.sph_cell_sort_noalloc(g, 0, None, None, None, None, None, 1, None, None)
