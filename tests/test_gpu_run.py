@@ -121,7 +121,8 @@ def test_group_convergence_fp64_follows_oracle(steps):
     # follows the oracle group by group.
     w = WL.square2d(h=0.04, seed=5, jitter=0.2)
     w["params"] = WL.scaled_controller(w["params"], sample_every=2, window=5, ramp_len=10, reset_period=25)
-    w["params"].update(threshold=1e-2, group_convergence=1)
+    # step counts found for a 2h support: the edges are done by step 56, the volume at 80
+    w["params"].update(threshold=1e-2, group_convergence=1, kappa=2.0)
     o, got, rep = run_both(w, 64, steps)
     gph = [rep.group_phase[g] for g in range(o.G)]
     assert gph[:5] == [o.ctrl.gphase[g] for g in range(5)]
