@@ -20,6 +20,9 @@ __device__ inline void window_reset(Ctrl* c) {
     }
 }
 
+constexpr int CTL_THREADS = 512;   // threads of the controller's block
+constexpr int CTL_GP = 8;          // groups summed per pass of the sampling reduction
+
 __device__ inline void group_window_reset(Ctrl& c, int g) {
     c.gwcount[g] = 0;
     c.gnwin[g] = 0;
@@ -157,7 +160,7 @@ __device__ void control_groups(Ctrl& sc, const Params& p, const double* vs, int 
     }
 }
 
-// One block of 256 threads per instance.  The controller state is copied into shared memory at once, the
+// One block of CTL_THREADS threads per instance.  The controller state is copied into shared memory at once, the
 // per-block V~ sums of a sampling step are reduced in a fixed order, and the controller for
 // step n runs with one thread per group (thread 0 keeps the scalar state):
 //  1. RAMP -> PHASE2 after ramp_len steps (windows restart);
@@ -171,7 +174,7 @@ __device__ void control_groups(Ctrl& sc, const Params& p, const double* vs, int 
 //  4. per group dt = min(dta, dtv/f), nullified (dt = dta) on the schedule or when dt falls
 //     below dt_collapse times the group's previous step; dt <= dt_cap (Eq. 24).
 // DONE freezes the state (dt = 0, the step counter stops).
-template <typename T, int D, bool ONE> __global__ void __launch_bounds__(256) k_control(State<T> s, One one) {
+template <typename T, int D, bool ONE> __global__ void __launch_bounds__(CTL_THREADS) k_control(State<T> s, One one) {
     dep_launch();
     dep_wait();
     __shared__ double vs[MAXF], et[MAXF], ea[MAXF];
@@ -193,16 +196,37 @@ template <typename T, int D, bool ONE> __global__ void __launch_bounds__(256) k_
     __syncthreads();
     const int G = p.G;
     if (sc.sample_now != 0) {
-        // the pair-pass blocks of this instance (BLOCK/LPP slots each)
+        // the pair-pass blocks of this instance (BLOCK/LPP slots each), CTL_GP groups at a
+        // time: every thread sums a fixed stride of blocks (many loads in flight), then a fixed
+        // shuffle tree per warp and the warps in order
         constexpr int PB = BLOCK / Lpp<D>::v;
+        constexpr int NWC = CTL_THREADS / 32;
+        __shared__ double wpart[CTL_GP][NWC];
         const int b0 = __ldg(s.inst_off + inst) / PB, b1 = __ldg(s.inst_off + inst + 1) / PB;
-        const int lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
-        for (int g = wid; g < G; g += nw) {
-            double acc = 0.0;
-            for (int b = b0 + lane; b < b1; b += 32) acc += s.partials[(size_t)b * MAXF + g];
+        const int lane = t & 31, wid = t >> 5;
+        for (int g0 = 0; g0 < G; g0 += CTL_GP) {
+            double acc[CTL_GP];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-            if (lane == 0) vs[g] = acc;
+            for (int q = 0; q < CTL_GP; ++q) acc[q] = 0.0;
+            for (int b = b0 + t; b < b1; b += CTL_THREADS) {
+                const double* row = s.partials + (size_t)b * MAXF + g0;
+#pragma unroll
+                for (int q = 0; q < CTL_GP; ++q)
+                    if (g0 + q < G) acc[q] += row[q];
+            }
+#pragma unroll
+            for (int q = 0; q < CTL_GP; ++q) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_down_sync(0xffffffffu, acc[q], o);
+                if (lane == 0) wpart[q][wid] = acc[q];
+            }
+            __syncthreads();
+            if (t < CTL_GP && g0 + t < G) {
+                double v = 0.0;
+                for (int w = 0; w < NWC; ++w) v += wpart[t][w];
+                vs[g0 + t] = v;
+            }
+            __syncthreads();
         }
     }
     if (p.group_conv) {
@@ -662,8 +686,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRAT
 }
 
 template <typename T, int D> void launch_control(const State<T>& s, const One* one, cudaStream_t st, bool pdl) {
-    if (one) launch_k(k_control<T, D, true>, s.NI, 256, st, pdl, s, *one);
-    else launch_k(k_control<T, D, false>, s.NI, 256, st, pdl, s, One());
+    if (one) launch_k(k_control<T, D, true>, s.NI, CTL_THREADS, st, pdl, s, *one);
+    else launch_k(k_control<T, D, false>, s.NI, CTL_THREADS, st, pdl, s, One());
 }
 template <typename T, int D>
 void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const Out<T>& o, cudaStream_t st,

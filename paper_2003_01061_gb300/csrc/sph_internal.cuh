@@ -95,26 +95,27 @@ template <typename T> struct Out {
 #define SPH_BUF_CAP 16
 #endif
 constexpr int BUF_CAP = SPH_BUF_CAP;   // kept candidates per lane between flushes of the walk (shared memory)
-// lanes per particle in the pair passes (measured: 1, 2, 4, 8 in 2D and 2, 4, 8, 16 in 3D;
-// fewer lanes repeat less of the per-particle stencil work, more lanes balance the candidates)
+// lanes per particle in the pair passes (measured with a 2.6h support: 2 in 2D beats 4 by
+// 7 %; in 3D 8 halves the pressure pass against 4 and beats 16; fewer lanes repeat less of the
+// per-particle stencil work, more lanes balance the candidates)
 #ifndef SPH_LPP_2D
 #define SPH_LPP_2D 2
 #endif
 #ifndef SPH_LPP_3D
-#define SPH_LPP_3D 4
+#define SPH_LPP_3D 8
 #endif
 template <int D> struct Lpp {
     static constexpr int v = D == 2 ? SPH_LPP_2D : SPH_LPP_3D;
 };
 // same-group pair slots per particle (SPH_VCAP_2D/3D) and per lane (Vcap) in the
-// pressure-to-viscous hand-over list (measured on the viscous pass, whose overflowing
-// particles walk the cells again: in 3D 96 slots are 29 % faster than 64, 128 no faster than
-// 96, 48 81 % slower than 64; in 2D 32 is 7 % faster than 24)
+// pressure-to-viscous hand-over list (measured on the viscous pass with a 2.6h support, whose
+// overflowing particles walk the cells again: in 2D 48 slots are 37 % faster than 32, 64 no
+// faster; in 3D 192 slots are 4.5x faster than 96, 256 no faster)
 #ifndef SPH_VCAP_2D
-#define SPH_VCAP_2D 32
+#define SPH_VCAP_2D 48
 #endif
 #ifndef SPH_VCAP_3D
-#define SPH_VCAP_3D 96
+#define SPH_VCAP_3D 192
 #endif
 template <int D> struct Vcap {
     static constexpr int v = D == 2 ? SPH_VCAP_2D / Lpp<2>::v : SPH_VCAP_3D / Lpp<3>::v;
@@ -159,8 +160,9 @@ static_assert(Lpp<2>::v % ILpp<2>::v == 0 && Lpp<3>::v % ILpp<3>::v == 0,
 #define SPH_INTEGRATE_MINB_3D 6
 #endif
 // cells per support of the cell grid when the parameters leave the choice to the library
+// (measured with a 2.6h support: 2 in 2D are 9 % faster than 1; 1 in 3D is 45 % slower than 2)
 #ifndef SPH_DEFAULT_CPS_2D
-#define SPH_DEFAULT_CPS_2D 1
+#define SPH_DEFAULT_CPS_2D 2
 #endif
 #ifndef SPH_DEFAULT_CPS_3D
 #define SPH_DEFAULT_CPS_3D 2
