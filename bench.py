@@ -79,6 +79,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cube", action="store_true")
     ap.add_argument("--cube-steps", type=int, default=100)
+    ap.add_argument("--cube-warmup", type=int, default=3)
     ap.add_argument("--no-presets", action="store_true")
     ap.add_argument("--preset-iters", type=int, default=40_000)
     return ap.parse_args()
@@ -398,7 +399,7 @@ def run_ours(args):
 
     cube = None
     if cube_w is not None:
-        cube = cube_run(S, torch, dev, cube_w, args.cube_steps)
+        cube = cube_run(S, torch, dev, cube_w, args.cube_steps, args.cube_warmup)
 
     presets = None
     if preset_w is not None:
@@ -497,13 +498,13 @@ def e2e_run(S, w, stream, steps):
             "job": f"upload of {n} particles, {steps} steps each with a controller-report read, final download"}
 
 
-def cube_run(S, torch, dev, w, steps):
+def cube_run(S, torch, dev, w, steps, warmup=3):
     """The 3D cube minus a sphere at ~1.2M particles, one instance, device-timed steps (graph
     without stage events), then up to 20 more steps with stage events for the split."""
     stream = torch.cuda.Stream(device=dev)
     m = S.Mesh(w, precision=32, stream=stream.cuda_stream)
     m.set_state()
-    m.step(3)
+    m.step(max(warmup, 1))
     m.sync()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
