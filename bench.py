@@ -55,7 +55,7 @@ FLOP_PER_PAIR = 50.0       # FP32 operations per interacting pair of the pressur
 # DRAM bytes (read + write) of one pressure-pass launch on this workload, from an ncu capture
 # (cold L2; profiles/k_interact_disk_holes_2d_120k.md); None once the kernel changes until it
 # is captured again
-INTERACT_DRAM_BYTES = None
+INTERACT_DRAM_BYTES = 6_631_936 + 775_936
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # one step: one-pass scan, scatter, gather, pressure pass, controller, update (+ next keys)
 KERNELS_PER_STEP = 6
