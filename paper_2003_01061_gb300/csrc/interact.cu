@@ -21,7 +21,7 @@
 namespace sph {
 
 template <typename T, int D, bool ONE>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? SPH_INTERACT_MINB : 4)
+__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTERACT_MINB : SPH_INTERACT_MINB_3D) : 4)
     k_interact(State<T> s, One one, T* dbg_sigma, T* dbg_gamma) {
     dep_launch();
     dep_wait();

@@ -147,11 +147,16 @@ static_assert(Lpp<2>::v % ILpp<2>::v == 0 && Lpp<3>::v % ILpp<3>::v == 0,
 
 // minimum resident blocks per SM asked of the compiler for the two pair passes (FP32 build;
 // the FP64 build asks for 4): it bounds the registers per thread, trading spills for occupancy
-// (measured on the pressure pass: 10 and 12 spill and are 17 % and 40 % slower than 8; on the
-// viscous pass with one lane per particle 7 is 3 % faster than 8 in 2D, and 6 is 5 % faster
+// (measured on the pressure pass: 10 and 12 spill and are 17 % and 40 % slower than 8; with
+// the 2.6h support and 8 lanes per particle in 3D, on a 1.2M cube, 5 / 6 / 7 / 9 / 10 were
+// 24 / 13 / 8 / 10 / 46 % slower than 8 although 8 spills a few words in the batched form,
+// and 9 in 2D 4 % slower; on the viscous pass with one lane per particle 7 is 3 % faster than 8 in 2D, and 6 is 5 % faster
 // than 7 in 3D but 26 % slower in 2D)
 #ifndef SPH_INTERACT_MINB
 #define SPH_INTERACT_MINB 8
+#endif
+#ifndef SPH_INTERACT_MINB_3D
+#define SPH_INTERACT_MINB_3D SPH_INTERACT_MINB
 #endif
 #ifndef SPH_INTEGRATE_MINB_2D
 #define SPH_INTEGRATE_MINB_2D 7
