@@ -306,7 +306,7 @@ def run_ours(args):
         from paper_2003_01061_gb300 import workloads as WL
 
         preset_w = WL.square_radial(seed=6)
-        cube_case_w = (WL.cube_radial(seed=7), WL.sphere01(seed=8))
+        cube_case_w = (WL.cube_radial(seed=7), WL.sphere01(seed=8), WL.sphere02(seed=9))
     if rank == 0 and not args.no_batch:
         specs, _ = _specs(64, 4, 1_000, 200_000, alternate=True)
         batch_ws = generate(specs)
@@ -406,6 +406,7 @@ def run_ours(args):
         presets = presets_run(S, preset_w, args.preset_iters)
         presets["cube_case"] = case_3d_run(S, cube_case_w[0], "cube_table", {"improved": 7000, "fu2019": 28800})
         presets["sphere01_case"] = case_3d_run(S, cube_case_w[1], "sphere01_table", {"improved": 4600, "fu2019": 17000})
+        presets["sphere02_case"] = case_3d_run(S, cube_case_w[2], "sphere02_table", {"improved": 3800})
 
     sampling = None
     if cube_w is not None:
@@ -637,13 +638,16 @@ def mesh_quality_3d(w, x):
 
 
 def case_3d_run(S, w, table, iters):
-    """A 3D case of Sec. 4 (the Cube of Eq. 28, Sphere01): the improved method and the earlier
-    method (fu2019 preset) for the paper's iteration counts, from the same initial particles;
-    the mesh quality of both final states beside the paper's table."""
+    """A 3D case of Sec. 4 (the Cube of Eq. 28, Sphere01, Sphere02): the improved method and,
+    where the paper's table has it, the earlier method (fu2019 preset) for the paper's iteration
+    counts, from the same initial particles; the mesh quality of the final states beside the
+    paper's table."""
     from paper_2003_01061_gb300 import workloads as WL
 
     out = {}
     for name, over in (("improved", {}), ("improved_threshold1e-2", {"threshold": 1e-2}), ("fu2019", {})):
+        if name.split("_")[0] not in iters:
+            continue
         m = S.Mesh(w, precision=32, params=dict(WL.method_preset(w["params"], name.split("_")[0]), **over))
         m.set_state()
         m.sync()

@@ -303,10 +303,24 @@ def sphere01(seed: int = 8, params: dict | None = None, mc_samples: int = 400_00
     the volume and the sphere surface.  Particles by rejection sampling proportional to rho_t
     per feature, counts from the integrals of rho_t (Eqs. 10, 11).  The paper's own initial
     distribution is not given."""
-    rng = np.random.default_rng(seed)
     R, hmin, hmax = 45.0, 0.375, 7.5
-    dom = dict(D=3, base="ball", lo=[-R, -R, -R], hi=[R, R, R], ball_c=[0.0, 0.0, 0.0], ball_r=R, holes=[])
     siz = dict(kind="radial", a=hmin, b=(hmax - hmin) / (2 * R), lo=hmin, hi=hmax, q=[R, 0.0, 0.0], refs=[])
+    return _ball_case("sphere01", R, siz, hmin, hmax, seed, params, mc_samples)
+
+
+def sphere02(seed: int = 9, params: dict | None = None, mc_samples: int = 400_000):
+    """The Sphere02 case of Sec. 4: h_t = 0.025 + 0.2 | |x| - 0.5 | (h_min = 0.025 on the inner
+    shell |x| = 0.5, h_max = 0.125 at the centre and on the surface), on the unit ball: the
+    paper does not print the radius, and R = 1 is the one at which both ends of its h range
+    are reached.  The sizing is the distance form to a sphere of radius 0.5 (the shell is a
+    refinement only, not a feature); volume and surface features as for Sphere01."""
+    siz = dict(kind="hole_dist", a=0.025, b=0.2, lo=0.025, hi=0.125, q=[0, 0, 0], refs=[([0.0, 0.0, 0.0], 0.5)])
+    return _ball_case("sphere02", 1.0, siz, 0.025, 0.125, seed, params, mc_samples)
+
+
+def _ball_case(name, R, siz, hmin, hmax, seed, params, mc_samples):
+    rng = np.random.default_rng(seed)
+    dom = dict(D=3, base="ball", lo=[-R, -R, -R], hi=[R, R, R], ball_c=[0.0, 0.0, 0.0], ball_r=R, holes=[])
     sphere = dict(kind="sphere", dim=2, c=[0.0, 0.0, 0.0], r=R, orient=1.0)
     nv = int(round(_mc_volume_count(np.random.default_rng(seed + 100), dom, siz, mc_samples)))
     m = 512
@@ -317,7 +331,7 @@ def sphere01(seed: int = 8, params: dict | None = None, mc_samples: int = 400_00
     ns = int(round(float(np.sum(np.sin(TH).ravel() * sizing_eval(siz, P) ** -2.0)) * R * R * (math.pi / m) ** 2))
     xs = [_sample_volume(rng, dom, siz, nv, hmin), _sample_sphere(rng, sphere, siz, ns, hmin)]
     gs = [np.zeros(nv), np.full(ns, 1)]
-    return _finish("sphere01", dom, siz, [dict(kind="volume", dim=3), sphere], xs, gs, params or PAPER_PARAMS,
+    return _finish(name, dom, siz, [dict(kind="volume", dim=3), sphere], xs, gs, params or PAPER_PARAMS,
                    h_lo=hmin, h_hi=hmax)
 
 

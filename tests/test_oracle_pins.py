@@ -272,3 +272,22 @@ def test_paper_particle_counts_follow_rho_t(case, tol):
                holes=[], features=[dict(kind="volume", dim=D)])
     m = O.feature_mass(O.make_domain(dom), O.make_sizing(siz), 0, nq=600 if D == 2 else 200)
     assert abs(m - g["n_particles"]) < tol * g["n_particles"]
+
+
+def test_sphere02_stand_in_follows_the_printed_sizing():
+    # Sec. 4 Sphere02: h_t = 0.025 + 0.2 | |x| - 0.5 |, h_min 0.025, h_max 0.125; on the unit
+    # ball both printed ends are reached (the inner shell and the centre / surface)
+    w = WL.sphere02(seed=9, mc_samples=50_000)
+    rng = np.random.default_rng(4)
+    P = rng.uniform(-1, 1, (20_000, 3))
+    P = P[np.linalg.norm(P, axis=1) <= 1.0]
+    ref = 0.025 + 0.2 * np.abs(np.linalg.norm(P, axis=1) - 0.5)
+    assert np.allclose(WL.sizing_eval(w["sizing"], P), ref, rtol=0, atol=1e-15)
+    ends = WL.sizing_eval(w["sizing"], np.array([[0, 0, 0], [0.5, 0, 0], [0, 0, 1.0]]))
+    assert np.allclose(ends, [0.125, 0.025, 0.125], rtol=0, atol=1e-15)
+    siz = O.make_sizing(w["sizing"])
+    assert np.allclose([O.h_at(siz, q) for q in P[:50]], ref[:50], rtol=0, atol=1e-15)
+    # every particle inside the closed ball, the surface group on it
+    r = np.linalg.norm(w["x"], axis=1)
+    assert np.all(r <= 1.0 + 1e-12)
+    assert np.abs(r[w["group"] == 1] - 1.0).max() < 1e-12
