@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(int ncell, int* __re
 constexpr unsigned long long TS_AGG = 1ull << 62, TS_PRE = 2ull << 62, TS_VAL = 0xffffffffull;
 constexpr int SCAN_SPIN_LIMIT = 1 << 20;
 
-template <typename T> __global__ void __launch_bounds__(SCAN_THREADS) k_scan_onepass(State<T> s) {
+template <typename T> __global__ void __launch_bounds__(SCAN1_THREADS) k_scan_onepass(State<T> s) {
     __shared__ int ws[32];
     __shared__ int sh_tile, sh_prefix;
     if (threadIdx.x == 0) sh_tile = atomicAdd(s.ticket, 1);
@@ -145,7 +145,7 @@ template <typename T> __global__ void __launch_bounds__(SCAN_THREADS) k_scan_one
     const int tile = sh_tile;
     const int ncell = s.ncell;
     // occupancy bits are rebuilt by the gather
-    for (int t = tile * SCAN_THREADS + threadIdx.x; t < s.nocc; t += gridDim.x * SCAN_THREADS) s.occ[t] = 0u;
+    for (int t = tile * SCAN1_THREADS + threadIdx.x; t < s.nocc; t += gridDim.x * SCAN1_THREADS) s.occ[t] = 0u;
     const int base = tile * SCAN1_TILE + threadIdx.x * SCAN1_ITEMS;
     int loc[SCAN1_ITEMS];
     int v = 0;
@@ -395,7 +395,7 @@ void launch_scan(int ncell, int* count, int* cell_start, int* bsum, cudaStream_t
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(ncell, count, bsum, cell_start);
 }
 template <typename T> void launch_scan_onepass(const State<T>& s, cudaStream_t st) {
-    k_scan_onepass<T><<<div_up(s.ncell, SCAN1_TILE), SCAN_THREADS, 0, st>>>(s);
+    k_scan_onepass<T><<<div_up(s.ncell, SCAN1_TILE), SCAN1_THREADS, 0, st>>>(s);
 }
 template <typename T> void launch_scatter(const State<T>& s, cudaStream_t st, bool pdl) {
     launch_k(k_scatter<T>, div_up(s.n, BLOCK), BLOCK, st, pdl, s);

@@ -210,13 +210,19 @@ __device__ __forceinline__ void own_cell(const Grid& g, const State<T>& s, int k
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
-// cells per thread and per tile of the step's one-pass scan (measured: 2 is 6 % faster than 4
-// in the rebuild, 8 and 16 are 27 % and 86 % slower)
+// cells per thread and threads per tile of the step's one-pass scan (measured: 2 is 6 % faster
+// than 4 in the rebuild, 8 and 16 are 27 % and 86 % slower; again with the 2.6h support and its
+// 1.41M-cell 2D grid: 1 / 4 / 8 per thread 20 / 9 / 65 % slower than 2; 512 x 2 and 256 x 4
+// threads x cells equal to 1024 x 2 within 1 %, 512 x 4 and 256 x 8 9 % and 35 % slower)
 #ifndef SPH_SCAN1_ITEMS
 #define SPH_SCAN1_ITEMS 2
 #endif
+#ifndef SPH_SCAN1_THREADS
+#define SPH_SCAN1_THREADS 1024
+#endif
 constexpr int SCAN1_ITEMS = SPH_SCAN1_ITEMS;
-constexpr int SCAN1_TILE = SCAN_THREADS * SCAN1_ITEMS;
+constexpr int SCAN1_THREADS = SPH_SCAN1_THREADS;
+constexpr int SCAN1_TILE = SCAN1_THREADS * SCAN1_ITEMS;
 
 inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 
