@@ -91,6 +91,8 @@ template <typename T> struct Out {
     int* count;        // ... and per-cell histogram, so that the next step needs no hash pass
 };
 
+// (measured with the 2.6h support: 12 / 20 / 24 make the whole 2D step 22 % slower / 1 % slower /
+// 5 % slower than 16, and the 1.2M cube's 33 % / 2 % / 11 %)
 #ifndef SPH_BUF_CAP
 #define SPH_BUF_CAP 16
 #endif
