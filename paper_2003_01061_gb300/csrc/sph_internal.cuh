@@ -152,8 +152,10 @@ static_assert(Lpp<2>::v % ILpp<2>::v == 0 && Lpp<3>::v % ILpp<3>::v == 0,
 // (measured on the pressure pass: 10 and 12 spill and are 17 % and 40 % slower than 8; with
 // the 2.6h support and 8 lanes per particle in 3D, on a 1.2M cube, 5 / 6 / 7 / 9 / 10 were
 // 24 / 13 / 8 / 10 / 46 % slower than 8 although 8 spills a few words in the batched form,
-// and 9 in 2D 4 % slower; on the viscous pass with one lane per particle 7 is 3 % faster than 8 in 2D, and 6 is 5 % faster
-// than 7 in 3D but 26 % slower in 2D)
+// and 9 in 2D 4 % slower; on the viscous pass with one lane per particle 7 is 3 % faster than
+// 8 in 2D, and 6 is 5 % faster than 7 in 3D but 26 % slower in 2D; again with the 2.6h support:
+// 2D 6 / 8 30 % / 3 % slower than 7, 3D 5 2 % faster than 6 on the pass (0.3 % on the step)
+// and 7 12 % slower)
 #ifndef SPH_INTERACT_MINB
 #define SPH_INTERACT_MINB 8
 #endif
