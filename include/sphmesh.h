@@ -551,9 +551,14 @@ void sph_server_destroy(sph_server* s);
  * allocating afterwards (so that its budget stays fixed), or a latency-critical loop in which a
  * cudaMalloc/cudaFree could synchronise the device or fail under memory pressure.
  *
- * It computes the same cell keys, cell starts and stable permutation as sph_debug_rebuild, for
- * positions x_dev, y_dev, z_dev (device arrays of n doubles each; z_dev may be NULL in 2D) and
- * smoothing lengths h_dev (n floats) on the grid `grid` (from sph_grid_spec or sph_mesh_grid).
+ * It computes the same cell keys, cell starts and stable permutation as sph_debug_rebuild of an
+ * FP32 mesh (precision 32), for positions x_dev, y_dev, z_dev (device arrays of n doubles each;
+ * z_dev may be NULL in 2D) and smoothing lengths h_dev (n floats) on the grid `grid` (from
+ * sph_grid_spec or sph_mesh_grid).  The level of a particle is chosen by comparing its float h
+ * with the grid's thresholds; an FP64 mesh compares its double h, so for an FP64 mesh the
+ * results agree only where every h is exactly representable as a float.  A grid whose coarser
+ * levels do not cover its finest level (each dims[l][a] >= ((dims[0][a] - 1) >> l) + 1, as
+ * sph_grid_spec makes them) is rejected with SPH_E_INVALID.
  * Outputs, all caller-owned device arrays: key_dev [n], cell_start_dev [n_cells + 1], perm_dev [n].
  * Work is enqueued on `stream` (a cudaStream_t, NULL for the default stream); the call does not
  * wait for it.
@@ -565,8 +570,13 @@ void sph_server_destroy(sph_server* s);
  * more than SPH_NOALLOC_MAX_CELLS cells are rejected with SPH_E_INVALID.  All calls share the
  * array: the counters are cleared at the start of each call, and calls whose work overlaps on
  * the GPU (other streams or other threads) race and give wrong results.  Positions outside
- * the grid are clamped into its border cells without a report.  The call never allocates or
- * frees memory.  Errors: SPH_E_INVALID, SPH_E_CUDA (message in sph_last_error()).
+ * the grid are clamped into its border cells without a report.  The call itself never
+ * allocates or frees memory.  The CUDA runtime, however, may load the library's device code
+ * lazily (the default since CUDA 12.2): the first call on a device may then load the module,
+ * and that load reserves the fixed array.  A caller that reserves the GPU's memory for its own
+ * pool should therefore make its first call at start-up, before it reserves the pool, or run
+ * with CUDA_MODULE_LOADING=EAGER.  Errors: SPH_E_INVALID, SPH_E_CUDA (message in
+ * sph_last_error()).
  * ------------------------------------------------------------------------------------------ */
 #define SPH_NOALLOC_MAX_CELLS (1 << 20)
 sph_status sph_cell_sort_noalloc(const sph_grid_info* grid, int64_t n, const double* x_dev,

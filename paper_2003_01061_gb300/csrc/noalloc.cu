@@ -58,9 +58,10 @@ __global__ void __launch_bounds__(BLOCK) k_na_hash(Grid g, int n, const double* 
     float o[3], off[3];
     fine_of<float, D>(g, x, c, o);              // finest cell, then the level's cell (c >> l)
     level_repr<float, D>(g, l, c, o, cell, off);
+    for (int a = 0; a < D; ++a) cell[a] = min(cell[a], g.dims[l][a] - 1);   // never past the level's grid
     int k = key_of(g, l, cell);
     key[i] = k;
-    atomicAdd(count + k, 1);
+    if ((unsigned)k < (unsigned)g.ncell) atomicAdd(count + k, 1);
 }
 
 __global__ void __launch_bounds__(BLOCK) k_na_scatter(int n, const int* __restrict__ key, int* __restrict__ count,
@@ -106,6 +107,12 @@ extern "C" sph_status sph_cell_sort_noalloc(const sph_grid_info* grid, int64_t n
             base += cells;
         }
         if (base != grid->n_cells) return na_fail(SPH_E_INVALID, "cell_sort_noalloc: grid dims do not add up to n_cells");
+        // a particle of level l takes the level cell (finest cell >> l) of a finest cell clamped
+        // into dims[0]: every coarser level must cover the finest grid shifted down by l
+        for (int l = 1; l < grid->levels; ++l)
+            for (int a = 0; a < grid->dim; ++a)
+                if (grid->dims[l][a] < ((grid->dims[0][a] - 1) >> l) + 1)
+                    return na_fail(SPH_E_INVALID, "cell_sort_noalloc: level %d does not cover the finest grid", l);
         if (!(grid->c0 > 0.0f)) return na_fail(SPH_E_INVALID, "cell_sort_noalloc: c0 must be positive");
     }
     if (n > 0 && (!x_dev || !y_dev || (grid->dim == 3 && !z_dev) || !h_dev || !key_dev || !perm_dev))

@@ -125,3 +125,23 @@ def test_method_presets_match_the_workload_table():
     p.boundary_correction = 2
     with pytest.raises(S.SphError):
         S.sph_mesh_create(d, z, p, 10)
+
+
+def test_noalloc_rejects_grid_with_undersized_coarse_level():
+    """A caller-built grid whose coarser level does not cover the finest grid shifted down to
+    that level would give keys past the level (and past the fixed scratch array at the top
+    level); the allocation-free rebuild must refuse it before any device work."""
+    g = S.sph_grid_spec(2, [0, 0, 0], [1, 1, 0], 0.01, 0.04, 2.0, 1)
+    assert g.levels >= 2 and g.n_cells <= (1 << 20)
+    need = ((g.dims[0][0] - 1) >> 1) + 1
+    assert g.dims[1][0] >= need
+    cells_l1 = lambda: g.dims[1][0] * g.dims[1][1] * g.dims[1][2]
+    old = cells_l1()
+    g.dims[1][0] = need - 1                 # one column short of the finest grid
+    shrink = old - cells_l1()
+    for l in range(2, g.levels):
+        g.base[l] -= shrink
+    g.n_cells -= shrink
+    with pytest.raises(S.SphError) as e:
+        S.sph_cell_sort_noalloc(g, 0, None, None, None, None, None, 1, None, None)
+    assert e.value.status == S.SPH_E_INVALID and "does not cover" in str(e.value)
