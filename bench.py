@@ -1,11 +1,13 @@
-"""Benchmark of the relaxation hot path: particle-steps/s on the 2D disk-with-holes workload.
+"""Benchmark of the relaxation hot path: particle-steps/s on the 3D cube-minus-sphere workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 A step is one pass of the whole hot path (cell-list rebuild, pressure pass with the feature
 boundary correction, controller, viscous update with projection) over every particle of the
-instance.  Workload: unit disk minus 3 seeded holes, h linear in the distance to the nearest
-hole (0.004-0.04 scaled to ~120k particles), FP32 pair sums with FP64 projection/reductions.
+instance.  Workload (headline): unit cube minus a centred sphere of radius 0.3, curve particles
+on the 12 edges, surface particles on the 6 faces and the sphere, volume particles inside, 8
+fixed corners, h = min(0.008 + 0.04 |d_sphere|, 0.05) scaled to ~1.2M particles, FP32 pair sums
+with FP64 projection/reductions -- the largest single-GPU configuration.
 
 * value:  particle-steps/s over K device-timed steps (CUDA events on the library's stream),
           L2 flushed (256 MiB write) between steps; inputs resident in HBM.
@@ -16,7 +18,10 @@ hole (0.004-0.04 scaled to ~120k particles), FP32 pair sums with FP64 projection
           second timed region (up to 1000 more steps, same L2 flush) whose step graph holds an
           event between the stages; the headline region runs the graph without them, so that
           its kernel-to-kernel edges keep their programmatic (early) launch.
-* cpu_baseline / --impl reference: the FP64 CPU oracle on the host cores (bounded sample).
+* cpu_baseline / --impl reference: the FP64 CPU oracle on the host cores (bounded sample of
+          the same workload).
+* disk_2d: the 2D unit disk minus 3 seeded holes (h linear in the distance to the nearest hole,
+          0.004-0.04 scaled to ~120k particles), device-timed steps with its own stage split.
 * batched: 64 independent instances (half 2D disks with holes, half 3D cubes minus a sphere,
           particle counts log-uniform over 1k-200k, seeded), one batch per dimension on its own
           stream, each step one CUDA graph per batch; particle-steps/s over all instances.
@@ -50,12 +55,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s"
-WORKLOAD = "disk_holes_2d_120k"
+WORKLOAD = "cube_sphere_3d_1.2M"
+DISK_WORKLOAD = "disk_holes_2d_120k"
 FLOP_PER_PAIR = 50.0       # FP32 operations per interacting pair of the pressure pass (see design notes)
-# DRAM bytes (read + write) of one pressure-pass launch on this workload, from an ncu capture
-# (cold L2; profiles/k_interact_disk_holes_2d_120k.md); None once the kernel changes until it
-# is captured again
-INTERACT_DRAM_BYTES = 6_631_936 + 775_936
+# DRAM bytes (read + write) of one launch of the dominant kernel on the headline workload, from
+# an ncu capture of the current build (profiles/); None until that kernel has been captured
+DOMINANT_DRAM_BYTES = None
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # one step: one-pass scan, scatter, gather, pressure pass, controller, update (+ next keys)
 KERNELS_PER_STEP = 6
@@ -67,7 +72,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=120_000)
+    ap.add_argument("--n", type=int, default=1_200_000)
+    ap.add_argument("--disk-n", type=int, default=120_000)
+    ap.add_argument("--no-disk", action="store_true")
+    ap.add_argument("--disk-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
@@ -78,8 +86,6 @@ def parse():
     ap.add_argument("--serve-max-n", type=int, default=200_000)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cube", action="store_true")
-    ap.add_argument("--cube-steps", type=int, default=100)
-    ap.add_argument("--cube-warmup", type=int, default=3)
     ap.add_argument("--no-presets", action="store_true")
     ap.add_argument("--preset-iters", type=int, default=40_000)
     return ap.parse_args()
@@ -181,6 +187,12 @@ def dist_env():
 
 
 def make_workload(n):
+    """The headline workload: the cube minus a sphere at n particles (seed 3), built in a worker
+    process (spawn) so that the calling process has made no GPU call when it forks nothing."""
+    return generate([(4, n, 3, 0.3)])[0]
+
+
+def make_disk(n):
     from paper_2003_01061_gb300 import workloads as WL
 
     return WL.disk_holes(n_target=n, seed=2)
@@ -225,38 +237,39 @@ def generate(specs):
 # CPU oracle timing (the reference arm and the cpu_baseline leg)
 # ----------------------------------------------------------------------------------------
 def oracle_rate(w, budget_s=15.0, sample=None, steps=None):
-    """Times the FP64 oracle's pressure pass + update on a fixed particle sample.
+    """Times the FP64 oracle's pressure pass + update on a fixed random sample of particles.
 
+    Every sampled particle runs with its full neighbourhood.  Unsampled neighbours carry
+    a_p = 0 in the viscous sum: with the sampled particle's own velocity nonzero every pair
+    term is still evaluated, so the work per sampled particle is that of the full step.
     Returns (particle-steps/s, description, threads, per-step seconds list)."""
     from oracle import oracle as O
 
     o = O.Oracle(w)
     n = o.n
-    full = o.interact(use_grid=True)               # untimed: a_p of every particle
-    a_all = full["a_p"].copy()
-    for g in range(o.G):
-        o.ctrl.dt[g] = full["dta"][g] if np.isfinite(full["dta"][g]) else 0.0
-        o.ctrl.reset[g] = 1
+    a_all = np.zeros((n, 3))
     rng = np.random.default_rng(0)
-    if sample is None:
-        t0 = time.perf_counter()
-        sub = np.sort(rng.choice(n, min(n, 4096), replace=False))
-        o.interact(sub=sub, use_grid=True)
-        o.integrate(a_all, sub=sub, use_grid=True)
-        per = (time.perf_counter() - t0) / len(sub)
-        sample = int(min(n, max(1024, budget_s / 3.0 / max(per, 1e-9))))
-    sub = np.sort(rng.choice(n, sample, replace=False))
-    times = []
-    nsteps = steps if steps is not None else 3
-    for _ in range(nsteps):
+
+    def one(sub):
         t0 = time.perf_counter()
         r = o.interact(sub=sub, use_grid=True)
+        for g in range(o.G):
+            o.ctrl.dt[g] = r["dta"][g] if np.isfinite(r["dta"][g]) else 0.0
+            o.ctrl.reset[g] = 1
         a_all[sub] = r["a_p"]
         o.integrate(a_all, sub=sub, use_grid=True)
-        times.append(time.perf_counter() - t0)
+        return time.perf_counter() - t0
+
+    if sample is None:
+        probe = np.sort(rng.choice(n, min(n, 2048), replace=False))
+        per = one(probe) / len(probe)
+        sample = int(min(n, max(1024, budget_s / 3.0 / max(per, 1e-9))))
+    sub = np.sort(rng.choice(n, sample, replace=False))
+    nsteps = steps if steps is not None else 3
+    times = [one(sub) for _ in range(nsteps)]
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     rate = sample * len(times) / sum(times)
-    desc = (f"FP64 oracle pressure pass + viscous update of {sample} sampled particles (of {n}) "
+    desc = (f"FP64 oracle pressure pass + viscous update of {sample} randomly sampled particles (of {n}) "
             f"with full neighbourhoods, {len(times)} steps")
     return rate, desc, threads, times
 
@@ -267,7 +280,7 @@ def run_reference(args):
         return
     w = make_workload(args.n)
     n = len(w["x"])
-    budget = 120.0
+    budget = 90.0
     per_step = budget / max(args.steps + args.warmup, 1)
     from oracle import oracle as O
 
@@ -280,7 +293,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": rate, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times) * n / sample,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "particles": n, "dim": 2, "precision": "fp64 oracle"},
+        "config": {"workload": WORKLOAD, "particles": n, "dim": 3, "precision": "fp64 oracle"},
         "cpu_baseline": {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": rate, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -295,12 +308,12 @@ def run_ours(args):
 
     ws, rank, local = dist_env()
     # batch and serving inputs, generated before the first GPU call
-    batch_ws, serve_ws, serve_t, cube_w = None, None, None, None
-    gen_s = None
-    if rank == 0 and not args.no_cube:
-        t0 = time.perf_counter()
-        cube_w = generate([(4, 1_200_000, 3, 0.3)])[0]
-        gen_s = time.perf_counter() - t0
+    batch_ws, serve_ws, serve_t = None, None, None
+    # the headline workload (every rank runs its own replica of it)
+    t0 = time.perf_counter()
+    w = make_workload(args.n)
+    gen_s = time.perf_counter() - t0
+    disk_w = make_disk(args.disk_n) if (rank == 0 and not args.no_disk) else None
     preset_w = cube_case_w = None
     if rank == 0 and not args.no_presets:
         from paper_2003_01061_gb300 import workloads as WL
@@ -324,82 +337,33 @@ def run_ours(args):
     from paper_2003_01061_gb300 import sphmesh as S
 
     B.build()
-    w = make_workload(args.n)
     n = len(w["x"])
     stream = torch.cuda.Stream(device=dev)
-    m = S.Mesh(w, precision=32, stream=stream.cuda_stream)
-    m.set_state()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    # warm-up (also captures the step graph)
-    m.step(max(args.warmup, 1))
-    m.sync()
-
-    def timed_steps(n_steps):
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
-        with torch.cuda.stream(stream):
-            for k in range(n_steps):
-                evs[k][0].record(stream)
-                m.step(1)
-                evs[k][1].record(stream)
-                flush.zero_()       # 256 MiB write between timed steps evicts the 129 MB L2
-        torch.cuda.synchronize()
-        return float(sum(a.elapsed_time(b) for a, b in evs))
-
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        time.sleep(0.3)             # let the sampler start before the timed region
-        # the whole step, as a user runs it (graph without stage events)
-        total_ms = timed_steps(args.steps)
-        if ws > 1:
-            torch.distributed.barrier()
-        # the per-kernel split: the same steps with an event between the stages (the events
-        # turn the kernel-to-kernel edges they sit on into ordinary ones)
-        S.sph_mesh_set_timing(m.h, 1)
-        m.step(1)                   # re-capture with the stage events
-        m.sync()
-        S.sph_mesh_set_timing(m.h, 1)   # zero the accumulators
-        stage_steps = min(args.steps, 1000)
-        staged_ms = timed_steps(stage_steps)
-        stage = S.sph_mesh_kernel_times(m.h)
-        S.sph_mesh_set_timing(m.h, 0)
-    m.sync()
+    head = timed_run(S, torch, w, stream, flush, args.steps, args.warmup, min(args.steps, 200),
+                     barrier=ws > 1, clock_index=local)
+    m = head.pop("mesh")
+    total_ms = head["total_ms"]
     rep = m.report()
-
     total_ms, value = replica_throughput(total_ms, n, args.steps, dev)
-
-    # per-stage averages and the dominant kernel's roofline
-    cand, accd = S.sph_debug_pair_counts(m.h)
-    stages = {k: {"launches": int(v[0]), "avg_ms": (v[1] / max(v[0], 1)) if k != "rebuild" else v[1] / max(stage_steps, 1)}
-              for k, v in stage.items()}
     peaks, peak_src = measured_peaks()
-    clocks = clk.summary()
-    fp32_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12       # TFLOP/s at the maximum SM clock
-    dom = max(("interact", "integrate", "control"), key=lambda k: stages.get(k, {}).get("avg_ms", 0.0))
-    t_dom = stages[dom]["avg_ms"] / 1e3
-    # algorithmic work of the pressure pass: FLOP_PER_PAIR per interacting pair; the viscous
-    # pass visits the same-group pairs only (counted the same way, a lower bound)
-    flops = FLOP_PER_PAIR * accd
-    achieved = flops / t_dom / 1e12
-    bytes_per_particle = {"interact": 2 * 16 + 8 + 4 + 16, "integrate": 16 + 16 + 8 + 4 + 16 + 8 + 4 + 4 + 4 + 4,
-                          "control": 0}
-    hbm_gbs = n * bytes_per_particle[dom] / t_dom / 1e9
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": INTERACT_DRAM_BYTES if dom == "interact" else None,
-                "kernel": dom,
-                "peak_source": f"FP32: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {SM_MAX_MHZ:.0f} MHz",
-                "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak(peaks), "hbm_frac": hbm_gbs / hbm_peak(peaks),
-                "hbm_peak_source": peak_src}
-
+    clocks = head["clocks"]
+    roofline = roofline_of(head, n, peaks, peak_src, dim=3)
     e2e = None
     if not args.no_e2e:
         e2e = e2e_run(S, w, stream, args.steps)
 
-    cube = None
-    if cube_w is not None:
-        cube = cube_run(S, torch, dev, cube_w, args.cube_steps, args.cube_warmup)
+    disk = None
+    if disk_w is not None:
+        dm = timed_run(S, torch, disk_w, stream, flush, args.disk_steps, 5, min(args.disk_steps, 200))
+        dm.pop("mesh").close()
+        disk = {"value": dm["value"], "unit": METRIC, "steps": args.disk_steps,
+                "ms_per_step": dm["total_ms"] / args.disk_steps, "particles": len(disk_w["x"]),
+                "stages_ms": dm["stages_ms"], "pairs_per_particle": dm["pairs_per_particle"],
+                "roofline": roofline_of(dm, len(disk_w["x"]), peaks, peak_src, dim=2),
+                "config": {"workload": DISK_WORKLOAD + ": unit disk minus 3 seeded holes, h linear in the "
+                                       "distance to the nearest hole (0.004-0.04) scaled to ~120k particles "
+                                       "(seed 2), FP32", "l2": "flushed between timed steps (256 MiB write)"}}
 
     presets = None
     if preset_w is not None:
@@ -409,8 +373,8 @@ def run_ours(args):
         presets["sphere02_case"] = case_3d_run(S, cube_case_w[2], "sphere02_table", {"improved": 3800})
 
     sampling = None
-    if cube_w is not None:
-        sampling = sampling_run(S, cube_w, gen_s, with_oracle=not args.no_cpu_baseline)
+    if rank == 0 and not args.no_cube:
+        sampling = sampling_run(S, w, gen_s, with_oracle=not args.no_cpu_baseline)
 
     batched = None
     if batch_ws is not None:
@@ -443,19 +407,23 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "particles": n, "dim": 2, "groups": m.n_groups,
+        "config": {"workload": WORKLOAD, "particles": n, "dim": 3, "groups": m.n_groups,
+                   "description": "unit cube minus a centred sphere r=0.3: 12 edge curves, 6 faces + the sphere "
+                                  "surface, volume, 8 fixed corners; h = min(0.008 + 0.04|d_sphere|, 0.05) scaled "
+                                  "to 1.2M particles (seed 3)",
                    "precision": "fp32 pair sums, fp64 projection and reductions", "replicas": ws,
-                   "l2": "flushed between timed steps (256 MiB write)", "phase_at_end": int(rep.phase),
-                   "iteration_at_end": int(rep.iteration)},
+                   "l2": "flushed between timed steps (256 MiB write); the working set is also larger than L2",
+                   "phase_at_end": int(rep.phase), "iteration_at_end": int(rep.iteration)},
         "roofline": roofline,
-        "stages_ms": {k: v["avg_ms"] for k, v in stages.items()},
-        "stages_timing": {"steps": stage_steps, "ms_per_step_with_stage_events": staged_ms / stage_steps},
-        "pairs_per_particle": {"candidates": cand / n, "interacting": accd / n},
+        "stages_ms": head["stages_ms"],
+        "stages_timing": {"steps": head["stage_steps"],
+                          "ms_per_step_with_stage_events": head["staged_ms"] / head["stage_steps"]},
+        "pairs_per_particle": head["pairs_per_particle"],
         "clocks": clocks,
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "e2e": e2e,
         "cpu_baseline": cpu,
-        "cube_3d": cube,
+        "disk_2d": disk,
         "method_presets": presets,
         "init_sampling": sampling,
         "batched": batched,
@@ -499,41 +467,91 @@ def e2e_run(S, w, stream, steps):
             "job": f"upload of {n} particles, {steps} steps each with a controller-report read, final download"}
 
 
-def cube_run(S, torch, dev, w, steps, warmup=3):
-    """The 3D cube minus a sphere at ~1.2M particles, one instance, device-timed steps (graph
-    without stage events), then up to 20 more steps with stage events for the split."""
-    stream = torch.cuda.Stream(device=dev)
+def timed_run(S, torch, w, stream, flush, steps, warmup, stage_steps, barrier=False, clock_index=None):
+    """One FP32 instance of w: `warmup` untimed steps (they also capture the step graph), then
+    `steps` device-timed steps (CUDA events on the library's stream, the graph without stage
+    events, L2 flushed between steps), then `stage_steps` more with an event between the
+    stages for the per-kernel split (those events turn the kernel-to-kernel edges they sit on
+    into ordinary ones, so they are kept out of the headline steps)."""
     m = S.Mesh(w, precision=32, stream=stream.cuda_stream)
     m.set_state()
     m.step(max(warmup, 1))
     m.sync()
+
+    def timed_steps(n_steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
+        with torch.cuda.stream(stream):
+            for k in range(n_steps):
+                evs[k][0].record(stream)
+                m.step(1)
+                evs[k][1].record(stream)
+                flush.zero_()       # 256 MiB write between timed steps evicts the 129 MB L2
+        torch.cuda.synchronize()
+        return float(sum(a.elapsed_time(b) for a, b in evs))
+
+    clk = Clocks(clock_index) if clock_index is not None else None
+    if clk:
+        clk.__enter__()
+        time.sleep(0.3)             # let the sampler start before the timed region
+    if barrier:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    m.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    total_ms = timed_steps(steps)
+    if barrier:
+        torch.distributed.barrier()
+    if clk:
+        clk.__exit__(None, None, None)
     S.sph_mesh_set_timing(m.h, 1)
-    m.step(1)
+    m.step(1)                       # re-capture with the stage events
     m.sync()
-    S.sph_mesh_set_timing(m.h, 1)
-    staged = min(steps, 20)
-    m.step(staged)
-    m.sync()
-    t = S.sph_mesh_kernel_times(m.h)
-    g = S.sph_mesh_grid(m.h)
-    n = len(w["x"])
-    out = {"value": n * steps / (ms / 1e3), "unit": METRIC, "steps": steps, "ms_per_step": ms / steps,
-           "particles": n, "cells_per_support": g.cells_per_support,
-           "stages_ms": {k: v[1] / max(staged, 1) for k, v in t.items()}, "stage_steps": staged,
-           "config": {"workload": "cube_sphere_3d_1.2M: unit cube minus a centred sphere r=0.3, "
-                                  "h = min(0.008 + 0.04|d|, 0.05) scaled to 1.2M particles (seed 3)",
-                      "l2": "working set larger than L2 (no flush)"}}
+    S.sph_mesh_set_timing(m.h, 1)   # zero the accumulators
+    stage_steps = max(stage_steps, 1)
+    staged_ms = timed_steps(stage_steps)
+    stage = S.sph_mesh_kernel_times(m.h)
     S.sph_mesh_set_timing(m.h, 0)
     m.sync()
-    m.close()
-    return out
+    cand, accd = S.sph_debug_pair_counts(m.h)
+    n = len(w["x"])
+    stages = {k: (v[1] / max(v[0], 1)) if k != "rebuild" else v[1] / stage_steps for k, v in stage.items()}
+    return {"mesh": m, "total_ms": total_ms, "value": n * steps / (total_ms / 1e3), "staged_ms": staged_ms,
+            "stage_steps": stage_steps, "stages_ms": stages, "accd": accd,
+            "clocks": clk.summary() if clk else None,
+            "pairs_per_particle": {"candidates": cand / n, "interacting": accd / n}}
+
+
+def algorithmic_bytes(kernel, dim):
+    """HBM bytes per particle of one launch if every array were read or written exactly once
+    (FP32 build; neighbour records served on chip):
+      pressure pass: own record (offsets + h, meta), (v, h), own cell, a_p + V~ written;
+      update: record, (v, h), a_p, stored cell + offset in, cell, offset, velocity, h, meta,
+              index and next key out."""
+    if kernel == "interact":
+        return (16 if dim == 2 else 20) + 16 + 4 * dim + 16
+    if kernel == "integrate":
+        return (16 if dim == 2 else 20) + 16 + 16 + 8 * dim + (8 * dim + 4 * dim + 4 + 4 + 4 + 4)
+    return 0
+
+
+def roofline_of(run, n, peaks, peak_src, dim):
+    """Roofline object of the dominant kernel from the live stage times of `run`: the pressure
+    pass is bounded by the FP32 pipes (FLOP_PER_PAIR per interacting pair); its HBM fraction on
+    algorithmic bytes is reported beside it."""
+    stages = run["stages_ms"]
+    dom = max(("interact", "integrate", "control"), key=lambda k: stages.get(k, 0.0))
+    t_dom = stages[dom] / 1e3
+    fp32_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12       # TFLOP/s at the maximum SM clock
+    achieved = FLOP_PER_PAIR * run["accd"] / t_dom / 1e12
+    bpp = algorithmic_bytes(dom, dim)
+    hbm_gbs = n * bpp / t_dom / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak,
+            "traffic": DOMINANT_DRAM_BYTES if (dom == "interact" and dim == 3) else None,
+            "kernel": dom, "avg_launch_ms": stages[dom],
+            "work": f"{FLOP_PER_PAIR:.0f} FP32 operations x {run['accd']} interacting pairs per launch",
+            "peak_source": f"FP32: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {SM_MAX_MHZ:.0f} MHz",
+            "algorithmic_bytes_per_particle": bpp,
+            "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak(peaks), "hbm_frac": hbm_gbs / hbm_peak(peaks),
+            "hbm_peak_source": peak_src}
 
 
 def mesh_quality_2d(w, x):
@@ -560,9 +578,12 @@ def mesh_quality_2d(w, x):
         a, b, c = e[:, k], e[:, (k + 1) % 3], e[:, (k + 2) % 3]
         ang.append(np.degrees(np.arccos(np.clip((b * b + c * c - a * a) / (2 * b * c), -1, 1))))
     ang = np.stack(ang, 1)
+    # radius ratio 2 r_in / r_circ (1 for the equilateral triangle)
+    rr = 2.0 * (area / (0.5 * e.sum(axis=1))) / (e.prod(axis=1) / (4.0 * area))
     return {"G_avg": float(G.mean()), "G_min": float(G.min()), "theta_max": float(ang.max()),
             "theta_min": float(ang.min()), "theta_min_avg": float(ang.min(axis=1).mean()),
-            "theta_lt30": int((ang.min(axis=1) < 30).sum()), "N_tri": int(len(P))}
+            "theta_lt30": int((ang.min(axis=1) < 30).sum()), "rr_min": float(rr.min()), "rr_avg": float(rr.mean()),
+            "N_tri": int(len(P))}
 
 
 def sampling_run(S, w, gen_s, with_oracle=True):

@@ -194,3 +194,62 @@ def test_autotune_keeps_the_state():
     b.sync()
     assert all(r.iteration == 50 for r in b.reports())
     b.close()
+
+
+def _oracle_h(w):
+    from oracle import oracle as O
+
+    siz = O.make_sizing(w["sizing"])
+    return np.array([O.h_at(siz, x) for x in w["x"]]).astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_batched_step_matches_oracle(dim):
+    """The kernels that read the per-instance tables (a batch of several instances) against the
+    oracle directly: one step of every instance from rest, with the paper's parameters (the
+    first step nullifies and takes dt = the Eq. 24 acceleration term).  Per instance: the
+    per-group step sizes, and every moving particle's position and velocity within 50 x 1e-5
+    of the step's scale (dt^2 S_i for x, dt S_i for v, S_i the sum of the pressure terms'
+    magnitudes), plus the part of the position error that the FP32 dt's own rounding explains.
+    Volume particles that end within 0.05 h of the boundary are held to the escape count
+    instead: there the decision to re-project can differ by rounding."""
+    from oracle import oracle as O
+
+    if dim == 2:
+        ws = [WL.square2d(h=0.05, seed=1), WL.disk_holes(n_target=6000, seed=5)]
+    else:
+        ws = [WL.cube_sphere(n_target=8000, seed=3, mc_samples=200_000),
+              WL.cube_sphere(n_target=6000, seed=4, sphere_r=0.25, mc_samples=200_000)]
+    hs = [_oracle_h(w) for w in ws]
+    b = S.Batch(ws, precision=32)
+    for i in range(len(ws)):
+        b.set_state(i, h=hs[i])
+    b.step(1)
+    b.sync()
+    reps = b.reports()
+    for i, w in enumerate(ws):
+        o = O.Oracle(w, h=hs[i])
+        r = o.interact(use_grid=True)
+        o.step(1, use_grid=True)
+        got = b.positions(i)
+        assert reps[i].iteration == o.iteration == 1
+        dt = np.array([o.ctrl.dt[g] for g in range(o.G)])
+        dtg = np.array(list(reps[i].dt)[: o.G])
+        for g in range(o.G):
+            assert abs(dtg[g] - dt[g]) <= 20e-5 * dt[g], (i, g, dtg[g], dt[g])
+        grp = w["group"]
+        moving = o.gdim[grp] > 0
+        dtp, ddt = dt[grp], np.abs(dtg - dt)[grp]
+        an = np.linalg.norm(r["a_p"], axis=1)
+        tol_x = 50e-5 * dtp ** 2 * r["S"] + 3.0 * ddt * dtp * an + 4e-16 * np.abs(o.x).max()
+        tol_v = 50e-5 * dtp * r["S"] + 3.0 * ddt * an + 1e-300
+        phi = WL.domain_phi(w["domain"], o.x)
+        near = (o.gdim[grp] == dim) & (phi < 0.05 * o.h)
+        sel = moving & ~near
+        ex = np.linalg.norm(got["x"] - o.x, axis=1)
+        ev = np.linalg.norm(got["v"] - o.v, axis=1)
+        assert np.all(ex[sel] <= tol_x[sel]), (i, (ex / tol_x)[sel].max())
+        assert np.all(ev[sel] <= tol_v[sel]), (i, (ev / tol_v)[sel].max())
+        assert abs(int(reps[i].escapes) - int(o.ctrl.escapes)) <= max(1, near.sum() // 100)
+        assert np.array_equal(got["x"][~moving], w["x"][~moving])
+    b.close()

@@ -2,11 +2,20 @@
 
 Trajectories of a particle relaxation drift apart from rounding differences, so after K steps
 the comparison is statistical (the acceptance bounds stated for the method): the histogram of
-nearest-neighbour spacing / h_t (50 bins on [0.5, 1.5]) within 1 % (L1) and the Delaunay
-quality (mean minimum angle, mean G = 2 sqrt(3) S/(P H), Sec. 4) within 0.5 degrees / 0.01.
-The disk case drifts faster (the oracle against itself with a 1e-7 relative perturbation of
-the start already differs by ~3 % L1 after 150 steps), so its histogram bound is 5 %.
-The FP64 build is also compared position by position over a shorter horizon.
+nearest-neighbour spacing / h_t (50 bins on [0.5, 1.5]) within 1 % (L1), the minimum angle of
+the Delaunay mesh within 0.5 degrees and its radius ratio (minimum and mean; 2 r_in / r_circ
+in 2D, 3 r_in / r_circ in 3D) within 0.01; in 3D also the minimum dihedral angle within 0.5
+degrees.  Two cases need a wider histogram bound, each set from the oracle against itself:
+  * the FP32 square: the FP32 path computes each step's forces with a relative error up to the
+    per-step tolerance 1e-5; the oracle whose accelerations carry a random relative error of
+    1e-5 in every step drifts from the unperturbed oracle by 1.5-1.9 % L1 in 200 steps (1e-6:
+    0.4-1.2 %), so the bound is 2 %;
+  * the disk (6,000 particles, 150 steps): the same per-step noise makes the oracle drift from
+    itself by 3.2-6.6 % L1 (1e-6: 3.9-5.5 %), about the sampling noise of a 50-bin histogram of
+    6,000 values once trajectories decorrelate, so its bound is 8 %.
+The minimum angle and the radius ratio move far less under the same perturbations (square:
+<= 0.03 degrees and <= 0.005; disk: <= 0.24 degrees and <= 0.0004).  The FP64 build is also compared position by position
+over a shorter horizon.
 """
 import math
 
@@ -18,6 +27,8 @@ from oracle import oracle as O
 from paper_2003_01061_gb300 import build as B
 from paper_2003_01061_gb300 import sphmesh as S
 from paper_2003_01061_gb300 import workloads as WL
+
+import bench
 
 pytestmark = pytest.mark.gpu
 
@@ -46,23 +57,9 @@ def spacing_hist(w, x, h_of):
 
 
 def quality_2d(w, x):
-    tri = Delaunay(x[:, :2])
-    P = x[tri.simplices][:, :, :2]
-    cen = np.concatenate([P.mean(axis=1), np.zeros((len(P), 1))], axis=1)
-    keep = WL.domain_phi(w["domain"], cen) > 0
-    P = P[keep]
-    e = np.stack([np.linalg.norm(P[:, 1] - P[:, 2], axis=1), np.linalg.norm(P[:, 0] - P[:, 2], axis=1),
-                  np.linalg.norm(P[:, 0] - P[:, 1], axis=1)], axis=1)
-    u, v = P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]
-    area = 0.5 * np.abs(u[:, 0] * v[:, 1] - u[:, 1] * v[:, 0])
-    half = e.sum(axis=1) / 2
-    G = 2 * math.sqrt(3) * area / (half * e.max(axis=1))
-    ang = []
-    for k in range(3):
-        a, b, c = e[:, k], e[:, (k + 1) % 3], e[:, (k + 2) % 3]
-        ang.append(np.degrees(np.arccos(np.clip((b * b + c * c - a * a) / (2 * b * c), -1, 1))))
-    tmin = np.min(np.stack(ang, 1), axis=1)
-    return float(tmin.mean()), float(G.mean())
+    """(mean minimum angle, mean G, minimum angle, minimum radius ratio, mean radius ratio)."""
+    q = bench.mesh_quality_2d(w, x)
+    return q["theta_min_avg"], q["G_avg"], q["theta_min"], q["rr_min"], q["rr_avg"]
 
 
 def run_both(w, prec, steps):
@@ -91,10 +88,12 @@ def test_square_200_steps_statistics(prec):
     assert rep.iteration == o.iteration
     hx = np.full(len(o.x), 0.02)
     hg, ho = spacing_hist(w, got["x"], hx), spacing_hist(w, o.x, hx)
-    # the 200-step square is an FP64 case (1 % L1); the FP32 path's trajectory drifts from the
-    # FP64 oracle's by its own rounding, so its histogram is held to 2 %
+    # FP64: 1 % L1; FP32: 2 %, the drift of the oracle whose forces carry the FP32 path's
+    # per-step tolerance as noise (module docstring)
     assert np.abs(hg - ho).sum() <= (0.01 if prec == 64 else 0.02)
     qg, qo = quality_2d(w, got["x"]), quality_2d(w, o.x)
+    assert abs(qg[2] - qo[2]) <= 0.5, (qg[2], qo[2])          # minimum angle
+    assert abs(qg[3] - qo[3]) <= 0.01 and abs(qg[4] - qo[4]) <= 0.01   # radius ratio
     assert abs(qg[0] - qo[0]) <= 0.5 and abs(qg[1] - qo[1]) <= 0.01
     # a relaxed lattice is at least as regular as the jittered start
     q0 = quality_2d(w, w["x"])
@@ -146,14 +145,41 @@ def test_disk_statistics_fp32():
     siz = w["sizing"]
     hg = spacing_hist(w, got["x"], WL.sizing_eval(siz, got["x"]))
     ho = spacing_hist(w, o.x, WL.sizing_eval(siz, o.x))
-    assert np.abs(hg - ho).sum() <= 0.05
+    assert np.abs(hg - ho).sum() <= 0.08, np.abs(hg - ho).sum()
     qg, qo = quality_2d(w, got["x"]), quality_2d(w, o.x)
+    assert abs(qg[2] - qo[2]) <= 0.5, (qg[2], qo[2])
+    assert abs(qg[3] - qo[3]) <= 0.01 and abs(qg[4] - qo[4]) <= 0.01
     assert abs(qg[0] - qo[0]) <= 0.5 and abs(qg[1] - qo[1]) <= 0.01
     # every curve particle stays on its circle (to the precision of the stored FP32 offset)
     for k, f in enumerate(w["domain"]["features"]):
         if f["kind"] == "circle":
             sel = got["group"] == k
             r = np.linalg.norm(got["x"][sel, :2] - np.asarray(f["c"][:2]), axis=1)
+            assert np.abs(r - f["r"]).max() < 1e-6 * w["h_lo"]
+
+
+def test_cube_sphere_statistics_fp32():
+    # the 3D workload's family (cube minus a sphere: edges, faces, sphere surface, volume,
+    # fixed corners) at ~8,000 particles for 100 steps; 3D trajectories drift little (the
+    # oracle with per-step force noise of 1e-5 stays within 0.05 % L1 of itself), so the
+    # 1 % histogram bound holds as stated
+    w = WL.cube_sphere(n_target=8000, seed=3, mc_samples=200_000)
+    w["params"] = WL.scaled_controller(w["params"], sample_every=5, window=10, ramp_len=50)
+    o, got, rep = run_both(w, 32, 100)
+    assert rep.status == 0 and rep.iteration == o.iteration
+    siz = w["sizing"]
+    hg = spacing_hist(w, got["x"], WL.sizing_eval(siz, got["x"]))
+    ho = spacing_hist(w, o.x, WL.sizing_eval(siz, o.x))
+    assert np.abs(hg - ho).sum() <= 0.01, np.abs(hg - ho).sum()
+    qg, qo = bench.mesh_quality_3d(w, got["x"]), bench.mesh_quality_3d(w, o.x)
+    assert abs(qg["theta_min"] - qo["theta_min"]) <= 0.5, (qg["theta_min"], qo["theta_min"])   # minimum dihedral
+    assert abs(qg["theta_min_avg"] - qo["theta_min_avg"]) <= 0.5
+    assert abs(qg["gamma_min"] - qo["gamma_min"]) <= 0.01 and abs(qg["gamma_avg"] - qo["gamma_avg"]) <= 0.01
+    # curve and surface particles stay on their features
+    for k, f in enumerate(w["domain"]["features"]):
+        sel = got["group"] == k
+        if f["kind"] == "sphere":
+            r = np.linalg.norm(got["x"][sel] - np.asarray(f["c"]), axis=1)
             assert np.abs(r - f["r"]).max() < 1e-6 * w["h_lo"]
 
 
