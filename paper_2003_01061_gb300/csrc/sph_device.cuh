@@ -587,10 +587,15 @@ __device__ __forceinline__ void walk_sub(const Grid& g, const int* __restrict__ 
     flush();
 }
 
-// sum over the LPP lanes of one particle (xor butterfly: every lane gets the same bits)
+// sum over the LPP lanes of one particle (xor butterfly: every lane gets the same bits).  The
+// lanes of a particle are consecutive and aligned, and the mask names only them: a caller may
+// branch per particle (all lanes of a particle take the same branch).
 template <int LPP, typename T> __device__ __forceinline__ T sub_sum(T v) {
+    static_assert(LPP >= 1 && LPP <= 32 && (LPP & (LPP - 1)) == 0, "lanes per particle: a power of two");
+    const unsigned mask =
+        LPP == 32 ? 0xffffffffu : ((1u << (LPP & 31)) - 1u) << ((threadIdx.x & 31u) & ~(unsigned)(LPP - 1));
 #pragma unroll
-    for (int o = 1; o < LPP; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 1; o < LPP; o <<= 1) v += __shfl_xor_sync(mask, v, o);
     return v;
 }
 

@@ -124,13 +124,15 @@ template <int D> struct Vcap {
 };
 // lanes per particle in the viscous pass; each lane reads Lpp/ILpp of the pressure pass's
 // hand-over columns, and the list-overflow fallback walks with ILpp lanes (measured: one lane
-// in 2D, 2 % faster than 2; in 3D, with 96 list slots per particle, 2 lanes are 19 % faster
-// than 4 and 1 lane 2 % faster than 2)
+// in 2D, 2 % faster than 2; in 3D with the 2.6h support and 192 list slots per particle, on the
+// 1.2M cube after 5 steps, 2 lanes make the pass 0.854 ms against 1.177 ms with one lane (27 %
+// faster; with 5 blocks per SM 0.891 ms), and 3 entries fetched together instead of 2 are 74 %
+// slower)
 #ifndef SPH_ILPP_2D
 #define SPH_ILPP_2D 1
 #endif
 #ifndef SPH_ILPP_3D
-#define SPH_ILPP_3D 1
+#define SPH_ILPP_3D 2
 #endif
 template <int D> struct ILpp {
     static constexpr int v = D == 2 ? SPH_ILPP_2D : SPH_ILPP_3D;
