@@ -44,7 +44,8 @@ class Params(C.Structure):
                 ("cfl_v", C.c_double), ("eps1", C.c_double), ("dt_cap", C.c_double), ("dt_collapse", C.c_double),
                 ("threshold", C.c_double), ("reset_period", C.c_int32), ("sample_every", C.c_int32),
                 ("window", C.c_int32), ("ramp_len", C.c_int32), ("boundary_rho", C.c_int32),
-                ("max_newton", C.c_int32), ("boundary_correction", C.c_int32), ("group_convergence", C.c_int32)]
+                ("max_newton", C.c_int32), ("boundary_correction", C.c_int32), ("group_convergence", C.c_int32),
+                ("feature_order", C.c_int32)]
 
 
 class Ctrl(C.Structure):
@@ -177,10 +178,14 @@ def make_sizing(s: dict) -> Sizing:
     return z
 
 
+# fields that parameter dictionaries may leave out (their value when absent)
+PARAM_DEFAULTS = {"feature_order": 0}
+
+
 def make_params(p: dict) -> Params:
     q = Params()
     for name, _ in Params._fields_:
-        setattr(q, name, p[name])
+        setattr(q, name, p[name] if name in p else PARAM_DEFAULTS[name])
     return q
 
 

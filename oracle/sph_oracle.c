@@ -684,12 +684,17 @@ static void group_step(const orc_params* prm, int g, const double* dta, const do
  * The instance's phase is that of its least advanced moving group (DONE when all are);
  * E_sys is the largest E_g; ramp_start is the step at which the last group left PHASE1.
  * ------------------------------------------------------------------------------------------ */
-static void control_per_group(const orc_params* prm, int G, const int32_t* gdim, const double* Vsum,
-                              const double* dta, const double* dtv, orc_ctrl* c) {
+typedef struct {
+    int lowest, evaluated;
+    double et, ea, es;
+} group_acc;
+
+/* steps 1-4 for the groups of intrinsic dimension `only_dim` (every moving group when 0) */
+static void group_pass(const orc_params* prm, int G, const int32_t* gdim, const double* Vsum,
+                       const double* dta, const double* dtv, orc_ctrl* c, int only_dim, group_acc* acc) {
     const int sampling = c->n % prm->sample_every == 0;
-    int lowest = ORC_DONE, evaluated = 0;
-    double et = 0, ea = 0, es = 0;
     for (int g = 0; g < G; ++g) {
+        if (only_dim > 0 && gdim[g] != only_dim) continue;
         if (gdim[g] < 1) { c->dt[g] = 0; c->reset[g] = 1; c->geps[g] = 0; c->gf[g] = 0; continue; }
         int ph = c->gphase[g];
         if (ph == ORC_RAMP && c->n - c->gramp_start[g] >= prm->ramp_len) {
@@ -711,9 +716,9 @@ static void control_per_group(const orc_params* prm, int G, const int32_t* gdim,
                 double e1 = rel_err(c->Vbar[g], c->A_last[g]);
                 double e2 = rel_err(c->A_last[g], c->A_prev[g]);
                 c->gE[g] = e1 > e2 ? e1 : e2;
-                if (e1 > et) et = e1;
-                if (e2 > ea) ea = e2;
-                evaluated = 1;
+                if (e1 > acc->et) acc->et = e1;
+                if (e2 > acc->ea) acc->ea = e2;
+                acc->evaluated = 1;
                 if (c->gE[g] < prm->threshold) {
                     if (ph == ORC_PHASE1) {
                         ph = ORC_RAMP;
@@ -726,8 +731,8 @@ static void control_per_group(const orc_params* prm, int G, const int32_t* gdim,
             }
         }
         c->gphase[g] = ph;
-        if (c->gE[g] > es) es = c->gE[g];
-        if (ph < lowest) lowest = ph;
+        if (c->gE[g] > acc->es) acc->es = c->gE[g];
+        if (ph < acc->lowest) acc->lowest = ph;
         if (ph == ORC_DONE) { c->dt[g] = 0; c->reset[g] = 1; c->geps[g] = 0; c->gf[g] = 0; continue; }
         double eps = prm->eps1, f = 1.0;
         int periodic = (c->n % prm->reset_period) == 0;
@@ -743,13 +748,25 @@ static void control_per_group(const orc_params* prm, int G, const int32_t* gdim,
         c->geps[g] = eps;
         c->gf[g] = f;
     }
-    if (evaluated) {
-        c->E_t = et;
-        c->E_avg = ea;
+}
+
+/* the instance's summary after every group has run: its phase is that of its least advanced
+ * moving group, E_sys the largest group error, ramp_start the step the last group left PHASE1 */
+static void group_summary(orc_ctrl* c, const group_acc* acc) {
+    if (acc->evaluated) {
+        c->E_t = acc->et;
+        c->E_avg = acc->ea;
     }
-    c->E_sys = es;
-    if (c->phase == ORC_PHASE1 && lowest > ORC_PHASE1) c->ramp_start = c->n;
-    c->phase = lowest;
+    c->E_sys = acc->es;
+    if (c->phase == ORC_PHASE1 && acc->lowest > ORC_PHASE1) c->ramp_start = c->n;
+    c->phase = acc->lowest;
+}
+
+static void control_per_group(const orc_params* prm, int G, const int32_t* gdim, const double* Vsum,
+                              const double* dta, const double* dtv, orc_ctrl* c) {
+    group_acc acc = {ORC_DONE, 0, 0.0, 0.0, 0.0};
+    group_pass(prm, G, gdim, Vsum, dta, dtv, c, 0, &acc);
+    group_summary(c, &acc);
 }
 
 /* ------------------------------------------------------------------------------------------
@@ -951,6 +968,51 @@ void orc_integrate(int64_t n, const orc_domain* dom, const orc_sizing* siz, cons
 }
 
 /* n_steps full steps of the relaxation (Jacobi over groups: every group reads state n). */
+/* One step in Algorithm 1's feature order (feature_order = 1): the groups are taken class by
+ * class in increasing intrinsic dimension (curves, surfaces, volume; singular points never
+ * move).  A class's pressure pass reads the positions that the lower classes reached in this
+ * step (they act on it as boundary particles, Eq. 19), its groups' controllers run on their own
+ * errors (group_convergence), and its viscous pass and update follow; groups of one class do
+ * not act on each other, so the order inside a class does not matter. */
+static void step_feature_order(int64_t n, const orc_domain* dom, const orc_sizing* siz, const orc_params* prm,
+                               orc_ctrl* c, double* x, double* v, double* h, const int32_t* grp, int32_t use_grid,
+                               const int32_t* gdim, double* sigma, double* ap, double* x2, double* v2, double* h2,
+                               int64_t* sub) {
+    const int G = dom->n_feat, D = dom->D;
+    group_acc acc = {ORC_DONE, 0, 0.0, 0.0, 0.0};
+    for (int d = 1; d <= D; ++d) {
+        int64_t m = 0;
+        for (int64_t i = 0; i < n; ++i)
+            if (gdim[grp[i]] == d) sub[m++] = i;
+        double dta[ORC_MAX_FEAT], dtv[ORC_MAX_FEAT], Vsum[ORC_MAX_FEAT];
+        for (int g = 0; g < G; ++g) { dta[g] = INFINITY; dtv[g] = INFINITY; Vsum[g] = 0; }
+        if (m > 0) {
+            orc_interact(n, dom, prm, x, h, grp, v, m, sub, use_grid, sigma, NULL, NULL, ap, NULL, dta, dtv);
+            for (int64_t s = 0; s < m; ++s)
+                if (sigma[s] > 0) Vsum[grp[sub[s]]] += 1.0 / sigma[s];
+        }
+        group_pass(prm, G, gdim, Vsum, dta, dtv, c, d, &acc);
+        if (m == 0) continue;
+        /* the viscous pass reads a_p of the class's particles by particle index */
+        double* ap_full = x2;   /* scratch: 3n doubles */
+        for (int64_t s = 0; s < m; ++s)
+            for (int a = 0; a < 3; ++a) ap_full[3 * sub[s] + a] = ap[3 * s + a];
+        int64_t esc = 0;
+        double* xo = ap;        /* scratch reuse: 3m doubles each */
+        orc_integrate(n, dom, siz, prm, c, x, h, grp, v, ap_full, m, sub, use_grid, xo, v2, h2, NULL, &esc);
+        for (int64_t s = 0; s < m; ++s) {
+            for (int a = 0; a < 3; ++a) {
+                x[3 * sub[s] + a] = xo[3 * s + a];
+                v[3 * sub[s] + a] = v2[3 * s + a];
+            }
+            h[sub[s]] = h2[s];
+        }
+        c->escapes += esc;
+    }
+    group_summary(c, &acc);
+    c->n += 1;
+}
+
 void orc_step(int64_t n, const orc_domain* dom, const orc_sizing* siz, const orc_params* prm,
               orc_ctrl* c, double* x, double* v, double* h, const int32_t* grp,
               int32_t use_grid, int32_t n_steps) {
@@ -958,6 +1020,18 @@ void orc_step(int64_t n, const orc_domain* dom, const orc_sizing* siz, const orc
     int32_t gdim[ORC_MAX_FEAT];
     for (int g = 0; g < G; ++g) gdim[g] = dom->feat[g].dim;
     size_t nn = (size_t)(n > 0 ? n : 1);
+    if (prm->feature_order == 1) {
+        double* sigma = (double*)malloc(sizeof(double) * nn);
+        double* ap = (double*)malloc(sizeof(double) * 3 * nn);
+        double* x2 = (double*)malloc(sizeof(double) * 3 * nn);
+        double* v2 = (double*)malloc(sizeof(double) * 3 * nn);
+        double* h2 = (double*)malloc(sizeof(double) * nn);
+        int64_t* sub = (int64_t*)malloc(sizeof(int64_t) * nn);
+        for (int s = 0; s < n_steps && c->phase != ORC_DONE; ++s)
+            step_feature_order(n, dom, siz, prm, c, x, v, h, grp, use_grid, gdim, sigma, ap, x2, v2, h2, sub);
+        free(sigma); free(ap); free(x2); free(v2); free(h2); free(sub);
+        return;
+    }
     double* sigma = (double*)malloc(sizeof(double) * nn);
     double* ap = (double*)malloc(sizeof(double) * 3 * nn);
     double* x2 = (double*)malloc(sizeof(double) * 3 * nn);

@@ -95,6 +95,11 @@ typedef struct {
     int32_t group_convergence;    /* 0: the instance changes phase on E_sys (Sec. 3.4.2);
                               1: every group runs its own phases on its own E_g and stops when
                               it has converged (Algorithm 1: "if V-bar_k is not converged")     */
+    int32_t feature_order;        /* 0: every group reads the state at the start of the step
+                              (Jacobi); 1: Algorithm 1's feature loop in sequence (Gauss-Seidel):
+                              the groups are advanced class by class in increasing intrinsic
+                              dimension, each class reading the positions the lower classes
+                              reached in this step (requires group_convergence = 1)            */
 } orc_params;
 
 /* two-phase controller state (Sec. 3.4) */
