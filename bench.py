@@ -81,9 +81,15 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=200)
-    ap.add_argument("--serve-jobs", type=int, default=32)
-    ap.add_argument("--serve-iters", type=int, default=600)
-    ap.add_argument("--serve-max-n", type=int, default=200_000)
+    ap.add_argument("--serve-jobs", type=int, default=24, help="arrivals of the 50 jobs/s stream served")
+    ap.add_argument("--serve-iters", type=int, default=3000, help="iteration limit of a served job")
+    ap.add_argument("--serve-max-n", type=int, default=2_000_000)
+    ap.add_argument("--serve-threshold", type=float, default=1e-2,
+                    help="Phase-One/Two threshold of served jobs (the level the method reaches under this "
+                         "build's readings; the paper's 5e-6 is never reached)")
+    ap.add_argument("--serve-70-jobs", type=int, default=12)
+    ap.add_argument("--fp64-subset-max-n", type=int, default=60_000)
+    ap.add_argument("--fp64-subset-jobs", type=int, default=4)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cube", action="store_true")
     ap.add_argument("--no-presets", action="store_true")
@@ -196,6 +202,24 @@ def make_disk(n):
     from paper_2003_01061_gb300 import workloads as WL
 
     return WL.disk_holes(n_target=n, seed=2)
+
+
+def _gen_problem(spec):
+    """A job given by its problem alone (its particles are drawn on the device at admission)."""
+    from paper_2003_01061_gb300 import workloads as WL
+
+    kind, n, seed, r = spec
+    if kind == 2:
+        return WL.disk_holes(n_target=n, seed=seed, mc_samples=100_000, sample=False)
+    return WL.cube_sphere(n_target=n, seed=seed, sphere_r=r, mc_samples=100_000, sample=False)
+
+
+def generate_problems(specs):
+    import multiprocessing as mp
+
+    procs = max(1, min(16, (os.cpu_count() or 2) - 1, len(specs)))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_gen_problem, specs, chunksize=1)
 
 
 def _gen_one(spec):
@@ -325,7 +349,7 @@ def run_ours(args):
         batch_ws = generate(specs)
     if rank == 0 and not args.no_serve:
         specs, serve_t = _specs(args.serve_jobs, 5, 1_000, args.serve_max_n, alternate=False, rate=50.0)
-        serve_ws = generate(specs)
+        serve_ws = generate_problems(specs)
     if ws > 1:
         import torch.distributed as dist
 
@@ -384,16 +408,7 @@ def run_ours(args):
                              "l2": "working set larger than L2 (no flush)"}
     serving = None
     if serve_ws is not None:
-        serving = serving_run(S, serve_ws, serve_t, args.serve_iters)
-        serving["config"] = {"workload": f"{args.serve_jobs} jobs, Poisson 50 jobs/s (seed 5), half 2D disks "
-                                         f"with holes / half 3D cubes minus a sphere, n log-uniform "
-                                         f"1k-{args.serve_max_n // 1000}k, paper controller, "
-                                         f"max {args.serve_iters} iterations, 20 steps per round"}
-        if not args.no_fp64:
-            serving["fp64_one_at_a_time"] = fp64_one_at_a_time(S, serve_ws, serve_t, args.serve_iters)
-        # the same arrivals given by their problems alone: particles drawn on the device at
-        # admission, inside each job's latency
-        serving["sampled_on_device"] = serving_run(S, serve_ws, serve_t, args.serve_iters, sampled=True)
+        serving = serving_legs(S, serve_ws, serve_t, args)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -781,24 +796,28 @@ def batched_run(S, torch, dev, ws, steps):
     return out
 
 
-def serving_run(S, jobs, times, max_iters, steps_per_poll=20, sampled=False):
-    """Real-time Poisson arrivals into the server; latency from the scheduled arrival.  With
-    sampled=True every job is submitted by its problem alone and its particles are drawn on the
-    device at admission (inside its latency)."""
-    srv = S.Server(precision=32, max_jobs=64, slot_capacity=(-1, -1), hbm_fraction=0.3,
+def serving_run(S, jobs, times, max_iters, threshold, precision=32, max_jobs=64, steps_per_poll=20):
+    """Real-time arrivals into the server, every job given by its problem alone (its particles
+    drawn on the device at admission, Sec. 3.6) with the paper's controller at `threshold`;
+    jobs retire when their two-phase criterion converges (DONE) or at max_iters.  Per job:
+    latency = finish - scheduled arrival, queueing = admission - scheduled arrival, service =
+    finish - admission (all host clock)."""
+    srv = S.Server(precision=precision, max_jobs=max_jobs, slot_capacity=(-1, -1), hbm_fraction=0.3,
                    steps_per_poll=steps_per_poll)
-    # warm the step graphs with one small job of each dimension
-    for w in {w["domain"]["D"]: w for w in jobs}.values():
-        srv.submit(w, steps_per_poll)
+    prm = [dict(w["params"], threshold=threshold) for w in jobs]
+    # warm the step graphs with one small job of each dimension (not counted)
+    for D in sorted({w["domain"]["D"] for w in jobs}):
+        i = next(i for i, w in enumerate(jobs) if w["domain"]["D"] == D)
+        srv.submit_sampled(jobs[i], steps_per_poll, seed=12345, params=prm[i])
     srv.drain()
-    ids, py_sub = [], []
+    ids, lag = [], []
     t0 = time.perf_counter()
     k = 0
     while True:
         now = time.perf_counter() - t0
         while k < len(jobs) and times[k] <= now:
-            ids.append(srv.submit_sampled(jobs[k], max_iters, seed=k + 1) if sampled else srv.submit(jobs[k], max_iters))
-            py_sub.append(time.perf_counter() - t0)
+            ids.append(srv.submit_sampled(jobs[k], max_iters, seed=k + 1, params=prm[k]))
+            lag.append((time.perf_counter() - t0) - times[k])    # submission after the scheduled arrival
             k += 1
         st = srv.poll()
         if k == len(jobs) and st.running == 0 and st.queued == 0:
@@ -806,44 +825,73 @@ def serving_run(S, jobs, times, max_iters, steps_per_poll=20, sampled=False):
         if st.running == 0 and st.queued == 0 and k < len(jobs):
             time.sleep(max(0.0, times[k] - (time.perf_counter() - t0)))
     wall = time.perf_counter() - t0
-    lat, psteps, states = [], 0.0, {}
+    lat, que, svc, work, iters, n_of, states = [], [], [], [], [], [], {}
     t_end = 0.0
     for i, jid in enumerate(ids):
         info, _ = srv.job(jid, with_result=False)
-        delay = py_sub[i] - times[i]
-        lat.append(info.t_finish - info.t_submit + delay)
-        psteps += info.n * info.iterations
+        lat.append(info.t_finish - info.t_submit + lag[i])
+        que.append(info.t_admit - info.t_submit + lag[i])
+        svc.append(info.t_finish - info.t_admit)
+        work.append(float(info.n) * float(info.iterations))
+        iters.append(int(info.iterations))
+        n_of.append(int(info.n))
         states[int(info.state)] = states.get(int(info.state), 0) + 1
         t_end = max(t_end, times[i] + lat[-1])
     srv.close()
-    lat = np.array(lat)
-    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_s": float(lat.mean()), "value": psteps / (t_end - times[0]), "unit": METRIC,
-            "wall_s": wall, "jobs": len(jobs), "particle_steps": psteps,
-            "done": states.get(S.JOB_DONE, 0), "not_converged": states.get(S.JOB_NOT_CONVERGED, 0),
-            "failed": states.get(S.JOB_FAILED, 0)}
+    lat, que, svc = np.array(lat), np.array(que), np.array(svc)
+    pct = lambda a, q: float(np.percentile(a, q))
+    return {"p50_s": pct(lat, 50), "p99_s": pct(lat, 99), "mean_s": float(lat.mean()),
+            "queueing_p50_s": pct(que, 50), "queueing_p99_s": pct(que, 99),
+            "service_p50_s": pct(svc, 50), "service_p99_s": pct(svc, 99),
+            "value": float(sum(work)) / (t_end - times[0]), "unit": METRIC, "wall_s": wall, "jobs": len(jobs),
+            "particle_steps": float(sum(work)), "mean_job_work": float(np.mean(work)),
+            "iterations_p50": pct(np.array(iters), 50), "particles": n_of, "iterations": iters,
+            "latency_s": lat.tolist(), "done": states.get(S.JOB_DONE, 0),
+            "not_converged": states.get(S.JOB_NOT_CONVERGED, 0), "failed": states.get(S.JOB_FAILED, 0)}
 
 
-def fp64_one_at_a_time(S, jobs, times, max_iters):
-    """The same jobs served one at a time by the plain FP64 single-instance path (FIFO)."""
-    service, psteps = [], 0.0
-    for w in jobs:
-        t = time.perf_counter()
-        m = S.Mesh(w, precision=64)
-        m.set_state()
-        ok, it = S.sph_mesh_run_until_converged(m.h, max_iters)
-        m.positions()
-        m.close()
-        service.append(time.perf_counter() - t)
-        psteps += len(w["x"]) * it
-    fin, lat = 0.0, []
-    for a, sv in zip(times, service):
-        fin = max(fin, a) + sv
-        lat.append(fin - a)
-    lat = np.array(lat)
-    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_s": float(lat.mean()), "value": psteps / (fin - times[0]), "unit": METRIC,
-            "service_s_total": float(sum(service)), "queueing": "FIFO on measured service times"}
+def serving_legs(S, jobs, times, args):
+    """cfg5: (1) the seeded Poisson stream at 50 jobs/s (first --serve-jobs arrivals), N
+    log-uniform over 1k-2M, half 2D disks with holes / half 3D cubes minus a sphere; (2) the same
+    job mix at 70 % of the capacity measured in (1); (3) the plain FP64 path serving one job at a
+    time (a server with one slot, precision 64) on a subset of (1)'s arrivals, beside the FP32
+    server's latencies for the same jobs in (1)."""
+    thr, cap_it = args.serve_threshold, args.serve_iters
+    out = serving_run(S, jobs, times, cap_it, thr)
+    out["config"] = {"workload": f"first {len(jobs)} arrivals of a Poisson stream at 50 jobs/s (seed 5), 2D disks "
+                                 f"with holes / 3D cubes minus a sphere with probability 1/2, n log-uniform "
+                                 f"1k-{args.serve_max_n // 1000}k, particles drawn on the device at admission, "
+                                 f"paper controller (sample every 20, window 10, ramp 200, reset period 100) with "
+                                 f"threshold {thr:g}, at most {cap_it} iterations, 20 steps per scheduling round",
+                     "threshold_reason": "the paper's 5e-6 is never reached under this build's readings of "
+                                         "Eq. 24 and the integrator (see the design notes); at this threshold "
+                                         "jobs retire on convergence"}
+    # (2) the same mix at 70 % of the measured capacity
+    cap = out["value"]
+    rate70 = 0.7 * cap / out["mean_job_work"]
+    k70 = min(args.serve_70_jobs, len(jobs))
+    rng = np.random.default_rng(55)
+    t70 = np.cumsum(rng.exponential(1.0 / rate70, k70)).tolist()
+    r70 = serving_run(S, jobs[:k70], t70, cap_it, thr)
+    r70["config"] = {"rate_jobs_per_s": rate70, "capacity_particle_steps_per_s": cap,
+                     "workload": f"the first {k70} problems of (1), Poisson arrivals (seed 55) at 70 % of the "
+                                 f"capacity measured in (1)"}
+    out["at_70pct_capacity"] = r70
+    # (3) the plain FP64 path, one job at a time, on a subset
+    sub = [i for i, w in enumerate(jobs) if w.get("n_expected", 0) <= args.fp64_subset_max_n][:args.fp64_subset_jobs]
+    if sub:
+        r64 = serving_run(S, [jobs[i] for i in sub], [times[i] - times[sub[0]] for i in sub], cap_it, thr,
+                          precision=64, max_jobs=1)
+        r64["config"] = {"subset": f"arrivals {sub} of (1) (the first {len(sub)} with n <= "
+                                   f"{args.fp64_subset_max_n}), same arrival times, one job at a time, FP64"}
+        r64["fp32_server_same_jobs_in_the_mix"] = {
+            "p50_s": float(np.percentile([out["latency_s"][i] for i in sub], 50)),
+            "p99_s": float(np.percentile([out["latency_s"][i] for i in sub], 99))}
+        # the same subset through the FP32 server alone (same arrivals, nothing else resident)
+        r32 = serving_run(S, [jobs[i] for i in sub], [times[i] - times[sub[0]] for i in sub], cap_it, thr)
+        r64["fp32_server_same_jobs_alone"] = {k: r32[k] for k in ("p50_s", "p99_s", "value", "done")}
+        out["fp64_one_at_a_time"] = r64
+    return out
 
 
 def main():

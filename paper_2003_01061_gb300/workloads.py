@@ -350,12 +350,13 @@ def _disk_holes_geometry(rng, n_holes=3):
 
 
 def disk_holes(n_target: int | None = 120_000, seed: int = 2, params: dict | None = None,
-               mc_samples: int = 2_000_000):
+               mc_samples: int = 2_000_000, sample: bool = True):
     """Unit disk minus 3 seeded holes; h linear in the distance to the nearest hole (0.004-0.04).
 
     ``n_target=None`` keeps the literal sizing; otherwise every length of h is scaled by one
     factor c chosen so that the integral of rho_t over all features is about n_target
-    (volume part by Monte Carlo with ``mc_samples`` points).
+    (volume part by Monte Carlo with ``mc_samples`` points).  ``sample=False`` returns the
+    problem alone (no particles; for jobs whose particles are drawn on the device).
     """
     rng = np.random.default_rng(seed)
     holes = _disk_holes_geometry(rng)
@@ -394,6 +395,10 @@ def disk_holes(n_target: int | None = 120_000, seed: int = 2, params: dict | Non
     siz = make_siz(scale)
     nv, nc = counts(siz)
     feats = [dict(kind="volume", dim=2)]
+    if not sample:
+        feats += [dict(kind="circle", dim=1, c=[cc[0], cc[1], 0.0], r=R, orient=o) for cc, R, o in circles]
+        return _finish("disk_holes", dom, siz, feats, [np.zeros((0, 3))], [np.zeros(0)], params or PAPER_PARAMS,
+                       scale=scale, h_lo=siz["lo"], h_hi=siz["hi"], n_expected=int(round(nv + sum(nc))))
     xs, gs = [], []
     xs.append(_sample_volume(rng, dom, siz, int(round(nv)), siz["lo"]))
     gs.append(np.zeros(len(xs[-1])))
@@ -406,7 +411,7 @@ def disk_holes(n_target: int | None = 120_000, seed: int = 2, params: dict | Non
 
 
 def cube_sphere(n_target: int | None = 1_200_000, seed: int = 3, params: dict | None = None, sphere_r: float = 0.3,
-                mc_samples: int = 2_000_000):
+                mc_samples: int = 2_000_000, sample: bool = True):
     """[0,1]^3 minus a centred sphere; h = min(0.008 + 0.04 |d_sphere|, 0.05), optionally scaled."""
     rng = np.random.default_rng(seed)
     cs = np.array([0.5, 0.5, 0.5])
@@ -472,6 +477,10 @@ def cube_sphere(n_target: int | None = 1_200_000, seed: int = 3, params: dict | 
     siz = make_siz(scale)
     nv, nf, ns, ne = counts(siz)
     feats = [dict(kind="volume", dim=3)] + faces + [sphere] + edges + corners
+    if not sample:   # the problem alone (particles drawn on the device)
+        return _finish("cube_sphere", dom, siz, feats, [np.zeros((0, 3))], [np.zeros(0)], params or PAPER_PARAMS,
+                       scale=scale, h_lo=siz["lo"], h_hi=siz["hi"],
+                       n_expected=int(round(nv + sum(nf) + ns + sum(ne) + len(corners))))
     xs = [_sample_volume(rng, dom, siz, int(round(nv)), siz["lo"])]
     gs = [np.zeros(len(xs[0]))]
     for k, f in enumerate(faces):
