@@ -131,6 +131,13 @@ typedef struct {
                               runs its own phases on its own error and stops moving once it
                               has converged (Algorithm 1 skips a converged feature); the
                               instance is then in the phase of its least advanced group   [0]  */
+    int32_t feature_order;  /* 0: every group reads the state at the start of the step (the
+                              data-parallel reading of Algorithm 1's feature loop); 1: the loop
+                              in sequence: a step advances the curves, then the surfaces, then
+                              the volume, each reading the positions the lower-dimensional
+                              features reached in the step (they act on it through Eq. 19).
+                              Requires group_convergence = 1 (the loop checks each feature's
+                              own convergence)                                             [0]  */
 } sph_params;
 
 /* Method presets of the comparison in Sec. 4.1 (Square, its table of N_iter): the improved

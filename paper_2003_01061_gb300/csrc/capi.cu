@@ -205,8 +205,10 @@ sph_status make_instance(const sph_domain_desc* dd, const sph_sizing_desc* sz, c
         !(pp->dt_cap > 0) || pp->dt_collapse < 0 || !(pp->threshold > 0) || pp->reset_period < 1 ||
         pp->sample_every < 1 || pp->window < 1 || pp->ramp_len < 1 || (pp->boundary_rho != 0 && pp->boundary_rho != 1) ||
         (pp->boundary_correction != 0 && pp->boundary_correction != 1) ||
-        (pp->group_convergence != 0 && pp->group_convergence != 1))
+        (pp->group_convergence != 0 && pp->group_convergence != 1) || (pp->feature_order != 0 && pp->feature_order != 1))
         return fail(SPH_E_INVALID, "params: value out of range");
+    if (pp->feature_order == 1 && pp->group_convergence != 1)
+        return fail(SPH_E_INVALID, "params: feature_order = 1 (Algorithm 1's loop in sequence) needs group_convergence = 1");
     if (max_particles < 0 || max_particles > (int64_t)1 << 30) return fail(SPH_E_INVALID, "max_particles out of range");
     if (sz->kind < 0 || sz->kind > 2 || !(sz->lo > 0) || !(sz->hi >= sz->lo) || sz->n_ref < 0 || sz->n_ref > SPH_MAX_HOLES)
         return fail(SPH_E_INVALID, "sizing: need kind 0..2, 0 < lo <= hi, n_ref <= %d", SPH_MAX_HOLES);
@@ -296,6 +298,7 @@ sph_status make_instance(const sph_domain_desc* dd, const sph_sizing_desc* sz, c
     p.boundary_rho = pp->boundary_rho;
     p.boundary_corr = pp->boundary_correction;
     p.group_conv = pp->group_convergence;
+    p.feature_order = pp->feature_order;
     p.kappa_f = (float)p.kappa;
     p.p0_f = (float)p.p0;
     p.visc_f = (float)p.visc;
@@ -725,6 +728,27 @@ template <typename T> Out<T> out_stored(const State<T>& s) {
 template <typename T, int D> void enqueue_step(sph_batch* b, bool timed) {
     const State<T>& s = st<T>(b);
     cudaStream_t stream = b->stream;
+    bool seq = false;
+    for (const Inst& I : b->in) seq = seq || (I.n > 0 && I.params.feature_order != 0);
+    if (seq) {
+        // Algorithm 1's feature loop in sequence: one pass per dimension class (curves, surfaces,
+        // volume), each re-sorting the state the previous pass left (the update writes the next
+        // keys and histogram) and moving its class; the stage events bracket the first pass and
+        // the step's end
+        for (int cls = 1; cls <= D; ++cls) {
+            const bool first = cls == 1;
+            if (timed && first) cudaEventRecordWithFlags(b->ev[0], stream, cudaEventRecordExternal);
+            enqueue_rebuild<T, D>(b, s, stream);
+            if (timed && first) cudaEventRecordWithFlags(b->ev[1], stream, cudaEventRecordExternal);
+            launch_interact<T, D>(s, one_of(b), nullptr, nullptr, stream, !timed, cls);
+            if (timed && first) cudaEventRecordWithFlags(b->ev[2], stream, cudaEventRecordExternal);
+            launch_control<T, D>(s, one_of(b), stream, !timed, cls);
+            if (timed && first) cudaEventRecordWithFlags(b->ev[3], stream, cudaEventRecordExternal);
+            launch_integrate<T, D>(s, one_of(b), s.ctrls, out_stored<T>(s), stream, !timed, cls);
+        }
+        if (timed) cudaEventRecordWithFlags(b->ev[4], stream, cudaEventRecordExternal);
+        return;
+    }
     if (timed) cudaEventRecordWithFlags(b->ev[0], stream, cudaEventRecordExternal);
     enqueue_rebuild<T, D>(b, s, stream);
     if (timed) cudaEventRecordWithFlags(b->ev[1], stream, cudaEventRecordExternal);

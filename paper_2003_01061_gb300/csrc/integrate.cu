@@ -38,21 +38,26 @@ __device__ inline void group_window_reset(Ctrl& c, int g) {
 // below the threshold moves the group PHASE1 -> RAMP or PHASE2 -> DONE; the group's eps, f,
 // nullification schedule and step size follow its phase; a DONE group does not move.  Thread
 // 0 then sets the instance's phase to that of its least advanced moving group (DONE when all
-// are), E_sys to the largest E_g and ramp_start to the step the last group left PHASE1.
+// are), E_sys to the largest E_g and ramp_start to the step the last group left PHASE1.  With
+// Algorithm 1's feature loop in sequence (feature_order), the pass for dimension class cls runs
+// the groups of that class only, the step's errors are gathered over its passes, and the
+// summary (and the step counter) closes the last pass.
 template <typename T>
-__device__ void control_groups(Ctrl& sc, const Params& p, const double* vs, int t) {
+__device__ void control_groups(Ctrl& sc, const Params& p, const double* vs, int t, int cls, int D) {
     __shared__ int gl[MAXF], gev[MAXF];
     __shared__ double ge1[MAXF], ge2[MAXF];
     const int G = p.G;
     const bool inst_done = sc.phase == PH_DONE;
     const bool sampling = sc.n % p.sample_every == 0;
+    // with the feature loop in sequence this pass serves the groups of dimension class cls only
+    const bool seq = cls != 0 && p.feature_order;
     if (t < MAXF) {
-        gl[t] = PH_DONE;
+        gl[t] = t < G ? sc.gphase[t] : PH_DONE;
         gev[t] = 0;
         ge1[t] = 0.0;
         ge2[t] = 0.0;
     }
-    if (t < G) {
+    if (t < G && (!seq || p.gdim[t] == cls)) {
         const int g = t;
         int ph = inst_done ? PH_DONE : sc.gphase[g];
         if (p.gdim[g] >= 1 && ph != PH_DONE) {
@@ -131,18 +136,42 @@ __device__ void control_groups(Ctrl& sc, const Params& p, const double* vs, int 
         sc.dtv_bits[t] = inf_bits<T>();
     }
     __syncthreads();
-    if (t == 0 && !inst_done) {
-        int lowest = PH_DONE, any = 0;
-        double es = 0.0, et = 0.0, ea = 0.0;
-        for (int g = 0; g < G; ++g) {
-            if (p.gdim[g] < 1) continue;
-            lowest = min(lowest, gl[g]);
-            es = fmax(es, sc.gE[g]);
-            if (gev[g]) {
+    if (t == 0 && !inst_done && seq) {   // the errors of the step's passes so far
+        int any = 0;
+        double et = 0.0, ea = 0.0;
+        for (int g = 0; g < G; ++g)
+            if (p.gdim[g] >= 1 && gev[g]) {
                 any = 1;
                 et = fmax(et, ge1[g]);
                 ea = fmax(ea, ge2[g]);
             }
+        if (cls == 1) {
+            sc.seq_et = 0.0;
+            sc.seq_ea = 0.0;
+            sc.seq_ev = 0;
+        }
+        sc.seq_et = fmax(sc.seq_et, et);
+        sc.seq_ea = fmax(sc.seq_ea, ea);
+        sc.seq_ev |= any;
+    }
+    if (t == 0 && !inst_done && (!seq || cls == D)) {
+        int lowest = PH_DONE;
+        double es = 0.0, et = 0.0, ea = 0.0;
+        int any = 0;
+        for (int g = 0; g < G; ++g) {
+            if (p.gdim[g] < 1) continue;
+            lowest = min(lowest, gl[g]);
+            es = fmax(es, sc.gE[g]);
+            if (!seq && gev[g]) {
+                any = 1;
+                et = fmax(et, ge1[g]);
+                ea = fmax(ea, ge2[g]);
+            }
+        }
+        if (seq) {
+            et = sc.seq_et;
+            ea = sc.seq_ea;
+            any = sc.seq_ev;
         }
         if (any) {
             sc.E_t = et;
@@ -174,7 +203,8 @@ __device__ void control_groups(Ctrl& sc, const Params& p, const double* vs, int 
 //  4. per group dt = min(dta, dtv/f), nullified (dt = dta) on the schedule or when dt falls
 //     below dt_collapse times the group's previous step; dt <= dt_cap (Eq. 24).
 // DONE freezes the state (dt = 0, the step counter stops).
-template <typename T, int D, bool ONE> __global__ void __launch_bounds__(CTL_THREADS) k_control(State<T> s, One one) {
+template <typename T, int D, bool ONE>
+__global__ void __launch_bounds__(CTL_THREADS) k_control(State<T> s, One one, int cls) {
     dep_launch();
     dep_wait();
     __shared__ double vs[MAXF], et[MAXF], ea[MAXF];
@@ -194,6 +224,8 @@ template <typename T, int D, bool ONE> __global__ void __launch_bounds__(CTL_THR
     if (!ONE) block_copy(&psh, s.params + inst);
     const Params& p = ONE ? one.p : psh;
     __syncthreads();
+    // an instance stepping all its groups at once runs its controller in the last class pass
+    if (cls != 0 && !p.feature_order && cls != D) return;
     const int G = p.G;
     if (sc.sample_now != 0) {
         // the pair-pass blocks of this instance (BLOCK/LPP slots each), CTL_GP groups at a
@@ -231,7 +263,7 @@ template <typename T, int D, bool ONE> __global__ void __launch_bounds__(CTL_THR
     }
     if (p.group_conv) {
         __syncthreads();
-        control_groups<T>(sc, p, vs, t);
+        control_groups<T>(sc, p, vs, t, cls, D);
         __syncthreads();
         for (int k = t; k < NW; k += blockDim.x) gw[k] = scw[k];
         return;
@@ -433,7 +465,7 @@ template <typename T> __device__ __forceinline__ T domain_phi_t(const Domain& do
 // Padding slots are copied through unchanged.
 template <typename T, int D, bool ONE>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRATE_MINB_2D : SPH_INTEGRATE_MINB_3D) : 4)
-    k_integrate(State<T> s, One one, const Ctrl* use, Out<T> o) {
+    k_integrate(State<T> s, One one, const Ctrl* use, Out<T> o, int cls) {
     dep_launch();
     dep_wait();
     constexpr int LPP = ILpp<D>::v, LPI = Lpp<D>::v, NCOL = LPI / LPP;
@@ -494,7 +526,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRAT
     // scalars need no load that waits for the particle's group
     bool done = cu->phase == PH_DONE;
     if (p.group_conv && !done && inrange && di > 0) done = cu->gphase[gi] == PH_DONE;
-    const bool moving = inrange && di > 0 && !done;
+    const bool moving = inrange && di > 0 && !done && in_pass(p, cls, di, D);
     T av[3] = {T(0), T(0), T(0)};
     T hnew = hi;
     T dt = T(0), f = T(1), eps = T(0);
@@ -685,21 +717,21 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRAT
     }
 }
 
-template <typename T, int D> void launch_control(const State<T>& s, const One* one, cudaStream_t st, bool pdl) {
-    if (one) launch_k(k_control<T, D, true>, s.NI, CTL_THREADS, st, pdl, s, *one);
-    else launch_k(k_control<T, D, false>, s.NI, CTL_THREADS, st, pdl, s, One());
+template <typename T, int D> void launch_control(const State<T>& s, const One* one, cudaStream_t st, bool pdl, int cls) {
+    if (one) launch_k(k_control<T, D, true>, s.NI, CTL_THREADS, st, pdl, s, *one, cls);
+    else launch_k(k_control<T, D, false>, s.NI, CTL_THREADS, st, pdl, s, One(), cls);
 }
 template <typename T, int D>
 void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const Out<T>& o, cudaStream_t st,
-                      bool pdl) {
+                      bool pdl, int cls) {
     const int nb = div_up((long long)s.n * ILpp<D>::v, BLOCK);
-    if (one) launch_k(k_integrate<T, D, true>, nb, BLOCK, st, pdl, s, *one, use, o);
-    else launch_k(k_integrate<T, D, false>, nb, BLOCK, st, pdl, s, One(), use, o);
+    if (one) launch_k(k_integrate<T, D, true>, nb, BLOCK, st, pdl, s, *one, use, o, cls);
+    else launch_k(k_integrate<T, D, false>, nb, BLOCK, st, pdl, s, One(), use, o, cls);
 }
 
 #define SPH_INST(T, D)                                                      \
-    template void launch_control<T, D>(const State<T>&, const One*, cudaStream_t, bool);      \
-    template void launch_integrate<T, D>(const State<T>&, const One*, const Ctrl*, const Out<T>&, cudaStream_t, bool);
+    template void launch_control<T, D>(const State<T>&, const One*, cudaStream_t, bool, int);      \
+    template void launch_integrate<T, D>(const State<T>&, const One*, const Ctrl*, const Out<T>&, cudaStream_t, bool, int);
 SPH_INST(float, 2)
 SPH_INST(float, 3)
 SPH_INST(double, 2)

@@ -22,7 +22,7 @@ namespace sph {
 
 template <typename T, int D, bool ONE>
 __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTERACT_MINB : SPH_INTERACT_MINB_3D) : 4)
-    k_interact(State<T> s, One one, T* dbg_sigma, T* dbg_gamma) {
+    k_interact(State<T> s, One one, T* dbg_sigma, T* dbg_gamma, int cls) {
     dep_launch();
     dep_wait();
     constexpr int LPP = Lpp<D>::v;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTERACT
     const int gi = inrange ? meta_group(mi) : -1;
     const int di = inrange ? meta_dim(mi) : 0;
     // a converged (DONE) instance is frozen: no pair work
-    bool active = inrange && di > 0 && ctrl->phase != PH_DONE;
+    bool active = inrange && di > 0 && ctrl->phase != PH_DONE && in_pass(p, cls, di, D);
     if (p.group_conv && active) active = ctrl->gphase[gi] != PH_DONE;   // the group itself converged
     T tg[3] = {T(0), T(0), T(0)};
     if (active && di < D) {
@@ -277,9 +277,10 @@ __global__ void __launch_bounds__(BLOCK) k_pair_counts(State<T> s, unsigned long
 }
 
 template <typename T, int D>
-void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, cudaStream_t st, bool pdl) {
-    if (one) launch_k(k_interact<T, D, true>, s.nblk, BLOCK, st, pdl, s, *one, dbg_sigma, dbg_gamma);
-    else launch_k(k_interact<T, D, false>, s.nblk, BLOCK, st, pdl, s, One(), dbg_sigma, dbg_gamma);
+void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, cudaStream_t st, bool pdl,
+                     int cls) {
+    if (one) launch_k(k_interact<T, D, true>, s.nblk, BLOCK, st, pdl, s, *one, dbg_sigma, dbg_gamma, cls);
+    else launch_k(k_interact<T, D, false>, s.nblk, BLOCK, st, pdl, s, One(), dbg_sigma, dbg_gamma, cls);
 }
 template <typename T, int D>
 void launch_neighbors(const State<T>& s, int mode, int* counts, const long long* offsets, int* lists, cudaStream_t st) {
@@ -290,7 +291,7 @@ template <typename T, int D> void launch_pair_counts(const State<T>& s, unsigned
 }
 
 #define SPH_INST(T, D)                                                                                        \
-    template void launch_interact<T, D>(const State<T>&, const One*, T*, T*, cudaStream_t, bool);             \
+    template void launch_interact<T, D>(const State<T>&, const One*, T*, T*, cudaStream_t, bool, int);        \
     template void launch_neighbors<T, D>(const State<T>&, int, int*, const long long*, int*, cudaStream_t);   \
     template void launch_pair_counts<T, D>(const State<T>&, unsigned long long*, cudaStream_t);
 SPH_INST(float, 2)

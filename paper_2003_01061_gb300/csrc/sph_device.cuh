@@ -88,6 +88,9 @@ struct Params {
     int reset_period, sample_every, window, ramp_len, boundary_rho;
     int boundary_corr;   // 0: the boundary sum of Eq. 19 is left out (earlier method, Sec. 4.1)
     int group_conv;      // 1: every group runs its own phases (Algorithm 1's per-feature check)
+    int feature_order;   // 1: Algorithm 1's feature loop in sequence: the step runs one pass per
+                         // intrinsic dimension (curves, surfaces, volume), each reading the lower
+                         // classes' new positions; 0: one pass for all (Jacobi)
     int G;
     int gdim[MAXF];      // intrinsic dimension of every group (feature)
     float kappa_f, p0_f, visc_f, cfl_a_f, cfl_v_f;   // float copies for the FP32 kernels
@@ -115,6 +118,9 @@ struct alignas(16) Ctrl {
     int gwcount[MAXF], gnwin[MAXF];
     long long gramp_start[MAXF];
     double gE[MAXF];
+    // feature order: the step's largest errors of the groups evaluated in the earlier class passes
+    double seq_et, seq_ea;
+    int seq_ev, seq_pad[3];
 };
 
 template <typename T> struct alignas(4 * sizeof(T)) Vec4 { T x, y, z, w; };

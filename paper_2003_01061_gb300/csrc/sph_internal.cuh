@@ -183,6 +183,15 @@ static_assert(Lpp<2>::v % ILpp<2>::v == 0 && Lpp<3>::v % ILpp<3>::v == 0,
 #define SPH_VISC_BATCH 2
 #endif
 
+// Whether a particle of intrinsic dimension di takes part in the step pass for dimension class
+// cls: 0 is the whole step at once; with Algorithm 1's feature loop in sequence (feature_order)
+// a step runs the passes cls = 1 .. D in turn and each moves the particles of its class, and an
+// instance without it (batched with one that has it) takes its whole step in the last pass.
+__device__ __forceinline__ bool in_pass(const Params& p, int cls, int di, int D) {
+    if (cls == 0) return true;
+    return p.feature_order ? di == cls : cls == D;
+}
+
 // instance of slot k, and whether the slot holds a particle
 template <typename T> __device__ __forceinline__ int inst_of(const State<T>& s, int k) {
     return __ldg(s.chunk_inst + k / CHUNK);
@@ -276,16 +285,17 @@ template <typename T, int D> void launch_repack(const State<T>& s, const int* ol
 // interact.cu
 template <typename T, int D>
 void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, cudaStream_t st,
-                     bool pdl = false);
+                     bool pdl = false, int cls = 0);
 template <typename T, int D>
 void launch_neighbors(const State<T>& s, int mode, int* counts, const long long* offsets, int* lists, cudaStream_t st);
 template <typename T, int D> void launch_pair_counts(const State<T>& s, unsigned long long* out2, cudaStream_t st);
 
 // integrate.cu
-template <typename T, int D> void launch_control(const State<T>& s, const One* one, cudaStream_t st, bool pdl = false);
+template <typename T, int D>
+void launch_control(const State<T>& s, const One* one, cudaStream_t st, bool pdl = false, int cls = 0);
 template <typename T, int D>
 void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const Out<T>& o, cudaStream_t st,
-                      bool pdl = false);
+                      bool pdl = false, int cls = 0);
 
 // sample.cu: midpoint-rule integrals of rho_t over every feature of dm (Eqs. 10, 11), and the
 // rejection sampling of counts[k] particles per feature into d_out[n][3] in feature order

@@ -52,7 +52,7 @@ class sph_params(C.Structure):
                 ("threshold", C.c_double), ("reset_period", C.c_int32), ("sample_every", C.c_int32),
                 ("window", C.c_int32), ("ramp_len", C.c_int32), ("boundary_rho", C.c_int32),
                 ("precision", C.c_int32), ("cells_per_support", C.c_int32), ("boundary_correction", C.c_int32),
-                ("group_convergence", C.c_int32)]
+                ("group_convergence", C.c_int32), ("feature_order", C.c_int32)]
 
 
 class sph_report(C.Structure):

@@ -103,6 +103,19 @@ def test_invalid_descriptors_are_rejected():
             S.sph_mesh_create(d, z, p, 10)
 
 
+def test_feature_order_needs_group_convergence():
+    # Algorithm 1's feature loop in sequence goes with its per-feature convergence check
+    w = WL.square2d(h=0.1)
+    for fo, gc, ok in ((1, 0, False), (2, 1, False), (1, 1, True), (0, 0, True)):
+        d, z, p = _descs(w)
+        p.feature_order, p.group_convergence = fo, gc
+        if ok:
+            continue          # creating a mesh needs a GPU; the rejections happen before any
+        with pytest.raises(S.SphError) as e:
+            S.sph_mesh_create(d, z, p, 10)
+        assert e.value.status == S.SPH_E_INVALID
+
+
 def test_params_default_are_the_papers():
     q = S.params_struct({})
     for k in ("kappa", "p0", "visc", "cfl_a", "cfl_v", "threshold", "reset_period", "sample_every", "window",
