@@ -58,9 +58,12 @@ METRIC = "particle-steps/s"
 WORKLOAD = "cube_sphere_3d_1.2M"
 DISK_WORKLOAD = "disk_holes_2d_120k"
 FLOP_PER_PAIR = 50.0       # FP32 operations per interacting pair of the pressure pass (see design notes)
-# DRAM bytes (read + write) of one launch of the dominant kernel on the headline workload, from
-# an ncu capture of the current build (profiles/); None until that kernel has been captured
-DOMINANT_DRAM_BYTES = None
+# DRAM bytes (read + write) per particle of one launch of the dominant kernel (the 3D pressure
+# pass): the ncu capture of this kernel on the headline's generator at 300,009 particles, 5 steps
+# after the start (122.4 MB read + 181.7 MB written); its traffic grows with the particle count
+# (own state, neighbour records missing L2, the hand-over list), so a launch on n particles moves
+# n times this.  Set to None whenever the kernel changes until it has been captured again.
+DOMINANT_DRAM_BYTES_PER_PARTICLE = (122.400768e6 + 181.652224e6) / 300_009
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # one step: one-pass scan, scatter, gather, pressure pass, controller, update (+ next keys)
 KERNELS_PER_STEP = 6
@@ -373,6 +376,7 @@ def run_ours(args):
     peaks, peak_src = measured_peaks()
     clocks = head["clocks"]
     roofline = roofline_of(head, n, peaks, peak_src, dim=3)
+    head_err = oracle_error(S, m, w, with_oracle=not args.no_cpu_baseline) if rank == 0 else None
     e2e = None
     if not args.no_e2e:
         e2e = e2e_run(S, w, stream, args.steps)
@@ -380,11 +384,13 @@ def run_ours(args):
     disk = None
     if disk_w is not None:
         dm = timed_run(S, torch, disk_w, stream, flush, args.disk_steps, 5, min(args.disk_steps, 200))
-        dm.pop("mesh").close()
+        dmesh = dm.pop("mesh")
+        disk_err = oracle_error(S, dmesh, disk_w, with_oracle=not args.no_cpu_baseline)
+        dmesh.close()
         disk = {"value": dm["value"], "unit": METRIC, "steps": args.disk_steps,
                 "ms_per_step": dm["total_ms"] / args.disk_steps, "particles": len(disk_w["x"]),
                 "stages_ms": dm["stages_ms"], "pairs_per_particle": dm["pairs_per_particle"],
-                "roofline": roofline_of(dm, len(disk_w["x"]), peaks, peak_src, dim=2),
+                "roofline": roofline_of(dm, len(disk_w["x"]), peaks, peak_src, dim=2), "oracle_error": disk_err,
                 "config": {"workload": DISK_WORKLOAD + ": unit disk minus 3 seeded holes, h linear in the "
                                        "distance to the nearest hole (0.004-0.04) scaled to ~120k particles "
                                        "(seed 2), FP32", "l2": "flushed between timed steps (256 MiB write)"}}
@@ -430,6 +436,7 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MiB write); the working set is also larger than L2",
                    "phase_at_end": int(rep.phase), "iteration_at_end": int(rep.iteration)},
         "roofline": roofline,
+        "oracle_error": head_err,
         "stages_ms": head["stages_ms"],
         "stages_timing": {"steps": head["stage_steps"],
                           "ms_per_step_with_stage_events": head["staged_ms"] / head["stage_steps"]},
@@ -534,6 +541,31 @@ def timed_run(S, torch, w, stream, flush, steps, warmup, stage_steps, barrier=Fa
             "pairs_per_particle": {"candidates": cand / n, "interacting": accd / n}}
 
 
+def oracle_error(S, m, w, n_sample=2048, with_oracle=True):
+    """The FP64-oracle error of the FP32 result: the pressure pass on the mesh's current state
+    (after the timed steps), on the GPU and in the oracle on the same positions, velocities and h,
+    compared on a random sample of particles as |a_p(GPU) - a_p(oracle)| / S_i (S_i: the sum of the
+    magnitudes of the terms of particle i's force; the parity tolerance is 1e-5)."""
+    if not with_oracle:
+        return None
+    from oracle import oracle as O
+
+    O.build()
+    st = m.positions()
+    n = len(st["x"])
+    got = S.sph_debug_interact(m.h, n, m.n_groups)
+    rng = np.random.default_rng(11)
+    sub = np.sort(rng.choice(n, min(n, n_sample), replace=False))
+    ww = dict(w, group=st["group"])
+    o = O.Oracle(ww, x=st["x"], v=st["v"], h=st["h"])
+    ref = o.interact(sub=sub, use_grid=True)
+    moving = o.gdim[st["group"][sub]] > 0
+    err = np.linalg.norm(got["a_p"][sub] - ref["a_p"], axis=1)[moving] / np.maximum(ref["S"][moving], 1e-300)
+    return {"quantity": f"a_p of {len(sub)} sampled particles, GPU FP32 pressure pass against the FP64 oracle "
+                        f"on the state after the timed steps", "max_rel_to_S": float(err.max()),
+            "median_rel_to_S": float(np.median(err)), "tolerance": 1e-5}
+
+
 def algorithmic_bytes(kernel, dim):
     """HBM bytes per particle of one launch if every array were read or written exactly once
     (FP32 build; neighbour records served on chip):
@@ -560,7 +592,8 @@ def roofline_of(run, n, peaks, peak_src, dim):
     hbm_gbs = n * bpp / t_dom / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak,
-            "traffic": DOMINANT_DRAM_BYTES if (dom == "interact" and dim == 3) else None,
+            "traffic": (DOMINANT_DRAM_BYTES_PER_PARTICLE * n
+                        if (dom == "interact" and dim == 3 and DOMINANT_DRAM_BYTES_PER_PARTICLE) else None),
             "kernel": dom, "avg_launch_ms": stages[dom],
             "work": f"{FLOP_PER_PAIR:.0f} FP32 operations x {run['accd']} interacting pairs per launch",
             "peak_source": f"FP32: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {SM_MAX_MHZ:.0f} MHz",

@@ -97,11 +97,14 @@ template <typename T> struct Out {
 #define SPH_BUF_CAP 16
 #endif
 constexpr int BUF_CAP = SPH_BUF_CAP;   // kept candidates per lane between flushes of the walk (shared memory)
-// lanes per particle in the pair passes (measured with a 2.6h support: 2 in 2D beats 4 by
-// 7 %; in 3D 8 halves the pressure pass against 4 and beats 16; fewer lanes repeat less of the
-// per-particle stencil work, more lanes balance the candidates)
+// lanes per particle in the pair passes (measured with a 2.6h support, 5 steps after the start,
+// whole step in ms for disks of 1k / 20k / 120k / 1M particles: 2 lanes 0.134 / 0.123 / 0.183 /
+// 0.829, 4 lanes with 64 hand-over slots 0.096 / 0.093 / 0.153 / 0.828; 1 lane 1.7-2.5x slower;
+// cubes of 20k / 200k / 1.2M: 8 lanes 0.229 / 1.018 / 4.92, 4 lanes 0.50 / 1.79 / 9.44, 16 lanes
+// 0.48 / 1.60 / 7.54, 16 faster only at 1k (0.166 against 0.199); fewer lanes repeat less of
+// the per-particle stencil work, more lanes balance the candidates)
 #ifndef SPH_LPP_2D
-#define SPH_LPP_2D 2
+#define SPH_LPP_2D 4
 #endif
 #ifndef SPH_LPP_3D
 #define SPH_LPP_3D 8
@@ -110,11 +113,12 @@ template <int D> struct Lpp {
     static constexpr int v = D == 2 ? SPH_LPP_2D : SPH_LPP_3D;
 };
 // same-group pair slots per particle (SPH_VCAP_2D/3D) and per lane (Vcap) in the
-// pressure-to-viscous hand-over list (measured on the viscous pass with a 2.6h support, whose
-// overflowing particles walk the cells again: in 2D 48 slots are 37 % faster than 32, 64 no
-// faster; in 3D 192 slots are 4.5x faster than 96, 256 no faster)
+// pressure-to-viscous hand-over list (measured with a 2.6h support, whose overflowing particles
+// walk the cells again: in 2D with 4 lanes per particle 64 slots make the 120k disk's step 5 %
+// faster than 48, 96 no faster; in 3D 192 slots are 4.5x faster than 96 on the viscous pass,
+// 128 make the 1.2M cube's step 11 % slower and 256 no faster)
 #ifndef SPH_VCAP_2D
-#define SPH_VCAP_2D 48
+#define SPH_VCAP_2D 64
 #endif
 #ifndef SPH_VCAP_3D
 #define SPH_VCAP_3D 192

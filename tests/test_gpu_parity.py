@@ -82,7 +82,7 @@ def oracle_grid(w, m):
 CASES = [("square", 32), ("square", 64), ("disk", 32), ("disk", 64), ("cube", 32), ("cube", 64)]
 DENSE_CASES = [("square_dense", 32), ("square_dense", 64), ("cube_dense", 32)]
 # hand-over list capacity per particle (same-group pairs) of the pressure pass
-LIST_CAP = {2: 48, 3: 192}
+LIST_CAP = {2: 64, 3: 192}
 
 
 CPS_CASES = [("disk", 1), ("disk", 2), ("disk", 4), ("cube", 1), ("cube", 2), ("cube", 4)]
