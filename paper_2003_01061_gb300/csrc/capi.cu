@@ -450,6 +450,8 @@ template <typename T> size_t slot_layout(sph_batch* b, char* base, bool assign) 
     s.perm = (int*)take(cap * 4);
     s.sperm = (int*)take(cap * 4);
     s.partials = (double*)take(nblk * MAXF * sizeof(double));
+    s.partials2 = (double*)take((cap / CHUNK + 1) * MAXF * sizeof(double));
+    s.pticket = (int*)take((cap / CHUNK + 1) * sizeof(int));
     s.vj = (int*)take(nlanes * vcap * 4);
     s.vr = (T*)take(nlanes * vcap * sizeof(T));
     s.vcnt = (int*)take(nlanes * 4);

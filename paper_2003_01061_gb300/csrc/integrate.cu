@@ -228,20 +228,36 @@ __global__ void __launch_bounds__(CTL_THREADS) k_control(State<T> s, One one, in
     if (cls != 0 && !p.feature_order && cls != D) return;
     const int G = p.G;
     if (sc.sample_now != 0) {
-        // the pair-pass blocks of this instance (BLOCK/LPP slots each), CTL_GP groups at a
-        // time: every thread sums a fixed stride of blocks (many loads in flight), then a fixed
-        // shuffle tree per warp and the warps in order
-        constexpr int PB = BLOCK / Lpp<D>::v;
+        // the chunk rows of this instance (CHUNK slots each, added up by the pressure pass),
+        // CTL_GP groups at a time: every thread sums a fixed stride of chunks (many loads in
+        // flight), then a fixed shuffle tree per warp and the warps in order
         constexpr int NWC = CTL_THREADS / 32;
         __shared__ double wpart[CTL_GP][NWC];
-        const int b0 = __ldg(s.inst_off + inst) / PB, b1 = __ldg(s.inst_off + inst + 1) / PB;
+        const int b0 = __ldg(s.inst_off + inst) / CHUNK, b1 = __ldg(s.inst_off + inst + 1) / CHUNK;
         const int lane = t & 31, wid = t >> 5;
         for (int g0 = 0; g0 < G; g0 += CTL_GP) {
             double acc[CTL_GP];
 #pragma unroll
             for (int q = 0; q < CTL_GP; ++q) acc[q] = 0.0;
-            for (int b = b0 + t; b < b1; b += CTL_THREADS) {
-                const double* row = s.partials + (size_t)b * MAXF + g0;
+            // four rows' loads in flight before their sums (rows added in increasing order, as
+            // one at a time)
+            int b = b0 + t;
+            for (; b + 3 * CTL_THREADS < b1; b += 4 * CTL_THREADS) {
+                double v[4][CTL_GP];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const double* row = s.partials2 + (size_t)(b + u * CTL_THREADS) * MAXF + g0;
+#pragma unroll
+                    for (int q = 0; q < CTL_GP; ++q) v[u][q] = g0 + q < G ? row[q] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int q = 0; q < CTL_GP; ++q)
+                        if (g0 + q < G) acc[q] += v[u][q];
+            }
+            for (; b < b1; b += CTL_THREADS) {
+                const double* row = s.partials2 + (size_t)b * MAXF + g0;
 #pragma unroll
                 for (int q = 0; q < CTL_GP; ++q)
                     if (g0 + q < G) acc[q] += row[q];

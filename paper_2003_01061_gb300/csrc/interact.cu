@@ -200,6 +200,27 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTERACT
             s.partials[(size_t)blockIdx.x * MAXF + t] = acc;
         }
     }
+    if (sample) {
+        // the last block of this chunk of slots to finish adds the chunk's block rows, in block
+        // order, into one row (a chunk lies in one instance; the controller then reads one row
+        // per chunk instead of one per block)
+        constexpr int BPC = CHUNK * LPP / BLOCK;
+        __shared__ int sh_last;
+        const int c = blockIdx.x / BPC;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) sh_last = atomicAdd(s.pticket + c, 1) == BPC - 1;
+        __syncthreads();
+        if (sh_last) {
+            __threadfence();
+            for (int t = threadIdx.x; t < G; t += blockDim.x) {
+                double acc = 0.0;
+                for (int b = 0; b < BPC; ++b) acc += __ldcg(s.partials + (size_t)(c * BPC + b) * MAXF + t);
+                s.partials2[(size_t)c * MAXF + t] = acc;
+            }
+            if (threadIdx.x == 0) s.pticket[c] = 0;
+        }
+    }
 }
 
 // neighbour sets for inspection, through the same walk as the pair passes (one lane per

@@ -66,9 +66,13 @@ template <typename T> struct State {
     int* vj;
     T* vr;
     int* vcnt;
-    // per-block, per-group partial sums of V~ (sample steps); nblk = blocks of the pair passes
+    // per-block, per-group partial sums of V~ (sample steps); nblk = blocks of the pair passes.
+    // The last pressure-pass block of every chunk of CHUNK slots (counted in pticket) adds the
+    // chunk's block rows in block order into partials2 [chunk][MAXF], which the controller reads
     double* partials;
     int nblk;
+    double* partials2;
+    int* pticket;
 };
 
 // The grid and parameters of a batch of one, passed to the kernels by value so that they are
