@@ -270,7 +270,8 @@ sph_status make_instance(const sph_domain_desc* dd, const sph_sizing_desc* sz, c
     g.sm = cps == 1 ? 0 : (cps == 2 ? 1 : 2);
     // occupancy cells: cps top-level cells per axis (a search window spans at most one of them
     // on each side), in 3D divided SPH_OCC_FINER times in two (there a level's search is
-    // skipped when the occupancy cells covering its own cell box hold none of its particles)
+    // skipped when the occupancy cells covering its own cell box hold none of its particles,
+    // and its radius taken from the largest h they hold)
     const int t = gi.levels - 1;
     const int fin = D == 3 ? std::min(SPH_OCC_FINER, t + g.sm) : 0;
     g.osh = t + g.sm - fin;
@@ -488,7 +489,7 @@ template <typename T> void set_cell_arrays(sph_batch* b) {
     s.tstate = (unsigned long long*)take((size_t)div_up((long long)b->cell_cap, SCAN1_TILE) * 8);
     s.ticket = (int*)take(4);
     s.ntile = div_up(b->ncell, SCAN1_TILE);
-    s.occ = (unsigned*)take(b->occ_cap * 4);
+    s.occ = (unsigned*)take(b->occ_cap * 4 * OCCW);
     s.ncell = b->ncell;
     s.nocc = b->nocc;
 }
@@ -534,7 +535,7 @@ sph_status relayout(sph_batch* b, int changed, int new_n, int desc) {
     if (!b->cpool || (size_t)keys > b->cell_cap || (size_t)occ > b->occ_cap) {
         const size_t kc = std::max({(size_t)keys, b->cell_cap, (size_t)1});
         const size_t oc = std::max({(size_t)occ, b->occ_cap, (size_t)1});
-        const size_t bytes = kc * 4 + (kc + 1) * 4 + (size_t)SCAN_TILE * 4 + oc * 4 +
+        const size_t bytes = kc * 4 + (kc + 1) * 4 + (size_t)SCAN_TILE * 4 + oc * 4 * OCCW +
                              (size_t)div_up((long long)kc, SCAN1_TILE) * 8 + 4 + 6 * 256;
         void* p = nullptr;
         if (cudaMalloc(&p, bytes) != cudaSuccess)
@@ -593,7 +594,7 @@ sph_status relayout(sph_batch* b, int changed, int new_n, int desc) {
     const State<double>& sd = b->sd;
     CK(cudaMemsetAsync(b->prec == 32 ? sf.count : sd.count, 0, (size_t)std::max<long long>(keys, 1) * 4, b->stream));
     CK(cudaMemsetAsync(b->prec == 32 ? sf.cell_start : sd.cell_start, 0, (size_t)(keys + 1) * 4, b->stream));
-    CK(cudaMemsetAsync(b->prec == 32 ? sf.occ : sd.occ, 0, (size_t)std::max<long long>(occ, 1) * 4, b->stream));
+    CK(cudaMemsetAsync(b->prec == 32 ? sf.occ : sd.occ, 0, (size_t)std::max<long long>(occ, 1) * 4 * OCCW, b->stream));
     CK(cudaMemsetAsync(b->prec == 32 ? sf.tstate : sd.tstate, 0, (size_t)div_up(std::max<long long>(keys, 1), SCAN1_TILE) * 8,
                        b->stream));
     CK(cudaMemsetAsync(b->prec == 32 ? sf.ticket : sd.ticket, 0, 4, b->stream));

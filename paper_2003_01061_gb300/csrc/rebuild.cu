@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(int nb, int ncell, in
                                                            int* __restrict__ cell_start, unsigned* __restrict__ occ,
                                                            int nocc) {
     __shared__ int ws[32];
-    for (int t = threadIdx.x; t < nocc; t += blockDim.x) occ[t] = 0u;   // rebuilt by the gather
+    for (int t = threadIdx.x; t < nocc * OCCW; t += blockDim.x) occ[t] = 0u;   // rebuilt by the gather
     int base = threadIdx.x * SCAN_ITEMS;
     int loc[SCAN_ITEMS];
     int v = 0;
@@ -144,8 +144,8 @@ template <typename T> __global__ void __launch_bounds__(SCAN1_THREADS) k_scan_on
     __syncthreads();
     const int tile = sh_tile;
     const int ncell = s.ncell;
-    // occupancy bits are rebuilt by the gather
-    for (int t = tile * SCAN1_THREADS + threadIdx.x; t < s.nocc; t += gridDim.x * SCAN1_THREADS) s.occ[t] = 0u;
+    // occupancy words are rebuilt by the gather
+    for (int t = tile * SCAN1_THREADS + threadIdx.x; t < s.nocc * OCCW; t += gridDim.x * SCAN1_THREADS) s.occ[t] = 0u;
     const int base = tile * SCAN1_TILE + threadIdx.x * SCAN1_ITEMS;
     int loc[SCAN1_ITEMS];
     int v = 0;
@@ -314,14 +314,16 @@ template <typename T, int D, bool ONE> __global__ void __launch_bounds__(BLOCK) 
     T off[3];
     level_repr<T, D>(g, l, c, o, cell, off);
     Rec<T, D>::store(s.P, s.Ms, k, off, h, (meta & 255u) | ((unsigned)cell[0] << 8));
-    if (s.occ) {   // level occupancy of the occupancy cell holding the particle
+    if (s.occ) {   // the largest h of the particle's level in the occupancy cell holding it
         const int sh = g.osh;
         int ct[3] = {0, 0, 0};
         for (int a = 0; a < D; ++a) ct[a] = min((cell[a] << l) >> sh, g.od[a] - 1);
         const int w = g.occ_base + (ct[2] * g.od[1] + ct[1]) * g.od[0] + ct[0];
-        // sorted neighbours share the word and the level: one atomic per distinct pair in the warp
+        // sorted neighbours share the cell and the level: one atomic per distinct pair in the
+        // warp (positive floats order as their bits)
         const unsigned peers = __match_any_sync(__activemask(), ((unsigned long long)w << 4) | (unsigned)l);
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicOr(s.occ + w, 1u << l);
+        const unsigned hbits = __reduce_max_sync(peers, __float_as_uint(float_up<T>(h)));
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(s.occ + (size_t)w * OCCW + l, hbits);
     }
 }
 

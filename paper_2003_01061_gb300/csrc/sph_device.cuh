@@ -23,6 +23,9 @@ namespace sph {
 constexpr int MAXF = 64;
 constexpr int MAXH = 8;
 constexpr int MAXL = 8;
+// words per occupancy cell: per level, the largest smoothing length of its particles in the
+// cell (float bits, rounded up; 0: none there)
+constexpr int OCCW = MAXL;
 #ifndef SPH_BLOCK
 #define SPH_BLOCK 128
 #endif
@@ -135,6 +138,10 @@ __device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(
 
 __device__ __forceinline__ unsigned long long min_bits(float v) { return (unsigned long long)__float_as_uint(v); }
 __device__ __forceinline__ unsigned long long min_bits(double v) { return (unsigned long long)__double_as_longlong(v); }
+// a working-precision value as a float not below it
+template <typename T> __device__ __forceinline__ float float_up(T v);
+template <> __device__ __forceinline__ float float_up<float>(float v) { return v; }
+template <> __device__ __forceinline__ float float_up<double>(double v) { return __double2float_ru(v); }
 template <typename T> __device__ __forceinline__ T from_bits(unsigned long long b);
 template <> __device__ __forceinline__ float from_bits<float>(unsigned long long b) { return __uint_as_float((unsigned)b); }
 template <> __device__ __forceinline__ double from_bits<double>(unsigned long long b) { return __longlong_as_double((long long)b); }
@@ -433,26 +440,28 @@ __device__ __forceinline__ double fast_rsqrt(double v) { return 1.0 / sqrt(v); }
 // ---- sub-warp stencil walk ----
 // For query particle i at level li with cell coordinates ci (at li) and offsets offi, the walk
 // visits every particle j stored in the cells that can hold a j with
-// |x_i - x_j| < max(kappa (h_i + h_j)/2, kappa h_i): at level l all particles have
-// kappa h_j <= c_l, so the radius R_l = max((kappa h_i + c_l)/2, kappa h_i) (widened by 2^-10)
-// bounds every candidate.  dx = x_i - x_j is computed as (off_i - off_j) + m c0 with
-// m = ci 2^li - cj 2^l (exact integers), r2 = |dx|^2, both op by op.
-// LPP consecutive lanes handle one particle.  They share the particle's stencil and split the
-// candidates of every stencil row between them (lane r takes s+r, s+r+LPP, ...).  A candidate j for which accept(j, dx, r2, h_j, meta_j) holds is kept in the
-// lane's slice of `buf` (CAP entries of (j, level | row), stride BLOCK, in shared memory); the
-// kept candidates are handed to fn(j, dx, r2, h_j, meta_j, off_j, l, cx_j, cy, cz) when the
-// buffer is full and at the end, so the per-pair work runs with the lanes mostly converged.
-// A level is skipped when no particle of it lies in the occupancy cells around the particle
-// (2D) or covering the level's cell box (3D) (bit l of `occ`, built by the gather).  Every lane count computes dx and r2 identically, so a candidate is
-// accepted or rejected the same way whatever LPP.  No warp-synchronous operation is used
-// inside.  (Measured and not kept: trimming rows to the chord of the search disc (in 3D, to the
-// search ball: 3 % slower on a 300k cube, no faster at 1.2M), sharing the
-// level-mask loads among the lanes, loading the next row's range ahead of the current row's
-// scan, deriving a 3D candidate's x cell from the row's cell starts instead of its meta word,
-// letting a particle's lanes set up LPP rows at once and pass the ranges round by shuffles,
-// and a warp-cooperative walk over the union of the warp's stencils with candidates
-// staged in shared memory -- the first five cost more registers or instructions than they saved,
-// the last tests about twice the candidates, since a warp's particles span several cells.)
+// |x_i - x_j| < max(kappa (h_i + h_j)/2, kappa h_i).  At level l all particles have
+// kappa h_j <= c_l, and those in the occupancy cells around i have h_j <= H_l (the largest h of
+// the level there, recorded by the gather; a level with none there is skipped), so the radius
+// R_l = max((kappa h_i + min(c_l, kappa H_l))/2, kappa h_i) (widened by 2^-10) bounds every
+// candidate.  dx = x_i - x_j is computed as (off_i - off_j) + m c0 with m = ci 2^li - cj 2^l
+// (exact integers), r2 = |dx|^2, both op by op.
+// LPP consecutive lanes handle one particle.  In 2D they split the candidates of every stencil
+// row between them (lane r takes s+r, s+r+LPP, ...); in 3D (the flat walk) each lane first cuts
+// one row to the cells that reach the ball of radius R_l, and the lanes then step through the
+// concatenated candidates of LPP rows.  A candidate j for which accept(j, dx, r2, h_j, meta_j)
+// holds is kept in the lane's slice of `buf` (CAP entries of (j, level | row), stride BLOCK, in
+// shared memory); the kept candidates are handed to fn(j, dx, r2, h_j, meta_j, off_j, l, cx_j,
+// cy, cz) when the buffer is full and at the end, so the per-pair work runs with the lanes
+// mostly converged.  Every lane count computes dx and r2 identically, so a candidate is
+// accepted or rejected the same way whatever LPP; the flat walk's only warp-synchronous
+// operations (the row-length scan and its shared-memory hand-off) name the particle's own
+// lanes, which all reach them.  (Measured and not kept: sharing the occupancy loads among the
+// lanes, loading the next row's range ahead of the current row's scan, deriving a 3D
+// candidate's x cell from the row's cell starts instead of its meta word, and a
+// warp-cooperative walk over the union of the warp's stencils with candidates staged in
+// shared memory -- the first three cost more registers or instructions than they saved, the
+// last tests about twice the candidates, since a warp's particles span several cells.)
 template <typename T, int D>
 __device__ __forceinline__ int candidate_dx(const Vec4<T>* __restrict__ P, const unsigned* __restrict__ M, int j,
                                             const int Pi[3], const T offi[3], T c0, int l, int cy, int cz, T offj[3],
@@ -468,48 +477,47 @@ __device__ __forceinline__ int candidate_dx(const Vec4<T>* __restrict__ P, const
     return cxj;
 }
 
-// bit l set: some particle of level l lies in the 3^D occupancy cells around the particle
-// (an occupancy cell spans at least one support of the largest particle: 2D grids)
+// the largest smoothing length of the level-l particles in the occupancy cells that cover the
+// level-l cell box lo..hb (recorded by the gather; 0: the level has none there, infinite: not
+// known)
 template <int D>
-__device__ __forceinline__ unsigned level_mask(const Grid& g, const unsigned* __restrict__ occ, const int Pi[3],
-                                               const int fl[3]) {
-    if (!occ) return (1u << g.L) - 1u;
-    int ct[3] = {0, 0, 0};
-    for (int a = 0; a < D; ++a) ct[a] = (Pi[a] + fl[a]) >> g.osh;
-    unsigned m = 0;
-    const int z0 = D == 3 ? max(ct[2] - 1, 0) : 0, z1 = D == 3 ? min(ct[2] + 1, g.od[2] - 1) : 0;
-    const int y0 = max(ct[1] - 1, 0), y1 = min(ct[1] + 1, g.od[1] - 1);
-    const int x0 = max(ct[0] - 1, 0), x1 = min(ct[0] + 1, g.od[0] - 1);
-    for (int z = z0; z <= z1; ++z)
-        for (int y = y0; y <= y1; ++y)
-            for (int x = x0; x <= x1; ++x) m |= __ldg(occ + g.occ_base + (z * g.od[1] + y) * g.od[0] + x);
-    return m;
-}
-
-// whether some particle of level l lies in the occupancy cells (bit l of a word, set by the
-// gather) that cover the level-l cell box lo..hb (3D grids)
-template <int D>
-__device__ __forceinline__ bool level_present(const Grid& g, const unsigned* __restrict__ occ, int l, const int lo[3],
-                                              const int hb[3]) {
-    if (!occ) return true;
+__device__ __forceinline__ float level_hmax(const Grid& g, const unsigned* __restrict__ occ, int l, const int lo[3],
+                                            const int hb[3]) {
+    if (!occ) return CUDART_INF_F;
     const int sh = g.osh;
     int o0[3] = {0, 0, 0}, o1[3] = {0, 0, 0};
     for (int a = 0; a < D; ++a) {   // a particle past the last occupancy cell is counted in it
         o0[a] = min((lo[a] << l) >> sh, g.od[a] - 1);
         o1[a] = min((hb[a] << l) >> sh, g.od[a] - 1);
     }
-    // a box of many occupancy cells is searched without the test (it would cost more loads
+    // a box of many occupancy cells is searched without the bound (it would cost more loads
     // than it can save)
-    if ((o1[0] - o0[0] + 1) * (o1[1] - o0[1] + 1) * (o1[2] - o0[2] + 1) > 64) return true;
-    const unsigned bit = 1u << l;
+    if ((o1[0] - o0[0] + 1) * (o1[1] - o0[1] + 1) * (o1[2] - o0[2] + 1) > 64) return CUDART_INF_F;
+    unsigned m = 0;   // positive floats order as their bits
     for (int z = o0[2]; z <= o1[2]; ++z)
-        for (int y = o0[1]; y <= o1[1]; ++y) {
-            unsigned m = 0;
-            for (int x = o0[0]; x <= o1[0]; ++x) m |= __ldg(occ + g.occ_base + (z * g.od[1] + y) * g.od[0] + x);
-            if (m & bit) return true;
-        }
-    return false;
+        for (int y = o0[1]; y <= o1[1]; ++y)
+            for (int x = o0[0]; x <= o1[0]; ++x) {
+                const unsigned v = __ldg(occ + (size_t)(g.occ_base + (z * g.od[1] + y) * g.od[0] + x) * OCCW + l);
+                m = v > m ? v : m;
+            }
+    return __uint_as_float(m);
 }
+
+// Flat walk of the stencil rows (below) per dimension; off, each row is walked on its own,
+// whole.  Measured on the 1.2M cube with 2 cells per support, 8 lanes per particle: the flat
+// walk visits 29 % fewer candidates (439 against 620 per particle) in 37 % fewer warp-level
+// loop bodies; with the local support bound the pressure pass takes 3.42 ms against 3.57 ms
+// for the row walk.  In 2D (4 lanes, ~7 rows per particle) it is 8 % slower, and with 4
+// cells per support in 3D the rows' set-up outweighs the tighter cut (3.91 ms).
+#ifndef SPH_FLAT_WALK_2D
+#define SPH_FLAT_WALK_2D 0
+#endif
+#ifndef SPH_FLAT_WALK_3D
+#define SPH_FLAT_WALK_3D 1
+#endif
+template <int D> struct FlatWalk {
+    static constexpr bool on = D == 2 ? SPH_FLAT_WALK_2D != 0 : SPH_FLAT_WALK_3D != 0;
+};
 
 template <typename T, int D, int LPP, int CAP, typename A, typename F>
 __device__ __forceinline__ void walk_sub(const Grid& g, const int* __restrict__ cell_start,
@@ -520,17 +528,12 @@ __device__ __forceinline__ void walk_sub(const Grid& g, const int* __restrict__ 
     const int sub = (int)(threadIdx.x % LPP);
     const T c0 = (T)g.c0;
     const T inv_c0 = T(1) / c0;
-    int Pi[3], fl[3];
+    int Pi[3];
     T fi[3];
     for (int a = 0; a < 3; ++a) {
         Pi[a] = ci[a] << li;
         fi[a] = offi[a] * inv_c0;
-        fl[a] = (int)t_floor(fi[a]);
     }
-    // 2D: the levels present around the particle, tested once; 3D: each level's own box
-    // (measured: the box test is 9 % faster in 3D and 3 % slower in 2D, where a particle
-    // visits ~7 stencil rows against ~85 in 3D)
-    const unsigned lmask = D == 2 ? level_mask<D>(g, occ, Pi, fl) : ~0u;
     const T rhi = kappa * hi;
     int cnt = 0;
     auto flush = [&]() {
@@ -545,26 +548,142 @@ __device__ __forceinline__ void walk_sub(const Grid& g, const int* __restrict__ 
         cnt = 0;
     };
     for (int l = 0; l < g.L; ++l) {
-        if (!((lmask >> l) & 1u)) continue;
         // every particle of level l has kappa h_j <= m c_l
         const T cl = wp<T>(g.c[l], g.cf[l]) * (T)(1 << g.sm);
         T R = T(0.5) * (rhi + cl);
         R = (R > rhi ? R : rhi) * T(1.0 + 1.0 / 1024.0);
-        const T Rc = R * inv_c0;
+        const T Rb = R * inv_c0;
         int lo[3] = {0, 0, 0}, hb[3] = {0, 0, 0};
         bool empty = false;
         for (int a = 0; a < D; ++a) {
-            const int a0 = (Pi[a] + (int)t_floor(fi[a] - Rc)) >> l;
-            const int a1 = (Pi[a] + (int)t_floor(fi[a] + Rc)) >> l;
+            const int a0 = (Pi[a] + (int)t_floor(fi[a] - Rb)) >> l;
+            const int a1 = (Pi[a] + (int)t_floor(fi[a] + Rb)) >> l;
             lo[a] = a0 < 0 ? 0 : a0;
             hb[a] = a1 > g.dims[l][a] - 1 ? g.dims[l][a] - 1 : a1;
             empty = empty || lo[a] > hb[a];
         }
-        if (empty || (D == 3 && !level_present<D>(g, occ, l, lo, hb))) continue;
+        if (empty) continue;
+        {
+            // the level's particles near this one: none, or R from their largest support when
+            // that is below the level's bound (a box of fewer cells, fewer candidates inside R).
+            // Measured against one test of the 3^D occupancy cells around the particle for all
+            // levels: 9 % faster per 3D step before the bound, and with it 2 % faster in 2D.
+            const float hm = level_hmax<D>(g, occ, l, lo, hb);
+            if (hm == 0.0f) continue;
+            const T cm = kappa * (T)hm;
+            if (cm < cl) {
+                R = T(0.5) * (rhi + cm);
+                R = (R > rhi ? R : rhi) * T(1.0 + 1.0 / 1024.0);
+                const T Rt = R * inv_c0;
+                for (int a = 0; a < D; ++a) {
+                    const int a0 = (Pi[a] + (int)t_floor(fi[a] - Rt)) >> l;
+                    const int a1 = (Pi[a] + (int)t_floor(fi[a] + Rt)) >> l;
+                    lo[a] = a0 < 0 ? 0 : a0;
+                    hb[a] = a1 > g.dims[l][a] - 1 ? g.dims[l][a] - 1 : a1;
+                    empty = empty || lo[a] > hb[a];
+                }
+                if (empty) continue;
+            }
+        }
+        const T Rc = R * inv_c0;
         // every radius the callers test at this level is below R: candidates beyond it are
         // rejected on the distance alone
         const T R2 = R * R;
         const int dxl = g.dims[l][0], dyl = g.dims[l][1];
+        auto test = [&](int j, T mcy, T mcz, int tag) {
+            T offj[3], hj, dx[3];
+            unsigned mj;
+            Rec<T, D>::load(P, M, j, offj, hj, mj);
+            dx[0] = rn_add(rn_sub(offi[0], offj[0]), rn_mul((T)(Pi[0] - (meta_cx(mj) << l)), c0));
+            dx[1] = rn_add(rn_sub(offi[1], offj[1]), mcy);
+            dx[2] = D == 3 ? rn_add(rn_sub(offi[2], offj[2]), mcz) : T(0);
+            T r2 = rn_add(rn_mul(dx[0], dx[0]), rn_mul(dx[1], dx[1]));
+            if (D == 3) r2 = rn_add(r2, rn_mul(dx[2], dx[2]));
+            if (r2 < R2 && accept(j, dx, r2, hj, mj)) {
+                buf[cnt * BLOCK] = make_int2(j, tag);
+                if (++cnt == CAP) flush();
+            }
+        };
+        if constexpr (FlatWalk<D>::on) {
+            // Flat walk.  The stencil rows are taken LPP at a time, one row per lane: the lane
+            // cuts its row to the cells that reach the ball of radius R (the row's nearest
+            // point in the other axes fixes the chord), the lengths are scanned across the
+            // particle's lanes, and the lanes then step through the concatenated candidates,
+            // so that no lane idles at the end of a short row.  The cut only drops candidates
+            // at distance >= R, which the test below rejects anyway: the accepted pairs are
+            // those of the full box.
+            __shared__ int4 s_row[BLOCK];   // (end of the row's span, first index - span start, tag, -)
+            __shared__ T s_mc[2 * BLOCK];   // the row's cell offsets in y and z, times c0
+            const unsigned pmask =
+                LPP == 32 ? 0xffffffffu
+                          : ((1u << (LPP & 31)) - 1u) << ((threadIdx.x & 31u) & ~(unsigned)(LPP - 1));
+            const int gb = (int)(threadIdx.x & ~(unsigned)(LPP - 1));
+            const T Rc2 = Rc * Rc;
+            const int wl = 1 << l;
+            const int ny = hb[1] - lo[1] + 1, nrows = ny * (hb[2] - lo[2] + 1);
+            for (int r0 = 0; r0 < nrows; r0 += LPP) {
+                const int r = r0 + sub;
+                int len = 0, first = 0, tag = 0;
+                T mcy = T(0), mcz = T(0);
+                if (r < nrows) {
+                    const int rz = r / ny, cz = lo[2] + rz, cy = lo[1] + (r - rz * ny);
+                    // the row's cells span [oy, oy + 2^l) and [oz, oz + 2^l) in finest cells,
+                    // counted from the particle's cell corner
+                    const int oy = (cy << l) - Pi[1], oz = (cz << l) - Pi[2];
+                    T dy = (T)oy - fi[1], ey = fi[1] - (T)(oy + wl);
+                    dy = dy > ey ? dy : ey;
+                    dy = dy > T(0) ? dy : T(0);
+                    T dz = T(0);
+                    if (D == 3) {
+                        T ez = fi[2] - (T)(oz + wl);
+                        dz = (T)oz - fi[2];
+                        dz = dz > ez ? dz : ez;
+                        dz = dz > T(0) ? dz : T(0);
+                    }
+                    const T d2 = dy * dy + dz * dz;
+                    if (d2 < Rc2) {
+                        const T w = t_sqrt(Rc2 - d2);
+                        const int a0 = max((Pi[0] + (int)t_floor(fi[0] - w)) >> l, lo[0]);
+                        const int a1 = min((Pi[0] + (int)t_floor(fi[0] + w)) >> l, hb[0]);
+                        if (a0 <= a1) {
+                            const int row = g.base[l] + (cz * dyl + cy) * dxl;
+                            first = max(__ldg(cell_start + row + a0), 0);
+                            len = max(min(__ldg(cell_start + row + a1 + 1), n) - first, 0);
+                        }
+                    }
+                    mcy = rn_mul((T)(Pi[1] - (cy << l)), c0);
+                    if (D == 3) mcz = rn_mul((T)(Pi[2] - (cz << l)), c0);
+                    tag = (l << 28) | (cz << 14) | cy;
+                }
+                int incl = len;
+#pragma unroll
+                for (int o = 1; o < LPP; o <<= 1) {
+                    const int v = __shfl_up_sync(pmask, incl, o, LPP);
+                    if (sub >= o) incl += v;
+                }
+                const int total = __shfl_sync(pmask, incl, LPP - 1, LPP);
+                __syncwarp(pmask);   // the lanes are done with the previous rows
+                s_row[threadIdx.x] = make_int4(incl, first - (incl - len), tag, 0);
+                s_mc[2 * threadIdx.x] = mcy;
+                s_mc[2 * threadIdx.x + 1] = mcz;
+                __syncwarp(pmask);
+                int cur = gb - 1, cend = 0, delta = 0, rtag = 0;
+                T my = T(0), mz = T(0);
+                for (int k = sub; k < total; k += LPP) {
+                    while (k >= cend) {   // ends rise to total: stops at a lane of this group
+                        ++cur;
+                        const int4 q = s_row[cur];
+                        cend = q.x;
+                        delta = q.y;
+                        rtag = q.z;
+                        my = s_mc[2 * cur];
+                        mz = s_mc[2 * cur + 1];
+                    }
+                    test(k + delta, my, mz, rtag);
+                }
+            }
+            continue;
+        }
         for (int cz = lo[2]; cz <= hb[2]; ++cz) {
             const T mcz = D == 3 ? rn_mul((T)(Pi[2] - (cz << l)), c0) : T(0);
             for (int cy = lo[1]; cy <= hb[1]; ++cy) {
@@ -573,20 +692,7 @@ __device__ __forceinline__ void walk_sub(const Grid& g, const int* __restrict__ 
                 const int row = g.base[l] + rid * dxl;
                 const int s = max(__ldg(cell_start + row + lo[0]), 0);
                 const int e = min(__ldg(cell_start + row + hb[0] + 1), n);
-                for (int j = s + sub; j < e; j += LPP) {
-                    T offj[3], hj, dx[3];
-                    unsigned mj;
-                    Rec<T, D>::load(P, M, j, offj, hj, mj);
-                    dx[0] = rn_add(rn_sub(offi[0], offj[0]), rn_mul((T)(Pi[0] - (meta_cx(mj) << l)), c0));
-                    dx[1] = rn_add(rn_sub(offi[1], offj[1]), mcy);
-                    dx[2] = D == 3 ? rn_add(rn_sub(offi[2], offj[2]), mcz) : T(0);
-                    T r2 = rn_add(rn_mul(dx[0], dx[0]), rn_mul(dx[1], dx[1]));
-                    if (D == 3) r2 = rn_add(r2, rn_mul(dx[2], dx[2]));
-                    if (r2 < R2 && accept(j, dx, r2, hj, mj)) {
-                        buf[cnt * BLOCK] = make_int2(j, (l << 28) | (cz << 14) | cy);
-                        if (++cnt == CAP) flush();
-                    }
-                }
+                for (int j = s + sub; j < e; j += LPP) test(j, mcy, mcz, (l << 28) | (cz << 14) | cy);
             }
         }
     }

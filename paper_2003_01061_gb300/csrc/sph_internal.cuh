@@ -57,7 +57,8 @@ template <typename T> struct State {
     int* perm;         // slot -> stored index as left by the scatter (unordered inside a cell)
     int* sperm;        // slot -> stored index, stable (ordered inside a cell; written by the gather)
     int ncell;         // total keys (all instances' cells and dummy cells)
-    // per top-level cell: bit l set when a particle of level l lies in it (built by the gather)
+    // per occupancy cell, OCCW words: per level the largest h of its particles in the cell
+    // (float bits, 0 for none; built by the gather)
     unsigned* occ;
     int nocc;
     // same-group pairs found by the pressure pass, handed to the viscous pass: for lane
