@@ -666,17 +666,21 @@ def sampling_run(S, w, gen_s, with_oracle=True):
     return out
 
 
-def mesh_quality_3d(w, x):
+def mesh_quality_3d(w, x, within=None):
     """Quality of the Delaunay tetrahedralisation of final 3D positions with the measures of
     Sec. 4: dihedral angles and the radius ratio gamma = 3 r_in / r_circ; tetrahedra whose
     centroid lies outside the domain, and flat ones (volume below 1e-9 of the mean), are
-    dropped.  Measurement only: the method never tetrahedralises."""
+    dropped.  within = (q, r): only the tetrahedra whose centroid lies within r of q are
+    measured (for a patch of a large state, away from the patch's own hull).  Measurement
+    only: the method never tetrahedralises."""
     from scipy.spatial import Delaunay
 
     from paper_2003_01061_gb300 import workloads as WL
 
     T = x[Delaunay(x).simplices]
     T = T[WL.domain_phi(w["domain"], T.mean(axis=1)) > 0]
+    if within is not None:
+        T = T[np.linalg.norm(T.mean(axis=1) - np.asarray(within[0]), axis=1) < within[1]]
     a, b, c = T[:, 1] - T[:, 0], T[:, 2] - T[:, 0], T[:, 3] - T[:, 0]
     trip = np.einsum("ij,ij->i", a, np.cross(b, c))
     vol = np.abs(trip) / 6.0
