@@ -192,7 +192,12 @@ sph_status sph_params_preset(sph_params* params, int32_t method);
  * resets the controller to Phase One, step 0.  x: [n][3] positions; group: feature index of
  * each particle; v: [n][3] velocities or NULL for zero; h: per-particle smoothing length or
  * NULL for h_t(x).  Positions must lie inside the bounding box and h in (0, hi*(1+2^-11)].
- * Errors: SPH_E_INVALID (n > max_particles, bad group, position or h out of range). */
+ * The host arrays (pinned or pageable; pinned ones are copied fastest) are copied as they are
+ * into a device staging buffer, allocated on the first call and grown when a larger set
+ * comes, then checked and converted on the device; a rejected set leaves the loaded state as
+ * it was, and the message names the first offending particle (its checks taken in the order
+ * group, position, h, velocity).  Errors: SPH_E_INVALID (n > max_particles, bad group,
+ * position or h out of range, non-finite velocity), SPH_E_NOMEM (staging buffer). */
 sph_status sph_mesh_set_state(sph_mesh* m, int64_t n, const double* x, const int32_t* group,
                               const double* v, const double* h);
 
@@ -258,7 +263,9 @@ sph_status sph_mesh_run_until_converged(sph_mesh* m, int64_t max_iters, int64_t*
 
 /* Copies the current state to host buffers in original order (any pointer may be NULL):
  * x_out [n][3], group_out [n], v_out [n][3], h_out [n].  capacity is the number of particles
- * the buffers hold.  Errors: SPH_E_INVALID (capacity < n). */
+ * the buffers hold.  The outputs are assembled in input order on the device (FP64 positions
+ * origin + cell c0 + offset) in the staging buffer of sph_mesh_set_state, then copied out one
+ * array each.  Errors: SPH_E_INVALID (capacity < n), SPH_E_NOMEM (staging buffer). */
 sph_status sph_mesh_positions(sph_mesh* m, double* x_out, int32_t* group_out, double* v_out,
                               double* h_out, int64_t capacity, int64_t* n_out);
 

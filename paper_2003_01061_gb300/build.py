@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsphmesh.so")
-UNITS = ["rebuild.cu", "interact.cu", "integrate.cu", "capi.cu", "noalloc.cu", "server.cu", "sample.cu"]
+UNITS = ["rebuild.cu", "interact.cu", "integrate.cu", "capi.cu", "noalloc.cu", "server.cu", "sample.cu", "state_io.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-I", INCLUDE]

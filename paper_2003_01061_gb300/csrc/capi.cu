@@ -144,6 +144,8 @@ struct sph_batch {
     int device = 0;
     void* pool = nullptr;             // per-slot arrays
     void* cpool = nullptr;            // per-cell arrays
+    void* stage = nullptr;            // the caller's arrays on the device (set_state, positions)
+    size_t stage_cap = 0;
     State<float> sf;
     State<double> sd;
     Grid* d_grids = nullptr;
@@ -628,6 +630,7 @@ void batch_free(sph_batch* b) {
         if (b->ev[k]) cudaEventDestroy(b->ev[k]);
     cudaFree(b->pool);
     cudaFree(b->cpool);
+    cudaFree(b->stage);
     cudaFree(b->d_grids);
     cudaFree(b->d_params);
     cudaFree(b->d_doms);
@@ -816,75 +819,89 @@ template <typename T, int D> sph_status step_impl(sph_batch* b, int32_t n_steps)
 }
 
 
+// a device buffer of at least `bytes` for the caller's arrays (grown on demand, kept)
+char* stage_buf(sph_batch* b, size_t bytes) {
+    if (b->stage_cap < bytes) {
+        if (b->stage) {
+            cudaStreamSynchronize(b->stream);
+            cudaFree(b->stage);
+            b->stage = nullptr;
+            b->stage_cap = 0;
+        }
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        b->stage = p;
+        b->stage_cap = bytes;
+    }
+    return static_cast<char*>(b->stage);
+}
+
+size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+IoGrid io_grid(const Inst& I) {
+    IoGrid g;
+    std::memset(&g, 0, sizeof g);
+    for (int a = 0; a < 3; ++a) {
+        g.origin[a] = I.grid.origin[a];
+        g.dims0[a] = I.grid.dims[0][a];
+    }
+    g.c0 = I.grid.c[0];
+    g.inv_c0 = I.grid.inv_c[0];
+    for (int k = 0; k < MAXF; ++k) g.fdim[k] = (unsigned char)I.dom.f[k].dim;
+    return g;
+}
+
 // one instance's slots in device memory -> host arrays in its original order (arrays indexed
-// by global slot; the instance's range is read)
+// by global slot; the instance's range is read).  A kernel writes the outputs in input order
+// into the staging buffer, then each requested array is copied out once.
 template <typename T>
 sph_status download(sph_batch* b, int inst, int* const Cd[3], T* const Od[3], T* const V[3], T* H, unsigned* G,
                     int* ID, double* x_out, int32_t* group_out, double* v_out, double* h_out) {
     const Inst& I = b->in[inst];
     const int ns = I.slots, o0 = I.off, n = I.n, D = b->D;
-    std::vector<int> id(ns);
-    CK(cudaMemcpyAsync(id.data(), ID + o0, sizeof(int) * ns, cudaMemcpyDeviceToHost, b->stream));
-    std::vector<int> cs(x_out ? (size_t)ns * 3 : 0);
-    std::vector<T> os(x_out ? (size_t)ns * 3 : 0);
-    std::vector<T> vs(v_out ? (size_t)ns * 3 : 0), hs(h_out ? ns : 0);
-    std::vector<unsigned> gs(group_out ? ns : 0);
+    const size_t nx = up256((size_t)n * 24), nh = up256((size_t)n * 8), ng = up256((size_t)n * 4);
+    char* p = stage_buf(b, 256 + 2 * nx + nh + ng);
+    if (!p) return fail(SPH_E_NOMEM, "device allocation of the positions' staging buffer failed");
+    int* cnt = reinterpret_cast<int*>(p);
+    double* dx = x_out ? reinterpret_cast<double*>(p + 256) : nullptr;
+    double* dv = v_out ? reinterpret_cast<double*>(p + 256 + nx) : nullptr;
+    double* dh = h_out ? reinterpret_cast<double*>(p + 256 + 2 * nx) : nullptr;
+    int* dg = group_out ? reinterpret_cast<int*>(p + 256 + 2 * nx + nh) : nullptr;
+    ConstSlotArrays<T> sa;
+    std::memset(&sa, 0, sizeof sa);
     for (int a = 0; a < D; ++a) {
-        if (x_out) {
-            CK(cudaMemcpyAsync(cs.data() + (size_t)a * ns, Cd[a] + o0, sizeof(int) * ns, cudaMemcpyDeviceToHost, b->stream));
-            CK(cudaMemcpyAsync(os.data() + (size_t)a * ns, Od[a] + o0, sizeof(T) * ns, cudaMemcpyDeviceToHost, b->stream));
-        }
-        if (v_out) CK(cudaMemcpyAsync(vs.data() + (size_t)a * ns, V[a] + o0, sizeof(T) * ns, cudaMemcpyDeviceToHost, b->stream));
+        sa.C[a] = Cd[a] + o0;
+        sa.O[a] = Od[a] + o0;
+        sa.V[a] = V[a] + o0;
     }
-    if (h_out) CK(cudaMemcpyAsync(hs.data(), H + o0, sizeof(T) * ns, cudaMemcpyDeviceToHost, b->stream));
-    if (group_out) CK(cudaMemcpyAsync(gs.data(), G + o0, sizeof(unsigned) * ns, cudaMemcpyDeviceToHost, b->stream));
+    sa.H = H + o0;
+    sa.G = G + o0;
+    sa.ID = ID + o0;
+    CK(cudaMemsetAsync(cnt, 0, 8, b->stream));
+    if (D == 2) launch_store_state<T, 2>(sa, io_grid(I), ns, n, dx, dg, dv, dh, cnt, b->stream);
+    else launch_store_state<T, 3>(sa, io_grid(I), ns, n, dx, dg, dv, dh, cnt, b->stream);
+    CK(cudaGetLastError());
+    int hc[2] = {0, 0};
+    CK(cudaMemcpyAsync(hc, cnt, 8, cudaMemcpyDeviceToHost, b->stream));
+    if (x_out) CK(cudaMemcpyAsync(x_out, dx, (size_t)n * 24, cudaMemcpyDeviceToHost, b->stream));
+    if (v_out) CK(cudaMemcpyAsync(v_out, dv, (size_t)n * 24, cudaMemcpyDeviceToHost, b->stream));
+    if (h_out) CK(cudaMemcpyAsync(h_out, dh, (size_t)n * 8, cudaMemcpyDeviceToHost, b->stream));
+    if (group_out) CK(cudaMemcpyAsync(group_out, dg, (size_t)n * 4, cudaMemcpyDeviceToHost, b->stream));
     CK(cudaStreamSynchronize(b->stream));
-    const Grid& g = I.grid;
-    int seen = 0;
-    for (int k = 0; k < ns; ++k) {
-        const int i = id[k];
-        if (i < 0) continue;   // padding
-        if (i >= n) return fail(SPH_E_CUDA, "corrupt particle index on the device");
-        ++seen;
-        for (int a = 0; a < 3; ++a) {
-            // FP64 position = origin + cell * c0 + offset
-            if (x_out)
-                x_out[(size_t)i * 3 + a] =
-                    a < D ? ((double)g.origin[a] + (double)cs[(size_t)a * ns + k] * g.c[0]) + (double)os[(size_t)a * ns + k]
-                          : 0.0;
-            if (v_out) v_out[(size_t)i * 3 + a] = a < D ? (double)vs[(size_t)a * ns + k] : 0.0;
-        }
-        if (h_out) h_out[i] = (double)hs[k];
-        if (group_out) group_out[i] = (int32_t)(gs[k] & 63u);
-    }
-    if (seen != n) return fail(SPH_E_CUDA, "corrupt particle index on the device");
+    if (hc[1] != 0 || hc[0] != n) return fail(SPH_E_CUDA, "corrupt particle index on the device");
     return SPH_OK;
 }
 
-sph_status check_args(const sph_batch* b, int inst, int64_t n, const double* x, const int32_t* group, const double* v,
-                      const double* h) {
+sph_status check_args(const sph_batch* b, int inst, int64_t n, const double* x, const int32_t* group, const double*,
+                      const double*) {
     const Inst& I = b->in[inst];
     const int64_t cap = b->mesh ? I.cap : (int64_t)b->slot_cap;
     if (n < 0 || n > cap) return fail(SPH_E_INVALID, "set_state: n=%lld outside [0, %lld]", (long long)n, (long long)cap);
     if (n > 0 && (!x || !group)) return fail(SPH_E_INVALID, "set_state: x and group are required");
-    const int D = b->D;
-    for (int64_t i = 0; i < n; ++i) {
-        if (group[i] < 0 || group[i] >= I.params.G)
-            return fail(SPH_E_INVALID, "set_state: particle %lld has group %d", (long long)i, group[i]);
-        for (int a = 0; a < D; ++a) {
-            const double xa = x[i * 3 + a], lo = I.dom.lo[a], hi = I.dom.hi[a];
-            if (!(xa >= lo - 1e-9 * (1 + std::fabs(lo)) && xa <= hi + 1e-9 * (1 + std::fabs(hi))))
-                return fail(SPH_E_INVALID, "set_state: particle %lld outside the bounding box", (long long)i);
-        }
-        // the grid's top level covers kappa*h_hi*(1+2^-10); allow h up to h_hi*(1+2^-11) so that
-        // values rounded to the working precision are accepted
-        if (h && !(h[i] > 0 && h[i] <= I.h_hi * (1 + 1.0 / 2048.0)))
-            return fail(SPH_E_INVALID, "set_state: h of particle %lld outside [lo, hi]", (long long)i);
-        if (v)
-            for (int a = 0; a < D; ++a)
-                if (!std::isfinite(v[i * 3 + a])) return fail(SPH_E_INVALID, "set_state: non-finite velocity");
-    }
-    return SPH_OK;
+    return SPH_OK;   // the particles themselves are checked on the device by set_state_impl
 }
 
 // Loads one instance's particles into its slots (live first, padding after) and resets its
@@ -896,39 +913,62 @@ template <typename T, int D> sph_status set_state_impl(sph_batch* b, int inst, i
     Inst& I = b->in[inst];
     const int nn = (int)n;
     CK(cudaSetDevice(b->device));
+    // the caller's arrays as they are, on the device: checked there before anything changes
+    const size_t nx = up256((size_t)nn * 24), ng = up256((size_t)nn * 4), nh = up256((size_t)nn * 8);
+    char* p = stage_buf(b, 256 + 2 * nx + ng + nh);
+    if (!p) return fail(SPH_E_NOMEM, "device allocation of the particles' staging buffer failed");
+    unsigned long long* first = reinterpret_cast<unsigned long long*>(p);
+    double* dx = reinterpret_cast<double*>(p + 256);
+    int* dg = reinterpret_cast<int*>(p + 256 + nx);
+    double* dv = v ? reinterpret_cast<double*>(p + 256 + nx + ng) : nullptr;
+    double* dh = h ? reinterpret_cast<double*>(p + 256 + 2 * nx + ng) : nullptr;
+    if (nn > 0) {
+        CK(cudaMemcpyAsync(dx, x, (size_t)nn * 24, cudaMemcpyHostToDevice, b->stream));
+        CK(cudaMemcpyAsync(dg, group, (size_t)nn * 4, cudaMemcpyHostToDevice, b->stream));
+        if (v) CK(cudaMemcpyAsync(dv, v, (size_t)nn * 24, cudaMemcpyHostToDevice, b->stream));
+        if (h) CK(cudaMemcpyAsync(dh, h, (size_t)nn * 8, cudaMemcpyHostToDevice, b->stream));
+        IoCheck c;
+        std::memset(&c, 0, sizeof c);
+        for (int a = 0; a < D; ++a) {
+            const double lo = I.dom.lo[a], hi = I.dom.hi[a];
+            c.lo[a] = lo - 1e-9 * (1 + std::fabs(lo));
+            c.hi[a] = hi + 1e-9 * (1 + std::fabs(hi));
+        }
+        // the grid's top level covers kappa*h_hi*(1+2^-10); h up to h_hi*(1+2^-11) is accepted so
+        // that values rounded to the working precision pass
+        c.hmax = I.h_hi * (1 + 1.0 / 2048.0);
+        c.G = I.params.G;
+        c.D = D;
+        CK(cudaMemsetAsync(first, 0xff, 8, b->stream));
+        launch_check_state(c, nn, dx, dg, dv, dh, first, b->stream);
+        CK(cudaGetLastError());
+        unsigned long long f = 0;
+        CK(cudaMemcpyAsync(&f, first, 8, cudaMemcpyDeviceToHost, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+        if (f != ~0ull) {
+            const long long i = (long long)(f >> 2);
+            switch ((int)(f & 3)) {
+            case 0: return fail(SPH_E_INVALID, "set_state: particle %lld has group %d", i, group[i]);
+            case 1: return fail(SPH_E_INVALID, "set_state: particle %lld outside the bounding box", i);
+            case 2: return fail(SPH_E_INVALID, "set_state: h of particle %lld outside [lo, hi]", i);
+            default: return fail(SPH_E_INVALID, "set_state: non-finite velocity");
+            }
+        }
+    }
     sph_status r = relayout(b, inst, nn, inst);   // makes room (moving the other instances)
     if (r != SPH_OK) return r;
     const int ns = I.slots, o0 = I.off;
-    std::vector<int> cs((size_t)ns * 3, 0);
-    std::vector<T> os((size_t)ns * 3, T(0)), vs((size_t)ns * 3, T(0)), hs(ns, T(0));
-    std::vector<unsigned> gs(ns, 0u);
-    std::vector<int> ids(ns, -1);
-    const Grid& g = I.grid;
-    const double c0 = g.c[0], inv_c0 = g.inv_c[0];
-    for (int i = 0; i < nn; ++i) {
-        const int gi = group[i];
-        for (int a = 0; a < D; ++a) {
-            // finest cell and offset: c = floor((x - origin) * (1/c0)), o = (x - origin) - c*c0
-            const double rel = x[(size_t)i * 3 + a] - (double)g.origin[a];
-            double t = std::floor(rel * inv_c0);
-            int ca = (int)std::fmax(std::fmin(t, 2.0e9), -2.0e9);
-            ca = std::min(std::max(ca, 0), g.dims[0][a] - 1);
-            cs[(size_t)a * ns + i] = ca;
-            os[(size_t)a * ns + i] = (T)(rel - (double)ca * c0);
-            if (v) vs[(size_t)a * ns + i] = (T)v[(size_t)i * 3 + a];
-        }
-        if (h) hs[i] = (T)h[i];
-        gs[i] = (unsigned)gi | ((unsigned)I.dom.f[gi].dim << 6);
-        ids[i] = i;
-    }
+    SlotArrays<T> sa;
+    std::memset(&sa, 0, sizeof sa);
     for (int a = 0; a < D; ++a) {
-        CK(cudaMemcpyAsync(s.C[a] + o0, cs.data() + (size_t)a * ns, sizeof(int) * ns, cudaMemcpyHostToDevice, b->stream));
-        CK(cudaMemcpyAsync(s.O[a] + o0, os.data() + (size_t)a * ns, sizeof(T) * ns, cudaMemcpyHostToDevice, b->stream));
-        CK(cudaMemcpyAsync(s.V[a] + o0, vs.data() + (size_t)a * ns, sizeof(T) * ns, cudaMemcpyHostToDevice, b->stream));
+        sa.C[a] = s.C[a] + o0;
+        sa.O[a] = s.O[a] + o0;
+        sa.V[a] = s.V[a] + o0;
     }
-    CK(cudaMemcpyAsync(s.G + o0, gs.data(), 4 * (size_t)ns, cudaMemcpyHostToDevice, b->stream));
-    CK(cudaMemcpyAsync(s.ID + o0, ids.data(), 4 * (size_t)ns, cudaMemcpyHostToDevice, b->stream));
-    CK(cudaMemcpyAsync(s.H + o0, hs.data(), sizeof(T) * ns, cudaMemcpyHostToDevice, b->stream));
+    sa.H = s.H + o0;
+    sa.G = s.G + o0;
+    sa.ID = s.ID + o0;
+    launch_load_state<T, D>(sa, io_grid(I), ns, nn, dx, dg, dv, dh, b->stream);
     if (!h && nn > 0) launch_init_h<T, D>(s, inst, b->stream);
     Ctrl c;
     host_ctrl_init(&c);

@@ -291,6 +291,48 @@ template <typename T, int D> void launch_gather(const State<T>& s, const One* on
 template <typename T, int D> void launch_init_h(const State<T>& s, int inst, cudaStream_t st);
 template <typename T, int D> void launch_repack(const State<T>& s, const int* old_off, const int* move_n, cudaStream_t st);
 
+// state_io.cu: an instance's slots from and to the caller's FP64 arrays (staged on the device)
+struct IoCheck {      // accepted ranges: positions inside [lo, hi] per axis, h in (0, hmax]
+    double lo[3], hi[3];
+    double hmax;
+    int G, D;
+};
+struct IoGrid {       // finest-level cell geometry of an instance, and each group's dimension
+    double origin[3];
+    double c0, inv_c0;
+    int dims0[3];
+    unsigned char fdim[MAXF];
+};
+template <typename T> struct SlotArrays {   // an instance's stored state, from its first slot
+    int* C[3];
+    T* O[3];
+    T* V[3];
+    T* H;
+    unsigned* G;
+    int* ID;
+};
+template <typename T> struct ConstSlotArrays {
+    const int* C[3];
+    const T* O[3];
+    const T* V[3];
+    const T* H;
+    const unsigned* G;
+    const int* ID;
+};
+// first offending particle as (index << 2) | check (0 group, 1 position, 2 h, 3 velocity) by
+// atomicMin into *first (the caller sets it to all ones)
+void launch_check_state(const IoCheck& c, int n, const double* x, const int* group, const double* v, const double* h,
+                        unsigned long long* first, cudaStream_t st);
+// slots [0, n) from the arrays (v, h may be null: zero), [n, ns) padding
+template <typename T, int D>
+void launch_load_state(const SlotArrays<T>& s, const IoGrid& g, int ns, int n, const double* x, const int* group,
+                       const double* v, const double* h, cudaStream_t st);
+// slots [0, ns) to the arrays in input order (any may be null); cnt[0] counts the particles
+// written, cnt[1] is set when a slot holds an index >= n (both zeroed by the caller)
+template <typename T, int D>
+void launch_store_state(const ConstSlotArrays<T>& s, const IoGrid& g, int ns, int n, double* x, int* group, double* v,
+                        double* h, int* cnt, cudaStream_t st);
+
 // interact.cu
 template <typename T, int D>
 void launch_interact(const State<T>& s, const One* one, T* dbg_sigma, T* dbg_gamma, cudaStream_t st,
