@@ -65,8 +65,9 @@ FLOP_PER_PAIR = 50.0       # FP32 operations per interacting pair of the pressur
 # n times this.  Set to None whenever the kernel changes until it has been captured again.
 DOMINANT_DRAM_BYTES_PER_PARTICLE = (116.619264e6 + 179.254272e6) / 300_009
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-# one step: one-pass scan, scatter, gather, pressure pass, controller, update (+ next keys)
-KERNELS_PER_STEP = 6
+# one 3D step: one-pass scan, scatter, gather, pressure pass, controller, viscous pass, update
+# (+ next keys)
+KERNELS_PER_STEP = 7
 
 
 def parse():
@@ -534,7 +535,7 @@ def timed_run(S, torch, w, stream, flush, steps, warmup, stage_steps, barrier=Fa
     m.sync()
     cand, accd = S.sph_debug_pair_counts(m.h)
     n = len(w["x"])
-    stages = {k: (v[1] / max(v[0], 1)) if k != "rebuild" else v[1] / stage_steps for k, v in stage.items()}
+    stages = {k: v[1] / stage_steps for k, v in stage.items()}   # ms per step of each stage
     return {"mesh": m, "total_ms": total_ms, "value": n * steps / (total_ms / 1e3), "staged_ms": staged_ms,
             "stage_steps": stage_steps, "stages_ms": stages, "accd": accd,
             "clocks": clk.summary() if clk else None,

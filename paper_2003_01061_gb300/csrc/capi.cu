@@ -107,9 +107,14 @@ struct KTime {
     int kernels;   // kernel launches per step in this stage
 };
 // the step graph: rebuild = one-pass scan, scatter, gather (the keys and histogram come from
-// the previous step's update); the update also computes the next keys
+// the previous step's update); the update also computes the next keys, and is two kernels
+// (viscous sum, update) where SPH_SPLIT_INTEGRATE_2D/3D says so
 constexpr int NSTAGE = 4;
 const KTime kStages[NSTAGE] = {{"rebuild", 3}, {"interact", 1}, {"control", 1}, {"integrate", 1}};
+int stage_kernels(int k, int D) {
+    if (k == 3) return (D == 2 ? SPH_SPLIT_INTEGRATE_2D : SPH_SPLIT_INTEGRATE_3D) ? 2 : 1;
+    return kStages[k].kernels;
+}
 
 // host copy of one instance
 struct Inst {
@@ -1560,7 +1565,7 @@ sph_status kernel_times_impl(sph_batch* b, sph_kernel_time* out, int32_t cap, in
     for (; k < NSTAGE && k < cap; ++k) {
         std::memset(out[k].name, 0, sizeof out[k].name);
         std::snprintf(out[k].name, sizeof out[k].name, "%s", kStages[k].name);
-        out[k].launches = b->stage_steps * kStages[k].kernels;
+        out[k].launches = b->stage_steps * stage_kernels(k, b->D);
         out[k].total_ms = b->stage_ms[k];
     }
     if (n_out) *n_out = k;

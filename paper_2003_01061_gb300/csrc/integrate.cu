@@ -479,12 +479,21 @@ template <typename T> __device__ __forceinline__ T domain_phi_t(const Domain& do
 // overflowed, over the walk of the pressure pass (same pairs, same predicate) with LPP lanes;
 // the lead lane does the update.  As in the pressure pass, a block lies in one instance.
 // Padding slots are copied through unchanged.
-template <typename T, int D, bool ONE>
-__global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRATE_MINB_2D : SPH_INTEGRATE_MINB_3D) : 4)
+// MODE 0 runs both parts; MODE 1 only the viscous sum, leaving the projected a_v of each moving
+// particle in o.V (the stored velocities, which nothing reads during a step once the rebuild
+// has gathered them); MODE 2 (one lane per particle) only the update, taking a_v from o.V.
+template <typename T, int D, int MODE> constexpr int integrate_minb() {
+    if (sizeof(T) != 4) return 4;
+    if (MODE == 1) return D == 2 ? SPH_VISC_MINB_2D : SPH_VISC_MINB_3D;
+    if (MODE == 2) return SPH_UPDATE_MINB;
+    return D == 2 ? SPH_INTEGRATE_MINB_2D : SPH_INTEGRATE_MINB_3D;
+}
+template <typename T, int D, bool ONE, int MODE>
+__global__ void __launch_bounds__(BLOCK, (integrate_minb<T, D, MODE>()))
     k_integrate(State<T> s, One one, const Ctrl* use, Out<T> o, int cls) {
     dep_launch();
     dep_wait();
-    constexpr int LPP = ILpp<D>::v, LPI = Lpp<D>::v, NCOL = LPI / LPP;
+    constexpr int LPP = MODE == 2 ? 1 : ILpp<D>::v, LPI = Lpp<D>::v, NCOL = LPI / LPP;
     __shared__ int2 sbuf[BUF_CAP * BLOCK];
     __shared__ Grid gsh;
     __shared__ Params psh;
@@ -499,10 +508,10 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRAT
     }
     const Grid& g = ONE ? one.g : gsh;
     const Params& p = ONE ? one.p : psh;
-    if (o.K) reset_scan_state(s);   // this kernel produces the next scan's histogram
+    if (MODE != 1 && o.K) reset_scan_state(s);   // this kernel produces the next scan's histogram
     const int k = (blockIdx.x * blockDim.x + threadIdx.x) / LPP;
     const bool lead = (threadIdx.x % LPP) == 0;
-    if (k < s.n && !live(s, inst, k)) {   // padding: keep the slot as it is
+    if (MODE != 1 && k < s.n && !live(s, inst, k)) {   // padding: keep the slot as it is
         if (lead) {
             const Vec4<T> vh = s.VH[k];
             const T vv[3] = {vh.x, vh.y, vh.z};
@@ -564,13 +573,13 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRAT
             const T vp = rs ? T(0) : f * v[a];
             vt[a] = vp + dt * (api[a] - eps * vp);
         }
-        if (di < D) {
+        if (MODE != 2 && di < D) {
             T xi[3];
             pos_t<T, D>(g, c, o3, xi);
             feature_tangent<T>(dom.f[gi], xi, tg);
         }
     }
-    if (p.visc > 0.0 && !done) {
+    if (MODE != 2 && p.visc > 0.0 && !done) {
         const T kappa = wp<T>(p.kappa, p.kappa_f), hk = T(0.5) * kappa, visc = wp<T>(p.visc, p.visc_f);
         T hid, hi2d;
         hpow(hi, di > 0 ? di : 1, hid, hi2d);
@@ -652,6 +661,13 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTEGRAT
         for (int a = 0; a < D; ++a) av[a] = sub_sum<LPP>(av[a]);
         if (moving) tangent_map<T>(di, D, tg, av);
     }
+    if constexpr (MODE == 1) {
+        if (lead && moving)
+            for (int a = 0; a < D; ++a) o.V[a][k] = av[a];
+        return;
+    }
+    if (MODE == 2 && moving)
+        for (int a = 0; a < D; ++a) av[a] = o.V[a][k];
     if (!lead) return;
     if (moving) {
         const Feat& fi = dom.f[gi];
@@ -741,8 +757,17 @@ template <typename T, int D>
 void launch_integrate(const State<T>& s, const One* one, const Ctrl* use, const Out<T>& o, cudaStream_t st,
                       bool pdl, int cls) {
     const int nb = div_up((long long)s.n * ILpp<D>::v, BLOCK);
-    if (one) launch_k(k_integrate<T, D, true>, nb, BLOCK, st, pdl, s, *one, use, o, cls);
-    else launch_k(k_integrate<T, D, false>, nb, BLOCK, st, pdl, s, One(), use, o, cls);
+    if (D == 2 ? SPH_SPLIT_INTEGRATE_2D : SPH_SPLIT_INTEGRATE_3D) {   // viscous sum, then update
+        const int nu = div_up((long long)s.n, BLOCK);
+        if (one) {
+            launch_k(k_integrate<T, D, true, 1>, nb, BLOCK, st, pdl, s, *one, use, o, cls);
+            launch_k(k_integrate<T, D, true, 2>, nu, BLOCK, st, pdl, s, *one, use, o, cls);
+        } else {
+            launch_k(k_integrate<T, D, false, 1>, nb, BLOCK, st, pdl, s, One(), use, o, cls);
+            launch_k(k_integrate<T, D, false, 2>, nu, BLOCK, st, pdl, s, One(), use, o, cls);
+        }
+    } else if (one) launch_k(k_integrate<T, D, true, 0>, nb, BLOCK, st, pdl, s, *one, use, o, cls);
+    else launch_k(k_integrate<T, D, false, 0>, nb, BLOCK, st, pdl, s, One(), use, o, cls);
 }
 
 #define SPH_INST(T, D)                                                      \

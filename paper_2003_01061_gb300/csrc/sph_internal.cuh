@@ -173,6 +173,25 @@ static_assert(Lpp<2>::v % ILpp<2>::v == 0 && Lpp<3>::v % ILpp<3>::v == 0,
 #ifndef SPH_INTERACT_MINB_3D
 #define SPH_INTERACT_MINB_3D SPH_INTERACT_MINB
 #endif
+// the viscous pass and the update as two kernels (each with its own register budget) instead
+// of one (measured on the 1.2M cube: 0.73 ms against 0.86 for the fused kernel, the viscous
+// kernel at 8 blocks/SM, 7 and 6 being 3 % and 7 % slower; on the 120k disk, with one viscous
+// lane per particle, 47 us against 39.5 us fused)
+#ifndef SPH_SPLIT_INTEGRATE_2D
+#define SPH_SPLIT_INTEGRATE_2D 0
+#endif
+#ifndef SPH_SPLIT_INTEGRATE_3D
+#define SPH_SPLIT_INTEGRATE_3D 1
+#endif
+#ifndef SPH_VISC_MINB_2D
+#define SPH_VISC_MINB_2D 8
+#endif
+#ifndef SPH_VISC_MINB_3D
+#define SPH_VISC_MINB_3D 8
+#endif
+#ifndef SPH_UPDATE_MINB
+#define SPH_UPDATE_MINB 6
+#endif
 #ifndef SPH_INTEGRATE_MINB_2D
 #define SPH_INTEGRATE_MINB_2D 7
 #endif
