@@ -26,9 +26,17 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTERACT
     dep_launch();
     dep_wait();
     constexpr int LPP = Lpp<D>::v;
-    __shared__ unsigned long long sh_dta[MAXF], sh_dtv[MAXF];
-    __shared__ double sh_part[BLOCK / 32][MAXF];
-    __shared__ int2 sbuf[BUF_CAP * BLOCK];
+    // the block's Eq. 24 minima and V~ partial sums live after the walk in the memory of its
+    // candidate buffers (which the walk alone uses), leaving more of the SM's memory to L1
+    constexpr bool ALIAS = (D == 2 ? SPH_ALIAS_TAIL_2D : SPH_ALIAS_TAIL_3D) != 0;
+    constexpr size_t TAIL = 2 * MAXF * sizeof(unsigned long long) + (BLOCK / 32) * MAXF * sizeof(double);
+    static_assert(!ALIAS || TAIL <= sizeof(int2) * BUF_CAP * BLOCK, "the tail fits in the candidate buffers");
+    __shared__ __align__(16) int2 sbuf[BUF_CAP * BLOCK];
+    __shared__ __align__(16) unsigned char sh_tail[ALIAS ? 16 : TAIL];
+    unsigned char* const tail = ALIAS ? reinterpret_cast<unsigned char*>(sbuf) : sh_tail;
+    unsigned long long* const sh_dta = reinterpret_cast<unsigned long long*>(tail);
+    unsigned long long* const sh_dtv = sh_dta + MAXF;
+    double (*const sh_part)[MAXF] = reinterpret_cast<double (*)[MAXF]>(sh_dtv + MAXF);
     __shared__ Grid gsh;
     __shared__ Params psh;
     const int inst = ONE ? 0 : __ldg(s.chunk_inst + (blockIdx.x * (BLOCK / LPP)) / CHUNK);
@@ -41,13 +49,16 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTERACT
     const Grid& g = ONE ? one.g : gsh;
     const Params& p = ONE ? one.p : psh;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int t = threadIdx.x; t < MAXF; t += blockDim.x) {
-        sh_dta[t] = inf_bits<T>();
-        sh_dtv[t] = inf_bits<T>();
-    }
     const bool sample = ctrl->sample_now != 0;
-    if (sample)
-        for (int t = threadIdx.x; t < (BLOCK / 32) * MAXF; t += blockDim.x) (&sh_part[0][0])[t] = 0.0;
+    auto init_tail = [&]() {
+        for (int t = threadIdx.x; t < MAXF; t += blockDim.x) {
+            sh_dta[t] = inf_bits<T>();
+            sh_dtv[t] = inf_bits<T>();
+        }
+        if (sample)
+            for (int t = threadIdx.x; t < (BLOCK / 32) * MAXF; t += blockDim.x) (&sh_part[0][0])[t] = 0.0;
+    };
+    if (!ALIAS) init_tail();
     __syncthreads();
     const int G = p.G;
 
@@ -143,6 +154,11 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTERACT
             }
         });
     if (inrange) s.vcnt[lg] = vc;
+    if (ALIAS) {   // every walk of the block is done before its buffers become the tail
+        __syncthreads();
+        init_tail();
+        __syncthreads();
+    }
     for (int a = 0; a < D; ++a) F[a] = sub_sum<LPP>(F[a]);
     sig = sub_sum<LPP>(sig);
     gam = sub_sum<LPP>(gam);

@@ -98,6 +98,15 @@ template <typename T> struct Out {
 
 // (measured with the 2.6h support: 12 / 20 / 24 make the whole 2D step 22 % slower / 1 % slower /
 // 5 % slower than 16, and the 1.2M cube's 33 % / 2 % / 11 %)
+// the pressure pass's per-block Eq. 24 minima and V~ partial sums in the memory of its
+// candidate buffers once the walk is done (1) or in arrays of their own (0) (measured: 3D
+// pressure pass on the 1.2M cube 3.36 ms against 3.42, 2D on the 120k disk 80.1 us against 79.0)
+#ifndef SPH_ALIAS_TAIL_2D
+#define SPH_ALIAS_TAIL_2D 0
+#endif
+#ifndef SPH_ALIAS_TAIL_3D
+#define SPH_ALIAS_TAIL_3D 1
+#endif
 #ifndef SPH_BUF_CAP
 #define SPH_BUF_CAP 16
 #endif
