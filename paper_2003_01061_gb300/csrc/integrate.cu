@@ -584,9 +584,20 @@ __global__ void __launch_bounds__(BLOCK, (integrate_minb<T, D, MODE>()))
         T hid, hi2d;
         hpow(hi, di > 0 ? di : 1, hid, hi2d);
         const T eta_i = visc * kappa * hi * t_sqrt(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]) * fast_rcp(hid);
-        // one same-group pair (j at distance r, its a_p and (v, h) loaded): the viscous term of Eq. 7
-        auto pair = [&](const Vec4<T>& aj, const Vec4<T>& vhj, T r) {
-            const T invr = fast_rcp(r);
+        // the pair's kernel factor of Eq. 7, (rho_i^-2 + rho_j^-2) W'(r, h_ij) / r (the pressure
+        // pass hands it over with the pair; computed here for the pairs of an overflowed list)
+        auto kfac = [&](T hj, T r) {
+            T hjd, hj2d;
+            hpow(hj, di, hjd, hj2d);
+            const T invR = fast_rcp(hk * (hi + hj));
+            const T q = r * invR;
+            const T t = T(1) - q;
+            const T dW = wendland_alpha<T>(di, invR) * (T(-20) * q * t * t * t) * invR;
+            return (hi2d + hj2d) * dW * fast_rcp(r);
+        };
+        // one same-group pair (its kernel factor kv, its a_p and (v, h) loaded): the viscous term
+        // of Eq. 7
+        auto pair = [&](const Vec4<T>& aj, const Vec4<T>& vhj, T kv) {
             const T hj = vhj.w;
             const T apj[3] = {aj.x, aj.y, aj.z};
             const T vj3[3] = {vhj.x, vhj.y, vhj.z};
@@ -602,11 +613,7 @@ __global__ void __launch_bounds__(BLOCK, (integrate_minb<T, D, MODE>()))
             const T es = eta_i + eta_j;
             if (!(es > T(0))) return;
             const T eb = T(2) * eta_i * eta_j / es;
-            const T invR = fast_rcp(hk * (hi + hj));
-            const T q = r * invR;
-            const T t = T(1) - q;
-            const T dW = wendland_alpha<T>(di, invR) * (T(-20) * q * t * t * t) * invR;
-            const T coef = eb * (hi2d + hj2d) * dW * invr;
+            const T coef = eb * kv;
             for (int a = 0; a < D; ++a) av[a] += coef * (vt[a] - vtj[a]);
         };
         // the pairs the pressure pass found (list), or the cell walk where the list overflowed
@@ -655,8 +662,8 @@ __global__ void __launch_bounds__(BLOCK, (integrate_minb<T, D, MODE>()))
             [&](int j, const T*, T r2, T hj, unsigned mj) -> bool {
                 return meta_group(mj) == gi && j != k && r2 < pair_rc2(hi, hj, hk) && r2 > T(0);
             },
-            [&](int j, const T*, T r2, T, unsigned, const T*, int, int, int, int) {
-                pair(s.A[j], s.VH[j], r2 * fast_rsqrt(r2));
+            [&](int j, const T*, T r2, T hj, unsigned, const T*, int, int, int, int) {
+                pair(s.A[j], s.VH[j], kfac(hj, r2 * fast_rsqrt(r2)));
             });
         for (int a = 0; a < D; ++a) av[a] = sub_sum<LPP>(av[a]);
         if (moving) tangent_map<T>(di, D, tg, av);

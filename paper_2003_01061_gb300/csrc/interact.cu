@@ -88,6 +88,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTERACT
     const T invRi = fast_rcp(kappa * hi);
     const T alpha_i = wendland_alpha<T>(di > 0 ? di : 1, invRi);
     const T Pi = p0 * ipow(hi, 2 * di);
+    T hid, hi2d;   // as the viscous pass computes them
+    hpow(hi, di > 0 ? di : 1, hid, hi2d);
     const bool brho = p.boundary_rho != 0;
     const T c0 = (T)g.c0;
     const T org[3] = {(T)g.origin[0], (T)g.origin[1], (T)g.origin[2]};
@@ -128,7 +130,8 @@ __global__ void __launch_bounds__(BLOCK, sizeof(T) == 4 ? (D == 2 ? SPH_INTERACT
                     if (D == 3) F[2] += c1 * dx[2];
                     if (vc < VCAP) {   // the pair again in the viscous sum (Eq. 7, second term)
                         s.vj[(size_t)vc * NL + lg] = j;
-                        s.vr[(size_t)vc * NL + lg] = r;
+                        // the viscous pass's kernel factor of the pair (Eq. 7): the same W' as here
+                        s.vr[(size_t)vc * NL + lg] = (hi2d + hj2d) * dW * invr;
                     }
                     ++vc;
                 }

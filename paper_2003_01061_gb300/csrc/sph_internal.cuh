@@ -62,7 +62,8 @@ template <typename T> struct State {
     unsigned* occ;
     int nocc;
     // same-group pairs found by the pressure pass, handed to the viscous pass: for lane
-    // g = k*LPP + r of particle k, entry c is (vj, vr)[c * n*LPP + g] (index, distance);
+    // g = k*LPP + r of particle k, entry c is (vj, vr)[c * n*LPP + g] (index, and the pair's
+    // kernel factor of Eq. 7, (rho_i^-2 + rho_j^-2) W'(r, h_ij) / r);
     // vcnt[g] counts them (> VCAP: the list overflowed and the viscous pass walks the cells)
     int* vj;
     T* vr;
