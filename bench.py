@@ -60,10 +60,10 @@ DISK_WORKLOAD = "disk_holes_2d_120k"
 FLOP_PER_PAIR = 50.0       # FP32 operations per interacting pair of the pressure pass (see design notes)
 # DRAM bytes (read + write) per particle of one launch of the dominant kernel (the 3D pressure
 # pass): the ncu capture of this kernel on the headline's generator at 300,009 particles, 5 steps
-# after the start (116.6 MB read + 178.3 MB written); its traffic grows with the particle count
+# after the start (116.7 MB read + 179.6 MB written); its traffic grows with the particle count
 # (own state, neighbour records missing L2, the hand-over list), so a launch on n particles moves
 # n times this.  Set to None whenever the kernel changes until it has been captured again.
-DOMINANT_DRAM_BYTES_PER_PARTICLE = (116.606720e6 + 178.318592e6) / 300_009
+DOMINANT_DRAM_BYTES_PER_PARTICLE = (116.726272e6 + 179.580416e6) / 300_009
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # one 3D step: one-pass scan, scatter, gather, pressure pass, controller, viscous pass, update
 # (+ next keys)
