@@ -185,8 +185,9 @@ static_assert(Lpp<2>::v % ILpp<2>::v == 0 && Lpp<3>::v % ILpp<3>::v == 0,
 #endif
 // the viscous pass and the update as two kernels (each with its own register budget) instead
 // of one (measured on the 1.2M cube: 0.73 ms against 0.86 for the fused kernel, the viscous
-// kernel at 8 blocks/SM, 7 and 6 being 3 % and 7 % slower; on the 120k disk, with one viscous
-// lane per particle, 47 us against 39.5 us fused)
+// kernel at 8 blocks/SM, 7 and 6 being 3 % and 7 % slower; with the kernel factor in the
+// hand-over list 0.64 ms, 9 blocks/SM 0.70; on the 120k disk, with one viscous lane per
+// particle, 47 us against 39.5 us fused)
 #ifndef SPH_SPLIT_INTEGRATE_2D
 #define SPH_SPLIT_INTEGRATE_2D 0
 #endif
