@@ -276,9 +276,9 @@ sph_status make_instance(const sph_domain_desc* dd, const sph_sizing_desc* sz, c
     g.ncell = I.ncell;
     g.sm = cps == 1 ? 0 : (cps == 2 ? 1 : 2);
     // occupancy cells: cps top-level cells per axis (a search window spans at most one of them
-    // on each side), in 3D divided SPH_OCC_FINER times in two (there a level's search is
-    // skipped when the occupancy cells covering its own cell box hold none of its particles,
-    // and its radius taken from the largest h they hold)
+    // on each side), in 3D divided SPH_OCC_FINER times in two.  A level's search is skipped when
+    // the occupancy cells covering its own cell box hold none of its particles, and its radius
+    // is taken from the largest h they hold.
     const int t = gi.levels - 1;
     const int fin = D == 3 ? std::min(SPH_OCC_FINER, t + g.sm) : 0;
     g.osh = t + g.sm - fin;
