@@ -490,6 +490,12 @@ def e2e_run(S, w, stream, steps):
             "job": f"upload of {n} particles, {steps} steps each with a controller-report read, final download"}
 
 
+def stages_per_step(times, steps):
+    """ms per step of each stage from the library's per-stage (launches, total ms) over `steps`
+    steps (a stage may launch several kernels per step: its time is not divided by them)."""
+    return {k: v[1] / max(steps, 1) for k, v in times.items()}
+
+
 def timed_run(S, torch, w, stream, flush, steps, warmup, stage_steps, barrier=False, clock_index=None):
     """One FP32 instance of w: `warmup` untimed steps (they also capture the step graph), then
     `steps` device-timed steps (CUDA events on the library's stream, the graph without stage
@@ -535,7 +541,7 @@ def timed_run(S, torch, w, stream, flush, steps, warmup, stage_steps, barrier=Fa
     m.sync()
     cand, accd = S.sph_debug_pair_counts(m.h)
     n = len(w["x"])
-    stages = {k: v[1] / stage_steps for k, v in stage.items()}   # ms per step of each stage
+    stages = stages_per_step(stage, stage_steps)
     return {"mesh": m, "total_ms": total_ms, "value": n * steps / (total_ms / 1e3), "staged_ms": staged_ms,
             "stage_steps": stage_steps, "stages_ms": stages, "accd": accd,
             "clocks": clk.summary() if clk else None,
@@ -826,7 +832,7 @@ def batched_run(S, torch, dev, ws, steps):
         out["per_dim"][f"{d}d"] = {"instances": b.n_inst, "particles": n, "slots": slots,
                                    "cells_per_support": b.tuned[0],
                                    "autotune_trial_ms": {"1": b.tuned[1][0], "2": b.tuned[1][1], "4": b.tuned[1][2]},
-                                   "stages_ms": {k: (v[1] / max(staged, 1)) for k, v in t.items()},
+                                   "stages_ms": stages_per_step(t, staged),
                                    "stage_steps": staged}
         S.sph_batch_set_timing(b.h, 0)
         b.sync()

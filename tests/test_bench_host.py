@@ -49,3 +49,10 @@ def test_algorithmic_bytes():
 def test_measured_peak_lookup():
     assert bench.hbm_peak({"hbm_gbs": 7000.0}) == 7000.0
     assert bench.hbm_peak({"other": 1}) == 6800.0
+
+
+def test_stage_times_are_per_step_not_per_launch():
+    # the 3D viscous pass + update stage launches two kernels per step
+    times = {"rebuild": (60, 2.0), "interact": (20, 68.0), "integrate": (40, 12.8)}
+    st = bench.stages_per_step(times, 20)
+    assert st == {"rebuild": 0.1, "interact": 3.4, "integrate": 0.64}
